@@ -1,0 +1,255 @@
+"""CPU oracle for randomized XR-preconditioned CholeskyQR (FP64, single thread).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package.  It shares no code with the CUDA
+path; the product never falls back to it.
+
+The arithmetic lives in ``rxr_oracle.c`` (plain C, compiled with
+-ffp-contract=off); this module compiles it on demand with gcc and wraps it
+with ctypes.  All matrices are float64 and column-major (Fortran order).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rxr_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "librxr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE = 0, 1, 2, 3
+VARIANT_LU, VARIANT_QR, VARIANT_NONE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/librxr_oracle.so (gcc, -O2)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d, i64, u64, u32, i = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+            vp = ctypes.c_void_p
+            lib.rxo_philox4x32_10.argtypes = [vp, vp, vp]
+            lib.rxo_logf.argtypes = [ctypes.c_float]
+            lib.rxo_logf.restype = ctypes.c_float
+            lib.rxo_sincos2pi.argtypes = [u32, vp, vp]
+            lib.rxo_normal4.argtypes = [u64, u64, u32, u32, vp]
+            lib.rxo_omega_z.argtypes = [u64, i64, i64, i64, vp]
+            lib.rxo_sketch.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
+            lib.rxo_geqr_r.argtypes = [vp, i64, i64, i64, vp, i64]
+            lib.rxo_getrf_u.argtypes = [vp, i64, i64, i64, vp, i64, vp]
+            lib.rxo_sign_normalise.argtypes = [vp, i64, i64]
+            lib.rxo_check_factor.argtypes = [vp, i64, i64]
+            lib.rxo_check_factor.restype = i
+            lib.rxo_trsm_right_upper.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
+            lib.rxo_gram.argtypes = [vp, i64, i64, i64, vp, i64]
+            lib.rxo_potrf_u.argtypes = [vp, i64, i64, vp, i64]
+            lib.rxo_potrf_u.restype = i
+            lib.rxo_trmm_upper.argtypes = [vp, i64, vp, i64, i64, vp, i64]
+            lib.rxo_rxr_cholqr.argtypes = [vp, i64, i64, i64, i, i64, u64, i, vp, i64, vp, i64,
+                                           vp, vp, vp, vp, vp, vp, vp]
+            lib.rxo_rxr_cholqr.restype = i
+            lib.rxo_householder_qr.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
+            lib.rxo_orth_error.argtypes = [vp, i64, i64, i64]
+            lib.rxo_orth_error.restype = d
+            lib.rxo_resid_error.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
+            lib.rxo_resid_error.restype = d
+            lib.rxo_dot2.argtypes = [vp, vp, i64]
+            lib.rxo_dot2.restype = d
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _ld(a: np.ndarray) -> int:
+    assert a.flags["F_CONTIGUOUS"]
+    return max(1, a.shape[0])
+
+
+# ---------------------------------------------------------------- generator
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    _load().rxo_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def logf(u: float) -> np.float32:
+    return np.float32(_load().rxo_logf(ctypes.c_float(u)))
+
+
+def sincos2pi(nint: int):
+    s = np.zeros(1, np.float32)
+    c = np.zeros(1, np.float32)
+    _load().rxo_sincos2pi(int(nint), _p(s), _p(c))
+    return s[0], c[0]
+
+
+def normal4(seed: int, i: int, k: int, stream: int = 0) -> np.ndarray:
+    z = np.zeros(4, np.float32)
+    _load().rxo_normal4(seed, i, k, stream, _p(z))
+    return z
+
+
+def omega_z(seed: int, s: int, i0: int, rows: int) -> np.ndarray:
+    """z values (float32) of Omega's columns i0..i0+rows-1: shape (rows, s)."""
+    z = np.zeros((rows, s), np.float32)
+    _load().rxo_omega_z(seed, s, i0, rows, _p(z))
+    return z
+
+
+def omega(seed: int, s: int, m: int) -> np.ndarray:
+    """The s x m sketch matrix Omega = z / sqrt(s) in float64 (small m only)."""
+    z = omega_z(seed, s, 0, m)
+    return np.asfortranarray((1.0 / np.sqrt(float(s))) * z.T.astype(np.float64))
+
+
+# ---------------------------------------------------------------- steps
+def sketch(A: np.ndarray, s: int, seed: int) -> np.ndarray:
+    A = _f64(A)
+    m, n = A.shape
+    Y = np.zeros((s, n), order="F")
+    _load().rxo_sketch(_p(A), m, n, _ld(A), s, seed, _p(Y), s)
+    return Y
+
+
+def geqr_r(W: np.ndarray) -> np.ndarray:
+    W = _f64(W).copy(order="F")
+    l, n = W.shape
+    R = np.zeros((n, n), order="F")
+    _load().rxo_geqr_r(_p(W), l, n, _ld(W), _p(R), n)
+    return R
+
+
+def getrf_u(W: np.ndarray):
+    W = _f64(W).copy(order="F")
+    l, n = W.shape
+    U = np.zeros((n, n), order="F")
+    piv = np.zeros(n, np.int64)
+    _load().rxo_getrf_u(_p(W), l, n, _ld(W), _p(U), n, _p(piv))
+    L = np.tril(W[:, :n], -1)
+    L[np.arange(n), np.arange(n)] = 1.0
+    return U, L, piv
+
+
+def sign_normalise(R: np.ndarray) -> np.ndarray:
+    R = _f64(R).copy(order="F")
+    _load().rxo_sign_normalise(_p(R), R.shape[0], _ld(R))
+    return R
+
+
+def check_factor(R: np.ndarray) -> int:
+    R = _f64(R)
+    return int(_load().rxo_check_factor(_p(R), R.shape[0], _ld(R)))
+
+
+def trsm_right_upper(A: np.ndarray, R: np.ndarray) -> np.ndarray:
+    A = _f64(A)
+    R = _f64(R)
+    m, n = A.shape
+    X = np.zeros((m, n), order="F")
+    _load().rxo_trsm_right_upper(_p(A), m, n, _ld(A), _p(R), _ld(R), _p(X), max(1, m))
+    return X
+
+
+def gram(X: np.ndarray) -> np.ndarray:
+    X = _f64(X)
+    m, n = X.shape
+    G = np.zeros((n, n), order="F")
+    _load().rxo_gram(_p(X), m, n, _ld(X), _p(G), n)
+    return G
+
+
+def potrf_u(G: np.ndarray):
+    """Upper Cholesky factor; returns (R, info) with info = breakdown column+1 or 0."""
+    G = _f64(G)
+    n = G.shape[0]
+    R = np.zeros((n, n), order="F")
+    info = _load().rxo_potrf_u(_p(G), n, _ld(G), _p(R), n)
+    return R, int(info)
+
+
+def trmm_upper(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    A = _f64(A)
+    B = _f64(B)
+    n = A.shape[0]
+    C = np.zeros((n, n), order="F")
+    _load().rxo_trmm_upper(_p(A), _ld(A), _p(B), _ld(B), n, _p(C), n)
+    return C
+
+
+class Result:
+    """Outputs and intermediates of one oracle factorisation."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def rxr_cholqr(A: np.ndarray, variant: int = VARIANT_QR, s: int | None = None, seed: int = 0,
+               passes: int = 2) -> Result:
+    """rLU-/rQR-CholeskyQR (Algorithms 4/5) with `passes` CholeskyQR passes."""
+    A = _f64(A)
+    m, n = A.shape
+    s = 2 * n if s is None else int(s)
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    Y = np.zeros((s, n), order="F")
+    mats = [np.zeros((n, n), order="F") for _ in range(5)]
+    info = np.zeros(2, np.int32)
+    st = _load().rxo_rxr_cholqr(_p(A), m, n, _ld(A), variant, s, seed, passes, _p(Q), max(1, m), _p(R), n,
+                                _p(Y), *[_p(x) for x in mats], _p(info))
+    return Result(status=int(st), Q=Q, R=R, Y=Y, Rs=mats[0], G1=mats[1], R1=mats[2], G2=mats[3], R2=mats[4],
+                  info=(int(info[0]), int(info[1])))
+
+
+def householder_qr(A: np.ndarray):
+    """Thin QR A = QR with diag(R) >= 0 by Householder reflections."""
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    _load().rxo_householder_qr(_p(A), m, n, _ld(A), _p(Q), max(1, m), _p(R), n)
+    return Q, R
+
+
+def orth_error(Q: np.ndarray) -> float:
+    Q = _f64(Q)
+    return float(_load().rxo_orth_error(_p(Q), Q.shape[0], Q.shape[1], _ld(Q)))
+
+
+def resid_error(A: np.ndarray, Q: np.ndarray, R: np.ndarray) -> float:
+    A, Q, R = _f64(A), _f64(Q), _f64(R)
+    return float(_load().rxo_resid_error(_p(A), A.shape[0], A.shape[1], _ld(A), _p(Q), _ld(Q), _p(R), _ld(R)))
+
+
+def dot2(x, y) -> float:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(_load().rxo_dot2(_p(x), _p(y), x.size))
