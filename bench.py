@@ -1,0 +1,298 @@
+"""Benchmark of randomized XR-preconditioned CholeskyQR on one GB300 (or N
+independent replicas, one per GPU, under torchrun).
+
+A step is one full factorisation A = QR (sketch, XR factor of the sketch, the
+fused precondition+Gram pass, two CholeskyQR passes, Q and R) of the
+tall-skinny workload m = 2^22, n = 64 (A = U Sigma V^T, kappa = 1e10, s = 2n
+Gaussian sketch, seed 0) with inputs resident in HBM.  The metric is the
+effective bandwidth B_alg / t with B_alg = 8 m n (P + 3) bytes: one read of A
+for the sketch, one per CholeskyQR pass, and a read plus a write for Q.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant qr|lu]
+                    [--prec fp64|split] [--impl reference]
+
+`--impl reference` times the CPU oracle (the plain FP64 implementation
+written from the paper) on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, S, KAPPA, SEED, PASSES = 2**22, 64, 128, 1e10, 0, 2
+METRIC = "tall-skinny QR effective GB/s (B_alg = 8mn(P+3)) at ||Q^T Q - I||_F <= 1e-13"
+WORKLOAD = "rQR-CholeskyQR2 m=2^22 n=64 s=128 kappa=1e10 FP64"
+
+
+def b_alg(m, n, passes):
+    return 8.0 * m * n * (passes + 3)
+
+
+def f_alg(m, n, s, passes):
+    # sketch 2smn, X = A R_s^{-1} mn^2, per pass Gram mn^2 and apply mn^2
+    return 2.0 * s * m * n + (2 * passes + 1) * m * n * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_cores() -> int:
+    return 1
+
+
+def oracle_rows(target_s: float = 15.0) -> int:
+    """Row count of the oracle sample: about `target_s` seconds of single-core work."""
+    return int(os.environ.get("RXR_BENCH_ORACLE_ROWS", 2**17))
+
+
+def run_oracle_sample(A_sample: np.ndarray, variant: str):
+    import oracle
+
+    ov = oracle.VARIANT_QR if variant == "qr" else oracle.VARIANT_LU
+    t0 = time.perf_counter()
+    r = oracle.rxr_cholqr(A_sample, ov, S, seed=SEED, passes=PASSES)
+    dt = time.perf_counter() - t0
+    if r.status != 0:
+        raise RuntimeError(f"oracle status {r.status}")
+    return dt
+
+
+def make_input():
+    from paper_2111_11148_gb300.inputs import usv_matrix
+
+    return usv_matrix(M, N, KAPPA, seed=SEED)
+
+
+def reference_arm(args, rank: int, world: int):
+    """Time the CPU oracle as it stands on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    rows = oracle_rows()
+    from paper_2111_11148_gb300.inputs import usv_matrix
+
+    A = usv_matrix(rows, N, KAPPA, seed=SEED)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        run_oracle_sample(A, args.variant)
+    times = [run_oracle_sample(A, args.variant) for _ in range(args.steps)]
+    t = statistics.median(times)
+    gbs = b_alg(rows, N, PASSES) / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "oracle_rows": rows, "m": M, "n": N, "s": S, "passes": PASSES,
+                   "variant": args.variant},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"{rows} x {N} rows of the same A = U Sigma V^T construction, full "
+                                   f"rxr_cholqr per step (single-threaded C oracle)"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def gpu_arm(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    A_np = make_input()
+    A = rxr.colmajor(torch.from_numpy(A_np).to(dev))
+    Q = rxr.empty_colmajor(M, N, device=dev)
+    R = rxr.empty_colmajor(N, N, device=dev)
+    h = rxr.Handle(local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        h.cholqr(A, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=Q, R=R)
+
+    peak_fp64 = rxr.fp64_peak_tflops()
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    value = world * b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9
+
+    # per-kernel device times (events on the launching stream), after the timed region
+    h.set_kernel_timing(True)
+    kms = {k: [] for k in range(4)}
+    for _ in range(3):
+        step()
+        for k in range(4):
+            kms[k].append(h.last_kernel_ms(k))
+    h.set_kernel_timing(False)
+    kmed = {k: statistics.median(v) for k, v in kms.items()}
+    sketch_flop = 2.0 * S * M * N
+    achieved = sketch_flop / (kmed[0] * 1e-3) / 1e12
+    # accuracy of the timed factorisation (GPU Dot2 evaluators)
+    orth = h.orth_error(Q)
+    resid = h.resid_error(A, Q, R)
+
+    # end to end through the host-buffer entry point
+    import ctypes
+
+    hA = torch.from_numpy(A_np).pin_memory().numpy()
+    hA = np.asfortranarray(hA) if not hA.flags["F_CONTIGUOUS"] else hA
+    hQ = torch.empty((N, M), dtype=torch.float64).pin_memory().numpy().T
+    hR = torch.empty((N, N), dtype=torch.float64).pin_memory().numpy().T
+    for _ in range(2):
+        h.cholqr_host(hA, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=hQ, R=hR)
+    e_steps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        h.cholqr_host(hA, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=hQ, R=hR)
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    e2e_val = world * b_alg(M, N, PASSES) / e2e_s / 1e9
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        rows = oracle_rows()
+        t_or = run_oracle_sample(np.asfortranarray(A_np[:rows]), args.variant)
+        cpu = {"value": b_alg(rows, N, PASSES) / t_or / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {rows} of {M} rows of the same A, one full rxr_cholqr (single-threaded C oracle), "
+                         f"{t_or:.2f} s"}
+
+    launches_per_step = 11 if PASSES == 2 else 9 + 2 * (PASSES - 1)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA, "seed": SEED, "passes": PASSES,
+                       "variant": args.variant, "prec": args.prec,
+                       "l2": "A (2.1 GB) larger than L2 (129 MB); no flush needed",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_sketch_fp64", "achieved": achieved, "peak": peak_fp64,
+                         "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": None,
+                         "peak_kind": "measured FP64 DFMA calibration (rxr_fp64_peak) on this GPU, same run"},
+            "kernels_ms": {"sketch": kmed[0], "precond_gram": kmed[1], "pass_gram": kmed[2], "apply": kmed[3]},
+            "gflops": world * f_alg(M, N, S, PASSES) / (ms * 1e-3) / 1e9,
+            "qr_per_s": world / (ms * 1e-3),
+            "accuracy": {"orth": orth, "resid": resid},
+            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 8 * M * N,
+                    "d2h_bytes_per_step": 8 * M * N + 8 * N * N},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--variant", default="qr", choices=["qr", "lu"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    gpu_arm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * rxr.h -- C ABI of librxr: randomized XR-preconditioned CholeskyQR
+ * (rLU- and rQR-CholeskyQR) of tall-and-skinny matrices on one GB300 GPU.
+ *
+ * Method: Fan, Guo & Lin, "A Novel Randomized XR-Based Preconditioned
+ * CholeskyQR Algorithm".  For A (m x n, m >= n, full rank) the library computes
+ * the thin QR factorisation A = QR of Section 1 (Q^T Q = I_n, R upper triangular)
+ * by
+ *   1. a Gaussian sketch Y = Omega A with s >= n rows (Section 2.3, "Gaussian
+ *      Ensemble"; the paper's l is s here), Omega drawn in-kernel from
+ *      Philox4x32-10 and never stored;
+ *   2. R_s = the R factor of Y by LU with partial pivoting (Algorithm 4) or by
+ *      Householder QR (Algorithm 5), rows scaled so that diag(R_s) > 0;
+ *   3. X = A R_s^{-1} (row-wise substitution), fused with G = X^T X;
+ *   4. CholeskyQR (Algorithm 1) on X, repeated `passes` times as in
+ *      CholeskyQR2 (Algorithm 2): R_p = chol(G_p), X <- X R_p^{-1};
+ *   5. Q = X and R = R_passes ... R_1 R_s.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are FP64, column-major (LAPACK style): entry (i, j) of a matrix
+ *    with leading dimension ld is p[i + j*ld].  lda >= m, ldq >= m, ldr >= n.
+ *  - Matrix pointers are DEVICE pointers owned by the caller unless the
+ *    function name ends in _host.  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; blocking calls synchronise it.
+ *  - Return value: 0 on success; -i when argument i (1-based) is invalid
+ *    (LAPACK `info` style, nothing is launched); a positive RXR_ERR_* code
+ *    when the computation ran but failed.  No C++ exception crosses the ABI and
+ *    there is no CPU fallback: without a usable GPU the calls return RXR_ERR_CUDA.
+ *  - Results are bitwise reproducible for fixed inputs, seed and launch
+ *    configuration (counter-based random numbers, fixed-order reductions).
+ */
+#ifndef RXR_H
+#define RXR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RXR_API __attribute__((visibility("default")))
+#else
+#define RXR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* XR factorisation of the sketch (Section 2.2).  RXR_NONE skips the sketch and
+ * takes R_s = I, i.e. plain CholeskyQR repeated `passes` times (Algorithms 1
+ * and 2), the paper's unpreconditioned comparator. */
+typedef enum { RXR_LU = 0, RXR_QR = 1, RXR_NONE = 2 } rxr_variant;
+
+/* Arithmetic of the two contractions that only shape the preconditioner (the
+ * sketch Y = Omega A and the first pass's Gram X^T X).
+ *   RXR_FP64       : FP64 throughout.
+ *   RXR_SPLIT_BF16 : those two contractions on tcgen05 tensor cores with BF16
+ *                    operand slices and FP32 accumulation in tensor memory,
+ *                    combined in FP64; everything else stays FP64.  Rounding in
+ *                    them changes only the preconditioner, not what A = QR the
+ *                    FP64 passes converge to (Appendix A). */
+typedef enum { RXR_FP64 = 0, RXR_SPLIT_BF16 = 1 } rxr_precision;
+
+/* Positive status codes. */
+enum {
+    RXR_OK = 0,
+    RXR_ERR_SKETCH_SINGULAR = 1, /* |pivot| <= n u max|pivot| or non-finite in step 2:
+                                    the sketch (or A) is rank deficient (Section 2.2) */
+    RXR_ERR_CHOL_BREAKDOWN = 2,  /* non-positive / non-finite Cholesky pivot (Section 2.1);
+                                    rxr_last_info() gives the pass and column */
+    RXR_ERR_NONFINITE = 3,       /* A holds NaN or Inf */
+    RXR_ERR_CUDA = 4,            /* a CUDA runtime call failed (no GPU, bad pointer, ...) */
+    RXR_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    RXR_ERR_NOMEM = 6,           /* the library could not allocate its workspace */
+    RXR_ERR_UNSUPPORTED = 7      /* valid arguments outside what this build supports */
+};
+
+/* Limits of this build. */
+#define RXR_MAX_N 512
+#define RXR_MAX_S 2048
+
+typedef struct rxr_ctx *rxr_handle;
+
+/* Create a handle bound to CUDA device `device`; it owns a workspace (grown on
+ * demand with cudaMalloc unless rxr_set_workspace supplied one), a device
+ * status word and pinned host staging.  Returns 0, -1 (h NULL), -2 (bad
+ * device) or RXR_ERR_CUDA. */
+RXR_API int rxr_create(rxr_handle *h, int device);
+
+/* Release everything the handle owns.  Safe on NULL. */
+RXR_API int rxr_destroy(rxr_handle h);
+
+/* Bytes of device workspace that rxr_cholqr needs for these sizes (the sketch
+ * and Gram partial sums, the s x n sketch, the n x n factors and the status
+ * word).  The m x n intermediate X lives in the caller's Q. */
+RXR_API int rxr_workspace_bytes(int64_t m, int64_t n, int64_t s, int prec, size_t *bytes);
+
+/* Give the handle caller-owned device workspace (e.g. from PyTorch's caching
+ * allocator); `bytes` must be at least rxr_workspace_bytes(...) of the calls
+ * that follow, else they return RXR_ERR_NOMEM.  NULL returns to self-managed
+ * workspace.  The memory must stay valid until replaced or the handle dies. */
+RXR_API int rxr_set_workspace(rxr_handle h, void *d_workspace, size_t bytes);
+
+/* Factorise A = QR (Algorithms 4/5 + repeated CholeskyQR pass, see top).
+ *   A (1)           device, m x n, read only (unless Q == A: in-place allowed
+ *                   when ldq == lda; A is then overwritten by Q).
+ *   m, n, lda (2-4) m >= n >= 1, n <= RXR_MAX_N, lda >= m.
+ *   variant (5)     RXR_LU, RXR_QR or RXR_NONE.
+ *   s (6)           sketch rows, n <= s <= RXR_MAX_S (paper: l >= n; l = 2n in
+ *                   Section 4).  Ignored for RXR_NONE.
+ *   seed (7)        Philox key of Omega.
+ *   passes (8)      CholeskyQR passes, 1..3 (Algorithms 4/5 print one; two =
+ *                   CholeskyQR2 on X).
+ *   Q, ldq (9-10)   device, m x n output (holds X between passes), ldq >= m.
+ *   R, ldr (11-12)  device, n x n output (strictly lower part written as 0),
+ *                   ldr >= n; R == NULL skips R ("R-less" QR, footnote to
+ *                   Algorithm 2).
+ *   prec (13)       rxr_precision.
+ *   stream (14)     cudaStream_t.
+ * Blocking: synchronises `stream` and returns the status.  On a positive code
+ * Q and R hold partial results. */
+RXR_API int rxr_cholqr(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int variant, int64_t s,
+               uint64_t seed, int passes, double *Q, int64_t ldq, double *R, int64_t ldr, int prec, void *stream);
+
+/* Same as rxr_cholqr but asynchronous and stream-capturable: nothing waits on
+ * the host.  The status is written on the device to d_status[0..3] = {code,
+ * pass, column, 0} (caller-owned device memory, 16 bytes) when the stream
+ * reaches the end of the sequence.  Argument errors are still returned
+ * synchronously. */
+RXR_API int rxr_cholqr_async(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int variant, int64_t s,
+                     uint64_t seed, int passes, double *Q, int64_t ldq, double *R, int64_t ldr, int prec,
+                     void *stream, int *d_status);
+
+/* End-to-end form with HOST buffers: copies A (pageable or pinned host
+ * memory) to the device, factorises, and copies Q and R back; the device
+ * buffers are owned by the handle.  Blocking.  Arguments as rxr_cholqr, with
+ * hA, hQ, hR host pointers (hR may be NULL). */
+RXR_API int rxr_cholqr_host(rxr_handle h, const double *hA, int64_t m, int64_t n, int64_t lda, int variant, int64_t s,
+                    uint64_t seed, int passes, double *hQ, int64_t ldq, double *hR, int64_t ldr, int prec,
+                    void *stream);
+
+/* Batched form: `count` independent problems A_k (m_k x n_k) factorised in one
+ * stream-ordered launch sequence (one launch per stage for the whole batch;
+ * the row panels of all problems share each launch's grid).  Arrays are HOST
+ * arrays of length `count`; the matrix pointers in them are device pointers.
+ * variant, passes and prec are common; s_k, seed_k per problem.  Per-problem
+ * status {code, pass, column, 0} goes to d_status[4k..4k+3] (device, caller
+ * owned).  Blocking; returns the first non-zero problem status (or 0). */
+RXR_API int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
+                       const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
+                       double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
+                       void *stream, int *d_status);
+
+/* Pass and column (0-based) of the last Cholesky breakdown seen by a blocking
+ * call on this handle; both -1 if none. */
+RXR_API int rxr_last_info(rxr_handle h, int *pass, int *column);
+
+/* Static string for a status code. */
+RXR_API const char *rxr_status_string(int code);
+
+/* ---- Stage entry points: each runs one step of the path on the device.  They
+ * expose the intermediates for testing and for callers that compose their own
+ * pipeline (e.g. the least-squares preconditioner of Section 5.2, which only
+ * needs R_s).  All are asynchronous on `stream` unless stated. ---- */
+
+/* Standard normals of Omega (Section 2.3, Gaussian ensemble): for rows
+ * i = row0..row0+rows-1 of A and sketch rows r < s, d_z[(i-row0)*s + r] = z,
+ * Omega = z / sqrt(s).  The counter convention: Philox4x32-10 with key
+ * (seed_lo, seed_hi) and counter (i_lo, i_hi, k, 0) gives z for r = 4k..4k+3
+ * by Box-Muller on FP32 uniforms u = ((x >> 8) + 1) 2^-24.  d_z device,
+ * rows * s floats. */
+RXR_API int rxr_omega(uint64_t seed, int64_t s, int64_t row0, int64_t rows, float *d_z, void *stream);
+
+/* Y = Omega A (s x n, column-major with leading dimension ldy >= s), step 1.
+ * prec selects FP64 or the split BF16 tensor-core contraction. */
+RXR_API int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+               double *Y, int64_t ldy, int prec, void *stream);
+
+/* R_s (n x n upper, diag > 0, zeros below) = R factor of Y (s x n) by LU with
+ * partial pivoting (RXR_LU) or Householder QR (RXR_QR), step 2.  Y is read
+ * only.  Blocking; returns 0 or RXR_ERR_SKETCH_SINGULAR. */
+RXR_API int rxr_xr_factor(rxr_handle h, const double *Y, int64_t s, int64_t n, int64_t ldy, int variant, double *Rs,
+                  int64_t ldrs, void *stream);
+
+/* X = A R^{-1} by row-wise substitution and G = X^T X (full symmetric n x n,
+ * leading dimension ldg >= n), step 3.  X may alias A (ldx == lda); X == NULL
+ * computes G only.  prec selects the Gram's arithmetic (the substitution is
+ * always FP64). */
+RXR_API int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *R,
+                     int64_t ldr, double *X, int64_t ldx, double *G, int64_t ldg, int prec, void *stream);
+
+/* Upper Cholesky factor R (R^T R = G; reads the upper triangle of G).
+ * Blocking; returns 0 or RXR_ERR_CHOL_BREAKDOWN (column in rxr_last_info). */
+RXR_API int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *R, int64_t ldr, void *stream);
+
+/* Accuracy measures of Section 4.2 with compensated (Dot2) dot products,
+ * computed on the device; blocking, result in *out (host).
+ *   rxr_orth_error : ||Q^T Q - I||_F
+ *   rxr_resid_error: ||A - Q R||_F / ||A||_F (R upper triangular)          */
+RXR_API int rxr_orth_error(rxr_handle h, const double *Q, int64_t m, int64_t n, int64_t ldq, double *out, void *stream);
+RXR_API int rxr_resid_error(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *Q,
+                    int64_t ldq, const double *R, int64_t ldr, double *out, void *stream);
+
+/* Measured FP64 FMA throughput of this GPU in TFLOP/s (a calibration kernel
+ * of independent DFMA chains over all SMs), the denominator of the FP64
+ * roofline.  Blocking. */
+RXR_API int rxr_fp64_peak(double *tflops, void *stream);
+
+/* Device time in milliseconds of the most recent launch of `kernel` made by
+ * a blocking or host call on this handle, measured with CUDA events on the
+ * launching stream (kernel: 0 sketch, 1 precondition+Gram, 2 pass-2 Gram,
+ * 3 Q apply).  Returns -1 for an unknown kernel id. */
+RXR_API int rxr_last_kernel_ms(rxr_handle h, int kernel, float *ms);
+
+/* Enable or disable the per-kernel events of rxr_last_kernel_ms (off by default). */
+RXR_API int rxr_set_kernel_timing(rxr_handle h, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RXR_H */

@@ -1,0 +1,897 @@
+// api.cu -- host side of librxr: argument checking, workspace, TMA descriptors,
+// and the launch sequence of rLU-/rQR-CholeskyQR (Algorithms 4 and 5 with the
+// repeated CholeskyQR pass of Algorithm 2) behind the C ABI of include/rxr.h.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "rxr_internal.cuh"
+
+namespace rxr {
+// stream_kernels.cu
+__global__ void k_omega(uint64_t, int64_t, int64_t, int64_t, float *);
+__global__ void k_sketch_fp64(const __grid_constant__ CUtensorMap, int, const double *, int64_t, int64_t, int, int,
+                              uint64_t, int64_t, int64_t, int, double *, RxrStatus *);
+__global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, int, double *, int64_t, RxrStatus *);
+cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &map, int use_tma,
+                              const double *src, int64_t lds, int64_t m, int n, const double *R, int64_t ldr,
+                              int unit_r, double *dst, int64_t ldd, int do_gram, double *Gpart, int64_t panels_total,
+                              int64_t panels_per_cta, int check_finite, RxrStatus *status);
+cudaError_t set_subst_gram_smem(int bytes);
+// small_kernels.cu
+__global__ void k_xr_factor(const double *, int, int, int64_t, int, double *, double *, int64_t, RxrStatus *);
+__global__ void k_factor(const double *, int, int64_t, double *, double *, double *, int, int, RxrStatus *);
+__global__ void k_copy_upper(const double *, int, double *, int64_t, const RxrStatus *);
+__global__ void k_identity(double *, int);
+__global__ void k_status_out(const RxrStatus *, int *);
+__global__ void k_orth_partial(const double *, int64_t, int, int64_t, int64_t, double *);
+__global__ void k_orth_final(const double *, int, int, double *);
+__global__ void k_resid_partial(const double *, int64_t, const double *, int64_t, const double *, int64_t, int64_t,
+                                int, double *);
+__global__ void k_resid_final(const double *, int, double *);
+__global__ void k_fp64_peak(double *, int, double, double);
+}  // namespace rxr
+
+using namespace rxr;
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct rxr_ctx {
+    int device = 0;
+    int sms = 152;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = true;
+    int *h_status = nullptr;  // pinned, 4 ints
+    int last_pass = -1, last_col = -1;
+    bool timing = false;
+    cudaEvent_t ev[4][2] = {};
+    float last_ms[4] = {0, 0, 0, 0};
+    bool ev_recorded[4] = {false, false, false, false};
+    // device staging for the _host entry point
+    double *dA = nullptr, *dQ = nullptr, *dR = nullptr;
+    size_t dA_bytes = 0, dQ_bytes = 0, dR_bytes = 0;
+    double *eval_buf = nullptr;
+    size_t eval_bytes = 0;
+};
+
+namespace {
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode()
+{
+    static std::once_flag once;
+    static PFN_encodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled)p;
+        else
+            (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D tiled descriptor of a column-major FP64 matrix (rows x cols, leading
+// dimension ld) with box (box_rows x box_cols).  Returns false where TMA's
+// rules are not met (16-byte aligned base, ld * 8 a multiple of 16, box sizes
+// in range); the kernels then stage panels with plain coalesced loads.
+bool encode_2d(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+               int box_cols)
+{
+    memset(map, 0, sizeof(*map));
+    PFN_encodeTiled enc = get_encode();
+    if (!enc || ptr == nullptr) return false;
+    if (((uintptr_t)ptr) % 16 != 0 || (ld * 8) % 16 != 0 || (box_rows * 8) % 16 != 0) return false;
+    if (box_rows < 1 || box_rows > 256 || box_cols < 1 || box_cols > 256) return false;
+    if (rows < 1 || cols < 1 || rows > (int64_t)1 << 31 || ld >= ((int64_t)1 << 37)) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    cuuint64_t gstride[1] = {(cuuint64_t)(ld * 8)};
+    cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            prev = -1;
+        }
+        ok = (cudaSetDevice(dev) == cudaSuccess);
+        if (!ok) (void)cudaGetLastError();
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+constexpr int kSkP = 64, kSkSTile = 128, kSkNTile = 64, kSgP = 128;
+constexpr int kMaxStreamN = 128;  // substitution kernels hold R in shared memory
+
+}  // namespace
+
+
+namespace {
+
+void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms)
+{
+    p.m = m;
+    p.n = n;
+    p.s = s;
+    p.prec = prec;
+    p.sms = sms;
+    const int64_t s_tiles = cdiv(s, kSkSTile), n_tiles = cdiv(n, kSkNTile);
+    p.sk_gy = (int)(s_tiles * n_tiles);
+    p.sk_panels = cdiv(m, kSkP);
+    int64_t gx = std::max<int64_t>(1, cdiv(2 * (int64_t)sms, p.sk_gy));
+    gx = std::min(gx, p.sk_panels);
+    p.sk_ppc = cdiv(p.sk_panels, gx);
+    p.sk_gx = (int)cdiv(p.sk_panels, p.sk_ppc);
+
+    const int64_t n4 = (n + 3) & ~3;
+    p.sg_smem = (size_t)(n4 * kSgP + n * (n + 1) / 2 + n) * sizeof(double);
+    const int per_sm = (p.sg_smem <= 110 * 1024) ? 2 : 1;
+    p.sg_panels = cdiv(m, kSgP);
+    int64_t g2 = std::min<int64_t>((int64_t)sms * per_sm, p.sg_panels);
+    p.sg_ppc = cdiv(p.sg_panels, g2);
+    p.sg_gx = (int)cdiv(p.sg_panels, p.sg_ppc);
+    const int64_t NT = n4 / 4, ntiles = NT * (NT + 1) / 2;
+    p.sg_maxt = (int)cdiv(ntiles, RXR_THREADS);
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const size_t o_status = take(sizeof(RxrStatus));
+    const size_t o_ypart = take((size_t)p.sk_gx * s * n * 8);
+    const size_t o_y = take((size_t)s * n * 8);
+    const size_t o_w = take((size_t)s * n * 8);
+    const size_t o_gpart = take((size_t)p.sg_gx * n * n * 8);
+    const size_t o_g = take((size_t)n * n * 8);
+    const size_t o_rs = take((size_t)n * n * 8);
+    const size_t o_rp = take((size_t)n * n * 8);
+    const size_t o_racc = take((size_t)n * n * 8);
+    const size_t o_c = take((size_t)n * n * 8);
+    size_t o_split = off;
+    if (prec == RXR_SPLIT_BF16) o_split = take(split_workspace_bytes(m, n, s, sms));
+    p.bytes = off;
+    p.base = nullptr;
+    p.status = nullptr;
+    (void)o_status;
+    p.Ypart = (double *)(uintptr_t)o_ypart;
+    p.Y = (double *)(uintptr_t)o_y;
+    p.W = (double *)(uintptr_t)o_w;
+    p.Gpart = (double *)(uintptr_t)o_gpart;
+    p.G = (double *)(uintptr_t)o_g;
+    p.Rs = (double *)(uintptr_t)o_rs;
+    p.Rp = (double *)(uintptr_t)o_rp;
+    p.Racc = (double *)(uintptr_t)o_racc;
+    p.C = (double *)(uintptr_t)o_c;
+    p.split = (char *)(uintptr_t)o_split;
+}
+
+void bind_plan(Plan &p, void *ws)
+{
+    char *b = (char *)ws;
+    p.base = b;
+    p.status = (RxrStatus *)b;
+    p.Ypart = (double *)(b + (uintptr_t)p.Ypart);
+    p.Y = (double *)(b + (uintptr_t)p.Y);
+    p.W = (double *)(b + (uintptr_t)p.W);
+    p.Gpart = (double *)(b + (uintptr_t)p.Gpart);
+    p.G = (double *)(b + (uintptr_t)p.G);
+    p.Rs = (double *)(b + (uintptr_t)p.Rs);
+    p.Rp = (double *)(b + (uintptr_t)p.Rp);
+    p.Racc = (double *)(b + (uintptr_t)p.Racc);
+    p.C = (double *)(b + (uintptr_t)p.C);
+    p.split = b + (uintptr_t)p.split;
+}
+
+int device_sms(int dev)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    return v;
+}
+
+int ensure_ws(rxr_handle h, size_t bytes)
+{
+    if (h->ws_bytes >= bytes) return 0;
+    if (!h->ws_owned) return RXR_ERR_NOMEM;
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_NOMEM;
+    }
+    h->ws_bytes = bytes;
+    return 0;
+}
+
+int grow(void **ptr, size_t *have, size_t need)
+{
+    if (*have >= need) return 0;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *have = 0;
+    if (cudaMalloc(ptr, need) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_NOMEM;
+    }
+    *have = need;
+    return 0;
+}
+
+bool kernel_attrs_set = false;
+std::mutex attr_mu;
+
+int set_kernel_attrs()
+{
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (kernel_attrs_set) return 0;
+    cudaError_t e = cudaSuccess;
+    const int big = 227 * 1024;
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_sketch_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    e = (cudaError_t)(e | set_subst_gram_smem(big));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_orth_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    e = (cudaError_t)(e | cudaFuncSetAttribute(k_resid_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    kernel_attrs_set = true;
+    return 0;
+}
+
+int launch_ok()
+{
+    cudaError_t e = cudaGetLastError();
+    return (e == cudaSuccess) ? 0 : RXR_ERR_CUDA;
+}
+
+// one substitution(+Gram) pass
+int enqueue_subst(const Plan &p, const double *src, int64_t lds, const double *R, int unit_r, double *dst,
+                  int64_t ldd, bool gram, bool check_finite, cudaStream_t st)
+{
+    CUtensorMap map;
+    const int use_tma = encode_2d(&map, src, p.m, p.n, lds, kSgP, (int)p.n) ? 1 : 0;
+    if (launch_subst_gram(p.sg_maxt, dim3(p.sg_gx), p.sg_smem, st, map, use_tma, src, lds, p.m, (int)p.n, R, p.n,
+                          unit_r, dst, ldd, gram ? 1 : 0, p.Gpart, p.sg_panels, p.sg_ppc, check_finite ? 1 : 0,
+                          p.status) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    if (launch_ok()) return RXR_ERR_CUDA;
+    if (gram) {
+        const int64_t nn = p.n * p.n;
+        k_reduce_parts<<<(int)cdiv(nn, 256), 256, 0, st>>>(p.Gpart, p.sg_gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G, p.n,
+                                                           p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    return 0;
+}
+
+int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st)
+{
+    if (p.prec == RXR_SPLIT_BF16) return split_sketch_enqueue(const_cast<Plan &>(p), A, lda, seed, st);
+    CUtensorMap map;
+    const int box_cols = (int)std::min<int64_t>(p.n, kSkNTile);
+    const int use_tma = encode_2d(&map, A, p.m, p.n, lda, kSkP, box_cols) ? 1 : 0;
+    const size_t smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
+    k_sketch_fp64<<<dim3(p.sk_gx, p.sk_gy), RXR_THREADS, smem, st>>>(map, use_tma, A, lda, p.m, (int)p.n, (int)p.s,
+                                                                     seed, p.sk_panels, p.sk_ppc, box_cols, p.Ypart,
+                                                                     p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    const int64_t sn = p.s * p.n;
+    k_reduce_parts<<<(int)cdiv(sn, 256), 256, 0, st>>>(p.Ypart, p.sk_gx, sn, (int)p.s, (int)p.n,
+                                                       1.0 / sqrt((double)p.s), 0, p.Y, p.s, p.status);
+    return launch_ok();
+}
+
+struct Timer {
+    rxr_handle h;
+    int id;
+    cudaStream_t st;
+    Timer(rxr_handle h_, int id_, cudaStream_t st_) : h(h_), id(id_), st(st_)
+    {
+        if (h && h->timing) cudaEventRecord(h->ev[id][0], st);
+    }
+    ~Timer()
+    {
+        if (h && h->timing) {
+            cudaEventRecord(h->ev[id][1], st);
+            h->ev_recorded[id] = true;
+        }
+    }
+};
+
+// The whole factorisation, stream-ordered, no host synchronisation.
+int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, int variant, uint64_t seed, int passes,
+                   double *Q, int64_t ldq, double *R, int64_t ldr, cudaStream_t st, bool timed)
+{
+    rxr_handle th = timed ? h : nullptr;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    const int n = (int)p.n;
+    // steps 1-2: sketch and its R factor (R_s = I without preconditioner)
+    if (variant == RXR_NONE) {
+        k_identity<<<(int)cdiv(p.n * p.n, 256), 256, 0, st>>>(p.Rs, n);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    } else {
+        {
+            Timer t(th, 0, st);
+            if (int e = enqueue_sketch(p, A, lda, seed, st)) return e;
+        }
+        k_xr_factor<<<1, 512, 0, st>>>(p.Y, (int)p.s, n, p.s, variant, p.W, p.Rs, p.n, p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(p.Racc, p.Rs, (size_t)p.n * p.n * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    // step 3: X = A R_s^{-1} into Q, fused with G_1 = X^T X
+    {
+        Timer t(th, 1, st);
+        if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
+            if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, false, st)) return e;
+            if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
+        } else {
+            if (int e = enqueue_subst(p, A, lda, p.Rs, variant == RXR_NONE ? 1 : 0, Q, ldq, true,
+                                      variant == RXR_NONE, st))
+                return e;
+        }
+    }
+    // step 4: CholeskyQR passes on X
+    for (int pass = 1; pass <= passes; ++pass) {
+        k_factor<<<1, 512, 0, st>>>(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+        const bool last = (pass == passes);
+        Timer t(th, last ? 3 : 2, st);
+        // X <- X R_p^{-1} (in place), with the next pass's Gram unless last
+        if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) return e;
+    }
+    if (R) {
+        k_copy_upper<<<(int)cdiv(p.n * p.n, 256), 256, 0, st>>>(p.Racc, n, R, ldr, p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    return 0;
+}
+
+int check_args(const double *A, int64_t m, int64_t n, int64_t lda, int variant, int64_t s, int passes,
+               const double *Q, int64_t ldq, const double *R, int64_t ldr, int prec)
+{
+    if (A == nullptr) return -1;
+    if (m < 1 || m < n) return -2;
+    if (n < 1) return -3;
+    if (lda < m) return -4;
+    if (variant != RXR_LU && variant != RXR_QR && variant != RXR_NONE) return -5;
+    if (variant != RXR_NONE && (s < n || s > RXR_MAX_S)) return -6;
+    if (passes < 1 || passes > 3) return -8;
+    if (Q == nullptr) return -9;
+    if (ldq < m) return -10;
+    if (R != nullptr && ldr < n) return -12;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -13;
+    if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    if (m > ((int64_t)1 << 31)) return RXR_ERR_UNSUPPORTED;
+    (void)Q;
+    return 0;
+}
+
+int finish_blocking(rxr_handle h, const RxrStatus *d_status, cudaStream_t st)
+{
+    if (cudaMemcpyAsync(h->h_status, d_status, 4 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    const int code = h->h_status[0];
+    if (code == RXR_ERR_CHOL_BREAKDOWN) {
+        h->last_pass = h->h_status[1];
+        h->last_col = h->h_status[2];
+    }
+    if (h->timing)
+        for (int k = 0; k < 4; ++k)
+            if (h->ev_recorded[k]) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, h->ev[k][0], h->ev[k][1]) == cudaSuccess) h->last_ms[k] = ms;
+                else (void)cudaGetLastError();
+                h->ev_recorded[k] = false;
+            }
+    return code;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int rxr_create(rxr_handle *h, int device)
+{
+    if (h == nullptr) return -1;
+    *h = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return -2;
+    DeviceGuard g(device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    rxr_ctx *c = new rxr_ctx();
+    c->device = device;
+    c->sms = device_sms(device);
+    if (cudaMallocHost(&c->h_status, 4 * sizeof(int)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return RXR_ERR_CUDA;
+    }
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 2; ++j) cudaEventCreate(&c->ev[k][j]);
+    if (set_kernel_attrs()) {
+        cudaFreeHost(c->h_status);
+        delete c;
+        return RXR_ERR_CUDA;
+    }
+    *h = c;
+    return 0;
+}
+
+int rxr_destroy(rxr_handle h)
+{
+    if (h == nullptr) return 0;
+    DeviceGuard g(h->device);
+    if (h->ws && h->ws_owned) cudaFree(h->ws);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->dA) cudaFree(h->dA);
+    if (h->dQ) cudaFree(h->dQ);
+    if (h->dR) cudaFree(h->dR);
+    if (h->eval_buf) cudaFree(h->eval_buf);
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 2; ++j)
+            if (h->ev[k][j]) cudaEventDestroy(h->ev[k][j]);
+    delete h;
+    return 0;
+}
+
+int rxr_workspace_bytes(int64_t m, int64_t n, int64_t s, int prec, size_t *bytes)
+{
+    if (bytes == nullptr) return -5;
+    if (m < 1 || n < 1 || m < n) return -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        dev = 0;
+    }
+    Plan p;
+    make_plan(p, m, n, std::max<int64_t>(s, n), prec, device_sms(dev));
+    *bytes = p.bytes;
+    return 0;
+}
+
+int rxr_set_workspace(rxr_handle h, void *d_ws, size_t bytes)
+{
+    if (h == nullptr) return -1;
+    DeviceGuard g(h->device);
+    if (h->ws && h->ws_owned) cudaFree(h->ws);
+    if (d_ws == nullptr) {
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+        h->ws_owned = true;
+    } else {
+        h->ws = d_ws;
+        h->ws_bytes = bytes;
+        h->ws_owned = false;
+    }
+    return 0;
+}
+
+static int cholqr_common(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int variant, int64_t s,
+                         uint64_t seed, int passes, double *Q, int64_t ldq, double *R, int64_t ldr, int prec,
+                         void *stream, int *d_status, bool blocking)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (variant == RXR_NONE && s < n) s = n;
+    if (int e = check_args(A, m, n, lda, variant, s, passes, Q, ldq, R, ldr, prec)) return e;
+    DeviceGuard g(h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    Plan p;
+    make_plan(p, m, n, s, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    int e = enqueue_cholqr(h, p, A, lda, variant, seed, passes, Q, ldq, R, ldr, st, blocking && h->timing);
+    if (e) return e;
+    if (d_status) {
+        k_status_out<<<1, 32, 0, st>>>(p.status, d_status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    if (!blocking) return 0;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_cholqr(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int variant, int64_t s, uint64_t seed,
+               int passes, double *Q, int64_t ldq, double *R, int64_t ldr, int prec, void *stream)
+{
+    return cholqr_common(h, A, m, n, lda, variant, s, seed, passes, Q, ldq, R, ldr, prec, stream, nullptr, true);
+}
+
+int rxr_cholqr_async(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int variant, int64_t s,
+                     uint64_t seed, int passes, double *Q, int64_t ldq, double *R, int64_t ldr, int prec, void *stream,
+                     int *d_status)
+{
+    if (d_status == nullptr) return -15;
+    return cholqr_common(h, A, m, n, lda, variant, s, seed, passes, Q, ldq, R, ldr, prec, stream, d_status, false);
+}
+
+int rxr_cholqr_host(rxr_handle h, const double *hA, int64_t m, int64_t n, int64_t lda, int variant, int64_t s,
+                    uint64_t seed, int passes, double *hQ, int64_t ldq, double *hR, int64_t ldr, int prec,
+                    void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (variant == RXR_NONE && s < n) s = n;
+    if (int e = check_args(hA, m, n, lda, variant, s, passes, hQ, ldq, hR, ldr, prec)) return e;
+    DeviceGuard g(h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    const int64_t ldd = (m + 1) & ~(int64_t)1;  // even leading dimension: TMA-compatible rows
+    const size_t mat = (size_t)ldd * n * 8;
+    if (grow((void **)&h->dA, &h->dA_bytes, mat) || grow((void **)&h->dQ, &h->dQ_bytes, mat) ||
+        grow((void **)&h->dR, &h->dR_bytes, (size_t)n * n * 8))
+        return RXR_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpy2DAsync(h->dA, ldd * 8, hA, lda * 8, m * 8, n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    Plan p;
+    make_plan(p, m, n, s, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    int e = enqueue_cholqr(h, p, h->dA, ldd, variant, seed, passes, h->dQ, ldd, hR ? h->dR : nullptr, n, st,
+                           h->timing);
+    if (e) return e;
+    if (cudaMemcpy2DAsync(hQ, ldq * 8, h->dQ, ldd * 8, m * 8, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        (hR && cudaMemcpy2DAsync(hR, ldr * 8, h->dR, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
+                       const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
+                       double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
+                       void *stream, int *d_status)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (count < 0) return -2;
+    if (count == 0) return 0;
+    if (!A || !m || !n || !lda || !s || !seed || !Q || !ldq || !R || !ldr || !d_status) return -3;
+    DeviceGuard g(h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    size_t need = 0;
+    for (int k = 0; k < count; ++k) {
+        const int64_t sk = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
+        if (int e = check_args(A[k], m[k], n[k], lda[k], variant, sk, passes, Q[k], ldq[k], R[k], ldr[k], prec))
+            return e;
+        Plan p;
+        make_plan(p, m[k], n[k], sk, prec, h->sms);
+        need = std::max(need, p.bytes);
+    }
+    if (int e = ensure_ws(h, need)) return e;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < count; ++k) {
+        const int64_t sk = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
+        Plan p;
+        make_plan(p, m[k], n[k], sk, prec, h->sms);
+        bind_plan(p, h->ws);
+        if (int e = enqueue_cholqr(h, p, A[k], lda[k], variant, seed[k], passes, Q[k], ldq[k], R[k], ldr[k], st,
+                                   false))
+            return e;
+        k_status_out<<<1, 32, 0, st>>>(p.status, d_status + 4 * k);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    // read back all statuses
+    int *hs = (int *)malloc((size_t)count * 4 * sizeof(int));
+    if (!hs) return RXR_ERR_NOMEM;
+    int code = 0;
+    if (cudaMemcpyAsync(hs, d_status, (size_t)count * 4 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        code = RXR_ERR_CUDA;
+    } else {
+        for (int k = 0; k < count && code == 0; ++k)
+            if (hs[4 * k]) {
+                code = hs[4 * k];
+                if (code == RXR_ERR_CHOL_BREAKDOWN) {
+                    h->last_pass = hs[4 * k + 1];
+                    h->last_col = hs[4 * k + 2];
+                }
+            }
+    }
+    free(hs);
+    return code;
+}
+
+int rxr_last_info(rxr_handle h, int *pass, int *column)
+{
+    if (h == nullptr) return -1;
+    if (pass) *pass = h->last_pass;
+    if (column) *column = h->last_col;
+    return 0;
+}
+
+const char *rxr_status_string(int code)
+{
+    switch (code) {
+    case RXR_OK: return "ok";
+    case RXR_ERR_SKETCH_SINGULAR: return "sketch factor singular (rank-deficient sketch or A)";
+    case RXR_ERR_CHOL_BREAKDOWN: return "Cholesky breakdown (non-positive pivot)";
+    case RXR_ERR_NONFINITE: return "A contains NaN or Inf";
+    case RXR_ERR_CUDA: return "CUDA error";
+    case RXR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RXR_ERR_NOMEM: return "workspace allocation failed or too small";
+    case RXR_ERR_UNSUPPORTED: return "arguments outside what this build supports";
+    default: return code < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+int rxr_omega(uint64_t seed, int64_t s, int64_t row0, int64_t rows, float *d_z, void *stream)
+{
+    if (s < 1) return -2;
+    if (row0 < 0) return -3;
+    if (rows < 0) return -4;
+    if (d_z == nullptr && rows > 0) return -5;
+    if (rows == 0) return 0;
+    const int64_t calls = rows * ((s + 3) / 4);
+    const int blocks = (int)std::min<int64_t>(cdiv(calls, 256), 152 * 16);
+    k_omega<<<blocks, 256, 0, (cudaStream_t)stream>>>(seed, s, row0, rows, d_z);
+    return launch_ok();
+}
+
+int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed, double *Y,
+               int64_t ldy, int prec, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (m < 1 || m < n) return -3;
+    if (n < 1) return -4;
+    if (lda < m) return -5;
+    if (s < 1 || s > RXR_MAX_S) return -6;
+    if (Y == nullptr) return -8;
+    if (ldy < s) return -9;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -10;
+    if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, m, n, s, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    if (int e = enqueue_sketch(p, A, lda, seed, st)) return e;
+    if (cudaMemcpy2DAsync(Y, ldy * 8, p.Y, s * 8, s * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_xr_factor(rxr_handle h, const double *Y, int64_t s, int64_t n, int64_t ldy, int variant, double *Rs,
+                  int64_t ldrs, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (Y == nullptr) return -2;
+    if (n < 1) return -4;
+    if (s < n || s > RXR_MAX_S) return -3;
+    if (ldy < s) return -5;
+    if (variant != RXR_LU && variant != RXR_QR) return -6;
+    if (Rs == nullptr) return -7;
+    if (ldrs < n) return -8;
+    if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, s, n, s, RXR_FP64, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    k_xr_factor<<<1, 512, 0, st>>>(Y, (int)s, (int)n, ldy, variant, p.W, Rs, ldrs, p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *R, int64_t ldr,
+                     double *X, int64_t ldx, double *G, int64_t ldg, int prec, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (m < 1 || m < n) return -3;
+    if (n < 1) return -4;
+    if (lda < m) return -5;
+    if (R == nullptr) return -6;
+    if (ldr < n) return -7;
+    if (X != nullptr && ldx < m) return -9;
+    if (G == nullptr) return -10;
+    if (ldg < n) return -11;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -12;
+    if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, m, n, n, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    // R may have any leading dimension: copy it to the packed n x n buffer
+    if (cudaMemcpy2DAsync(p.Rp, n * 8, R, ldr * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    if (prec == RXR_SPLIT_BF16) {
+        if (X == nullptr) return RXR_ERR_UNSUPPORTED;
+        if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, false, false, st)) return e;
+        if (int e = split_gram_enqueue(p, X, ldx, st)) return e;
+    } else {
+        if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, true, false, st)) return e;
+    }
+    if (cudaMemcpy2DAsync(G, ldg * 8, p.G, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *R, int64_t ldr, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (G == nullptr) return -2;
+    if (n < 1) return -3;
+    if (ldg < n) return -4;
+    if (R == nullptr) return -5;
+    if (ldr < n) return -6;
+    if (n > RXR_MAX_N) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, n, n, n, RXR_FP64, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    k_factor<<<1, 512, 0, st>>>(G, (int)n, ldg, p.Rp, p.Racc, p.C, 1, 0, p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    if (cudaMemcpy2DAsync(R, ldr * 8, p.Rp, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_orth_error(rxr_handle h, const double *Q, int64_t m, int64_t n, int64_t ldq, double *out, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (Q == nullptr) return -2;
+    if (m < 1) return -3;
+    if (n < 1 || n > RXR_MAX_N) return -4;
+    if (ldq < m) return -5;
+    if (out == nullptr) return -6;
+    DeviceGuard g(h->device);
+    const int npairs = (int)(n * (n + 1) / 2);
+    const int gy = (int)cdiv(npairs, 256);
+    const int64_t chunks = std::min<int64_t>(cdiv(m, 64), std::max<int64_t>(1, 2 * h->sms / gy + 1));
+    const int64_t rpc = cdiv(cdiv(m, chunks), 64) * 64;
+    const int64_t nch = cdiv(m, rpc);
+    if (grow((void **)&h->eval_buf, &h->eval_bytes, ((size_t)nch * npairs * 2 + 8) * 8)) return RXR_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t smem = (size_t)64 * n * 8;
+    k_orth_partial<<<dim3((unsigned)nch, gy), 256, smem, st>>>(Q, m, (int)n, ldq, rpc, h->eval_buf);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    double *res = h->eval_buf + (size_t)nch * npairs * 2;
+    k_orth_final<<<1, 1024, 0, st>>>(h->eval_buf, (int)nch, (int)n, res);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    if (cudaMemcpyAsync(out, res, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    return 0;
+}
+
+int rxr_resid_error(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *Q, int64_t ldq,
+                    const double *R, int64_t ldr, double *out, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (m < 1) return -3;
+    if (n < 1 || n > RXR_MAX_N) return -4;
+    if (lda < m) return -5;
+    if (Q == nullptr) return -6;
+    if (ldq < m) return -7;
+    if (R == nullptr) return -8;
+    if (ldr < n) return -9;
+    if (out == nullptr) return -10;
+    DeviceGuard g(h->device);
+    const int blocks = (int)std::min<int64_t>(cdiv(m, 256), 4 * h->sms);
+    if (grow((void **)&h->eval_buf, &h->eval_bytes, ((size_t)blocks * 2 + 8) * 8)) return RXR_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t smem = (size_t)(n * (n + 1) / 2) * 8;
+    k_resid_partial<<<blocks, 256, smem, st>>>(A, lda, Q, ldq, R, ldr, m, (int)n, h->eval_buf);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    double *res = h->eval_buf + (size_t)blocks * 2;
+    k_resid_final<<<1, 32, 0, st>>>(h->eval_buf, blocks, res);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    if (cudaMemcpyAsync(out, res, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    return 0;
+}
+
+int rxr_fp64_peak(double *tflops, void *stream)
+{
+    if (tflops == nullptr) return -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RXR_ERR_CUDA;
+    const int sms = device_sms(dev);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)blocks * threads * 8) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_NOMEM;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int rc = 0;
+    for (int rep = 0; rep < 4 && rc == 0; ++rep) {
+        cudaEventRecord(e0, st);
+        k_fp64_peak<<<blocks, threads, 0, st>>>(buf, iters, 0.999, 1e-3);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = RXR_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc) {
+        (void)cudaGetLastError();
+        return rc;
+    }
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    return 0;
+}
+
+int rxr_last_kernel_ms(rxr_handle h, int kernel, float *ms)
+{
+    if (h == nullptr || ms == nullptr) return -1;
+    if (kernel < 0 || kernel > 3) return -1;
+    *ms = h->last_ms[kernel];
+    return 0;
+}
+
+int rxr_set_kernel_timing(rxr_handle h, int enable)
+{
+    if (h == nullptr) return -1;
+    h->timing = enable != 0;
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,274 @@
+// rxr_internal.cuh -- device helpers shared by the librxr CUDA translation units.
+// Randomized XR-preconditioned CholeskyQR (Fan, Guo & Lin), GB300 (sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rxr.h"
+
+#define RXR_THREADS 256
+
+// ---------------------------------------------------------------------------
+// Device status word {code, pass, column, flags}.  Kernels set the first
+// failure with atomicCAS on code so that the earliest failure in stream order
+// wins; every streaming kernel returns immediately when code != 0.
+// ---------------------------------------------------------------------------
+struct RxrStatus {
+    int code;
+    int pass;
+    int column;
+    int flags;
+};
+
+__device__ __forceinline__ void rxr_fail(RxrStatus *st, int code, int pass, int column)
+{
+    if (atomicCAS(&st->code, 0, code) == 0) {
+        st->pass = pass;
+        st->column = column;
+    }
+}
+
+__device__ __forceinline__ bool rxr_failed(const RxrStatus *st)
+{
+    return *((volatile const int *)&st->code) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of
+//   (c0,c1,c2,c3) -> (hi(Mb*c2)^c1^k0, lo(Mb*c2), hi(Ma*c0)^c3^k1, lo(Ma*c0))
+// with the key bumped by the golden-ratio Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0,
+                                              uint32_t k1)
+{
+    constexpr uint32_t Ma = 0xD2511F53u, Mb = 0xCD9E8D57u;
+    constexpr uint32_t Wa = 0x9E3779B9u, Wb = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hiA = __umulhi(Ma, c0), loA = Ma * c0;
+        const uint32_t hiB = __umulhi(Mb, c2), loB = Mb * c2;
+        const uint32_t n0 = hiB ^ c1 ^ k0;
+        const uint32_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0;
+        c1 = loB;
+        c2 = n2;
+        c3 = loA;
+        k0 += Wa;
+        k1 += Wb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-precision log on (0,1] from log x = 2 atanh((x-1)/(x+1)), with
+// u = 2^e x, x in [1/sqrt2, sqrt2]; odd series in t = (x-1)/(x+1) through
+// t^13, then e*ln2 added in two pieces.  Only explicitly rounded intrinsics, so
+// the bits are fixed by IEEE single precision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rxr_logf(float u)
+{
+    const uint32_t b = __float_as_uint(u);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    float x = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (__float_as_uint(x) > 0x3FB504F3u) {  // above sqrt(2): halve (exact)
+        x = __fmul_rn(x, 0.5f);
+        e += 1;
+    }
+    const float t = __fdiv_rn(__fsub_rn(x, 1.0f), __fadd_rn(x, 1.0f));
+    const float t2 = __fmul_rn(t, t);
+    float p = (float)(2.0 / 13.0);
+    p = __fmaf_rn(p, t2, (float)(2.0 / 11.0));
+    p = __fmaf_rn(p, t2, (float)(2.0 / 9.0));
+    p = __fmaf_rn(p, t2, (float)(2.0 / 7.0));
+    p = __fmaf_rn(p, t2, (float)(2.0 / 5.0));
+    p = __fmaf_rn(p, t2, (float)(2.0 / 3.0));
+    const float lx = __fmaf_rn(__fmul_rn(t, t2), p, __fadd_rn(t, t));
+    constexpr double kLn2 = 0.6931471805599453094172321214581766;
+    constexpr float kLn2Hi = (float)kLn2;
+    constexpr float kLn2Lo = (float)(kLn2 - (double)kLn2Hi);
+    const float fe = __int2float_rn(e);
+    return __fmaf_rn(fe, kLn2Hi, __fmaf_rn(fe, kLn2Lo, lx));
+}
+
+// sin and cos of 2 pi u with u = n 2^-24: the quadrant q = round(4u) is taken in
+// integers, the remainder f = 4u - q in [-1/2, 1/2) is exact, and
+// sin(pi f / 2), cos(pi f / 2) come from their Maclaurin series in f.
+__device__ __forceinline__ void rxr_sincos2pi(uint32_t n, float &s_out, float &c_out)
+{
+    constexpr double h = 1.5707963267948966192313216916397514;  // pi / 2
+    constexpr double h2 = h * h;
+    constexpr float s1 = (float)h, s3 = (float)(-h * h2 / 6.0), s5 = (float)(h * h2 * h2 / 120.0);
+    constexpr float s7 = (float)(-h * h2 * h2 * h2 / 5040.0), s9 = (float)(h * h2 * h2 * h2 * h2 / 362880.0);
+    constexpr float c0 = 1.0f, c2 = (float)(-h2 / 2.0), c4 = (float)(h2 * h2 / 24.0);
+    constexpr float c6 = (float)(-h2 * h2 * h2 / 720.0), c8 = (float)(h2 * h2 * h2 * h2 / 40320.0);
+    constexpr float c10 = (float)(-h2 * h2 * h2 * h2 * h2 / 3628800.0);
+    const int q = (int)((n + (1u << 21)) >> 22);
+    const int r = (int)n - q * (1 << 22);
+    const float f = __fmul_rn(__int2float_rn(r), 0x1p-22f);
+    const float f2 = __fmul_rn(f, f);
+    float sp = s9;
+    sp = __fmaf_rn(sp, f2, s7);
+    sp = __fmaf_rn(sp, f2, s5);
+    sp = __fmaf_rn(sp, f2, s3);
+    const float sn = __fmaf_rn(__fmul_rn(f, f2), sp, __fmul_rn(s1, f));
+    float cp = c10;
+    cp = __fmaf_rn(cp, f2, c8);
+    cp = __fmaf_rn(cp, f2, c6);
+    cp = __fmaf_rn(cp, f2, c4);
+    cp = __fmaf_rn(cp, f2, c2);
+    const float cs = __fmaf_rn(cp, f2, c0);
+    switch (q & 3) {
+    case 0: s_out = sn; c_out = cs; break;
+    case 1: s_out = cs; c_out = -sn; break;
+    case 2: s_out = -sn; c_out = -cs; break;
+    default: s_out = -cs; c_out = sn; break;
+    }
+}
+
+// Four N(0,1) values for sketch rows 4k..4k+3 of column i (row i of A):
+// Philox counter (i_lo, i_hi, k, stream), key (seed_lo, seed_hi); uniforms
+// u = ((x >> 8) + 1) 2^-24 in (0,1]; Box-Muller pairs (x0,x1) and (x2,x3).
+__device__ __forceinline__ void rxr_normal4(uint64_t seed, uint64_t i, uint32_t k, uint32_t stream, float z[4])
+{
+    uint32_t c0 = (uint32_t)i, c1 = (uint32_t)(i >> 32), c2 = k, c3 = stream;
+    philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t xs[4] = {c0, c1, c2, c3};
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const uint32_t na = (xs[2 * hh] >> 8) + 1u, nb = (xs[2 * hh + 1] >> 8) + 1u;
+        const float ua = __fmul_rn(__uint2float_rn(na), 0x1p-24f);
+        const float rad = __fsqrt_rn(__fmul_rn(-2.0f, rxr_logf(ua)));
+        float sn, cs;
+        rxr_sincos2pi(nb, sn, cs);
+        z[2 * hh] = __fmul_rn(rad, cs);
+        z[2 * hh + 1] = __fmul_rn(rad, sn);
+    }
+}
+
+// Exact float -> double by bit manipulation on the integer pipes (the FP64
+// pipe of this part is scarce).  Valid for zero and normal floats, which is
+// all the Box-Muller outputs can be.
+__device__ __forceinline__ double rxr_f2d_exact(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b & 0x80000000u;
+    const uint32_t mag = b & 0x7FFFFFFFu;
+    if (mag == 0u) return __hiloint2double((int)sign, 0);
+    const uint32_t e = (mag >> 23) + (1023u - 127u);
+    const uint32_t mant = mag & 0x007FFFFFu;
+    const uint32_t hi = sign | (e << 20) | (mant >> 3);
+    const uint32_t lo = mant << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// Non-finite test on the integer pipes: exponent field all ones.
+__device__ __forceinline__ bool rxr_nonfinite(double v)
+{
+    return (((uint32_t)__double2hiint(v)) & 0x7FF00000u) == 0x7FF00000u;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + TMA (cp.async.bulk.tensor) helpers.  Every wait is bounded: after
+// kSpinLimit polls the waiter records RXR_ERR_TIMEOUT and gives up.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Returns false (and records a timeout) if the phase never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, RxrStatus *st)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    rxr_fail(st, RXR_ERR_TIMEOUT, -1, -1);
+    return false;
+}
+
+// 2-D tiled TMA load of a box at element coordinates (x = row, y = column)
+// into shared memory, completing on `bar`.  x * 8 must be a multiple of 16.
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(smem_dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+namespace rxr {
+// Launch geometry and workspace offsets of one factorisation.
+struct Plan {
+    int64_t m, n, s;
+    int prec;
+    int sms;
+    // sketch
+    int sk_gx, sk_gy;
+    int64_t sk_panels, sk_ppc;
+    // substitution + Gram
+    int sg_gx;
+    int64_t sg_panels, sg_ppc;
+    size_t sg_smem;
+    int sg_maxt;
+    // workspace pieces
+    char *base;
+    RxrStatus *status;
+    double *Ypart, *Y, *W, *Gpart, *G, *Rs, *Rp, *Racc, *C;
+    char *split;  // split-precision scratch
+    size_t bytes;
+};
+}  // namespace rxr
+
+namespace rxr {
+// split-precision contractions (split_kernels.cu)
+int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st);
+int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
+size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
+}  // namespace rxr

@@ -1,0 +1,419 @@
+// small_kernels.cu -- the O(s n^2) and O(n^3) steps that run on one CTA between
+// the streaming passes, plus the accuracy evaluators and the FP64 calibration.
+//   * k_xr_factor : R_s = R factor of the sketch Y (s x n) by Householder QR
+//                   (Algorithm 5 step 2) or LU with partial pivoting (Algorithm
+//                   4 step 2), rows scaled so that diag(R_s) > 0, singularity
+//                   test |R_kk| <= n u max|R_jj| (Section 2.2: a degenerate R_1
+//                   from bad sampling or a rank-deficient A);
+//   * k_factor    : R_p = chol(G_p) (Algorithm 1 step 2; breakdown reported as
+//                   in Section 2.1) and R_acc <- R_p R_acc (R = R_2 R_1 R_s,
+//                   Algorithms 2/4/5 last steps);
+//   * k_copy_upper: R to the caller's layout with zeros below the diagonal;
+//   * k_orth_* / k_resid_*: ||Q^T Q - I||_F and ||A - QR||_F / ||A||_F of
+//                   Section 4.2 with Dot2 compensated dot products (Ogita, Rump
+//                   & Oishi 2005);
+//   * k_fp64_peak : independent DFMA chains on every SM.
+#include "rxr_internal.cuh"
+
+namespace rxr {
+
+constexpr int kSmallThreads = 512;
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// ---------------------------------------------------------------------------
+// Step 2.  W (workspace, ld s) receives a copy of Y and is factorised in place.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSmallThreads)
+    k_xr_factor(const double *__restrict__ Y, int s, int n, int64_t ldy, int variant, double *__restrict__ W,
+                double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double red[33];
+    __shared__ double sh_beta, sh_v0, sh_piv;
+    __shared__ int sh_idx[32];
+    __shared__ double sh_val[32];
+    __shared__ int sh_p;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+    for (int64_t e = tid; e < (int64_t)s * n; e += blockDim.x) {
+        const int i = (int)(e % s), j = (int)(e / s);
+        W[e] = Y[i + j * ldy];
+    }
+    __syncthreads();
+
+    if (variant == RXR_QR) {
+        for (int k = 0; k < n; ++k) {
+            double part = 0.0;
+            for (int i = k + tid; i < s; i += blockDim.x) part = fma(W[i + (int64_t)k * s], W[i + (int64_t)k * s], part);
+            const double ss = block_sum(part, red);
+            if (tid == 0) {
+                const double alpha = sqrt(ss);
+                const double x0 = W[k + (int64_t)k * s];
+                const double sg = (x0 < 0.0) ? -1.0 : 1.0;
+                sh_v0 = x0 + sg * alpha;
+                // beta = 2 / v^T v with v^T v = 2 alpha (alpha + |x0|)
+                sh_beta = (alpha > 0.0) ? 1.0 / (alpha * (alpha + fabs(x0))) : 0.0;
+                W[k + (int64_t)k * s] = -sg * alpha;
+            }
+            __syncthreads();
+            const double beta = sh_beta, v0 = sh_v0;
+            // apply H_k to columns j > k, one warp per column
+            for (int j = k + 1 + warp; j < n; j += nwarps) {
+                double w = 0.0;
+                for (int i = k + 1 + lane; i < s; i += 32) w = fma(W[i + (int64_t)k * s], W[i + (int64_t)j * s], w);
+                w = warp_sum(w);
+                w = fma(v0, W[k + (int64_t)j * s], w);
+                const double f = beta * w;
+                if (lane == 0) W[k + (int64_t)j * s] = fma(-f, v0, W[k + (int64_t)j * s]);
+                for (int i = k + 1 + lane; i < s; i += 32)
+                    W[i + (int64_t)j * s] = fma(-f, W[i + (int64_t)k * s], W[i + (int64_t)j * s]);
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            // pivot: largest |W(i,k)|, i >= k, lowest index on ties
+            double bv = -1.0;
+            int bi = s;
+            for (int i = k + tid; i < s; i += blockDim.x) {
+                const double a = fabs(W[i + (int64_t)k * s]);
+                if (a > bv) {
+                    bv = a;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+                const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sh_val[warp] = bv;
+                sh_idx[warp] = bi;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double v = sh_val[0];
+                int idx = sh_idx[0];
+                for (int w = 1; w < nwarps; ++w)
+                    if (sh_val[w] > v || (sh_val[w] == v && sh_idx[w] < idx)) {
+                        v = sh_val[w];
+                        idx = sh_idx[w];
+                    }
+                sh_p = (idx < s) ? idx : k;
+            }
+            __syncthreads();
+            const int p = sh_p;
+            if (p != k)
+                for (int j = tid; j < n; j += blockDim.x) {
+                    const double t = W[k + (int64_t)j * s];
+                    W[k + (int64_t)j * s] = W[p + (int64_t)j * s];
+                    W[p + (int64_t)j * s] = t;
+                }
+            __syncthreads();
+            if (tid == 0) sh_piv = W[k + (int64_t)k * s];
+            __syncthreads();
+            const double d = sh_piv;
+            if (d != 0.0) {
+                const double dinv = 1.0 / d;
+                // rows i > k: multiplier and trailing update, one thread per row
+                for (int i = k + 1 + tid; i < s; i += blockDim.x) {
+                    const double l = W[i + (int64_t)k * s] * dinv;
+                    W[i + (int64_t)k * s] = l;
+                    for (int j = k + 1; j < n; ++j)
+                        W[i + (int64_t)j * s] = fma(-l, W[k + (int64_t)j * s], W[i + (int64_t)j * s]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // sign normalisation and singularity test
+    __shared__ int sh_bad;
+    if (tid == 0) {
+        double mx = 0.0;
+        int bad = 0;
+        for (int k = 0; k < n; ++k) {
+            const double d = fabs(W[k + (int64_t)k * s]);
+            if (rxr_nonfinite(d)) bad = 1;
+            mx = fmax(mx, d);
+        }
+        const double tol = (double)n * 0x1p-53 * mx;
+        for (int k = 0; k < n; ++k)
+            if (!(fabs(W[k + (int64_t)k * s]) > tol)) bad = 1;
+        sh_bad = bad;
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        double v = 0.0;
+        if (i <= j) {
+            v = W[i + (int64_t)j * s];
+            if (W[i + (int64_t)i * s] < 0.0) v = -v;
+        }
+        Rs[i + j * ldrs] = v;
+    }
+    if (tid == 0 && sh_bad) rxr_fail(st, RXR_ERR_SKETCH_SINGULAR, 0, -1);
+}
+
+// ---------------------------------------------------------------------------
+// R_p = chol(G) (upper, from G's upper triangle), then R_acc <- R_p R_acc.
+// C is n x n workspace.  Right-looking: for column j, R_jj = sqrt(C_jj),
+// R_jl = C_jl / R_jj, then C_kl -= R_jk R_jl for j < k <= l.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSmallThreads)
+    k_factor(const double *__restrict__ G, int n, int64_t ldg, double *__restrict__ Rp, double *__restrict__ Racc,
+             double *__restrict__ C, int pass, int update_racc, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ int sh_bad;
+    __shared__ double sh_rjj;
+    const int tid = threadIdx.x;
+    for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        C[e] = (i <= j) ? G[i + j * ldg] : 0.0;
+        Rp[e] = 0.0;
+    }
+    if (tid == 0) sh_bad = -1;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            const double d = C[j + (int64_t)j * n];
+            if (!(d > 0.0) || rxr_nonfinite(d)) {
+                sh_bad = j;
+            } else {
+                sh_rjj = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (sh_bad >= 0) break;
+        const double rjj = sh_rjj, inv = 1.0 / rjj;
+        for (int l = j + tid; l < n; l += blockDim.x)
+            Rp[j + (int64_t)l * n] = (l == j) ? rjj : C[j + (int64_t)l * n] * inv;
+        __syncthreads();
+        const int w = n - j - 1;
+        const int64_t pairs = (int64_t)w * w;
+        for (int64_t e = tid; e < pairs; e += blockDim.x) {
+            const int k = j + 1 + (int)(e % w), l = j + 1 + (int)(e / w);
+            if (k <= l) C[k + (int64_t)l * n] = fma(-Rp[j + (int64_t)k * n], Rp[j + (int64_t)l * n], C[k + (int64_t)l * n]);
+        }
+        __syncthreads();
+    }
+    if (sh_bad >= 0) {
+        if (tid == 0) rxr_fail(st, RXR_ERR_CHOL_BREAKDOWN, pass, sh_bad);
+        return;
+    }
+    if (!update_racc) return;
+    // C <- R_p R_acc (upper x upper), then R_acc <- C
+    for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        double acc = 0.0;
+        if (i <= j)
+            for (int k = i; k <= j; ++k) acc = fma(Rp[i + (int64_t)k * n], Racc[k + (int64_t)j * n], acc);
+        C[e] = acc;
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) Racc[e] = C[e];
+}
+
+// R (n x n, ld n) -> out (ld ldo), zeros strictly below the diagonal.
+__global__ void k_copy_upper(const double *__restrict__ R, int n, double *__restrict__ out, int64_t ldo,
+                             const RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        out[i + j * ldo] = (i <= j) ? R[e] : 0.0;
+    }
+}
+
+// Identity into an n x n (ld n) matrix.
+__global__ void k_identity(double *__restrict__ R, int n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        R[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
+}
+
+// Copy the device status into a caller-owned int[4].
+__global__ void k_status_out(const RxrStatus *st, int *out)
+{
+    if (threadIdx.x == 0) {
+        out[0] = st->code;
+        out[1] = st->pass;
+        out[2] = st->column;
+        out[3] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dot2 accumulator: (p, s) with p + s the compensated value.
+// ---------------------------------------------------------------------------
+struct Dot2 {
+    double p, s;
+};
+__device__ __forceinline__ void dot2_add(Dot2 &d, double x, double y)
+{
+    const double h = x * y;
+    const double r = fma(x, y, -h);
+    const double p = d.p + h;
+    const double z = p - d.p;
+    const double q = (d.p - (p - z)) + (h - z);
+    d.p = p;
+    d.s += q + r;
+}
+
+// Orthogonality: per (pair, row chunk) partial Dot2 sums of Q^T Q.  grid.x =
+// row chunks, grid.y = pair blocks of blockDim.x pairs (j <= l).
+constexpr int kEvP = 64;
+__global__ void __launch_bounds__(256)
+    k_orth_partial(const double *__restrict__ Q, int64_t m, int n, int64_t ldq, int64_t rows_per_chunk,
+                   double *__restrict__ parts)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *qp = reinterpret_cast<double *>(smem_raw);  // [n][kEvP]
+    const int npairs = n * (n + 1) / 2;
+    const int pair = blockIdx.y * blockDim.x + threadIdx.x;
+    int j = -1, l = -1;
+    if (pair < npairs) {
+        int rem = pair;
+        j = 0;
+        while (rem >= n - j) {
+            rem -= n - j;
+            ++j;
+        }
+        l = j + rem;
+    }
+    Dot2 d = {0.0, 0.0};
+    const int64_t r_begin = blockIdx.x * rows_per_chunk;
+    const int64_t r_end = min(m, r_begin + rows_per_chunk);
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += kEvP) {
+        for (int e = threadIdx.x; e < kEvP * n; e += blockDim.x) {
+            const int row = e % kEvP, col = e / kEvP;
+            const int64_t gr = r0 + row;
+            qp[e] = (gr < r_end) ? Q[gr + (int64_t)col * ldq] : 0.0;
+        }
+        __syncthreads();
+        if (j >= 0)
+            for (int r = 0; r < kEvP; ++r) dot2_add(d, qp[j * kEvP + r], qp[l * kEvP + r]);
+        __syncthreads();
+    }
+    if (pair < npairs) {
+        parts[((int64_t)blockIdx.x * npairs + pair) * 2 + 0] = d.p;
+        parts[((int64_t)blockIdx.x * npairs + pair) * 2 + 1] = d.s;
+    }
+}
+
+// Combine the chunks per pair (error-free sums of the p parts plus the s
+// parts), subtract the identity, and sum squares (off-diagonal pairs twice).
+__global__ void k_orth_final(const double *__restrict__ parts, int nchunks, int n, double *out)
+{
+    __shared__ double red[33];
+    const int npairs = n * (n + 1) / 2;
+    double acc = 0.0;
+    for (int pair = threadIdx.x; pair < npairs; pair += blockDim.x) {
+        int rem = pair, j = 0;
+        while (rem >= n - j) {
+            rem -= n - j;
+            ++j;
+        }
+        const int l = j + rem;
+        Dot2 d = {0.0, 0.0};
+        if (j == l) dot2_add(d, -1.0, 1.0);
+        for (int c = 0; c < nchunks; ++c) {
+            dot2_add(d, parts[((int64_t)c * npairs + pair) * 2 + 0], 1.0);
+            d.s += parts[((int64_t)c * npairs + pair) * 2 + 1];
+        }
+        const double e = d.p + d.s;
+        acc += (j == l ? 1.0 : 2.0) * e * e;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[0] = sqrt(acc);
+}
+
+// Residual: one thread per row; for every column j the entry A_ij - sum_k
+// Q_ik R_kj as one Dot2 sum; per-CTA partial sums of squares of the residual
+// and of A.
+__global__ void __launch_bounds__(256)
+    k_resid_partial(const double *__restrict__ A, int64_t lda, const double *__restrict__ Q, int64_t ldq,
+                    const double *__restrict__ R, int64_t ldr, int64_t m, int n, double *__restrict__ parts)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *rs = reinterpret_cast<double *>(smem_raw);  // packed upper R
+    __shared__ double red[33];
+    for (int j = 0; j < n; ++j)
+        for (int k = threadIdx.x; k <= j; k += blockDim.x) rs[j * (j + 1) / 2 + k] = R[k + (int64_t)j * ldr];
+    __syncthreads();
+    double num = 0.0, den = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int j = 0; j < n; ++j) {
+            Dot2 d = {0.0, 0.0};
+            const double a = A[i + (int64_t)j * lda];
+            dot2_add(d, a, 1.0);
+            const double *rc = rs + j * (j + 1) / 2;
+            for (int k = 0; k <= j; ++k) dot2_add(d, -Q[i + (int64_t)k * ldq], rc[k]);
+            const double e = d.p + d.s;
+            num = fma(e, e, num);
+            den = fma(a, a, den);
+        }
+    }
+    num = block_sum(num, red);
+    den = block_sum(den, red);
+    if (threadIdx.x == 0) {
+        parts[2 * blockIdx.x] = num;
+        parts[2 * blockIdx.x + 1] = den;
+    }
+}
+
+__global__ void k_resid_final(const double *__restrict__ parts, int nparts, double *out)
+{
+    if (threadIdx.x == 0) {
+        double num = 0.0, den = 0.0;
+        for (int c = 0; c < nparts; ++c) {
+            num += parts[2 * c];
+            den += parts[2 * c + 1];
+        }
+        out[0] = sqrt(num) / sqrt(den);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 calibration: 8 independent FMA chains per thread.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fp64_peak(double *out, int iters, double a, double b)
+{
+    double acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = threadIdx.x * 1e-3 + c;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = fma(acc[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace rxr

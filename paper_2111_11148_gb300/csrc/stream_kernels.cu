@@ -1,0 +1,414 @@
+// stream_kernels.cu -- the passes that stream A (m x n, m >> n) through HBM:
+//   * k_omega        : the z values of the Gaussian sketch (test hook);
+//   * k_sketch_fp64  : Y = Omega A with Omega generated in-kernel (Section 2.3);
+//   * k_subst_gram   : X = B R^{-1} by row-wise substitution, optionally written
+//                      out, fused with G = X^T X (Algorithm 1 steps 1 and 3 and
+//                      steps 3 of Algorithms 4/5);
+//   * k_reduce_parts : fixed-order sum of the per-CTA partial sums (the
+//                      paper's MPI reduce of local Grams, Section 2.4).
+//
+// On GB300 the FP64 pipe issues about 2 FMAs per clock per SM (64 times fewer
+// than FP32), so these kernels are bound by FP64 arithmetic, not by HBM: they
+// are written to issue nothing but useful DFMAs on the FP64 pipe; the random
+// numbers, conversions, finiteness checks and address arithmetic all run on
+// the FP32/integer pipes alongside.
+#include "rxr_internal.cuh"
+
+namespace rxr {
+
+// ---------------------------------------------------------------------------
+// Omega test hook: d_z[(i - row0) * s + r]
+// ---------------------------------------------------------------------------
+__global__ void k_omega(uint64_t seed, int64_t s, int64_t row0, int64_t rows, float *__restrict__ z)
+{
+    const int64_t calls_per_row = (s + 3) / 4;
+    const int64_t total = rows * calls_per_row;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = c / calls_per_row;
+        const uint32_t k = (uint32_t)(c % calls_per_row);
+        float v[4];
+        rxr_normal4(seed, (uint64_t)(row0 + i), k, 0u, v);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t r = 4 * (int64_t)k + t;
+            if (r < s) z[i * s + r] = v[t];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Panel staging: rows [r0, r0 + P) x columns [c0, c0 + nc) of a column-major
+// matrix into shared memory, column-major with leading dimension P.  With a
+// valid tensor map one thread issues a 2-D TMA box load (rows past m arrive as
+// zeros); otherwise all threads copy with coalesced loads.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, bool use_tma, uint64_t *bar,
+                                           uint32_t &phase, const double *__restrict__ src, int64_t ld, int64_t m,
+                                           int64_t r0, int c0, int P, int nc, int ncols_total, RxrStatus *st)
+{
+    if (use_tma) {
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(bar, (uint32_t)(P * nc * 8));
+            tma_load_2d(dst, map, (int)r0, c0, bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, phase, st);
+        phase ^= 1u;
+        return ok;
+    }
+    const int total = P * nc;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int row = e % P, col = e / P;
+        const int64_t gr = r0 + row;
+        dst[e] = (gr < m && c0 + col < ncols_total) ? src[gr + (int64_t)(c0 + col) * ld] : 0.0;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Sketch Y = Omega A in FP64.  grid.x = row chunks (contiguous runs of P-row
+// panels), grid.y = (s-tile, n-tile) output tiles of at most 128 x 64.  Each
+// thread owns an 8 x 4 register block of the tile; when the tile is small the
+// CTA splits into `ngroups` row groups that walk interleaved rows and are
+// summed in a fixed order at the end.  Omega's column for each row of A is
+// generated into shared memory once per panel; the unscaled sum
+// Ypart = sum_i z_i a_i^T is written per chunk (the scale 1/sqrt(s) is
+// applied by the reduction).
+// ---------------------------------------------------------------------------
+constexpr int kSkP = 64;      // rows per panel
+constexpr int kSkSTile = 128; // max sketch rows per tile
+constexpr int kSkNTile = 64;  // max columns per tile
+
+__global__ void __launch_bounds__(RXR_THREADS, 2)
+    k_sketch_fp64(const __grid_constant__ CUtensorMap tmapA, int use_tma, const double *__restrict__ A, int64_t lda,
+                  int64_t m, int n, int s, uint64_t seed, int64_t panels_total, int64_t panels_per_cta,
+                  int box_cols, double *__restrict__ Ypart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    double *ap = reinterpret_cast<double *>(smem_raw);  // [kSkNTile][kSkP]
+    double *zp = ap + kSkNTile * kSkP;                   // [kSkP][kSkSTile]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int bad_flag;
+
+    const int n_tiles = (n + kSkNTile - 1) / kSkNTile;
+    const int si = blockIdx.y / n_tiles, ni = blockIdx.y % n_tiles;
+    const int s0 = si * kSkSTile, c0 = ni * kSkNTile;
+    const int sw = min(kSkSTile, s - s0), nw = min(kSkNTile, n - c0);
+    const int ts = (sw + 7) / 8, tn = (nw + 3) / 4;
+    const int tg = ts * tn;
+    const int ngroups = RXR_THREADS / tg;
+    const int g = threadIdx.x / tg, lt = threadIdx.x % tg;
+    const bool active = g < ngroups;
+    const int sb = lt / tn, nb = lt % tn;
+    const int k0 = s0 / 4, kcount = (sw + 3) / 4;  // Philox calls per row for this tile
+
+    if (threadIdx.x == 0) {
+        bad_flag = 0;
+        if (use_tma) {
+            mbar_init(&bar, 1);
+            fence_barrier_init();
+        }
+    }
+    // zero the padding columns once (TMA writes only the first nw columns)
+    for (int e = threadIdx.x; e < kSkNTile * kSkP; e += blockDim.x) ap[e] = 0.0;
+    __syncthreads();
+    uint32_t phase = 0;
+
+    double acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    const int64_t p_begin = blockIdx.x * panels_per_cta;
+    const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
+    for (int64_t p = p_begin; p < p_end; ++p) {
+        const int64_t r0 = p * kSkP;
+        if (!load_panel(ap, &tmapA, use_tma, &bar, phase, A, lda, m, r0, c0, kSkP, box_cols, n, st)) return;
+        // Omega columns for the panel's rows: zp[row][r - s0]
+        for (int c = threadIdx.x; c < kSkP * kcount; c += blockDim.x) {
+            const int row = c / kcount, kk = c % kcount;
+            float v[4];
+            rxr_normal4(seed, (uint64_t)(r0 + row), (uint32_t)(k0 + kk), 0u, v);
+            double *zr = zp + row * kSkSTile + 4 * kk;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) zr[t] = rxr_f2d_exact(v[t]);
+        }
+        // non-finite entries of A (integer test on the loaded panel)
+        {
+            bool bad = false;
+            for (int e = threadIdx.x; e < kSkP * nw; e += blockDim.x) bad |= rxr_nonfinite(ap[e]);
+            if (bad) bad_flag = 1;
+        }
+        __syncthreads();
+        if (active) {
+            // rows g, g + ngroups, ... of the panel, visited in an order rotated
+            // by nb so that threads of a warp read different shared-memory banks
+            const int cnt = (kSkP - g + ngroups - 1) / ngroups;
+            for (int i = 0; i < cnt; ++i) {
+                int ii = i + nb;
+                ii = (ii >= cnt) ? ii - cnt * (ii / cnt) : ii;
+                const int row = g + ii * ngroups;
+                const double *zr = zp + row * kSkSTile + sb * 8;
+                double zv[8], av[4];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) zv[a] = zr[a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) av[b] = ap[(nb * 4 + b) * kSkP + row];
+#pragma unroll
+                for (int a = 0; a < 8; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(zv[a], av[b], acc[a][b]);
+            }
+        }
+        __syncthreads();
+    }
+    if (bad_flag) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+
+    // combine the row groups in a fixed order (group 0 first)
+    double *out = Ypart + (int64_t)blockIdx.x * s * n;
+    if (ngroups == 1) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int r = s0 + sb * 8 + a, c = c0 + nb * 4 + b;
+                if (r < s && c < n) out[r + (int64_t)c * s] = acc[a][b];
+            }
+        return;
+    }
+    double *red = reinterpret_cast<double *>(smem_raw);  // [ngroups][tg][32]
+    if (active) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) red[((int64_t)g * tg + lt) * 32 + a * 4 + b] = acc[a][b];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tg * 32; e += blockDim.x) {
+        const int l = e / 32, ab = e % 32;
+        const int r = s0 + (l / tn) * 8 + ab / 4, c = c0 + (l % tn) * 4 + ab % 4;
+        double v = red[e];
+        for (int gg = 1; gg < ngroups; ++gg) v += red[(int64_t)gg * tg * 32 + e];
+        if (r < s && c < n) out[r + (int64_t)c * s] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// out[r + c*ldo] = scale * sum_{x < nparts} parts[x*stride + r + c*rows], in
+// the order x = 0, 1, ...  (deterministic).  With `symmetric`, only entries
+// r <= c are summed and mirrored (Gram matrices).
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_parts(const double *__restrict__ parts, int nparts, int64_t stride, int rows, int cols,
+                               double scale, int symmetric, double *__restrict__ out, int64_t ldo, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % rows), c = (int)(e / rows);
+        if (symmetric && r > c) continue;
+        double v = 0.0;
+        for (int x = 0; x < nparts; ++x) v += parts[x * stride + e];
+        v *= scale;
+        out[r + c * ldo] = v;
+        if (symmetric && r != c) out[c + r * ldo] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// X = B R^{-1} (row-wise forward substitution, x R = b) fused with the Gram
+// G += X^T X.  B is read from `src` (A or the previous pass's X), X optionally
+// written to `dst` (may equal src: each panel is read completely before it is
+// written).  R (n x n upper, global) is packed into shared memory column by
+// column and read as a broadcast; 1/R_jj is precomputed.  Panel = P rows,
+// one thread per row for the substitution; for the Gram each thread owns up
+// to MAXT 4 x 4 tiles of the upper triangle.  unit_r skips the substitution
+// (R = I, plain CholeskyQR).
+// ---------------------------------------------------------------------------
+constexpr int kSgP = 128;
+
+template <int MAXT>
+__global__ void __launch_bounds__(RXR_THREADS)
+    k_subst_gram(const __grid_constant__ CUtensorMap tmapB, int use_tma, const double *__restrict__ src, int64_t lds,
+                 int64_t m, int n, const double *__restrict__ R, int64_t ldr, int unit_r, double *dst, int64_t ldd,
+                 int do_gram, double *__restrict__ Gpart, int64_t panels_total, int64_t panels_per_cta,
+                 int check_finite, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int n4 = (n + 3) & ~3;
+    double *xp = reinterpret_cast<double *>(smem_raw);  // [n4][kSgP]
+    double *rp = xp + (int64_t)n4 * kSgP;                // packed upper R: column j at j(j+1)/2
+    double *dinv = rp + (int64_t)n * (n + 1) / 2;        // [n]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int bad_flag;
+
+    if (threadIdx.x == 0) {
+        bad_flag = 0;
+        if (use_tma) {
+            mbar_init(&bar, 1);
+            fence_barrier_init();
+        }
+    }
+    for (int e = threadIdx.x; e < n4 * kSgP; e += blockDim.x) xp[e] = 0.0;
+    if (!unit_r) {
+        for (int j = 0; j < n; ++j)
+            for (int k = threadIdx.x; k <= j; k += blockDim.x) rp[j * (j + 1) / 2 + k] = R[k + j * ldr];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) dinv[j] = 1.0 / R[j + j * ldr];
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+
+    // Gram tiles owned by this thread
+    const int NT = n4 / 4;
+    const int ntiles = NT * (NT + 1) / 2;
+    int tbj[MAXT], tbl[MAXT];
+    double acc[MAXT][16];
+#pragma unroll
+    for (int q = 0; q < MAXT; ++q) {
+        const int tau = threadIdx.x + q * RXR_THREADS;
+        int bj = -1, bl = -1;
+        if (do_gram && tau < ntiles) {
+            int rem = tau;
+            bj = 0;
+            while (rem >= NT - bj) {
+                rem -= NT - bj;
+                ++bj;
+            }
+            bl = bj + rem;
+        }
+        tbj[q] = bj;
+        tbl[q] = bl;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[q][e] = 0.0;
+    }
+
+    const int64_t p_begin = blockIdx.x * panels_per_cta;
+    const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
+    for (int64_t p = p_begin; p < p_end; ++p) {
+        const int64_t r0 = p * kSgP;
+        if (!load_panel(xp, &tmapB, use_tma, &bar, phase, src, lds, m, r0, 0, kSgP, n, n, st)) return;
+        if (check_finite) {
+            bool bad = false;
+            for (int e = threadIdx.x; e < kSgP * n; e += blockDim.x) bad |= rxr_nonfinite(xp[e]);
+            if (bad) bad_flag = 1;
+        }
+        // substitution, one thread per row: x_j = (b_j - sum_{k<j} x_k R_kj) / R_jj
+        // as one FMA chain seeded with b_j (no FP64 operation beyond the
+        // n(n-1)/2 FMAs and n multiplications by 1/R_jj)
+        if (!unit_r && threadIdx.x < kSgP) {
+            const int t = threadIdx.x;
+            for (int j = 0; j < n; ++j) {
+                const double *rc = rp + j * (j + 1) / 2;
+                double accj = xp[j * kSgP + t];
+#pragma unroll 4
+                for (int k = 0; k < j; ++k) accj = fma(-xp[k * kSgP + t], rc[k], accj);
+                xp[j * kSgP + t] = accj * dinv[j];
+            }
+        }
+        __syncthreads();
+        if (dst != nullptr) {
+            for (int e = threadIdx.x; e < kSgP * n; e += blockDim.x) {
+                const int row = e % kSgP, col = e / kSgP;
+                const int64_t gr = r0 + row;
+                if (gr < m) dst[gr + (int64_t)col * ldd] = xp[e];
+            }
+        }
+        if (do_gram) {
+#pragma unroll
+            for (int q = 0; q < MAXT; ++q) {
+                const int bj = tbj[q], bl = tbl[q];
+                if (bj < 0) continue;
+                const double *cj = xp + (bj * 4) * kSgP;
+                const double *cl = xp + (bl * 4) * kSgP;
+                // rows visited from a per-tile offset so that the threads of a
+                // warp (different tiles, same step) hit different banks
+                const int rot = (threadIdx.x & 31) * 4;
+                if (bj == bl) {
+                    for (int i = 0; i < kSgP; ++i) {
+                        const int r = (i + rot) & (kSgP - 1);
+                        const double x0 = cj[r], x1 = cj[kSgP + r], x2 = cj[2 * kSgP + r], x3 = cj[3 * kSgP + r];
+                        acc[q][0] = fma(x0, x0, acc[q][0]);
+                        acc[q][1] = fma(x0, x1, acc[q][1]);
+                        acc[q][2] = fma(x0, x2, acc[q][2]);
+                        acc[q][3] = fma(x0, x3, acc[q][3]);
+                        acc[q][5] = fma(x1, x1, acc[q][5]);
+                        acc[q][6] = fma(x1, x2, acc[q][6]);
+                        acc[q][7] = fma(x1, x3, acc[q][7]);
+                        acc[q][10] = fma(x2, x2, acc[q][10]);
+                        acc[q][11] = fma(x2, x3, acc[q][11]);
+                        acc[q][15] = fma(x3, x3, acc[q][15]);
+                    }
+                } else {
+                    for (int i = 0; i < kSgP; ++i) {
+                        const int r = (i + rot) & (kSgP - 1);
+                        double u[4], v[4];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            u[a] = cj[a * kSgP + r];
+                            v[a] = cl[a * kSgP + r];
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[q][a * 4 + b] = fma(u[a], v[b], acc[q][a * 4 + b]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad_flag) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+    if (do_gram) {
+        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+#pragma unroll
+        for (int q = 0; q < MAXT; ++q) {
+            const int bj = tbj[q], bl = tbl[q];
+            if (bj < 0) continue;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int r = bj * 4 + a, c = bl * 4 + b;
+                    if (r < n && c < n && r <= c) out[r + (int64_t)c * n] = acc[q][a * 4 + b];
+                }
+        }
+    }
+}
+
+// Host-side dispatch over the tile count (template kernels stay in this unit).
+cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &map, int use_tma,
+                              const double *src, int64_t lds, int64_t m, int n, const double *R, int64_t ldr,
+                              int unit_r, double *dst, int64_t ldd, int do_gram, double *Gpart, int64_t panels_total,
+                              int64_t panels_per_cta, int check_finite, RxrStatus *status)
+{
+    switch (maxt) {
+    case 1:
+        k_subst_gram<1><<<grid, RXR_THREADS, smem, st>>>(map, use_tma, src, lds, m, n, R, ldr, unit_r, dst, ldd,
+                                                         do_gram, Gpart, panels_total, panels_per_cta, check_finite,
+                                                         status);
+        break;
+    case 2:
+        k_subst_gram<2><<<grid, RXR_THREADS, smem, st>>>(map, use_tma, src, lds, m, n, R, ldr, unit_r, dst, ldd,
+                                                         do_gram, Gpart, panels_total, panels_per_cta, check_finite,
+                                                         status);
+        break;
+    default:
+        k_subst_gram<3><<<grid, RXR_THREADS, smem, st>>>(map, use_tma, src, lds, m, n, R, ldr, unit_r, dst, ldd,
+                                                         do_gram, Gpart, panels_total, panels_per_cta, check_finite,
+                                                         status);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_subst_gram_smem(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_subst_gram<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subst_gram<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subst_gram<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+}  // namespace rxr

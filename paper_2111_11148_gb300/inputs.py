@@ -38,6 +38,22 @@ def sigma_profile(n: int, kappa: float) -> np.ndarray:
     return np.power(float(kappa), -e)
 
 
+def _householder_q(g: np.ndarray) -> np.ndarray:
+    """Orthonormal Q of the thin Householder QR of g (LAPACK geqrf/orgqr).  For
+    large matrices the multithreaded LAPACK behind torch is used; numpy's
+    otherwise."""
+    if g.shape[0] * g.shape[1] >= 2**20:
+        try:
+            import torch
+
+            q, _ = torch.linalg.qr(torch.from_numpy(np.ascontiguousarray(g)))
+            return q.numpy()
+        except ImportError:
+            pass
+    q, _ = np.linalg.qr(g)
+    return q
+
+
 def _haar(n: int, rng: np.random.Generator) -> np.ndarray:
     g = rng.standard_normal((n, n))
     q, r = np.linalg.qr(g)
@@ -57,7 +73,7 @@ def usv_matrix(m: int, n: int, kappa: float, seed: int = 0, *, order: str = "F",
     if m < n or n < 1:
         raise ValueError("need m >= n >= 1")
     g = _rng(seed, 1).standard_normal((m, n))
-    u, _ = np.linalg.qr(g)                       # Householder (LAPACK dgeqrf/dorgqr)
+    u = _householder_q(g)
     v = _haar(n, _rng(seed, 2))
     sig = sigma_profile(n, kappa)
     a = (u * sig) @ v.T

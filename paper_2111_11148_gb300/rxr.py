@@ -1,0 +1,314 @@
+"""Thin ctypes binding of librxr (include/rxr.h): argument marshalling only.
+
+Every step of the factorisation runs in the CUDA kernels of librxr.so; there is
+no CPU fallback.  Importing works without a GPU, but every call raises
+``RxrError`` if the library is missing or returns an error.
+
+Device matrices are torch CUDA tensors in column-major layout: shape (m, n)
+with stride (1, ld), ld >= m (``colmajor`` makes one).  Host matrices for the
+``*_host`` entry point are Fortran-ordered float64 numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librxr.so")
+
+LU, QR, NONE = 0, 1, 2
+FP64, SPLIT_BF16 = 0, 1
+OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED = range(8)
+KERNEL_SKETCH, KERNEL_PRECOND_GRAM, KERNEL_PASS_GRAM, KERNEL_APPLY = range(4)
+
+_VARIANTS = {"lu": LU, "qr": QR, "none": NONE, LU: LU, QR: QR, NONE: NONE}
+_PRECS = {"fp64": FP64, "split": SPLIT_BF16, "split_bf16": SPLIT_BF16, FP64: FP64, SPLIT_BF16: SPLIT_BF16}
+
+
+class RxrError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        msg = status_string(code) if _lib is not None else f"status {code}"
+        super().__init__(f"{what}: {msg} (code {code})" if what else f"{msg} (code {code})")
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load librxr.so (built by paper_2111_11148_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RxrError(CUDA_ERROR, f"librxr.so not built at {LIB_PATH}; run paper_2111_11148_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, u64, i, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "rxr_create": ([P(vp), i], i),
+        "rxr_destroy": ([vp], i),
+        "rxr_workspace_bytes": ([i64, i64, i64, i, P(ctypes.c_size_t)], i),
+        "rxr_set_workspace": ([vp, vp, ctypes.c_size_t], i),
+        "rxr_cholqr": ([vp, vp, i64, i64, i64, i, i64, u64, i, vp, i64, vp, i64, i, vp], i),
+        "rxr_cholqr_async": ([vp, vp, i64, i64, i64, i, i64, u64, i, vp, i64, vp, i64, i, vp, vp], i),
+        "rxr_cholqr_host": ([vp, vp, i64, i64, i64, i, i64, u64, i, vp, i64, vp, i64, i, vp], i),
+        "rxr_cholqr_batched": ([vp, i, vp, vp, vp, vp, i, vp, vp, i, vp, vp, vp, vp, i, vp, vp], i),
+        "rxr_last_info": ([vp, P(i), P(i)], i),
+        "rxr_status_string": ([i], ctypes.c_char_p),
+        "rxr_omega": ([u64, i64, i64, i64, vp, vp], i),
+        "rxr_sketch": ([vp, vp, i64, i64, i64, i64, u64, vp, i64, i, vp], i),
+        "rxr_xr_factor": ([vp, vp, i64, i64, i64, i, vp, i64, vp], i),
+        "rxr_precond_gram": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, i, vp], i),
+        "rxr_cholesky": ([vp, vp, i64, i64, vp, i64, vp], i),
+        "rxr_orth_error": ([vp, vp, i64, i64, i64, P(d), vp], i),
+        "rxr_resid_error": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, P(d), vp], i),
+        "rxr_fp64_peak": ([P(d), vp], i),
+        "rxr_last_kernel_ms": ([vp, i, P(ctypes.c_float)], i),
+        "rxr_set_kernel_timing": ([vp, i], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in ("rxr_create", "rxr_destroy", "rxr_workspace_bytes", "rxr_set_workspace", "rxr_cholqr",
+                        "rxr_cholqr_async", "rxr_cholqr_host", "rxr_cholqr_batched", "rxr_last_info",
+                        "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_xr_factor", "rxr_precond_gram",
+                        "rxr_cholesky", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
+                        "rxr_last_kernel_ms", "rxr_set_kernel_timing")]
+
+
+def status_string(code: int) -> str:
+    return load().rxr_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise RxrError(code, what)
+
+
+# ------------------------------------------------------------------ tensors
+def colmajor(t, ld: Optional[int] = None):
+    """Column-major copy of a 2-D torch tensor (stride (1, ld))."""
+    import torch
+
+    m, n = t.shape
+    ld = m if ld is None else int(ld)
+    buf = torch.empty((n, ld), dtype=t.dtype, device=t.device)
+    out = buf.t()[:m]
+    out.copy_(t)
+    return out
+
+
+def empty_colmajor(m: int, n: int, device="cuda", dtype=None, ld: Optional[int] = None):
+    import torch
+
+    ld = m if ld is None else int(ld)
+    return torch.empty((n, ld), dtype=dtype or torch.float64, device=device).t()[:m]
+
+
+def _ld(t) -> int:
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    m, n = t.shape
+    if n == 1:
+        return max(int(t.stride(1)) if t.stride(1) >= m else m, m)
+    if t.stride(0) != 1 or t.stride(1) < m:
+        raise ValueError("tensor must be column-major (stride (1, ld) with ld >= rows)")
+    return int(t.stride(1))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Handle:
+    """An rxr_handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        self._h = ctypes.c_void_p()
+        _check(lib.rxr_create(ctypes.byref(self._h), int(device)), "rxr_create")
+        self.device = int(device)
+
+    def close(self):
+        if self._h:
+            load().rxr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- main calls
+    def cholqr(self, A, variant="qr", s: Optional[int] = None, seed: int = 0, passes: int = 2, prec="fp64",
+               Q=None, R=None, want_r: bool = True, stream=None, raise_on_error: bool = True):
+        """Q, R = rLU/rQR-CholeskyQR(A).  Returns (Q, R, status)."""
+        import torch
+
+        m, n = A.shape
+        s = 2 * n if s is None else int(s)
+        if Q is None:
+            Q = empty_colmajor(m, n, device=A.device)
+        if R is None and want_r:
+            R = empty_colmajor(n, n, device=A.device)
+        code = load().rxr_cholqr(self._h, _ptr(A), m, n, _ld(A), _VARIANTS[variant], s, seed & (2**64 - 1),
+                                 int(passes), _ptr(Q), _ld(Q), _ptr(R) if R is not None else None,
+                                 _ld(R) if R is not None else n, _PRECS[prec], _stream(stream))
+        if raise_on_error and code != 0:
+            raise RxrError(code, "rxr_cholqr")
+        return Q, R, code
+
+    def cholqr_async(self, A, Q, R, status, variant="qr", s=None, seed=0, passes=2, prec="fp64", stream=None):
+        m, n = A.shape
+        s = 2 * n if s is None else int(s)
+        code = load().rxr_cholqr_async(self._h, _ptr(A), m, n, _ld(A), _VARIANTS[variant], s, seed, int(passes),
+                                       _ptr(Q), _ld(Q), _ptr(R) if R is not None else None,
+                                       _ld(R) if R is not None else n, _PRECS[prec], _stream(stream), _ptr(status))
+        _check(code, "rxr_cholqr_async")
+
+    def cholqr_host(self, A: np.ndarray, variant="qr", s=None, seed=0, passes=2, prec="fp64", Q=None, R=None,
+                    stream=None):
+        """Host-buffer form: numpy (Fortran-order float64) in, numpy out."""
+        m, n = A.shape
+        if not A.flags["F_CONTIGUOUS"] or A.dtype != np.float64:
+            raise ValueError("A must be a Fortran-ordered float64 array")
+        s = 2 * n if s is None else int(s)
+        Q = np.empty((m, n), order="F") if Q is None else Q
+        R = np.empty((n, n), order="F") if R is None else R
+        code = load().rxr_cholqr_host(self._h, A.ctypes.data_as(ctypes.c_void_p), m, n, m, _VARIANTS[variant], s,
+                                      seed, int(passes), Q.ctypes.data_as(ctypes.c_void_p), m,
+                                      R.ctypes.data_as(ctypes.c_void_p), n, _PRECS[prec], _stream(stream))
+        _check(code, "rxr_cholqr_host")
+        return Q, R
+
+    def cholqr_batched(self, As: Sequence, variant="qr", s: Optional[Sequence[int]] = None,
+                       seeds: Optional[Sequence[int]] = None, passes=2, prec="fp64", stream=None):
+        """Factorise a list of column-major CUDA tensors; returns (Qs, Rs, statuses)."""
+        import torch
+
+        cnt = len(As)
+        Qs = [empty_colmajor(a.shape[0], a.shape[1], device=a.device) for a in As]
+        Rs = [empty_colmajor(a.shape[1], a.shape[1], device=a.device) for a in As]
+        s = [2 * a.shape[1] for a in As] if s is None else list(s)
+        seeds = list(range(cnt)) if seeds is None else list(seeds)
+        arr = lambda T, v: (T * cnt)(*v)
+        vp = ctypes.c_void_p
+        st = torch.zeros(4 * cnt, dtype=torch.int32, device=As[0].device if cnt else "cuda")
+        code = load().rxr_cholqr_batched(
+            self._h, cnt, arr(vp, [a.data_ptr() for a in As]), arr(ctypes.c_int64, [a.shape[0] for a in As]),
+            arr(ctypes.c_int64, [a.shape[1] for a in As]), arr(ctypes.c_int64, [_ld(a) for a in As]),
+            _VARIANTS[variant], arr(ctypes.c_int64, s), arr(ctypes.c_uint64, seeds), int(passes),
+            arr(vp, [q.data_ptr() for q in Qs]), arr(ctypes.c_int64, [_ld(q) for q in Qs]),
+            arr(vp, [r.data_ptr() for r in Rs]), arr(ctypes.c_int64, [_ld(r) for r in Rs]), _PRECS[prec],
+            _stream(stream), _ptr(st))
+        if code < 0:
+            raise RxrError(code, "rxr_cholqr_batched")
+        return Qs, Rs, st.view(cnt, 4).cpu().numpy()
+
+    # ---------------------------------------------------------------- stages
+    def sketch(self, A, s: int, seed: int = 0, prec="fp64", stream=None):
+        m, n = A.shape
+        Y = empty_colmajor(s, n, device=A.device)
+        _check(load().rxr_sketch(self._h, _ptr(A), m, n, _ld(A), s, seed, _ptr(Y), _ld(Y), _PRECS[prec],
+                                 _stream(stream)), "rxr_sketch")
+        return Y
+
+    def xr_factor(self, Y, variant="qr", stream=None, raise_on_error=True):
+        s, n = Y.shape
+        Rs = empty_colmajor(n, n, device=Y.device)
+        code = load().rxr_xr_factor(self._h, _ptr(Y), s, n, _ld(Y), _VARIANTS[variant], _ptr(Rs), _ld(Rs),
+                                    _stream(stream))
+        if raise_on_error:
+            _check(code, "rxr_xr_factor")
+        return Rs, code
+
+    def precond_gram(self, A, R, X=None, write_x=True, prec="fp64", stream=None):
+        m, n = A.shape
+        if X is None and write_x:
+            X = empty_colmajor(m, n, device=A.device)
+        G = empty_colmajor(n, n, device=A.device)
+        _check(load().rxr_precond_gram(self._h, _ptr(A), m, n, _ld(A), _ptr(R), _ld(R),
+                                       _ptr(X) if X is not None else None, _ld(X) if X is not None else m,
+                                       _ptr(G), _ld(G), _PRECS[prec], _stream(stream)), "rxr_precond_gram")
+        return X, G
+
+    def cholesky(self, G, stream=None, raise_on_error=True):
+        n = G.shape[0]
+        R = empty_colmajor(n, n, device=G.device)
+        code = load().rxr_cholesky(self._h, _ptr(G), n, _ld(G), _ptr(R), _ld(R), _stream(stream))
+        if raise_on_error:
+            _check(code, "rxr_cholesky")
+        return R, code
+
+    def orth_error(self, Q, stream=None) -> float:
+        m, n = Q.shape
+        out = ctypes.c_double()
+        _check(load().rxr_orth_error(self._h, _ptr(Q), m, n, _ld(Q), ctypes.byref(out), _stream(stream)),
+               "rxr_orth_error")
+        return out.value
+
+    def resid_error(self, A, Q, R, stream=None) -> float:
+        m, n = A.shape
+        out = ctypes.c_double()
+        _check(load().rxr_resid_error(self._h, _ptr(A), m, n, _ld(A), _ptr(Q), _ld(Q), _ptr(R), _ld(R),
+                                      ctypes.byref(out), _stream(stream)), "rxr_resid_error")
+        return out.value
+
+    def last_info(self):
+        p, c = ctypes.c_int(), ctypes.c_int()
+        load().rxr_last_info(self._h, ctypes.byref(p), ctypes.byref(c))
+        return p.value, c.value
+
+    def set_kernel_timing(self, on: bool = True):
+        load().rxr_set_kernel_timing(self._h, 1 if on else 0)
+
+    def last_kernel_ms(self, kernel: int) -> float:
+        v = ctypes.c_float()
+        load().rxr_last_kernel_ms(self._h, int(kernel), ctypes.byref(v))
+        return v.value
+
+
+def omega(seed: int, s: int, row0: int, rows: int, device="cuda", stream=None):
+    """z values of the Gaussian sketch computed on the GPU: tensor (rows, s) float32."""
+    import torch
+
+    z = torch.empty((rows, s), dtype=torch.float32, device=device)
+    _check(load().rxr_omega(seed, s, row0, rows, _ptr(z), _stream(stream)), "rxr_omega")
+    return z
+
+
+def fp64_peak_tflops(stream=None) -> float:
+    v = ctypes.c_double()
+    _check(load().rxr_fp64_peak(ctypes.byref(v), _stream(stream)), "rxr_fp64_peak")
+    return v.value
+
+
+def workspace_bytes(m: int, n: int, s: int, prec="fp64") -> int:
+    v = ctypes.c_size_t()
+    _check(load().rxr_workspace_bytes(m, n, s, _PRECS[prec], ctypes.byref(v)), "rxr_workspace_bytes")
+    return v.value
