@@ -172,7 +172,7 @@ __device__ __forceinline__ bool rxr_nonfinite(double v)
 // mbarrier + TMA (cp.async.bulk.tensor) helpers.  Every wait is bounded: after
 // kSpinLimit polls the waiter records RXR_ERR_TIMEOUT and gives up.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint32_t kSpinLimit = 1u << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

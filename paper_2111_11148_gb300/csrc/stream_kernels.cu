@@ -54,7 +54,8 @@ __device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, 
         }
         const bool ok = mbar_wait_bounded(bar, phase, st);
         phase ^= 1u;
-        return ok;
+        // every thread leaves with the same verdict (no thread left at a barrier)
+        return __syncthreads_or(ok ? 0 : 1) == 0;
     }
     const int total = P * nc;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
