@@ -256,16 +256,21 @@ int set_kernel_attrs()
 {
     std::lock_guard<std::mutex> lk(attr_mu);
     if (kernel_attrs_set) return 0;
-    cudaError_t e = cudaSuccess;
-    const int big = 227 * 1024;
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_sketch_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    e = (cudaError_t)(e | set_subst_gram_smem(big));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_orth_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    e = (cudaError_t)(e | cudaFuncSetAttribute(k_resid_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return RXR_ERR_CUDA;
-    }
+    // dynamic shared memory above 48 KB must be opted into; leave room for the
+    // kernels' static shared memory under the 227 KB per-block limit
+    const int big = 220 * 1024;
+    const cudaError_t es[] = {
+        cudaFuncSetAttribute(k_sketch_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
+        set_subst_gram_smem(big),
+        cudaFuncSetAttribute(k_orth_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
+        cudaFuncSetAttribute(k_resid_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
+    };
+    for (cudaError_t e : es)
+        if (e != cudaSuccess) {
+            fprintf(stderr, "librxr: cudaFuncSetAttribute failed: %s\n", cudaGetErrorString(e));
+            (void)cudaGetLastError();
+            return RXR_ERR_CUDA;
+        }
     kernel_attrs_set = true;
     return 0;
 }
