@@ -103,7 +103,7 @@ def cpu_cores() -> int:
 
 def oracle_rows(target_s: float = 15.0) -> int:
     """Row count of the oracle sample: about `target_s` seconds of single-core work."""
-    return int(os.environ.get("RXR_BENCH_ORACLE_ROWS", 2**17))
+    return int(os.environ.get("RXR_BENCH_ORACLE_ROWS", 2**19))
 
 
 def run_oracle_sample(A_sample: np.ndarray, variant: str):
@@ -218,7 +218,32 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
     resid = h.resid_error(A, Q, R)
 
     # end to end through the host-buffer entry point
-    import ctypes
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_leg(h, A_np, args, world)
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        rows = min(oracle_rows(), M)
+        t_or = run_oracle_sample(np.asfortranarray(A_np[:rows]), args.variant)
+        cpu = {"value": b_alg(rows, N, PASSES) / t_or / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {rows} of {M} rows of the same A, one full rxr_cholqr (single-threaded C oracle), "
+                         f"{t_or:.2f} s"}
+    _emit(args, rank, world, ms, value, peak_fp64, achieved, kmed, orth, resid, e2e, clk, cpu)
+    h.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_leg(h, A_np, args, world):
+    """Same metric through rxr_cholqr_host: pinned host A in, pinned host Q, R out,
+    host<->device copies inside the timed region."""
+    import torch
 
     hA = torch.from_numpy(A_np).pin_memory().numpy()
     hA = np.asfortranarray(hA) if not hA.flags["F_CONTIGUOUS"] else hA
@@ -231,20 +256,11 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
     for _ in range(e_steps):
         h.cholqr_host(hA, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=hQ, R=hR)
     e2e_s = (time.perf_counter() - t0) / e_steps
-    e2e_val = world * b_alg(M, N, PASSES) / e2e_s / 1e9
+    return {"value": world * b_alg(M, N, PASSES) / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * M * N,
+            "d2h_bytes_per_step": 8 * M * N + 8 * N * N}
 
-    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
 
-        oracle.build()
-        rows = oracle_rows()
-        t_or = run_oracle_sample(np.asfortranarray(A_np[:rows]), args.variant)
-        cpu = {"value": b_alg(rows, N, PASSES) / t_or / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"first {rows} of {M} rows of the same A, one full rxr_cholqr (single-threaded C oracle), "
-                         f"{t_or:.2f} s"}
-
+def _emit(args, rank, world, ms, value, peak_fp64, achieved, kmed, orth, resid, e2e, clk, cpu):
     launches_per_step = 11 if PASSES == 2 else 9 + 2 * (PASSES - 1)
     if rank == 0:
         line = {
@@ -262,17 +278,12 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
             "gflops": world * f_alg(M, N, S, PASSES) / (ms * 1e-3) / 1e9,
             "qr_per_s": world / (ms * 1e-3),
             "accuracy": {"orth": orth, "resid": resid},
-            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 8 * M * N,
-                    "d2h_bytes_per_step": 8 * M * N + 8 * N * N},
+            "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    h.close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 def main():
@@ -284,7 +295,13 @@ def main():
     ap.add_argument("--variant", default="qr", choices=["qr", "lu"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
     args = ap.parse_args()
+    if args.m:
+        global M, WORKLOAD
+        M = int(args.m)
+        WORKLOAD = WORKLOAD.replace("m=2^22", f"m={M}")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

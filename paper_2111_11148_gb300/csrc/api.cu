@@ -156,8 +156,10 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms)
     int64_t g2 = std::min<int64_t>((int64_t)sms * per_sm, p.sg_panels);
     p.sg_ppc = cdiv(p.sg_panels, g2);
     p.sg_gx = (int)cdiv(p.sg_panels, p.sg_ppc);
-    const int64_t NT = n4 / 4, ntiles = NT * (NT + 1) / 2;
-    p.sg_maxt = (int)cdiv(ntiles, RXR_THREADS);
+    // Gram tile list: off-diagonal tiles, then the diagonal ones from the next
+    // multiple of 32 (see k_subst_gram)
+    const int64_t NT = n4 / 4, n_off = NT * (NT - 1) / 2, d0 = (n_off + 31) & ~(int64_t)31;
+    p.sg_maxt = (int)cdiv(d0 + NT, RXR_THREADS);
 
     size_t off = 0;
     auto take = [&](size_t bytes) {

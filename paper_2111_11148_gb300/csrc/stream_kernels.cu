@@ -261,28 +261,38 @@ __global__ void __launch_bounds__(RXR_THREADS)
     __syncthreads();
     uint32_t phase = 0;
 
-    // Gram tiles owned by this thread
+    // Gram tiles owned by this thread.  The upper triangle is cut into 4 x 4
+    // tiles; the NT(NT-1)/2 off-diagonal tiles are numbered first and the NT
+    // diagonal tiles start at the next multiple of 32, so that no warp mixes
+    // the two kinds (a diagonal tile needs 10 FMAs per row, an off-diagonal
+    // one 16; a mixed warp would issue both sequences).  Thread t owns entries
+    // t, t + 256, ... of that list.
     const int NT = n4 / 4;
-    const int ntiles = NT * (NT + 1) / 2;
+    const int n_off = NT * (NT - 1) / 2;
+    const int d0 = (n_off + 31) & ~31;
     int tbj[MAXT], tbl[MAXT];
     double acc[MAXT][16];
 #pragma unroll
     for (int q = 0; q < MAXT; ++q) {
-        const int tau = threadIdx.x + q * RXR_THREADS;
+        const int e = threadIdx.x + q * RXR_THREADS;
         int bj = -1, bl = -1;
-        if (do_gram && tau < ntiles) {
-            int rem = tau;
-            bj = 0;
-            while (rem >= NT - bj) {
-                rem -= NT - bj;
-                ++bj;
+        if (do_gram) {
+            if (e < n_off) {
+                int rem = e;
+                bj = 0;
+                while (rem >= NT - 1 - bj) {
+                    rem -= NT - 1 - bj;
+                    ++bj;
+                }
+                bl = bj + 1 + rem;
+            } else if (e >= d0 && e - d0 < NT) {
+                bj = bl = e - d0;
             }
-            bl = bj + rem;
         }
         tbj[q] = bj;
         tbl[q] = bl;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[q][e] = 0.0;
+        for (int k = 0; k < 16; ++k) acc[q][k] = 0.0;
     }
 
     const int64_t p_begin = blockIdx.x * panels_per_cta;
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(RXR_THREADS)
                 const double *cl = xp + (bl * 4) * kSgP;
                 // rows visited from a per-tile offset so that the threads of a
                 // warp (different tiles, same step) hit different banks
-                const int rot = (threadIdx.x & 31) * 4;
+                const int rot = threadIdx.x & 31;
                 if (bj == bl) {
                     for (int i = 0; i < kSgP; ++i) {
                         const int r = (i + rot) & (kSgP - 1);
