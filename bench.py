@@ -35,6 +35,12 @@ METRIC = "tall-skinny QR effective GB/s (B_alg = 8mn(P+3)) at ||Q^T Q - I||_F <=
 WORKLOAD = "rQR-CholeskyQR2 m=2^22 n=64 s=128 kappa=1e10 FP64"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one precondition+Gram launch,
+# ncu capture at m = 2^19 scaled by 8 rows-for-rows (profiles/k_subst_gram_precond_m524288_n64.md)
+TRAFFIC_PG = (268.552704e6 + 225.660672e6) * 8
+HBM_GBS = 6795.5  # measured copy bandwidth of this GPU pool (STREAM-style copy)
+
+
 def b_alg(m, n, passes):
     return 8.0 * m * n * (passes + 3)
 
@@ -211,8 +217,11 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
             kms[k].append(h.last_kernel_ms(k))
     h.set_kernel_timing(False)
     kmed = {k: statistics.median(v) for k, v in kms.items()}
-    sketch_flop = 2.0 * S * M * N
-    achieved = sketch_flop / (kmed[0] * 1e-3) / 1e12
+    # roofline kernel: the fused precondition + Gram launch (k_subst_gram reading
+    # A, writing X = A R_s^{-1}, accumulating G = X^T X).  Algorithmic FP64 work
+    # per row: n(n-1)/2 substitution FMAs + n scalings + n(n+1)/2 Gram FMAs.
+    pg_flop = (2.0 * N * N + N) * M
+    achieved = pg_flop / (kmed[1] * 1e-3) / 1e12
     # accuracy of the timed factorisation (GPU Dot2 evaluators)
     orth = h.orth_error(Q)
     resid = h.resid_error(A, Q, R)
@@ -271,9 +280,11 @@ def _emit(args, rank, world, ms, value, peak_fp64, achieved, kmed, orth, resid, 
                        "variant": args.variant, "prec": args.prec,
                        "l2": "A (2.1 GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_sketch_fp64", "achieved": achieved, "peak": peak_fp64,
-                         "unit": "TFLOP/s", "frac": achieved / peak_fp64, "traffic": None,
-                         "peak_kind": "measured FP64 DFMA calibration (rxr_fp64_peak) on this GPU, same run"},
+            "roofline": {"bound": "alu", "kernel": "k_subst_gram (fused precondition + Gram launch)",
+                         "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
+                         "traffic": TRAFFIC_PG if (M == 2**22 and args.prec == "fp64") else None,
+                         "hbm_frac": (16.0 * M * N / (kmed[1] * 1e-3) / 1e9) / HBM_GBS,
+                         "peak_kind": "FP64 DFMA pipe, measured by the rxr_fp64_peak calibration kernel in this run"},
             "kernels_ms": {"sketch": kmed[0], "precond_gram": kmed[1], "pass_gram": kmed[2], "apply": kmed[3]},
             "gflops": world * f_alg(M, N, S, PASSES) / (ms * 1e-3) / 1e9,
             "qr_per_s": world / (ms * 1e-3),
