@@ -215,6 +215,35 @@ RXR_API int rxr_last_kernel_ms(rxr_handle h, int kernel, float *ms);
 /* Enable or disable the per-kernel events of rxr_last_kernel_ms (off by default). */
 RXR_API int rxr_set_kernel_timing(rxr_handle h, int enable);
 
+/* ---- Allocation-free sketch.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code that runs
+ * while a stream is captured in global mode (cudaMalloc is not allowed there),
+ * processes whose device memory is reserved in full by another allocator, or
+ * loops that forbid allocation after start-up -- and so cannot create a handle
+ * or hand over a workspace.
+ *
+ * Y = Omega A exactly as rxr_sketch with RXR_FP64 (same kernels, same Omega),
+ * but its scratch (the per-chunk partial sums and the status word) lives in a
+ * fixed array of RXR_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
+ * that loads the library holds until the process exits.  The number of row
+ * chunks is capped so that the partial sums fit, so the result may differ
+ * from rxr_sketch's in rounding (not in the tolerance).
+ *   A, m, n, lda (1-4)  device, column-major, m >= n >= 1, n <= 128, lda >= m.
+ *   s (5), seed (6)     sketch rows (1..RXR_MAX_S) and the Philox key.
+ *   Y, ldy (7-8)        device output, s x n, ldy >= s.
+ *   stream (9)          cudaStream_t; the call is blocking (synchronises it).
+ * Returns 0, -i for an invalid argument i, RXR_ERR_NOMEM when s * n exceeds
+ * what the scratch array holds, RXR_ERR_NONFINITE, or RXR_ERR_CUDA.
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its first call on a device (the current device) looks up the
+ * array's device address and sets the kernel's shared-memory limit; make that
+ * first call before any stream capture.  Every call uses the same array, so
+ * calls whose work overlaps on the GPU (other threads, other streams) race:
+ * serialise them. */
+#define RXR_NOALLOC_SCRATCH_BYTES (16u << 20)
+RXR_API int rxr_sketch_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                               double *Y, int64_t ldy, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ def load() -> ctypes.CDLL:
         "rxr_fp64_peak": ([P(d), vp], i),
         "rxr_last_kernel_ms": ([vp, i, P(ctypes.c_float)], i),
         "rxr_set_kernel_timing": ([vp, i], i),
+        "rxr_sketch_noalloc": ([vp, i64, i64, i64, i64, u64, vp, i64, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -83,7 +84,7 @@ def exported_symbols() -> list[str]:
                         "rxr_cholqr_async", "rxr_cholqr_host", "rxr_cholqr_batched", "rxr_last_info",
                         "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_xr_factor", "rxr_precond_gram",
                         "rxr_cholesky", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
-                        "rxr_last_kernel_ms", "rxr_set_kernel_timing")]
+                        "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc")]
 
 
 def status_string(code: int) -> str:
@@ -300,6 +301,16 @@ def omega(seed: int, s: int, row0: int, rows: int, device="cuda", stream=None):
     z = torch.empty((rows, s), dtype=torch.float32, device=device)
     _check(load().rxr_omega(seed, s, row0, rows, _ptr(z), _stream(stream)), "rxr_omega")
     return z
+
+
+def sketch_noalloc(A, s: int, seed: int = 0, Y=None, stream=None):
+    """Y = Omega A through the allocation-free entry point (no handle)."""
+    m, n = A.shape
+    if Y is None:
+        Y = empty_colmajor(s, n, device=A.device)
+    _check(load().rxr_sketch_noalloc(_ptr(A), m, n, _ld(A), s, seed, _ptr(Y), _ld(Y), _stream(stream)),
+           "rxr_sketch_noalloc")
+    return Y
 
 
 def fp64_peak_tflops(stream=None) -> float:
