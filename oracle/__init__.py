@@ -55,6 +55,7 @@ def _load():
             lib.rxo_normal4.argtypes = [u64, u64, u32, u32, vp]
             lib.rxo_omega_z.argtypes = [u64, i64, i64, i64, vp]
             lib.rxo_sketch.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
+            lib.rxo_sketch_quantised.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
             lib.rxo_geqr_r.argtypes = [vp, i64, i64, i64, vp, i64]
             lib.rxo_getrf_u.argtypes = [vp, i64, i64, i64, vp, i64, vp]
             lib.rxo_sign_normalise.argtypes = [vp, i64, i64]
@@ -138,6 +139,21 @@ def sketch(A: np.ndarray, s: int, seed: int) -> np.ndarray:
     Y = np.zeros((s, n), order="F")
     _load().rxo_sketch(_p(A), m, n, _ld(A), s, seed, _p(Y), s)
     return Y
+
+
+def sketch_quantised(A: np.ndarray, s: int, seed: int) -> np.ndarray:
+    """Y' = Omega' A with Omega' = rint(4096 z) / 4096 / sqrt(s): the sketch matrix
+    of the split-precision path (the same draws on the 2^-12 grid)."""
+    A = _f64(A)
+    m, n = A.shape
+    Y = np.zeros((s, n), order="F")
+    _load().rxo_sketch_quantised(_p(A), m, n, _ld(A), s, seed, _p(Y), s)
+    return Y
+
+
+def omega_quantised(seed: int, s: int, m: int) -> np.ndarray:
+    z = omega_z(seed, s, 0, m).astype(np.float64)
+    return np.asfortranarray((1.0 / np.sqrt(float(s))) * (np.rint(z * 4096.0) / 4096.0).T)
 
 
 def geqr_r(W: np.ndarray) -> np.ndarray:

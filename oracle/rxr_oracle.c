@@ -235,8 +235,26 @@ static void pw_finish(pairwise_t *p, double *out)
     if (first) memset(out, 0, (size_t)p->len * sizeof(double));
 }
 
+/* The split-precision sketch uses the same draws quantised to the 2^-12 grid,
+ * z' = rint(4096 z) / 4096 (round half to even), so that each entry is two
+ * 8-bit integers; quantise != 0 selects that matrix. */
+static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                        double *Y, int64_t ldy, int quantise);
+
 void rxo_sketch(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                 double *Y, int64_t ldy)
+{
+    sketch_impl(A, m, n, lda, s, seed, Y, ldy, 0);
+}
+
+void rxo_sketch_quantised(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                          double *Y, int64_t ldy)
+{
+    sketch_impl(A, m, n, lda, s, seed, Y, ldy, 1);
+}
+
+static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                        double *Y, int64_t ldy, int quantise)
 {
     const double c = 1.0 / sqrt((double)s);
     double *blk = (double *)malloc((size_t)(s * n) * sizeof(double));
@@ -251,7 +269,9 @@ void rxo_sketch(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, u
             for (int64_t j = 0; j < n; ++j) {
                 double a = A[(b0 + i) + j * lda];
                 for (int64_t r = 0; r < s; ++r) {
-                    double om = c * (double)z[i * s + r];
+                    double zr = (double)z[i * s + r];
+                    if (quantise) zr = nearbyint(zr * 4096.0) / 4096.0;
+                    double om = c * zr;
                     blk[r + j * s] += om * a;
                 }
             }

@@ -181,3 +181,22 @@ def test_appendix_a_perturbation_bound():
     assert g * cond_x < 1
     assert np.linalg.cond(Xh) <= (1 + g) / (1 - g) * cond_x * (1 + 1e-12)
     assert g < 1e3 * 1e10 * U                              # beta-stability of the substitution
+
+
+def test_quantised_sketch_matches_explicit_product_and_is_close_to_gaussian():
+    # Omega' = rint(4096 z)/4096/sqrt(s): every entry is an integer multiple of
+    # 2^-12/sqrt(s) within 2^-13/sqrt(s) of Omega, and the oracle's Y' equals Omega' A
+    m, n, s = 900, 6, 13
+    A = usv_matrix(m, n, 1e4, seed=21)
+    Oq = o.omega_quantised(3, s, m)
+    Om = o.omega(3, s, m)
+    k = Oq * math.sqrt(s) * 4096.0          # integers up to the rounding of the 1/sqrt(s) scale
+    assert np.max(np.abs(k - np.rint(k))) < 1e-9
+    assert np.max(np.abs(Oq - Om)) <= 2.0**-13 / math.sqrt(s) * (1 + 1e-9)   # ties are exactly 2^-13 away
+    Yq = o.sketch_quantised(A, s, seed=3)
+    np.testing.assert_allclose(Yq, Oq @ A, rtol=0, atol=1e-14 * np.abs(Oq).sum(1).max() * np.abs(A).max())
+    # Proposition 3.1 holds for any sketch matrix: cond(A R^{-1}) = cond(Omega' Q_A)
+    Rq = o.sign_normalise(o.geqr_r(Yq))
+    X = o.trsm_right_upper(A, Rq)
+    Qa, _ = np.linalg.qr(A)
+    assert abs(np.linalg.cond(X) - np.linalg.cond(Oq @ Qa)) <= 1e-8 * np.linalg.cond(X)
