@@ -21,6 +21,7 @@ cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st,
                               int unit_r, double *dst, int64_t ldd, int do_gram, double *Gpart, int64_t panels_total,
                               int64_t panels_per_cta, int check_finite, RxrStatus *status);
 cudaError_t set_subst_gram_smem(int bytes);
+cudaError_t set_split_smem();
 // small_kernels.cu
 __global__ void k_xr_factor(const double *, int, int, int64_t, int, double *, double *, int64_t, RxrStatus *);
 __global__ void k_factor(const double *, int, int64_t, double *, double *, double *, int, int, RxrStatus *);
@@ -266,6 +267,7 @@ int set_kernel_attrs()
         set_subst_gram_smem(big),
         cudaFuncSetAttribute(k_orth_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
         cudaFuncSetAttribute(k_resid_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
+        set_split_smem(),
     };
     for (cudaError_t e : es)
         if (e != cudaSuccess) {

@@ -1,13 +1,516 @@
-// split_kernels.cu -- split-precision (BF16 slices on tcgen05 tensor cores)
-// forms of the two contractions that only shape the preconditioner.
+// split_kernels.cu -- the two contractions that only shape the preconditioner,
+// computed on the 5th-generation tensor cores (tcgen05, BF16 operands in shared
+// memory, FP32 accumulators in tensor memory) instead of the scarce FP64 pipe.
+//
+// k_sketch_split: Y' = Omega' A (Section 2.3, Gaussian ensemble) with
+//   Omega' = rint(4096 z) / 4096 / sqrt(s), the same Philox draws on the 2^-12
+//   grid, so every entry is two 8-bit integers: 4096 z' = 256 zeta0 + zeta1.
+//   A is cut into 512-row windows; in each window column j is written in fixed
+//   point relative to 2^(e_j+1) (e_j = the largest exponent of the column in the
+//   window) as a 55-bit integer, cut into seven 8-bit digits alpha_0..alpha_6
+//   (balanced, |alpha| <= 128).  Every product
+//   zeta_p * alpha_q is an integer below 2^14, the pairs with equal weight
+//   p + q = d share one tensor-memory accumulator (at most two pairs), and a
+//   window of 512 rows keeps every accumulated sum below 2^24: the FP32
+//   accumulation is exact.  Once per window the seven accumulators are combined
+//   (weights 2^-8d) and added to FP64 registers.  The result equals Omega' A up
+//   to the dropped digit products (weight <= 2^-53 relative to the column) and
+//   the FP64 sums: an FP64-grade sketch of A for any conditioning.
+// k_gram_split: G = X^T X (the first CholeskyQR pass's Gram, Algorithm 1 step 1)
+//   with each entry of X cut into three BF16 pieces (the top three 8-bit chunks
+//   of its significand) and the six piece products of combined weight >= 2^-16
+//   accumulated in FP32 in tensor memory, drained to FP64 every 512 rows.
+//   Relative accuracy ~2^-22: enough because X = A R_s^{-1} is well conditioned
+//   (Theorem 3.4) and the error of G only perturbs R_1, which the second, FP64
+//   CholeskyQR pass corrects (Algorithm 2).
+#include <cuda_bf16.h>
+
 #include "rxr_internal.cuh"
 
 namespace rxr {
 
-size_t split_workspace_bytes(int64_t, int64_t, int64_t, int) { return 0; }
+// ---------------------------------------------------------------------------
+// tcgen05 helpers
+// ---------------------------------------------------------------------------
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8
+// rows x 16 bytes stored contiguously; lbo = byte step between core matrices
+// along K, sbo = byte step between 8-row groups along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;
+}
 
-int split_sketch_enqueue(Plan &, const double *, int64_t, uint64_t, cudaStream_t) { return RXR_ERR_UNSUPPORTED; }
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
-int split_gram_enqueue(Plan &, const double *, int64_t, cudaStream_t) { return RXR_ERR_UNSUPPORTED; }
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
+}
+
+// Byte offset of element (row, k) in a K-major, no-swizzle operand tile with
+// K = 64 (8 core matrices of 128 bytes along K per 8-row group).
+__device__ __forceinline__ int kmaj_off(int row, int k)
+{
+    return (row & 7) * 16 + (row >> 3) * 1024 + (k & 7) * 2 + (k >> 3) * 128;
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char *base, int off, float v)
+{
+    *reinterpret_cast<unsigned short *>(base + off) = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// Wait for the tensor-core work committed to `bar` (phase `phase`), bounded;
+// the verdict is made block-uniform.
+__device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t phase, RxrStatus *st)
+{
+    const bool ok = mbar_wait_bounded(bar, phase, st);
+    return __syncthreads_or(ok ? 0 : 1) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Split sketch
+// ---------------------------------------------------------------------------
+constexpr int kSpWin = 512;  // rows per exact-accumulation window
+constexpr int kSpSub = 64;   // rows per operand tile (MMA K extent 4 x 16)
+constexpr int kSpM = 128;    // sketch rows per tile (MMA M)
+constexpr int kSpN = 64;     // columns per tile (MMA N)
+constexpr int kSpDigits = 7; // balanced 8-bit digits of A
+constexpr int kSpZ = 2;      // 8-bit pieces of 4096 z'
+constexpr int kSpB = kSpN * kSpSub * 2;  // bytes of one B tile (8 KB)
+constexpr int kSpA = kSpM * kSpSub * 2;  // bytes of one A tile (16 KB)
+constexpr size_t kSpSmem = (size_t)kSpDigits * kSpB + (size_t)kSpZ * kSpA;
+
+__global__ void __launch_bounds__(256, 1)
+    k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed,
+                   int64_t win_total, int64_t win_per_cta, double *__restrict__ Ypart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *bop = smem;                   // kSpDigits tiles, N x K
+    unsigned char *aop = smem + kSpDigits * kSpB; // kSpZ tiles, M x K
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int colexp[kSpN];
+    __shared__ int bad_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = (n + kSpN - 1) / kSpN;
+    const int si = blockIdx.y / n_tiles, ni = blockIdx.y % n_tiles;
+    const int s0 = si * kSpM, c0 = ni * kSpN;
+    const int sw = min(kSpM, s - s0), nw = min(kSpN, n - c0);
+    const int kcount = (sw + 3) / 4;
+
+    for (int e = tid; e < (int)(kSpSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        bad_flag = 0;
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16(kSpM, kSpN);
+
+    // epilogue ownership: tensor-memory lane quarter (warp % 4) = sketch rows,
+    // column half (warp / 4)
+    const int q4 = warp & 3, half = warp >> 2;
+    const int my_row = 32 * q4 + lane;
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+
+    uint32_t phase = 0;
+    bool pending = false, ok = true;
+    const int64_t w_begin = blockIdx.x * win_per_cta;
+    const int64_t w_end = min(win_total, w_begin + win_per_cta);
+    for (int64_t w = w_begin; w < w_end && ok; ++w) {
+        const int64_t wr0 = w * kSpWin;
+        // 1. largest exponent of each column in the window (integer pipes)
+        if (tid < kSpN) colexp[tid] = 0;
+        __syncthreads();
+        for (int e = tid; e < kSpWin * nw; e += blockDim.x) {
+            const int row = e & (kSpWin - 1), col = e >> 9;
+            const int64_t gr = wr0 + row;
+            unsigned ex = 0;
+            if (gr < m) ex = ((unsigned)__double2hiint(A[gr + (int64_t)(c0 + col) * lda]) >> 20) & 0x7FFu;
+            if (ex == 0x7FFu) bad_flag = 1;
+            ex = __reduce_max_sync(0xFFFFFFFFu, ex);
+            if (lane == 0) atomicMax(&colexp[col], (int)ex);
+        }
+        __syncthreads();
+        // 2. eight operand tiles of 64 rows
+        for (int sp = 0; sp < kSpWin / kSpSub; ++sp) {
+            const int64_t r0 = wr0 + sp * kSpSub;
+            if (pending) {
+                ok = mma_wait(&mma_bar, phase, st);
+                if (!ok) break;
+                phase ^= 1u;
+                pending = false;
+            }
+            // digits of A: element (row k, column j) -> B tile (j, k)
+            for (int e = tid; e < kSpSub * kSpN; e += blockDim.x) {
+                const int k = e & (kSpSub - 1), j = e >> 6;
+                const int64_t gr = r0 + k;
+                long long T = 0;
+                if (j < nw && gr < m) {
+                    const double v = A[gr + (int64_t)(c0 + j) * lda];
+                    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+                    const int ea = (int)((bits >> 52) & 0x7FF);
+                    if (ea > 0 && ea < 0x7FF) {
+                        // T = a / 2^(e_j + 1) * 2^55, |T| < 2^55 (rounded to an integer)
+                        const long long m53 = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+                        const int sh = colexp[j] - ea;  // >= 0
+                        if (sh <= 2)
+                            T = m53 << (2 - sh);
+                        else if (sh < 56)
+                            T = (m53 + (1ll << (sh - 3))) >> (sh - 2);
+                        if (bits >> 63) T = -T;
+                    }
+                }
+                // six balanced digits in [-128, 127] from the bottom; the rest,
+                // |T / 2^48| rounded, is the top digit and lies in [-128, 128]
+#pragma unroll
+                for (int q = kSpDigits - 1; q >= 1; --q) {
+                    const long long d = ((T + 128) & 255) - 128;
+                    T = (T - d) >> 8;
+                    st_bf16(bop + q * kSpB, kmaj_off(j, k), (float)d);
+                }
+                st_bf16(bop, kmaj_off(j, k), (float)T);
+            }
+            // Omega' pieces: A tile (sketch row r, k)
+            for (int c = tid; c < kSpSub * kcount; c += blockDim.x) {
+                const int k = c / kcount, kk = c % kcount;
+                float z[4];
+                rxr_normal4(seed, (uint64_t)(r0 + k), (uint32_t)(s0 / 4 + kk), 0u, z);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int r = 4 * kk + t;
+                    if (r < sw) {
+                        const int q = __float2int_rn(__fmul_rn(z[t], 4096.0f));
+                        const int z0 = (q + 128) >> 8;
+                        const int z1 = q - (z0 << 8);
+                        const int off = kmaj_off(r, k);
+                        st_bf16(aop, off, (float)z0);
+                        st_bf16(aop + kSpA, off, (float)z1);
+                    }
+                }
+            }
+            fence_proxy_async_shared();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(aop), b0 = smem_u32(bop);
+#pragma unroll
+                for (int kk = 0; kk < kSpSub / 16; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < kSpZ; ++p)
+#pragma unroll
+                        for (int q = 0; q + p < kSpDigits; ++q) {
+                            const uint32_t acc_on = (sp > 0 || kk > 0 || p > 0) ? 1u : 0u;
+                            tc_mma(tmem + (uint32_t)((p + q) * kSpN),
+                                   smem_desc(a0 + p * kSpA + kk * 256, 128, 1024),
+                                   smem_desc(b0 + q * kSpB + kk * 256, 128, 1024), idesc, acc_on);
+                        }
+                }
+                tc_commit(&mma_bar);
+            }
+            pending = true;
+        }
+        if (!ok) break;
+        // 3. drain the window: combine the seven weights in FP32 pairs, add in FP64
+        ok = mma_wait(&mma_bar, phase, st);
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc_fence_after();
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+            const int col0 = half * 32 + c16 * 16;
+            float hi[16], lo[16], v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) lo[t] = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kSpDigits; ++d) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + d * kSpN + col0, v);
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);  // 2^-8d
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float x = __fmul_rn(v[t], w8);
+                    const float sum = __fadd_rn(hi[t], x);
+                    const float bb = __fsub_rn(sum, hi[t]);
+                    const float err = __fadd_rn(__fsub_rn(hi[t], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                    hi[t] = sum;
+                    lo[t] = __fadd_rn(lo[t], err);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int ce = colexp[min(col0 + t, kSpN - 1)];
+                const double scale = (ce > 10) ? __hiloint2double((ce - 10) << 20, 0) : 0.0;  // 2^(e_j - 1033)
+                const double val = rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
+                acc[c16 * 16 + t] = fma(val, scale, acc[c16 * 16 + t]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    // an abandoned wait may leave tensor-core work in flight: wait for it once
+    // more (bounded) before releasing tensor memory
+    if (pending) {
+        mma_wait(&mma_bar, phase, st);
+        tc_fence_after();
+    }
+    if (bad_flag) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+    if (ok) {
+        double *out = Ypart + (int64_t)blockIdx.x * s * n;
+        const int r = s0 + my_row;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int c = c0 + half * 32 + t;
+            if (my_row < sw && c < c0 + nw) out[r + (int64_t)c * s] = acc[t];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// Split Gram
+// ---------------------------------------------------------------------------
+constexpr int kGsWin = 512;
+constexpr int kGsSub = 64;
+constexpr int kGsM = 128;               // n <= 128, rows >= n of the tiles are zero
+constexpr int kGsPieces = 3;
+constexpr int kGsTile = kGsM * kGsSub * 2;  // 16 KB
+constexpr size_t kGsSmem = (size_t)kGsPieces * kGsTile;
+
+// The j-th BF16 piece (j = 0, 1, 2) of x: the 8-bit chunk of its significand
+// starting at bit 7 + 8j below the leading one, with x's sign and weight.
+__device__ __forceinline__ float piece_of(unsigned long long bits, int j)
+{
+    const int ea = (int)((bits >> 52) & 0x7FF);
+    if (ea == 0 || ea == 0x7FF) return 0.0f;
+    const int e = ea - 1023 - 7 - 8 * j;  // weight of the chunk's lowest bit
+    if (e < -120 || e > 120) return 0.0f;
+    const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned c = (unsigned)((m53 >> (45 - 8 * j)) & 255u);
+    const float w = __uint_as_float((uint32_t)(e + 127) << 23);
+    const float v = __fmul_rn(__uint2float_rn(c), w);
+    return (bits >> 63) ? -v : v;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_gram_split(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t win_total, int64_t win_per_cta,
+                 double *__restrict__ Gpart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = (n + 15) & ~15;
+
+    for (int e = tid; e < (int)(kGsSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 128);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_bf16(kGsM, N);
+
+    const int q4 = warp & 3, half = warp >> 2;
+    const int my_row = 32 * q4 + lane;  // row j of G
+    double acc[64];
+#pragma unroll
+    for (int t = 0; t < 64; ++t) acc[t] = 0.0;
+
+    uint32_t phase = 0;
+    bool pending = false, ok = true;
+    const int64_t w_begin = blockIdx.x * win_per_cta;
+    const int64_t w_end = min(win_total, w_begin + win_per_cta);
+    for (int64_t w = w_begin; w < w_end && ok; ++w) {
+        for (int sp = 0; sp < kGsWin / kGsSub; ++sp) {
+            const int64_t r0 = w * kGsWin + sp * kGsSub;
+            if (pending) {
+                ok = mma_wait(&mma_bar, phase, st);
+                if (!ok) break;
+                phase ^= 1u;
+                pending = false;
+            }
+            for (int e = tid; e < kGsSub * n; e += blockDim.x) {
+                const int k = e & (kGsSub - 1), j = e >> 6;
+                const int64_t gr = r0 + k;
+                const unsigned long long bits =
+                    (gr < m) ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)j * ldx]) : 0ull;
+                const int off = kmaj_off(j, k);
+#pragma unroll
+                for (int pc = 0; pc < kGsPieces; ++pc) st_bf16(smem + pc * kGsTile, off, piece_of(bits, pc));
+            }
+            fence_proxy_async_shared();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t b0 = smem_u32(smem);
+#pragma unroll
+                for (int kk = 0; kk < kGsSub / 16; ++kk) {
+                    int first = 1;
+#pragma unroll
+                    for (int p = 0; p < kGsPieces; ++p)
+#pragma unroll
+                        for (int q = 0; p + q < kGsPieces; ++q) {
+                            const uint32_t acc_on = (sp > 0 || kk > 0 || !first) ? 1u : 0u;
+                            first = 0;
+                            tc_mma(tmem, smem_desc(b0 + p * kGsTile + kk * 256, 128, 1024),
+                                   smem_desc(b0 + q * kGsTile + kk * 256, 128, 1024), idesc, acc_on);
+                        }
+                }
+                tc_commit(&mma_bar);
+            }
+            pending = true;
+        }
+        if (!ok) break;
+        ok = mma_wait(&mma_bar, phase, st);
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc_fence_after();
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16) {
+            const int col0 = half * 64 + c16 * 16;
+            if (col0 < N) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, v);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) acc[c16 * 16 + t] += rxr_f2d_exact(v[t]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (pending) {
+        mma_wait(&mma_bar, phase, st);
+        tc_fence_after();
+    }
+    if (ok && my_row < n) {
+        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+#pragma unroll
+        for (int t = 0; t < 64; ++t) {
+            const int c = half * 64 + t;
+            if (c < n && my_row <= c) out[my_row + (int64_t)c * n] = acc[t];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+__global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, int, double *, int64_t, RxrStatus *);
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+size_t split_workspace_bytes(int64_t, int64_t, int64_t, int) { return 0; }  // partials reuse the FP64 buffers
+
+cudaError_t set_split_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGsSmem);
+    return e;
+}
+
+int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st)
+{
+    const int64_t gy = cdiv64(p.s, kSpM) * cdiv64(p.n, kSpN);
+    const int64_t win_total = cdiv64(p.m, kSpWin);
+    int64_t gx = std::max<int64_t>(1, p.sms / gy);
+    gx = std::min(gx, win_total);
+    const int64_t wpc = cdiv64(win_total, gx);
+    gx = cdiv64(win_total, wpc);
+    if (gx > p.sk_gx) return RXR_ERR_NOMEM;  // partial buffer sized by the FP64 plan
+    k_sketch_split<<<dim3((unsigned)gx, (unsigned)gy), 256, kSpSmem, st>>>(A, lda, p.m, (int)p.n, (int)p.s, seed,
+                                                                         win_total, wpc, p.Ypart, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    const int64_t sn = p.s * p.n;
+    k_reduce_parts<<<(int)cdiv64(sn, 256), 256, 0, st>>>(p.Ypart, (int)gx, sn, (int)p.s, (int)p.n,
+                                                         1.0 / sqrt((double)p.s), 0, p.Y, p.s, p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
+{
+    if (p.n > kGsM) return RXR_ERR_UNSUPPORTED;
+    const int64_t win_total = cdiv64(p.m, kGsWin);
+    int64_t gx = std::min<int64_t>(p.sms, win_total);
+    const int64_t wpc = cdiv64(win_total, gx);
+    gx = cdiv64(win_total, wpc);
+    if (gx > p.sg_gx) return RXR_ERR_NOMEM;
+    k_gram_split<<<(unsigned)gx, 256, kGsSmem, st>>>(X, ldx, p.m, (int)p.n, win_total, wpc, p.Gpart, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    const int64_t nn = p.n * p.n;
+    k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(p.Gpart, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G, p.n,
+                                                         p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
 
 }  // namespace rxr

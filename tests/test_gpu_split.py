@@ -1,0 +1,82 @@
+"""Parity of the split-precision (tcgen05 tensor-core) contractions with the
+CPU oracle.
+
+The split sketch computes Y' = Omega' A with Omega' the same Philox draws on
+the 2^-12 grid (the oracle's sketch_quantised); its digit decomposition of A
+is exact up to 2^-55 of each column's largest entry per 512-row window, and its
+tensor-memory sums are exact integers, so it must meet the FP64 sketch bound
+plus that truncation term.  The split Gram keeps three 8-bit significand chunks
+per entry and accumulates in FP32 per 512-row window: its bound is
+2^-19 (|X|^T |X|) entrywise.  End to end, the split path must reach the same
+accuracy targets as the FP64 path for every kappa."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+from gpu_util import U, to_dev, to_host
+from paper_2111_11148_gb300.inputs import usv_matrix
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2111_11148_gb300 import rxr  # noqa: E402
+
+OV = {"lu": o.VARIANT_LU, "qr": o.VARIANT_QR}
+
+
+@pytest.fixture(scope="module")
+def h():
+    with rxr.Handle(0) as hh:
+        yield hh
+
+
+@pytest.mark.parametrize("m,n,s,kappa", [(1, 1, 1, 1.0), (700, 5, 13, 1e3), (1500, 64, 128, 1e12),
+                                         (2049, 70, 140, 1e6), (1100, 128, 256, 1e15), (513, 16, 33, 1e8)])
+def test_split_sketch_parity(h, m, n, s, kappa):
+    A = usv_matrix(m, n, kappa, seed=m + 3)
+    Y = to_host(h.sketch(to_dev(A), s, seed=5, prec="split"))
+    ref = o.sketch_quantised(A, s, seed=5)
+    Oq = o.omega_quantised(5, s, m)
+    colmax = np.abs(A).max(axis=0)
+    bound = 8 * (math.log2(m) + 4) * U * (np.abs(Oq) @ np.abs(A)) + \
+        2.0**-54 * np.abs(Oq).sum(axis=1)[:, None] * colmax[None, :]
+    assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / bound)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (600, 8), (5000, 64), (3000, 100), (2100, 128), (511, 17)])
+def test_split_gram_parity(h, m, n):
+    A = usv_matrix(m, n, 1e3, seed=n)
+    R = o.rxr_cholqr(A, o.VARIANT_QR, 2 * n, seed=1, passes=1).Rs
+    X, G = h.precond_gram(to_dev(A), to_dev(R), prec="split")
+    Xg, Gg = to_host(X), to_host(G)
+    Go = o.gram(Xg)
+    bound = 2.0**-19 * (np.abs(Xg).T @ np.abs(Xg))
+    assert np.all(np.abs(Gg - Go) <= bound), np.max(np.abs(Gg - Go) / bound)
+    assert np.array_equal(Gg, Gg.T)
+
+
+@pytest.mark.parametrize("variant", ["qr", "lu"])
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e12, 1e15])
+def test_split_cholqr_accuracy(h, variant, kappa):
+    m, n = 6000, 32
+    A = usv_matrix(m, n, kappa, seed=2)
+    Q, R, code = h.cholqr(to_dev(A), variant=variant, s=64, seed=0, passes=2, prec="split")
+    assert code == 0
+    Qg, Rg = to_host(Q), to_host(R)
+    assert o.orth_error(Qg) <= 1e-13
+    assert o.resid_error(A, Qg, Rg) <= 1e-14
+    ref = o.rxr_cholqr(A, OV[variant], 64, seed=0, passes=2)
+    assert np.linalg.norm(Rg - ref.R) / np.linalg.norm(ref.R) <= max(100 * kappa * U, 1e-13)
+
+
+def test_split_matches_fp64_factorisation(h):
+    A = to_dev(usv_matrix(20000, 64, 1e10, seed=4))
+    Qs, Rs, _ = h.cholqr(A, variant="qr", seed=0, prec="split")
+    Qf, Rf, _ = h.cholqr(A, variant="qr", seed=0, prec="fp64")
+    rel = (torch.linalg.norm(Rs - Rf) / torch.linalg.norm(Rf)).item()
+    assert rel <= 100 * 1e10 * U
+    assert h.orth_error(Qs) <= 1e-13
