@@ -275,14 +275,14 @@ def _emit(args, rank, world, ms, value, peak_fp64, achieved, kmed, orth, resid, 
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f64+bf16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA, "seed": SEED, "passes": PASSES,
                        "variant": args.variant, "prec": args.prec,
-                       "l2": "A (2.1 GB) larger than L2 (129 MB); no flush needed",
+                       "l2": f"A ({8 * M * N / 1e9:.1f} GB) larger than L2 (129 MB); no flush needed",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "kernel": "k_subst_gram (fused precondition + Gram launch)",
                          "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
-                         "traffic": TRAFFIC_PG if (M == 2**22 and args.prec == "fp64") else None,
+                         "traffic": TRAFFIC_PG if (M == 2**22 and N == 64 and args.prec == "fp64") else None,
                          "hbm_frac": (16.0 * M * N / (kmed[1] * 1e-3) / 1e9) / HBM_GBS,
                          "peak_kind": "FP64 DFMA pipe, measured by the rxr_fp64_peak calibration kernel in this run"},
             "kernels_ms": {"sketch": kmed[0], "precond_gram": kmed[1], "pass_gram": kmed[2], "apply": kmed[3]},
@@ -308,11 +308,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
+    ap.add_argument("--n", type=int, default=None, help="columns (s = 2n)")
+    ap.add_argument("--kappa", type=float, default=None, help="condition number of A")
     args = ap.parse_args()
+    global M, N, S, KAPPA, WORKLOAD
     if args.m:
-        global M, WORKLOAD
         M = int(args.m)
-        WORKLOAD = WORKLOAD.replace("m=2^22", f"m={M}")
+    if args.n:
+        N, S = int(args.n), 2 * int(args.n)
+    if args.kappa:
+        KAPPA = float(args.kappa)
+    WORKLOAD = (f"{'rQR' if args.variant == 'qr' else 'rLU'}-CholeskyQR2 m={'2^22' if M == 2**22 else M} n={N} "
+                f"s={S} kappa={KAPPA:g} {'FP64' if args.prec == 'fp64' else 'split BF16 sketch+Gram1, FP64 rest'}")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -19,11 +19,15 @@
 // k_gram_split: G = X^T X (the first CholeskyQR pass's Gram, Algorithm 1 step 1)
 //   with each entry of X cut into three BF16 pieces (the top three 8-bit chunks
 //   of its significand) and the six piece products of combined weight >= 2^-16
-//   accumulated in FP32 in tensor memory, drained to FP64 every 512 rows.
-//   Relative accuracy ~2^-22: enough because X = A R_s^{-1} is well conditioned
+//   accumulated in FP32 in tensor memory, drained to FP64 every 64 rows (the
+//   tensor core's FP32 accumulation truncates, so its error grows with the
+//   number of accumulations: 24 per drain, <= 24 * 2^-23 of the partial sums).
+//   Relative accuracy ~2^-19: enough because X = A R_s^{-1} is well conditioned
 //   (Theorem 3.4) and the error of G only perturbs R_1, which the second, FP64
 //   CholeskyQR pass corrects (Algorithm 2).
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "rxr_internal.cuh"
 
@@ -178,16 +182,25 @@ __global__ void __launch_bounds__(256, 1)
     for (int64_t w = w_begin; w < w_end && ok; ++w) {
         const int64_t wr0 = w * kSpWin;
         // 1. largest exponent of each column in the window (integer pipes)
-        if (tid < kSpN) colexp[tid] = 0;
-        __syncthreads();
-        for (int e = tid; e < kSpWin * nw; e += blockDim.x) {
-            const int row = e & (kSpWin - 1), col = e >> 9;
-            const int64_t gr = wr0 + row;
+        // one warp per column, 16 loads in flight per lane
+        for (int col = warp; col < kSpN; col += 8) {
             unsigned ex = 0;
-            if (gr < m) ex = ((unsigned)__double2hiint(A[gr + (int64_t)(c0 + col) * lda]) >> 20) & 0x7FFu;
-            if (ex == 0x7FFu) bad_flag = 1;
+            if (col < nw) {
+                const double *colp = A + (int64_t)(c0 + col) * lda + wr0;
+                unsigned hv[kSpWin / 32];
+#pragma unroll
+                for (int t = 0; t < kSpWin / 32; ++t) {
+                    const int64_t gr = wr0 + lane + 32 * t;
+                    hv[t] = (gr < m) ? (unsigned)__double2hiint(colp[lane + 32 * t]) : 0u;
+                }
+#pragma unroll
+                for (int t = 0; t < kSpWin / 32; ++t) ex = max(ex, (hv[t] >> 20) & 0x7FFu);
+            }
             ex = __reduce_max_sync(0xFFFFFFFFu, ex);
-            if (lane == 0) atomicMax(&colexp[col], (int)ex);
+            if (lane == 0) {
+                colexp[col] = (int)ex;
+                if (ex == 0x7FFu) bad_flag = 1;
+            }
         }
         __syncthreads();
         // 2. eight operand tiles of 64 rows
@@ -199,14 +212,24 @@ __global__ void __launch_bounds__(256, 1)
                 phase ^= 1u;
                 pending = false;
             }
-            // digits of A: element (row k, column j) -> B tile (j, k)
-            for (int e = tid; e < kSpSub * kSpN; e += blockDim.x) {
+            // digits of A: element (row k, column j) -> B tile (j, k); the
+            // thread's 16 elements are loaded first (all in flight together)
+            unsigned long long vbits[kSpSub * kSpN / 256];
+#pragma unroll
+            for (int t = 0; t < kSpSub * kSpN / 256; ++t) {
+                const int e = tid + 256 * t;
                 const int k = e & (kSpSub - 1), j = e >> 6;
                 const int64_t gr = r0 + k;
+                vbits[t] = (j < nw && gr < m) ? (unsigned long long)__double_as_longlong(A[gr + (int64_t)(c0 + j) * lda])
+                                              : 0ull;
+            }
+#pragma unroll
+            for (int t = 0; t < kSpSub * kSpN / 256; ++t) {
+                const int e = tid + 256 * t;
+                const int k = e & (kSpSub - 1), j = e >> 6;
                 long long T = 0;
-                if (j < nw && gr < m) {
-                    const double v = A[gr + (int64_t)(c0 + j) * lda];
-                    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+                {
+                    const unsigned long long bits = vbits[t];
                     const int ea = (int)((bits >> 52) & 0x7FF);
                     if (ea > 0 && ea < 0x7FF) {
                         // T = a / 2^(e_j + 1) * 2^55, |T| < 2^55 (rounded to an integer)
@@ -331,7 +354,7 @@ __global__ void __launch_bounds__(256, 1)
 // ---------------------------------------------------------------------------
 // Split Gram
 // ---------------------------------------------------------------------------
-constexpr int kGsWin = 512;
+constexpr int kGsWin = 64;   // drain after every tile: the tensor core truncates FP32 sums
 constexpr int kGsSub = 64;
 constexpr int kGsM = 128;               // n <= 128, rows >= n of the tiles are zero
 constexpr int kGsPieces = 3;
@@ -395,14 +418,30 @@ __global__ void __launch_bounds__(256, 1)
                 phase ^= 1u;
                 pending = false;
             }
-            for (int e = tid; e < kGsSub * n; e += blockDim.x) {
-                const int k = e & (kGsSub - 1), j = e >> 6;
-                const int64_t gr = r0 + k;
-                const unsigned long long bits =
-                    (gr < m) ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)j * ldx]) : 0ull;
-                const int off = kmaj_off(j, k);
+            // up to 32 elements per thread (n <= 128), in two batches of 16
+            // loads in flight
 #pragma unroll
-                for (int pc = 0; pc < kGsPieces; ++pc) st_bf16(smem + pc * kGsTile, off, piece_of(bits, pc));
+            for (int hb = 0; hb < 2; ++hb) {
+                unsigned long long vbits[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int e = tid + 256 * (16 * hb + t);
+                    const int k = e & (kGsSub - 1), j = e >> 6;
+                    const int64_t gr = r0 + k;
+                    vbits[t] = (j < n && gr < m) ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)j * ldx])
+                                                 : 0ull;
+                }
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int e = tid + 256 * (16 * hb + t);
+                    const int k = e & (kGsSub - 1), j = e >> 6;
+                    if (j < n) {
+                        const int off = kmaj_off(j, k);
+#pragma unroll
+                        for (int pc = 0; pc < kGsPieces; ++pc)
+                            st_bf16(smem + pc * kGsTile, off, piece_of(vbits[t], pc));
+                    }
+                }
             }
             fence_proxy_async_shared();
             __syncthreads();
@@ -469,7 +508,13 @@ __global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, i
 // ---------------------------------------------------------------------------
 static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-size_t split_workspace_bytes(int64_t, int64_t, int64_t, int) { return 0; }  // partials reuse the FP64 buffers
+// Extra workspace of the split path: the split Gram's per-CTA partial sums
+// (the split sketch reuses the FP64 sketch's partial buffer, which is larger).
+size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
+{
+    const int64_t gx = std::min<int64_t>(sms, cdiv64(m, kGsWin));
+    return (size_t)gx * n * n * sizeof(double);
+}
 
 cudaError_t set_split_smem()
 {
@@ -504,11 +549,12 @@ int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
     int64_t gx = std::min<int64_t>(p.sms, win_total);
     const int64_t wpc = cdiv64(win_total, gx);
     gx = cdiv64(win_total, wpc);
-    if (gx > p.sg_gx) return RXR_ERR_NOMEM;
-    k_gram_split<<<(unsigned)gx, 256, kGsSmem, st>>>(X, ldx, p.m, (int)p.n, win_total, wpc, p.Gpart, p.status);
+    if ((size_t)gx * p.n * p.n * sizeof(double) > split_workspace_bytes(p.m, p.n, p.s, p.sms)) return RXR_ERR_NOMEM;
+    double *parts = reinterpret_cast<double *>(p.split);
+    k_gram_split<<<(unsigned)gx, 256, kGsSmem, st>>>(X, ldx, p.m, (int)p.n, win_total, wpc, parts, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t nn = p.n * p.n;
-    k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(p.Gpart, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G, p.n,
+    k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(parts, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G, p.n,
                                                          p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }

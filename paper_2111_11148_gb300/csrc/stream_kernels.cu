@@ -310,12 +310,30 @@ __global__ void __launch_bounds__(RXR_THREADS)
         // n(n-1)/2 FMAs and n multiplications by 1/R_jj)
         if (!unit_r && threadIdx.x < kSgP) {
             const int t = threadIdx.x;
-            for (int j = 0; j < n; ++j) {
-                const double *rc = rp + j * (j + 1) / 2;
-                double accj = xp[j * kSgP + t];
+            if (n <= 64) {
+                for (int j = 0; j < n; ++j) {
+                    const double *rc = rp + j * (j + 1) / 2;
+                    double accj = xp[j * kSgP + t];
 #pragma unroll 4
-                for (int k = 0; k < j; ++k) accj = fma(-xp[k * kSgP + t], rc[k], accj);
-                xp[j * kSgP + t] = accj * dinv[j];
+                    for (int k = 0; k < j; ++k) accj = fma(-xp[k * kSgP + t], rc[k], accj);
+                    xp[j * kSgP + t] = accj * dinv[j];
+                }
+            } else {
+                // wide rows run one CTA per SM (one warp per scheduler in this
+                // phase): two interleaved chains hide the FMA latency, for one
+                // extra addition per column
+                for (int j = 0; j < n; ++j) {
+                    const double *rc = rp + j * (j + 1) / 2;
+                    double acc0 = xp[j * kSgP + t], acc1 = 0.0;
+                    int k = 0;
+#pragma unroll 4
+                    for (; k + 1 < j; k += 2) {
+                        acc0 = fma(-xp[k * kSgP + t], rc[k], acc0);
+                        acc1 = fma(-xp[(k + 1) * kSgP + t], rc[k + 1], acc1);
+                    }
+                    if (k < j) acc0 = fma(-xp[k * kSgP + t], rc[k], acc0);
+                    xp[j * kSgP + t] = (acc0 + acc1) * dinv[j];
+                }
             }
         }
         __syncthreads();
