@@ -160,6 +160,64 @@ def reference_arm(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def batched_arm(args, rank: int, world: int, local_rank: int):
+    """512 independent problems (m log-uniform in [2^12, 2^18], n in {8..128},
+    kappa log-uniform in [1e2, 1e12], matrix k seed k), one rxr_cholqr_batched per
+    step: every stage is one launch over the whole batch."""
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+    from paper_2111_11148_gb300.inputs import batch_specs, usv_matrix
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    specs = batch_specs(args.count, seed=0)
+    t0 = time.perf_counter()
+    As = [rxr.colmajor(torch.from_numpy(usv_matrix(sp.m, sp.n, sp.kappa, seed=sp.seed)).to(dev)) for sp in specs]
+    gen_s = time.perf_counter() - t0
+    h = rxr.Handle(local_rank)
+    seeds = [sp.seed for sp in specs]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return h.cholqr_batched(As, variant=args.variant, seeds=seeds, passes=PASSES)
+
+    for _ in range(max(3, args.warmup)):
+        Qs, Rs, st = step()
+    assert (st[:, 0] == 0).all(), st[st[:, 0] != 0][:4]
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    bytes_alg = sum(b_alg(sp.m, sp.n, PASSES) for sp in specs)
+    flops_alg = sum(f_alg(sp.m, sp.n, 2 * sp.n, PASSES) for sp in specs)
+    worst_orth = max(h.orth_error(Q) for Q in Qs[:: max(1, len(Qs) // 32)])
+    peak_fp64 = rxr.fp64_peak_tflops()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * bytes_alg / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched rQR-CholeskyQR2, {len(specs)} problems", "count": len(specs),
+                       "total_rows": sum(sp.m for sp in specs), "bytes_A": sum(8 * sp.m * sp.n for sp in specs),
+                       "generation_s": gen_s},
+            "roofline": {"bound": "alu", "kernel": "whole batch", "achieved": flops_alg / (ms * 1e-3) / 1e12,
+                         "peak": peak_fp64, "unit": "TFLOP/s", "frac": flops_alg / (ms * 1e-3) / 1e12 / peak_fp64,
+                         "traffic": None},
+            "qr_per_s": world * len(specs) / (ms * 1e-3), "gflops": world * flops_alg / (ms * 1e-3) / 1e9,
+            "accuracy": {"worst_orth_sampled": worst_orth}, "gpu_launches": 12 * args.steps, "clocks": clk,
+        }), flush=True)
+    h.close()
+
+
 def gpu_arm(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -310,6 +368,8 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (s = 2n)")
     ap.add_argument("--kappa", type=float, default=None, help="condition number of A")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
     args = ap.parse_args()
     global M, N, S, KAPPA, WORKLOAD
     if args.m:
@@ -325,6 +385,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "batched":
+        batched_arm(args, rank, world, local_rank)
         return
     gpu_arm(args, rank, world, local_rank)
 

@@ -1,12 +1,14 @@
 // api.cu -- host side of librxr: argument checking, workspace, TMA descriptors,
 // and the launch sequence of rLU-/rQR-CholeskyQR (Algorithms 4 and 5 with the
 // repeated CholeskyQR pass of Algorithm 2) behind the C ABI of include/rxr.h.
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "rxr_internal.cuh"
 
@@ -21,6 +23,13 @@ cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st,
                               int unit_r, double *dst, int64_t ldd, int do_gram, double *Gpart, int64_t panels_total,
                               int64_t panels_per_cta, int check_finite, RxrStatus *status);
 cudaError_t set_subst_gram_smem(int bytes);
+cudaError_t set_batched_smem(int bytes);
+__global__ void k_sketch_fp64_batched(const SketchJob *, const int *, int);
+__global__ void k_reduce_parts_batched(const ReduceJob *, const int *, int);
+__global__ void k_subst_gram_batched(const SubstJob *, const int *, int, int);
+__global__ void k_xr_factor_batched(const XrJob *);
+__global__ void k_factor_batched(const FactorJob *, int);
+__global__ void k_finish_batched(const FinishJob *);
 cudaError_t set_split_smem();
 // small_kernels.cu
 __global__ void k_xr_factor(const double *, int, int, int64_t, int, double *, double *, int64_t, RxrStatus *);
@@ -58,6 +67,8 @@ struct rxr_ctx {
     size_t dA_bytes = 0, dQ_bytes = 0, dR_bytes = 0;
     double *eval_buf = nullptr;
     size_t eval_bytes = 0;
+    void *h_stage = nullptr;  // pinned host staging of batched job tables
+    size_t h_stage_bytes = 0;
 };
 
 namespace {
@@ -135,7 +146,7 @@ constexpr int kMaxStreamN = 128;  // substitution kernels hold R in shared memor
 
 namespace {
 
-void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms)
+void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int64_t max_chunks = INT64_MAX)
 {
     p.m = m;
     p.n = n;
@@ -146,7 +157,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms)
     p.sk_gy = (int)(s_tiles * n_tiles);
     p.sk_panels = cdiv(m, kSkP);
     int64_t gx = std::max<int64_t>(1, cdiv(2 * (int64_t)sms, p.sk_gy));
-    gx = std::min(gx, p.sk_panels);
+    gx = std::min(std::min(gx, p.sk_panels), std::max<int64_t>(1, max_chunks));
     p.sk_ppc = cdiv(p.sk_panels, gx);
     p.sk_gx = (int)cdiv(p.sk_panels, p.sk_ppc);
 
@@ -154,7 +165,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms)
     p.sg_smem = (size_t)(n4 * kSgP + n * (n + 1) / 2 + n) * sizeof(double);
     const int per_sm = (p.sg_smem <= 110 * 1024) ? 2 : 1;
     p.sg_panels = cdiv(m, kSgP);
-    int64_t g2 = std::min<int64_t>((int64_t)sms * per_sm, p.sg_panels);
+    int64_t g2 = std::min<int64_t>(std::min<int64_t>((int64_t)sms * per_sm, p.sg_panels), std::max<int64_t>(1, max_chunks));
     p.sg_ppc = cdiv(p.sg_panels, g2);
     p.sg_gx = (int)cdiv(p.sg_panels, p.sg_ppc);
     // Gram tile list: off-diagonal tiles, then the diagonal ones from the next
@@ -268,6 +279,7 @@ int set_kernel_attrs()
         cudaFuncSetAttribute(k_orth_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
         cudaFuncSetAttribute(k_resid_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
         set_split_smem(),
+        set_batched_smem(big),
     };
     for (cudaError_t e : es)
         if (e != cudaSuccess) {
@@ -479,6 +491,7 @@ int rxr_destroy(rxr_handle h)
     if (h->dQ) cudaFree(h->dQ);
     if (h->dR) cudaFree(h->dR);
     if (h->eval_buf) cudaFree(h->eval_buf);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
     for (int k = 0; k < 4; ++k)
         for (int j = 0; j < 2; ++j)
             if (h->ev[k][j]) cudaEventDestroy(h->ev[k][j]);
@@ -599,49 +612,148 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     if (count < 0) return -2;
     if (count == 0) return 0;
     if (!A || !m || !n || !lda || !s || !seed || !Q || !ldq || !R || !ldr || !d_status) return -3;
+    if (prec != RXR_FP64) return RXR_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     if (!g.ok) return RXR_ERR_CUDA;
-    size_t need = 0;
+    std::vector<int64_t> sk(count);
+    int64_t total_rows = 0;
     for (int k = 0; k < count; ++k) {
-        const int64_t sk = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
-        if (int e = check_args(A[k], m[k], n[k], lda[k], variant, sk, passes, Q[k], ldq[k], R[k], ldr[k], prec))
+        sk[k] = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
+        if (int e = check_args(A[k], m[k], n[k], lda[k], variant, sk[k], passes, Q[k], ldq[k], R[k], ldr[k], prec))
             return e;
-        Plan p;
-        make_plan(p, m[k], n[k], sk, prec, h->sms);
-        need = std::max(need, p.bytes);
+        total_rows += m[k];
     }
-    if (int e = ensure_ws(h, need)) return e;
+    // row chunks in proportion to each problem's rows, about eight CTAs per SM
+    // per streaming stage over the whole batch
+    const int64_t target_rows = std::max<int64_t>(kSgP, total_rows / (8 * (int64_t)h->sms));
+    std::vector<Plan> plans(count);
+    std::vector<size_t> base(count);
+    size_t off = align256((size_t)count * sizeof(RxrStatus));
+    for (int k = 0; k < count; ++k) {
+        make_plan(plans[k], m[k], n[k], sk[k], prec, h->sms, cdiv(m[k], target_rows));
+        base[k] = off;
+        off += align256(plans[k].bytes);
+    }
+    // job tables
+    const size_t o_skj = off;
+    off += align256(count * sizeof(SketchJob));
+    const size_t o_ryj = off;
+    off += align256(count * sizeof(ReduceJob));
+    const size_t o_xrj = off;
+    off += align256(count * sizeof(XrJob));
+    const size_t o_prej = off;
+    off += align256(count * sizeof(SubstJob));
+    const size_t o_passj = off;
+    off += align256(count * sizeof(SubstJob));
+    const size_t o_rgj = off;
+    off += align256(count * sizeof(ReduceJob));
+    const size_t o_fj = off;
+    off += align256(count * sizeof(FactorJob));
+    const size_t o_finj = off;
+    off += align256(count * sizeof(FinishJob));
+    const size_t o_starts = off;
+    off += align256(4 * (size_t)(count + 1) * sizeof(int));
+    const size_t tables_bytes = off - o_skj;
+    if (int e = ensure_ws(h, off)) return e;
+    char *ws = (char *)h->ws;
+    if (h->h_stage_bytes < tables_bytes) {
+        if (h->h_stage) cudaFreeHost(h->h_stage);
+        h->h_stage = nullptr;
+        h->h_stage_bytes = 0;
+        if (cudaMallocHost(&h->h_stage, tables_bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return RXR_ERR_NOMEM;
+        }
+        h->h_stage_bytes = tables_bytes;
+    }
+    char *hs = (char *)h->h_stage;
+    auto host_at = [&](size_t o) { return hs + (o - o_skj); };
+    SketchJob *skj = (SketchJob *)host_at(o_skj);
+    ReduceJob *ryj = (ReduceJob *)host_at(o_ryj);
+    XrJob *xrj = (XrJob *)host_at(o_xrj);
+    SubstJob *prej = (SubstJob *)host_at(o_prej);
+    SubstJob *passj = (SubstJob *)host_at(o_passj);
+    ReduceJob *rgj = (ReduceJob *)host_at(o_rgj);
+    FactorJob *fj = (FactorJob *)host_at(o_fj);
+    FinishJob *finj = (FinishJob *)host_at(o_finj);
+    int *st_sk = (int *)host_at(o_starts);
+    int *st_ry = st_sk + (count + 1);
+    int *st_sg = st_ry + (count + 1);
+    int *st_rg = st_sg + (count + 1);
+    RxrStatus *statuses = (RxrStatus *)ws;
+    size_t sg_smem = 0;
+    st_sk[0] = st_ry[0] = st_sg[0] = st_rg[0] = 0;
+    for (int k = 0; k < count; ++k) {
+        Plan &p = plans[k];
+        bind_plan(p, ws + base[k]);
+        p.status = statuses + k;
+        const int nn = (int)n[k];
+        skj[k] = SketchJob{A[k], lda[k], m[k], nn, (int)sk[k], seed[k], p.sk_panels, p.sk_ppc,
+                           (int)std::min<int64_t>(n[k], kSkNTile), p.sk_gx, p.Ypart, p.status};
+        ryj[k] = ReduceJob{p.Ypart, p.sk_gx, sk[k] * n[k], (int)sk[k], nn, 1.0 / sqrt((double)sk[k]), 0, p.Y, sk[k],
+                           p.status};
+        xrj[k] = XrJob{p.Y, (int)sk[k], nn, sk[k], variant, p.W, p.Rs, p.Racc, p.status};
+        prej[k] = SubstJob{A[k], lda[k], m[k], nn, p.Rs, n[k], variant == RXR_NONE ? 1 : 0, Q[k], ldq[k], 1, p.Gpart,
+                           p.sg_panels, p.sg_ppc, variant == RXR_NONE ? 1 : 0, p.status};
+        passj[k] = SubstJob{Q[k], ldq[k], m[k], nn, p.Rp, n[k], 0, Q[k], ldq[k], 1, p.Gpart, p.sg_panels, p.sg_ppc, 0,
+                            p.status};
+        rgj[k] = ReduceJob{p.Gpart, p.sg_gx, n[k] * n[k], nn, nn, 1.0, 1, p.G, n[k], p.status};
+        fj[k] = FactorJob{p.G, nn, p.Rp, p.Racc, p.C, p.status};
+        finj[k] = FinishJob{p.Racc, nn, R[k], ldr[k], p.status, d_status + 4 * k};
+        st_sk[k + 1] = st_sk[k] + p.sk_gx * p.sk_gy;
+        st_ry[k + 1] = st_ry[k] + (int)cdiv(sk[k] * n[k], 256);
+        st_sg[k + 1] = st_sg[k] + p.sg_gx;
+        st_rg[k + 1] = st_rg[k] + (int)cdiv(n[k] * n[k], 256);
+        sg_smem = std::max(sg_smem, p.sg_smem);
+    }
+    // sg_smem was sized for MAXT <= 3 tiles of n <= 128, which the batched kernel covers
     cudaStream_t st = (cudaStream_t)stream;
-    for (int k = 0; k < count; ++k) {
-        const int64_t sk = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
-        Plan p;
-        make_plan(p, m[k], n[k], sk, prec, h->sms);
-        bind_plan(p, h->ws);
-        if (int e = enqueue_cholqr(h, p, A[k], lda[k], variant, seed[k], passes, Q[k], ldq[k], R[k], ldr[k], st,
-                                   false))
-            return e;
-        k_status_out<<<1, 32, 0, st>>>(p.status, d_status + 4 * k);
-        if (launch_ok()) return RXR_ERR_CUDA;
+    auto dev = [&](size_t o) { return ws + o; };
+    if (cudaMemcpyAsync(dev(o_skj), hs, tables_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(statuses, 0, (size_t)count * sizeof(RxrStatus), st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
     }
-    // read back all statuses
-    int *hs = (int *)malloc((size_t)count * 4 * sizeof(int));
-    if (!hs) return RXR_ERR_NOMEM;
-    int code = 0;
-    if (cudaMemcpyAsync(hs, d_status, (size_t)count * 4 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    const int *d_st_sk = (const int *)dev(o_starts);
+    const int *d_st_ry = d_st_sk + (count + 1);
+    const int *d_st_sg = d_st_ry + (count + 1);
+    const int *d_st_rg = d_st_sg + (count + 1);
+    const size_t sk_smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
+    if (variant != RXR_NONE) {
+        k_sketch_fp64_batched<<<st_sk[count], RXR_THREADS, sk_smem, st>>>((const SketchJob *)dev(o_skj), d_st_sk,
+                                                                         count);
+        k_reduce_parts_batched<<<st_ry[count], 256, 0, st>>>((const ReduceJob *)dev(o_ryj), d_st_ry, count);
+    }
+    k_xr_factor_batched<<<count, 512, 0, st>>>((const XrJob *)dev(o_xrj));
+    k_subst_gram_batched<<<st_sg[count], RXR_THREADS, sg_smem, st>>>((const SubstJob *)dev(o_prej), d_st_sg, count,
+                                                                     -1);
+    k_reduce_parts_batched<<<st_rg[count], 256, 0, st>>>((const ReduceJob *)dev(o_rgj), d_st_rg, count);
+    for (int pass = 1; pass <= passes; ++pass) {
+        const bool last = (pass == passes);
+        k_factor_batched<<<count, 512, 0, st>>>((const FactorJob *)dev(o_fj), pass);
+        k_subst_gram_batched<<<st_sg[count], RXR_THREADS, sg_smem, st>>>((const SubstJob *)dev(o_passj), d_st_sg,
+                                                                         count, last ? 0 : 1);
+        if (!last)
+            k_reduce_parts_batched<<<st_rg[count], 256, 0, st>>>((const ReduceJob *)dev(o_rgj), d_st_rg, count);
+    }
+    k_finish_batched<<<count, 256, 0, st>>>((const FinishJob *)dev(o_finj));
+    if (launch_ok()) return RXR_ERR_CUDA;
+    std::vector<int> hs_status((size_t)count * 4);
+    if (cudaMemcpyAsync(hs_status.data(), d_status, (size_t)count * 4 * sizeof(int), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         (void)cudaGetLastError();
-        code = RXR_ERR_CUDA;
-    } else {
-        for (int k = 0; k < count && code == 0; ++k)
-            if (hs[4 * k]) {
-                code = hs[4 * k];
-                if (code == RXR_ERR_CHOL_BREAKDOWN) {
-                    h->last_pass = hs[4 * k + 1];
-                    h->last_col = hs[4 * k + 2];
-                }
-            }
+        return RXR_ERR_CUDA;
     }
-    free(hs);
+    int code = 0;
+    for (int k = 0; k < count && code == 0; ++k)
+        if (hs_status[4 * k]) {
+            code = hs_status[4 * k];
+            if (code == RXR_ERR_CHOL_BREAKDOWN) {
+                h->last_pass = hs_status[4 * k + 1];
+                h->last_col = hs_status[4 * k + 2];
+            }
+        }
     return code;
 }
 

@@ -244,6 +244,66 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 namespace rxr {
+// Per-problem arguments of the batched launches (one entry per problem).
+struct SketchJob {
+    const double *A;
+    int64_t lda, m;
+    int n, s;
+    uint64_t seed;
+    int64_t panels_total, panels_per_cta;
+    int box_cols, gx;
+    double *Ypart;
+    RxrStatus *st;
+};
+struct ReduceJob {
+    const double *parts;
+    int nparts;
+    int64_t stride;
+    int rows, cols;
+    double scale;
+    int symmetric;
+    double *out;
+    int64_t ldo;
+    RxrStatus *st;
+};
+struct SubstJob {
+    const double *src;
+    int64_t lds, m;
+    int n;
+    const double *R;
+    int64_t ldr;
+    int unit_r;
+    double *dst;
+    int64_t ldd;
+    int do_gram;
+    double *Gpart;
+    int64_t panels_total, panels_per_cta;
+    int check_finite;
+    RxrStatus *st;
+};
+struct XrJob {
+    const double *Y;
+    int s, n;
+    int64_t ldy;
+    int variant;
+    double *W, *Rs, *Racc;
+    RxrStatus *st;
+};
+struct FactorJob {
+    const double *G;
+    int n;
+    double *Rp, *Racc, *C;
+    RxrStatus *st;
+};
+struct FinishJob {
+    const double *Racc;
+    int n;
+    double *R;
+    int64_t ldr;
+    const RxrStatus *st;
+    int *status_out;
+};
+
 // Launch geometry and workspace offsets of one factorisation.
 struct Plan {
     int64_t m, n, s;

@@ -39,9 +39,8 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 // ---------------------------------------------------------------------------
 // Step 2.  W (workspace, ld s) receives a copy of Y and is factorised in place.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSmallThreads)
-    k_xr_factor(const double *__restrict__ Y, int s, int n, int64_t ldy, int variant, double *__restrict__ W,
-                double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
+__device__ __forceinline__ void xr_body(const double *__restrict__ Y, int s, int n, int64_t ldy, int variant,
+                                        double *__restrict__ W, double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
     __shared__ double red[33];
@@ -176,14 +175,21 @@ __global__ void __launch_bounds__(kSmallThreads)
     if (tid == 0 && sh_bad) rxr_fail(st, RXR_ERR_SKETCH_SINGULAR, 0, -1);
 }
 
+__global__ void __launch_bounds__(kSmallThreads)
+    k_xr_factor(const double *__restrict__ Y, int s, int n, int64_t ldy, int variant, double *__restrict__ W,
+                double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
+{
+    xr_body(Y, s, n, ldy, variant, W, Rs, ldrs, st);
+}
+
 // ---------------------------------------------------------------------------
 // R_p = chol(G) (upper, from G's upper triangle), then R_acc <- R_p R_acc.
 // C is n x n workspace.  Right-looking: for column j, R_jj = sqrt(C_jj),
 // R_jl = C_jl / R_jj, then C_kl -= R_jk R_jl for j < k <= l.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSmallThreads)
-    k_factor(const double *__restrict__ G, int n, int64_t ldg, double *__restrict__ Rp, double *__restrict__ Racc,
-             double *__restrict__ C, int pass, int update_racc, RxrStatus *st)
+__device__ __forceinline__ void factor_body(const double *__restrict__ G, int n, int64_t ldg, double *__restrict__ Rp,
+                                            double *__restrict__ Racc, double *__restrict__ C, int pass,
+                                            int update_racc, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
     __shared__ int sh_bad;
@@ -234,6 +240,57 @@ __global__ void __launch_bounds__(kSmallThreads)
     }
     __syncthreads();
     for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) Racc[e] = C[e];
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+    k_factor(const double *__restrict__ G, int n, int64_t ldg, double *__restrict__ Rp, double *__restrict__ Racc,
+             double *__restrict__ C, int pass, int update_racc, RxrStatus *st)
+{
+    factor_body(G, n, ldg, Rp, Racc, C, pass, update_racc, st);
+}
+
+// Batched forms of the one-CTA steps: block k serves problem k.  The XR step
+// also seeds R_acc = R_s (R_s = I without preconditioner).
+__global__ void __launch_bounds__(kSmallThreads) k_xr_factor_batched(const XrJob *__restrict__ jobs)
+{
+    const XrJob j = jobs[blockIdx.x];
+    if (j.variant == RXR_NONE) {
+        if (rxr_failed(j.st)) return;
+        for (int64_t e = threadIdx.x; e < (int64_t)j.n * j.n; e += blockDim.x) {
+            const double v = ((e % j.n) == (e / j.n)) ? 1.0 : 0.0;
+            j.Rs[e] = v;
+            j.Racc[e] = v;
+        }
+        return;
+    }
+    xr_body(j.Y, j.s, j.n, j.s, j.variant, j.W, j.Rs, j.n, j.st);
+    __syncthreads();
+    if (rxr_failed(j.st)) return;
+    for (int64_t e = threadIdx.x; e < (int64_t)j.n * j.n; e += blockDim.x) j.Racc[e] = j.Rs[e];
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_factor_batched(const FactorJob *__restrict__ jobs, int pass)
+{
+    const FactorJob j = jobs[blockIdx.x];
+    factor_body(j.G, j.n, j.n, j.Rp, j.Racc, j.C, pass, 1, j.st);
+}
+
+// R to the caller's layout and the status to the caller's array.
+__global__ void k_finish_batched(const FinishJob *__restrict__ jobs)
+{
+    const FinishJob j = jobs[blockIdx.x];
+    const bool failed = rxr_failed(j.st);
+    if (!failed && j.R != nullptr)
+        for (int64_t e = threadIdx.x; e < (int64_t)j.n * j.n; e += blockDim.x) {
+            const int i = (int)(e % j.n), c = (int)(e / j.n);
+            j.R[i + c * j.ldr] = (i <= c) ? j.Racc[e] : 0.0;
+        }
+    if (threadIdx.x == 0) {
+        j.status_out[0] = j.st->code;
+        j.status_out[1] = j.st->pass;
+        j.status_out[2] = j.st->column;
+        j.status_out[3] = 0;
+    }
 }
 
 // R (n x n, ld n) -> out (ld ldo), zeros strictly below the diagonal.

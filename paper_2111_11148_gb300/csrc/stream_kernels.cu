@@ -80,10 +80,10 @@ constexpr int kSkP = 64;      // rows per panel
 constexpr int kSkSTile = 128; // max sketch rows per tile
 constexpr int kSkNTile = 64;  // max columns per tile
 
-__global__ void __launch_bounds__(RXR_THREADS, 2)
-    k_sketch_fp64(const __grid_constant__ CUtensorMap tmapA, int use_tma, const double *__restrict__ A, int64_t lda,
-                  int64_t m, int n, int s, uint64_t seed, int64_t panels_total, int64_t panels_per_cta,
-                  int box_cols, double *__restrict__ Ypart, RxrStatus *st)
+__device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tma, const double *__restrict__ A,
+                                            int64_t lda, int64_t m, int n, int s, uint64_t seed, int64_t panels_total,
+                                            int64_t panels_per_cta, int box_cols, double *__restrict__ Ypart,
+                                            RxrStatus *st, int bx, int by)
 {
     if (rxr_failed(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(RXR_THREADS, 2)
     __shared__ int bad_flag;
 
     const int n_tiles = (n + kSkNTile - 1) / kSkNTile;
-    const int si = blockIdx.y / n_tiles, ni = blockIdx.y % n_tiles;
+    const int si = by / n_tiles, ni = by % n_tiles;
     const int s0 = si * kSkSTile, c0 = ni * kSkNTile;
     const int sw = min(kSkSTile, s - s0), nw = min(kSkNTile, n - c0);
     const int ts = (sw + 7) / 8, tn = (nw + 3) / 4;
@@ -122,11 +122,11 @@ __global__ void __launch_bounds__(RXR_THREADS, 2)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-    const int64_t p_begin = blockIdx.x * panels_per_cta;
+    const int64_t p_begin = bx * panels_per_cta;
     const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
     for (int64_t p = p_begin; p < p_end; ++p) {
         const int64_t r0 = p * kSkP;
-        if (!load_panel(ap, &tmapA, use_tma, &bar, phase, A, lda, m, r0, c0, kSkP, box_cols, n, st)) return;
+        if (!load_panel(ap, tmapA, use_tma, &bar, phase, A, lda, m, r0, c0, kSkP, box_cols, n, st)) return;
         // Omega columns for the panel's rows: zp[row][r - s0]
         for (int c = threadIdx.x; c < kSkP * kcount; c += blockDim.x) {
             const int row = c / kcount, kk = c % kcount;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(RXR_THREADS, 2)
     if (bad_flag) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
 
     // combine the row groups in a fixed order (group 0 first)
-    double *out = Ypart + (int64_t)blockIdx.x * s * n;
+    double *out = Ypart + (int64_t)bx * s * n;
     if (ngroups == 1) {
 #pragma unroll
         for (int a = 0; a < 8; ++a)
@@ -196,17 +196,27 @@ __global__ void __launch_bounds__(RXR_THREADS, 2)
     }
 }
 
+__global__ void __launch_bounds__(RXR_THREADS, 2)
+    k_sketch_fp64(const __grid_constant__ CUtensorMap tmapA, int use_tma, const double *__restrict__ A, int64_t lda,
+                  int64_t m, int n, int s, uint64_t seed, int64_t panels_total, int64_t panels_per_cta,
+                  int box_cols, double *__restrict__ Ypart, RxrStatus *st)
+{
+    sketch_body(&tmapA, use_tma, A, lda, m, n, s, seed, panels_total, panels_per_cta, box_cols, Ypart, st,
+                blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // out[r + c*ldo] = scale * sum_{x < nparts} parts[x*stride + r + c*rows], in
 // the order x = 0, 1, ...  (deterministic).  With `symmetric`, only entries
 // r <= c are summed and mirrored (Gram matrices).
 // ---------------------------------------------------------------------------
-__global__ void k_reduce_parts(const double *__restrict__ parts, int nparts, int64_t stride, int rows, int cols,
-                               double scale, int symmetric, double *__restrict__ out, int64_t ldo, RxrStatus *st)
+__device__ __forceinline__ void reduce_body(const double *__restrict__ parts, int nparts, int64_t stride, int rows,
+                                            int cols, double scale, int symmetric, double *__restrict__ out,
+                                            int64_t ldo, RxrStatus *st, int bx, int nbx)
 {
     if (rxr_failed(st)) return;
     const int64_t total = (int64_t)rows * cols;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)nbx * blockDim.x) {
         const int r = (int)(e % rows), c = (int)(e / rows);
         if (symmetric && r > c) continue;
         double v = 0.0;
@@ -215,6 +225,12 @@ __global__ void k_reduce_parts(const double *__restrict__ parts, int nparts, int
         out[r + c * ldo] = v;
         if (symmetric && r != c) out[c + r * ldo] = v;
     }
+}
+
+__global__ void k_reduce_parts(const double *__restrict__ parts, int nparts, int64_t stride, int rows, int cols,
+                               double scale, int symmetric, double *__restrict__ out, int64_t ldo, RxrStatus *st)
+{
+    reduce_body(parts, nparts, stride, rows, cols, scale, symmetric, out, ldo, st, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,11 +246,11 @@ __global__ void k_reduce_parts(const double *__restrict__ parts, int nparts, int
 constexpr int kSgP = 128;
 
 template <int MAXT>
-__global__ void __launch_bounds__(RXR_THREADS)
-    k_subst_gram(const __grid_constant__ CUtensorMap tmapB, int use_tma, const double *__restrict__ src, int64_t lds,
-                 int64_t m, int n, const double *__restrict__ R, int64_t ldr, int unit_r, double *dst, int64_t ldd,
-                 int do_gram, double *__restrict__ Gpart, int64_t panels_total, int64_t panels_per_cta,
-                 int check_finite, RxrStatus *st)
+__device__ __forceinline__ void subst_gram_body(const CUtensorMap *tmapB, int use_tma, const double *__restrict__ src,
+                                                int64_t lds, int64_t m, int n, const double *__restrict__ R,
+                                                int64_t ldr, int unit_r, double *dst, int64_t ldd, int do_gram,
+                                                double *__restrict__ Gpart, int64_t panels_total,
+                                                int64_t panels_per_cta, int check_finite, RxrStatus *st, int bx)
 {
     if (rxr_failed(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -295,11 +311,11 @@ __global__ void __launch_bounds__(RXR_THREADS)
         for (int k = 0; k < 16; ++k) acc[q][k] = 0.0;
     }
 
-    const int64_t p_begin = blockIdx.x * panels_per_cta;
+    const int64_t p_begin = bx * panels_per_cta;
     const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
     for (int64_t p = p_begin; p < p_end; ++p) {
         const int64_t r0 = p * kSgP;
-        if (!load_panel(xp, &tmapB, use_tma, &bar, phase, src, lds, m, r0, 0, kSgP, n, n, st)) return;
+        if (!load_panel(xp, tmapB, use_tma, &bar, phase, src, lds, m, r0, 0, kSgP, n, n, st)) return;
         if (check_finite) {
             bool bad = false;
             for (int e = threadIdx.x; e < kSgP * n; e += blockDim.x) bad |= rxr_nonfinite(xp[e]);
@@ -390,7 +406,7 @@ __global__ void __launch_bounds__(RXR_THREADS)
     }
     if (bad_flag) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
     if (do_gram) {
-        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+        double *out = Gpart + (int64_t)bx * n * n;
 #pragma unroll
         for (int q = 0; q < MAXT; ++q) {
             const int bj = tbj[q], bl = tbl[q];
@@ -404,6 +420,65 @@ __global__ void __launch_bounds__(RXR_THREADS)
                 }
         }
     }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(RXR_THREADS)
+    k_subst_gram(const __grid_constant__ CUtensorMap tmapB, int use_tma, const double *__restrict__ src, int64_t lds,
+                 int64_t m, int n, const double *__restrict__ R, int64_t ldr, int unit_r, double *dst, int64_t ldd,
+                 int do_gram, double *__restrict__ Gpart, int64_t panels_total, int64_t panels_per_cta,
+                 int check_finite, RxrStatus *st)
+{
+    subst_gram_body<MAXT>(&tmapB, use_tma, src, lds, m, n, R, ldr, unit_r, dst, ldd, do_gram, Gpart, panels_total,
+                          panels_per_cta, check_finite, st, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch serves every problem of a batch.  Block b belongs
+// to the problem k with start[k] <= b < start[k+1] (binary search over the
+// per-stage block offsets); the problem's own block index is b - start[k].
+// Panels are staged with plain coalesced loads (no per-problem tensor maps).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_job(const int *__restrict__ start, int count, int b)
+{
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(RXR_THREADS, 2)
+    k_sketch_fp64_batched(const SketchJob *__restrict__ jobs, const int *__restrict__ start, int count)
+{
+    const int k = find_job(start, count, blockIdx.x);
+    const SketchJob j = jobs[k];
+    const int local = blockIdx.x - start[k];
+    sketch_body(nullptr, 0, j.A, j.lda, j.m, j.n, j.s, j.seed, j.panels_total, j.panels_per_cta, j.box_cols,
+                j.Ypart, j.st, local % j.gx, local / j.gx);
+}
+
+__global__ void k_reduce_parts_batched(const ReduceJob *__restrict__ jobs, const int *__restrict__ start, int count)
+{
+    const int k = find_job(start, count, blockIdx.x);
+    const ReduceJob j = jobs[k];
+    reduce_body(j.parts, j.nparts, j.stride, j.rows, j.cols, j.scale, j.symmetric, j.out, j.ldo, j.st,
+                blockIdx.x - start[k], start[k + 1] - start[k]);
+}
+
+// do_gram < 0 keeps each job's own flag; 0 or 1 overrides it for all jobs
+__global__ void __launch_bounds__(RXR_THREADS)
+    k_subst_gram_batched(const SubstJob *__restrict__ jobs, const int *__restrict__ start, int count, int do_gram)
+{
+    const int k = find_job(start, count, blockIdx.x);
+    const SubstJob j = jobs[k];
+    subst_gram_body<3>(nullptr, 0, j.src, j.lds, j.m, j.n, j.R, j.ldr, j.unit_r, j.dst, j.ldd,
+                       do_gram < 0 ? j.do_gram : do_gram, j.Gpart, j.panels_total, j.panels_per_cta, j.check_finite,
+                       j.st, blockIdx.x - start[k]);
 }
 
 // Host-side dispatch over the tile count (template kernels stay in this unit).
@@ -430,6 +505,13 @@ cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st,
         break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t set_batched_smem(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_fp64_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_subst_gram_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 cudaError_t set_subst_gram_smem(int bytes)

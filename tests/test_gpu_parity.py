@@ -318,13 +318,46 @@ def test_host_entry_point_matches_device(h):
 
 
 def test_batched_matches_single_calls(h):
-    shapes = [(5000, 8, 1e3), (700, 16, 1e9), (4096, 32, 1e12), (129, 64, 1e5), (3000, 128, 1e2)]
-    As = [to_dev(usv_matrix(m, n, k, seed=i)) for i, (m, n, k) in enumerate(shapes)]
+    # one launch per stage for the whole batch; row chunks differ from the
+    # single-call plan, so results agree to rounding (R-factor bound), not bitwise
+    shapes = [(5000, 8, 1e3), (700, 16, 1e9), (4096, 32, 1e12), (129, 64, 1e5), (3000, 128, 1e2), (1, 1, 1.0),
+              (40, 40, 1e4), (20000, 24, 1e15)]
+    As_np = [usv_matrix(m, n, k, seed=i) for i, (m, n, k) in enumerate(shapes)]
+    As = [to_dev(a) for a in As_np]
     Qs, Rs, st = h.cholqr_batched(As, variant="qr", seeds=list(range(len(As))))
     assert np.all(st == 0)
-    for i, A in enumerate(As):
+    for i, (A, (m, n, kappa)) in enumerate(zip(As, shapes)):
         Q, R, _ = h.cholqr(A, variant="qr", seed=i)
-        assert torch.equal(Qs[i], Q) and torch.equal(Rs[i], R)
+        Qb, Rb = to_host(Qs[i]), to_host(Rs[i])
+        assert o.orth_error(Qb) <= 1e-13
+        assert o.resid_error(As_np[i], Qb, Rb) <= 1e-14
+        rel = np.linalg.norm(Rb - to_host(R)) / np.linalg.norm(to_host(R))
+        assert rel <= max(100 * kappa * U, 1e-14), (i, rel)
+
+
+@pytest.mark.parametrize("variant", ["lu", "none"])
+def test_batched_mixed_statuses(h, variant):
+    rng = np.random.default_rng(7)
+    shapes = [(int(m), int(n)) for m, n in zip(rng.integers(64, 3000, 24), rng.choice([1, 3, 8, 16, 33, 64, 100], 24))]
+    shapes = [(max(m, n), n) for m, n in shapes]
+    As_np = [usv_matrix(m, n, 1e3, seed=i) for i, (m, n) in enumerate(shapes)]
+    bad = {3: "nan", 11: "zero"}
+    As_np[3] = As_np[3].copy(order="F")
+    As_np[3][0, 0] = np.nan
+    if shapes[11][1] > 1:
+        As_np[11] = As_np[11].copy(order="F")
+        As_np[11][:, -1] = 0.0
+    As = [to_dev(a) for a in As_np]
+    Qs, Rs, st = h.cholqr_batched(As, variant=variant)
+    for i in range(len(As)):
+        if i == 3:
+            assert st[i, 0] == rxr.NONFINITE
+        elif i == 11 and shapes[11][1] > 1:
+            assert st[i, 0] in (rxr.SKETCH_SINGULAR, rxr.CHOL_BREAKDOWN)
+        else:
+            assert st[i, 0] == 0, (i, st[i])
+            Qb, Rb = to_host(Qs[i]), to_host(Rs[i])
+            assert o.orth_error(Qb) <= 1e-13 and o.resid_error(As_np[i], Qb, Rb) <= 1e-14
 
 
 # ------------------------------------------------------------------ evaluators
