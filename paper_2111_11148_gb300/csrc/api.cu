@@ -24,6 +24,10 @@ cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st,
                               int64_t panels_per_cta, int check_finite, RxrStatus *status);
 cudaError_t set_subst_gram_smem(int bytes);
 cudaError_t set_batched_smem(int bytes);
+cudaError_t set_wide_smem();
+__global__ void k_subst_wide(const double *, int64_t, int64_t, int, const double *, int64_t, double *, int64_t, int64_t,
+                             int64_t, RxrStatus *);
+__global__ void k_gram_tiles(const double *, int64_t, int64_t, int, int64_t, int64_t, double *, RxrStatus *);
 __global__ void k_sketch_fp64_batched(const SketchJob *, const int *, int);
 __global__ void k_reduce_parts_batched(const ReduceJob *, const int *, int);
 __global__ void k_subst_gram_batched(const SubstJob *, const int *, int, int);
@@ -37,7 +41,7 @@ __global__ void k_factor(const double *, int, int64_t, double *, double *, doubl
 __global__ void k_copy_upper(const double *, int, double *, int64_t, const RxrStatus *);
 __global__ void k_identity(double *, int);
 __global__ void k_status_out(const RxrStatus *, int *);
-__global__ void k_orth_partial(const double *, int64_t, int, int64_t, int64_t, double *);
+__global__ void k_orth_partial(const double *, int64_t, int, int64_t, int64_t, int, double *);
 __global__ void k_orth_final(const double *, int, int, double *);
 __global__ void k_resid_partial(const double *, int64_t, const double *, int64_t, const double *, int64_t, int64_t,
                                 int, double *);
@@ -139,7 +143,9 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 constexpr int kSkP = 64, kSkSTile = 128, kSkNTile = 64, kSgP = 128;
-constexpr int kMaxStreamN = 128;  // substitution kernels hold R in shared memory
+constexpr int kMaxStreamN = RXR_MAX_N;  // n > 128 uses the column-blocked kernels
+constexpr int kNarrowN = 128;            // up to here R lives in shared memory
+constexpr int kWP = 128, kWB = 64;
 
 }  // namespace
 
@@ -161,17 +167,38 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     p.sk_ppc = cdiv(p.sk_panels, gx);
     p.sk_gx = (int)cdiv(p.sk_panels, p.sk_ppc);
 
+    p.wide = n > kNarrowN;
+    if (p.wide) {
+        // one CTA per SM for the blocked substitution; Gram over 64 x 64 block pairs
+        const int64_t panels = cdiv(m, kWP);
+        p.sg_panels = panels;
+        p.sg_ppc = cdiv(panels, std::min<int64_t>(std::min<int64_t>(sms, panels), std::max<int64_t>(1, max_chunks)));
+        p.sg_gx = (int)cdiv(panels, p.sg_ppc);
+        p.sg_smem = (size_t)(2 * kWB * kWP + kWB * kWB + kWB) * sizeof(double);
+        p.sg_maxt = 3;
+        const int64_t nb = cdiv(n, kWB);
+        p.gt_gy = (int)(nb * (nb + 1) / 2);
+        int64_t cg = std::max<int64_t>(1, cdiv(2 * (int64_t)sms, p.gt_gy));
+        cg = std::min(cg, panels);
+        p.gt_ppc = cdiv(panels, cg);
+        p.gt_gx = (int)cdiv(panels, p.gt_ppc);
+    }
     const int64_t n4 = (n + 3) & ~3;
-    p.sg_smem = (size_t)(n4 * kSgP + n * (n + 1) / 2 + n) * sizeof(double);
-    const int per_sm = (p.sg_smem <= 110 * 1024) ? 2 : 1;
-    p.sg_panels = cdiv(m, kSgP);
-    int64_t g2 = std::min<int64_t>(std::min<int64_t>((int64_t)sms * per_sm, p.sg_panels), std::max<int64_t>(1, max_chunks));
-    p.sg_ppc = cdiv(p.sg_panels, g2);
-    p.sg_gx = (int)cdiv(p.sg_panels, p.sg_ppc);
-    // Gram tile list: off-diagonal tiles, then the diagonal ones from the next
-    // multiple of 32 (see k_subst_gram)
-    const int64_t NT = n4 / 4, n_off = NT * (NT - 1) / 2, d0 = (n_off + 31) & ~(int64_t)31;
-    p.sg_maxt = (int)cdiv(d0 + NT, RXR_THREADS);
+    if (!p.wide) p.sg_smem = (size_t)(n4 * kSgP + n * (n + 1) / 2 + n) * sizeof(double);
+    if (!p.wide) {
+        const int per_sm = (p.sg_smem <= 110 * 1024) ? 2 : 1;
+        p.sg_panels = cdiv(m, kSgP);
+        int64_t g2 = std::min<int64_t>(std::min<int64_t>((int64_t)sms * per_sm, p.sg_panels),
+                                       std::max<int64_t>(1, max_chunks));
+        p.sg_ppc = cdiv(p.sg_panels, g2);
+        p.sg_gx = (int)cdiv(p.sg_panels, p.sg_ppc);
+        // Gram tile list: off-diagonal tiles, then the diagonal ones from the next
+        // multiple of 32 (see k_subst_gram)
+        const int64_t NT = n4 / 4, n_off = NT * (NT - 1) / 2, d0 = (n_off + 31) & ~(int64_t)31;
+        p.sg_maxt = (int)cdiv(d0 + NT, RXR_THREADS);
+        p.gt_gx = p.gt_gy = 0;
+        p.gt_ppc = 0;
+    }
 
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -183,7 +210,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     const size_t o_ypart = take((size_t)p.sk_gx * s * n * 8);
     const size_t o_y = take((size_t)s * n * 8);
     const size_t o_w = take((size_t)s * n * 8);
-    const size_t o_gpart = take((size_t)p.sg_gx * n * n * 8);
+    const size_t o_gpart = take((size_t)std::max(p.sg_gx, p.gt_gx) * n * n * 8);
     const size_t o_g = take((size_t)n * n * 8);
     const size_t o_rs = take((size_t)n * n * 8);
     const size_t o_rp = take((size_t)n * n * 8);
@@ -280,6 +307,7 @@ int set_kernel_attrs()
         cudaFuncSetAttribute(k_resid_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, big),
         set_split_smem(),
         set_batched_smem(big),
+        set_wide_smem(),
     };
     for (cudaError_t e : es)
         if (e != cudaSuccess) {
@@ -301,6 +329,23 @@ int launch_ok()
 int enqueue_subst(const Plan &p, const double *src, int64_t lds, const double *R, int unit_r, double *dst,
                   int64_t ldd, bool gram, bool check_finite, cudaStream_t st)
 {
+    if (p.wide) {
+        // column-blocked substitution writes X, then the tiled Gram reads it back
+        if (unit_r || dst == nullptr) return RXR_ERR_UNSUPPORTED;
+        k_subst_wide<<<p.sg_gx, RXR_THREADS, p.sg_smem, st>>>(src, lds, p.m, (int)p.n, R, p.n, dst, ldd, p.sg_panels,
+                                                              p.sg_ppc, p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+        if (gram) {
+            k_gram_tiles<<<dim3(p.gt_gx, p.gt_gy), RXR_THREADS, 2 * kWB * kWP * sizeof(double), st>>>(
+                dst, ldd, p.m, (int)p.n, p.sg_panels, p.gt_ppc, p.Gpart, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+            const int64_t nn = p.n * p.n;
+            k_reduce_parts<<<(int)cdiv(nn, 256), 256, 0, st>>>(p.Gpart, p.gt_gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G,
+                                                               p.n, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        }
+        return 0;
+    }
     CUtensorMap map;
     const int use_tma = encode_2d(&map, src, p.m, p.n, lds, kSgP, (int)p.n) ? 1 : 0;
     if (launch_subst_gram(p.sg_maxt, dim3(p.sg_gx), p.sg_smem, st, map, use_tma, src, lds, p.m, (int)p.n, R, p.n,
@@ -375,7 +420,8 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     // step 3: X = A R_s^{-1} into Q, fused with G_1 = X^T X
     {
         Timer t(th, 1, st);
-        if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
+        // the split Gram covers n <= 128; wider panels keep the FP64 tiled Gram
+        if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE && !p.wide) {
             if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, false, st)) return e;
             if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
         } else {
@@ -415,6 +461,7 @@ int check_args(const double *A, int64_t m, int64_t n, int64_t lda, int variant, 
     if (R != nullptr && ldr < n) return -12;
     if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -13;
     if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    if (n > kNarrowN && variant == RXR_NONE) return RXR_ERR_UNSUPPORTED;
     if (m > ((int64_t)1 << 31)) return RXR_ERR_UNSUPPORTED;
     (void)Q;
     return 0;
@@ -613,6 +660,8 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     if (count == 0) return 0;
     if (!A || !m || !n || !lda || !s || !seed || !Q || !ldq || !R || !ldr || !d_status) return -3;
     if (prec != RXR_FP64) return RXR_ERR_UNSUPPORTED;
+    for (int k = 0; k < count; ++k)
+        if (n[k] > kNarrowN) return RXR_ERR_UNSUPPORTED;  // batched form: n <= 128
     DeviceGuard g(h->device);
     if (!g.ok) return RXR_ERR_CUDA;
     std::vector<int64_t> sk(count);
@@ -868,7 +917,7 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
     // R may have any leading dimension: copy it to the packed n x n buffer
     if (cudaMemcpy2DAsync(p.Rp, n * 8, R, ldr * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;
-    if (prec == RXR_SPLIT_BF16) {
+    if (prec == RXR_SPLIT_BF16 && !p.wide) {
         if (X == nullptr) return RXR_ERR_UNSUPPORTED;
         if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, false, false, st)) return e;
         if (int e = split_gram_enqueue(p, X, ldx, st)) return e;
@@ -919,8 +968,9 @@ int rxr_orth_error(rxr_handle h, const double *Q, int64_t m, int64_t n, int64_t 
     const int64_t nch = cdiv(m, rpc);
     if (grow((void **)&h->eval_buf, &h->eval_bytes, ((size_t)nch * npairs * 2 + 8) * 8)) return RXR_ERR_NOMEM;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t smem = (size_t)64 * n * 8;
-    k_orth_partial<<<dim3((unsigned)nch, gy), 256, smem, st>>>(Q, m, (int)n, ldq, rpc, h->eval_buf);
+    const int evp = (n <= 128) ? 64 : 32;  // rows staged per step: evp * n doubles of shared memory
+    const size_t smem = (size_t)evp * n * 8;
+    k_orth_partial<<<dim3((unsigned)nch, gy), 256, smem, st>>>(Q, m, (int)n, ldq, rpc, evp, h->eval_buf);
     if (launch_ok()) return RXR_ERR_CUDA;
     double *res = h->eval_buf + (size_t)nch * npairs * 2;
     k_orth_final<<<1, 1024, 0, st>>>(h->eval_buf, (int)nch, (int)n, res);
@@ -949,7 +999,7 @@ int rxr_resid_error(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t
     const int blocks = (int)std::min<int64_t>(cdiv(m, 256), 4 * h->sms);
     if (grow((void **)&h->eval_buf, &h->eval_bytes, ((size_t)blocks * 2 + 8) * 8)) return RXR_ERR_NOMEM;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t smem = (size_t)(n * (n + 1) / 2) * 8;
+    const size_t smem = (n * (n + 1) / 2 <= 16384) ? (size_t)(n * (n + 1) / 2) * 8 : 0;
     k_resid_partial<<<blocks, 256, smem, st>>>(A, lda, Q, ldq, R, ldr, m, (int)n, h->eval_buf);
     if (launch_ok()) return RXR_ERR_CUDA;
     double *res = h->eval_buf + (size_t)blocks * 2;

@@ -317,6 +317,10 @@ struct Plan {
     int64_t sg_panels, sg_ppc;
     size_t sg_smem;
     int sg_maxt;
+    // wide panels (n > 128): column-blocked substitution + tiled Gram
+    int wide;
+    int gt_gx, gt_gy;
+    int64_t gt_ppc;
     // workspace pieces
     char *base;
     RxrStatus *status;

@@ -343,9 +343,8 @@ __device__ __forceinline__ void dot2_add(Dot2 &d, double x, double y)
 
 // Orthogonality: per (pair, row chunk) partial Dot2 sums of Q^T Q.  grid.x =
 // row chunks, grid.y = pair blocks of blockDim.x pairs (j <= l).
-constexpr int kEvP = 64;
 __global__ void __launch_bounds__(256)
-    k_orth_partial(const double *__restrict__ Q, int64_t m, int n, int64_t ldq, int64_t rows_per_chunk,
+    k_orth_partial(const double *__restrict__ Q, int64_t m, int n, int64_t ldq, int64_t rows_per_chunk, int kEvP,
                    double *__restrict__ parts)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -417,10 +416,12 @@ __global__ void __launch_bounds__(256)
                     const double *__restrict__ R, int64_t ldr, int64_t m, int n, double *__restrict__ parts)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *rs = reinterpret_cast<double *>(smem_raw);  // packed upper R
+    double *rs = reinterpret_cast<double *>(smem_raw);  // packed upper R (when it fits)
     __shared__ double red[33];
-    for (int j = 0; j < n; ++j)
-        for (int k = threadIdx.x; k <= j; k += blockDim.x) rs[j * (j + 1) / 2 + k] = R[k + (int64_t)j * ldr];
+    const bool r_smem = (int64_t)n * (n + 1) / 2 <= 16384;
+    if (r_smem)
+        for (int j = 0; j < n; ++j)
+            for (int k = threadIdx.x; k <= j; k += blockDim.x) rs[j * (j + 1) / 2 + k] = R[k + (int64_t)j * ldr];
     __syncthreads();
     double num = 0.0, den = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -428,8 +429,12 @@ __global__ void __launch_bounds__(256)
             Dot2 d = {0.0, 0.0};
             const double a = A[i + (int64_t)j * lda];
             dot2_add(d, a, 1.0);
-            const double *rc = rs + j * (j + 1) / 2;
-            for (int k = 0; k <= j; ++k) dot2_add(d, -Q[i + (int64_t)k * ldq], rc[k]);
+            if (r_smem) {
+                const double *rc = rs + j * (j + 1) / 2;
+                for (int k = 0; k <= j; ++k) dot2_add(d, -Q[i + (int64_t)k * ldq], rc[k]);
+            } else {
+                for (int k = 0; k <= j; ++k) dot2_add(d, -Q[i + (int64_t)k * ldq], R[k + (int64_t)j * ldr]);
+            }
             const double e = d.p + d.s;
             num = fma(e, e, num);
             den = fma(a, a, den);

@@ -66,6 +66,23 @@ __device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, 
     return true;
 }
 
+// b - sum_{k<j} x[k * xs] r[k * rstride] with four interleaved FMA chains
+// (combined as ((c0 + c1) + (c2 + c3)), a fixed order).
+__device__ __forceinline__ double chain4_dot(const double *x, int xs, const double *r, int rstride, int j, double b)
+{
+    double c0 = b, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    int k = 0;
+#pragma unroll 2
+    for (; k + 3 < j; k += 4) {
+        c0 = fma(-x[k * xs], r[k * rstride], c0);
+        c1 = fma(-x[(k + 1) * xs], r[(k + 1) * rstride], c1);
+        c2 = fma(-x[(k + 2) * xs], r[(k + 2) * rstride], c2);
+        c3 = fma(-x[(k + 3) * xs], r[(k + 3) * rstride], c3);
+    }
+    for (; k < j; ++k) c0 = fma(-x[k * xs], r[k * rstride], c0);
+    return (c0 + c1) + (c2 + c3);
+}
+
 // ---------------------------------------------------------------------------
 // Sketch Y = Omega A in FP64.  grid.x = row chunks (contiguous runs of P-row
 // panels), grid.y = (s-tile, n-tile) output tiles of at most 128 x 64.  Each
@@ -336,19 +353,11 @@ __device__ __forceinline__ void subst_gram_body(const CUtensorMap *tmapB, int us
                 }
             } else {
                 // wide rows run one CTA per SM (one warp per scheduler in this
-                // phase): two interleaved chains hide the FMA latency, for one
-                // extra addition per column
+                // phase): four interleaved chains hide the FMA latency (ncu:
+                // a single chain stalls on the fixed-latency dependency), for
+                // three extra additions per column
                 for (int j = 0; j < n; ++j) {
-                    const double *rc = rp + j * (j + 1) / 2;
-                    double acc0 = xp[j * kSgP + t], acc1 = 0.0;
-                    int k = 0;
-#pragma unroll 4
-                    for (; k + 1 < j; k += 2) {
-                        acc0 = fma(-xp[k * kSgP + t], rc[k], acc0);
-                        acc1 = fma(-xp[(k + 1) * kSgP + t], rc[k + 1], acc1);
-                    }
-                    if (k < j) acc0 = fma(-xp[k * kSgP + t], rc[k], acc0);
-                    xp[j * kSgP + t] = (acc0 + acc1) * dinv[j];
+                    xp[j * kSgP + t] = chain4_dot(xp + t, kSgP, rp + j * (j + 1) / 2, 1, j, xp[j * kSgP + t]) * dinv[j];
                 }
             }
         }
@@ -479,6 +488,170 @@ __global__ void __launch_bounds__(RXR_THREADS)
     subst_gram_body<3>(nullptr, 0, j.src, j.lds, j.m, j.n, j.R, j.ldr, j.unit_r, j.dst, j.ldd,
                        do_gram < 0 ? j.do_gram : do_gram, j.Gpart, j.panels_total, j.panels_per_cta, j.check_finite,
                        j.st, blockIdx.x - start[k]);
+}
+
+// ---------------------------------------------------------------------------
+// Wide panels (n > 128): R no longer fits in shared memory next to a panel.
+// k_subst_wide: X = B R^{-1} by 64-column blocks, per panel of 128 rows:
+//   X_J = (B_J - sum_{I<J} X_I R_IJ) R_JJ^{-1}.
+// The sum is a register-tiled FP64 product (each thread owns 4 rows x 8
+// columns of the block) with X_I (already written to dst by this CTA) and R_IJ
+// staged through shared memory; the diagonal block is solved by row-wise
+// substitution.  dst may equal src (block J of B is read before X_J is written).
+// k_gram_tiles: G_IJ = X_I^T X_J for the 64 x 64 blocks I <= J of the upper
+// triangle (grid.y = block pair), per row chunk, fixed-order partials.
+// ---------------------------------------------------------------------------
+constexpr int kWP = 128;  // rows per panel
+constexpr int kWB = 64;   // column block
+
+__global__ void __launch_bounds__(RXR_THREADS, 1)
+    k_subst_wide(const double *__restrict__ src, int64_t lds, int64_t m, int n, const double *__restrict__ R,
+                 int64_t ldr, double *dst, int64_t ldd, int64_t panels_total, int64_t panels_per_cta, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    double *ut = reinterpret_cast<double *>(smem_raw);  // [kWB][kWP] block being solved
+    double *xi = ut + kWB * kWP;                          // [kWB][kWP] an earlier block of X
+    double *rb = xi + kWB * kWP;                          // [kWB cols][kWB rows] block of R
+    double *dv = rb + kWB * kWB;                          // [kWB] 1 / R_jj
+    const int tid = threadIdx.x;
+    const int tr = tid & 31, tc = tid >> 5;  // thread tile: rows 4 tr..4 tr+3, columns 8 tc..8 tc+7
+    const int nb = (n + kWB - 1) / kWB;
+    const int64_t p_begin = blockIdx.x * panels_per_cta;
+    const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
+    for (int64_t p = p_begin; p < p_end; ++p) {
+        const int64_t r0 = p * kWP;
+        for (int J = 0; J < nb; ++J) {
+            const int cJ = J * kWB, wJ = min(kWB, n - cJ);
+            double acc[4][8];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int64_t gr = r0 + 4 * tr + a;
+                    const int c = 8 * tc + b;
+                    acc[a][b] = (gr < m && c < wJ) ? src[gr + (int64_t)(cJ + c) * lds] : 0.0;
+                }
+            for (int I = 0; I < J; ++I) {
+                const int cI = I * kWB;
+                __syncthreads();
+                for (int e = tid; e < kWB * kWP; e += blockDim.x) {
+                    const int row = e % kWP, col = e / kWP;
+                    const int64_t gr = r0 + row;
+                    xi[e] = (gr < m) ? dst[gr + (int64_t)(cI + col) * ldd] : 0.0;
+                }
+                for (int e = tid; e < kWB * kWB; e += blockDim.x) {
+                    const int k = e % kWB, c = e / kWB;
+                    rb[e] = (c < wJ) ? R[(cI + k) + (int64_t)(cJ + c) * ldr] : 0.0;
+                }
+                __syncthreads();
+#pragma unroll 2
+                for (int k = 0; k < kWB; ++k) {
+                    double xv[4], rv[8];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) xv[a] = xi[k * kWP + 4 * tr + a];
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) rv[b] = rb[(8 * tc + b) * kWB + k];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 8; ++b) acc[a][b] = fma(-xv[a], rv[b], acc[a][b]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) ut[(8 * tc + b) * kWP + 4 * tr + a] = acc[a][b];
+            for (int e = tid; e < kWB * kWB; e += blockDim.x) {
+                const int k = e % kWB, c = e / kWB;
+                rb[e] = (c < wJ && k < wJ) ? R[(cJ + k) + (int64_t)(cJ + c) * ldr] : 0.0;
+            }
+            if (tid < kWB) dv[tid] = (tid < wJ) ? 1.0 / R[(cJ + tid) + (int64_t)(cJ + tid) * ldr] : 0.0;
+            __syncthreads();
+            if (tid < kWP) {
+                for (int j = 0; j < wJ; ++j)
+                    ut[j * kWP + tid] = chain4_dot(ut + tid, kWP, rb + j * kWB, 1, j, ut[j * kWP + tid]) * dv[j];
+            }
+            __syncthreads();
+            for (int e = tid; e < kWB * kWP; e += blockDim.x) {
+                const int row = e % kWP, col = e / kWP;
+                const int64_t gr = r0 + row;
+                if (gr < m && col < wJ) dst[gr + (int64_t)(cJ + col) * ldd] = ut[e];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RXR_THREADS)
+    k_gram_tiles(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t panels_total,
+                 int64_t panels_per_cta, double *__restrict__ Gpart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    double *xa = reinterpret_cast<double *>(smem_raw);  // [kWB][kWP]
+    double *xb = xa + kWB * kWP;
+    const int nb = (n + kWB - 1) / kWB;
+    // block pair (I, J), I <= J, from blockIdx.y
+    int I = 0, rem = blockIdx.y;
+    while (rem >= nb - I) {
+        rem -= nb - I;
+        ++I;
+    }
+    const int J = I + rem;
+    const int cI = I * kWB, cJ = J * kWB;
+    const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;  // 4 x 4 outputs per thread
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    const int64_t p_begin = blockIdx.x * panels_per_cta;
+    const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
+    for (int64_t p = p_begin; p < p_end; ++p) {
+        const int64_t r0 = p * kWP;
+        __syncthreads();
+        for (int e = tid; e < kWB * kWP; e += blockDim.x) {
+            const int row = e % kWP, col = e / kWP;
+            const int64_t gr = r0 + row;
+            xa[e] = (gr < m && cI + col < n) ? X[gr + (int64_t)(cI + col) * ldx] : 0.0;
+            xb[e] = (gr < m && cJ + col < n) ? X[gr + (int64_t)(cJ + col) * ldx] : 0.0;
+        }
+        __syncthreads();
+        const int rot = tid & 31;
+        for (int i = 0; i < kWP; ++i) {
+            const int r = (i + rot) & (kWP - 1);
+            double u[4], v[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                u[a] = xa[(4 * ti + a) * kWP + r];
+                v[a] = xb[(4 * tj + a) * kWP + r];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(u[a], v[b], acc[a][b]);
+        }
+    }
+    double *out = Gpart + (int64_t)blockIdx.x * n * n;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = cI + 4 * ti + a, c = cJ + 4 * tj + b;
+            if (r < n && c < n && r <= c) out[r + (int64_t)c * n] = acc[a][b];
+        }
+}
+
+cudaError_t set_wide_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_subst_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((2 * kWB * kWP + kWB * kWB + kWB) * sizeof(double)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gram_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * kWB * kWP * sizeof(double)));
+    return e;
 }
 
 // Host-side dispatch over the tile count (template kernels stay in this unit).

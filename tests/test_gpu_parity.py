@@ -369,3 +369,31 @@ def test_gpu_evaluators_match_oracle(h):
     e2 = h.resid_error(to_dev(A), Qd, Rd)
     assert abs(e1 - o.orth_error(ref.Q)) <= 1e-3 * o.orth_error(ref.Q)
     assert abs(e2 - o.resid_error(A, ref.Q, ref.R)) <= 1e-3 * o.resid_error(A, ref.Q, ref.R)
+
+
+# ------------------------------------------------------------------ wide panels (n > 128)
+@pytest.mark.parametrize("m,n,kappa,variant,prec", [(400, 129, 1e4, "qr", "fp64"), (1000, 200, 1e8, "lu", "fp64"),
+                                                    (700, 256, 1e12, "qr", "split"), (1500, 512, 1e13, "qr", "fp64"),
+                                                    (1100, 512, 1e6, "lu", "split")])
+def test_wide_panel_cholqr(h, m, n, kappa, variant, prec):
+    A = usv_matrix(m, n, kappa, seed=n)
+    Q, R, code = h.cholqr(to_dev(A), variant=variant, s=2 * n, seed=1, passes=2, prec=prec)
+    assert code == 0
+    Qg, Rg = to_host(Q), to_host(R)
+    assert o.orth_error(Qg) <= 1e-13
+    assert o.resid_error(A, Qg, Rg) <= 1e-14
+    assert abs(h.orth_error(Q) - o.orth_error(Qg)) <= 1e-3 * o.orth_error(Qg) + 1e-30
+    ref = o.rxr_cholqr(A, OV[variant], 2 * n, seed=1, passes=2)
+    assert np.linalg.norm(Rg - ref.R) / np.linalg.norm(ref.R) <= max(100 * kappa * U, 1e-13)
+
+
+def test_wide_panel_precond_gram_parity(h):
+    m, n = 777, 200
+    A = usv_matrix(m, n, 1e3, seed=3)
+    R = o.rxr_cholqr(A, o.VARIANT_QR, 2 * n, seed=2, passes=1).Rs
+    X, G = h.precond_gram(to_dev(A), to_dev(R))
+    Xg, Gg = to_host(X), to_host(G)
+    Xo = o.trsm_right_upper(A, R)
+    bound = 4 * n * U * (np.abs(Xo) @ np.abs(R) @ np.abs(np.linalg.inv(R))) + 1e-300
+    assert np.all(np.abs(Xg - Xo) <= bound), np.max(np.abs(Xg - Xo) / bound)
+    assert np.all(np.abs(Gg - o.gram(Xg)) <= 4 * (m + 2) * U * (np.abs(Xg).T @ np.abs(Xg)))
