@@ -189,6 +189,13 @@ RXR_API int rxr_xr_factor(rxr_handle h, const double *Y, int64_t s, int64_t n, i
 RXR_API int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *R,
                      int64_t ldr, double *X, int64_t ldx, double *G, int64_t ldg, int prec, void *stream);
 
+/* G = X^T X (full symmetric n x n, ldg >= n) of a tall-skinny X (Algorithm 1
+ * step 1).  RXR_FP64: FP64 FMAs.  RXR_SPLIT_BF16: the tensor-core Gram with
+ * exact 7-digit splitting (FP64-grade: error about 2^-53 of |X|^T |X|
+ * column-normwise), n <= 128.  Blocking. */
+RXR_API int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, double *G, int64_t ldg, int prec,
+                     void *stream);
+
 /* Upper Cholesky factor R (R^T R = G; reads the upper triangle of G).
  * Blocking; returns 0 or RXR_ERR_CHOL_BREAKDOWN (column in rxr_last_info). */
 RXR_API int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *R, int64_t ldr, void *stream);

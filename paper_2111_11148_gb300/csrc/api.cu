@@ -436,8 +436,18 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         if (launch_ok()) return RXR_ERR_CUDA;
         const bool last = (pass == passes);
         Timer t(th, last ? 3 : 2, st);
-        // X <- X R_p^{-1} (in place), with the next pass's Gram unless last
-        if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) return e;
+        // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
+        // split path takes that Gram from the tensor cores at FP64 grade
+        if (p.prec == RXR_SPLIT_BF16 && !last && !p.wide) {
+            if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, false, false, st)) return e;
+            if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
+        } else if (p.prec == RXR_SPLIT_BF16 && last && pass > 1 && p.n <= 64) {
+            // the last pass's R_P is within rounding of I: apply its explicit
+            // inverse on the tensor cores at FP64 grade
+            if (int e = ozaki_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
+        } else if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) {
+            return e;
+        }
     }
     if (R) {
         k_copy_upper<<<(int)cdiv(p.n * p.n, 256), 256, 0, st>>>(p.Racc, n, R, ldr, p.status);
@@ -923,6 +933,35 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
         if (int e = split_gram_enqueue(p, X, ldx, st)) return e;
     } else {
         if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, true, false, st)) return e;
+    }
+    if (cudaMemcpy2DAsync(G, ldg * 8, p.G, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, double *G, int64_t ldg, int prec,
+             void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (X == nullptr) return -2;
+    if (m < 1) return -3;
+    if (n < 1) return -4;
+    if (ldx < m) return -5;
+    if (G == nullptr) return -6;
+    if (ldg < n) return -7;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -8;
+    if (n > kNarrowN) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, m, n, n, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    if (prec == RXR_SPLIT_BF16) {
+        if (int e = ozaki_gram_enqueue(p, X, ldx, st)) return e;
+    } else if (int e = enqueue_subst(p, X, ldx, nullptr, 1, nullptr, m, true, false, st)) {
+        return e;
     }
     if (cudaMemcpy2DAsync(G, ldg * 8, p.G, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;

@@ -334,5 +334,7 @@ namespace rxr {
 // split-precision contractions (split_kernels.cu)
 int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st);
 int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
+int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
+int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
 }  // namespace rxr

@@ -501,6 +501,401 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
+// ---------------------------------------------------------------------------
+// FP64-grade Gram on the tensor cores (Ozaki-style exact splitting): for each
+// 128-row window, column j of X is written in fixed point relative to 2^(e_j+1)
+// as seven 8-bit digits (the same digits as the split sketch's A).  The
+// ordered digit pairs (p, q), p + q <= 6, accumulate into seven tensor-memory
+// groups d = p + q; a group holds at most seven pairs of products below 2^14
+// over 128 rows, so every sum stays below 2^24 and the FP32 accumulation is
+// exact.  Per window the groups are combined (weights 2^-8d) and added in FP64
+// with the scale 2^(e_j + e_l).  The result is X^T X to about 2^-53 of
+// |X|^T |X| column-normwise: it serves the CholeskyQR passes that must be
+// FP64-accurate (the second pass's Gram).  n <= 128; grid.y = 64-column
+// blocks of G.
+// ---------------------------------------------------------------------------
+constexpr int kOzWin = 128;
+constexpr int kOzSub = 64;
+constexpr int kOzM = 128;
+constexpr int kOzN = 64;
+constexpr int kOzDigits = 7;
+constexpr int kOzTile = kOzM * kOzSub * 2;  // 16 KB per digit
+constexpr size_t kOzSmem = (size_t)kOzDigits * kOzTile;
+
+// Seven digits of a 55-bit fixed-point value of x relative to 2^(emax+1),
+// emax = biased exponent of the largest entry of its group: six balanced
+// digits in [-128, 127] from the bottom, the rest (in [-128, 128]) on top.
+// Digit q has weight 2^(emax - 1029 - 8q).
+__device__ __forceinline__ void digits7(unsigned long long bits, int emax, float dg[kOzDigits])
+{
+    long long T = 0;
+    const int ea = (int)((bits >> 52) & 0x7FF);
+    if (ea > 0 && ea < 0x7FF) {
+        const long long m53 = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+        const int sh = emax - ea;
+        if (sh <= 2)
+            T = m53 << (2 - sh);
+        else if (sh < 56)
+            T = (m53 + (1ll << (sh - 3))) >> (sh - 2);
+        if (bits >> 63) T = -T;
+    }
+#pragma unroll
+    for (int q = kOzDigits - 1; q >= 1; --q) {
+        const long long d = ((T + 128) & 255) - 128;
+        T = (T - d) >> 8;
+        dg[q] = (float)d;
+    }
+    dg[0] = (float)T;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_gram_ozaki(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t win_total, int64_t win_per_cta,
+                 double *__restrict__ Gpart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int colexp[kOzM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = blockIdx.y * kOzN;
+
+    for (int e = tid; e < (int)(kOzSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16(kOzM, kOzN);
+    const int q4 = warp & 3, half = warp >> 2;
+    const int my_row = 32 * q4 + lane;  // row j of G
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+
+    uint32_t phase = 0;
+    bool pending = false, ok = true;
+    const int64_t w_begin = blockIdx.x * win_per_cta;
+    const int64_t w_end = min(win_total, w_begin + win_per_cta);
+    for (int64_t w = w_begin; w < w_end && ok; ++w) {
+        const int64_t wr0 = w * kOzWin;
+        // largest exponent of every column in the window: one warp per column
+        for (int col = warp; col < kOzM; col += 8) {
+            unsigned ex = 0;
+            if (col < n) {
+                unsigned hv[kOzWin / 32];
+#pragma unroll
+                for (int t = 0; t < kOzWin / 32; ++t) {
+                    const int64_t gr = wr0 + lane + 32 * t;
+                    hv[t] = (gr < m) ? (unsigned)__double2hiint(X[gr + (int64_t)col * ldx]) : 0u;
+                }
+#pragma unroll
+                for (int t = 0; t < kOzWin / 32; ++t) ex = max(ex, (hv[t] >> 20) & 0x7FFu);
+            }
+            ex = __reduce_max_sync(0xFFFFFFFFu, ex);
+            if (lane == 0) colexp[col] = (int)ex;
+        }
+        __syncthreads();
+        for (int sp = 0; sp < kOzWin / kOzSub; ++sp) {
+            const int64_t r0 = wr0 + sp * kOzSub;
+            if (pending) {
+                ok = mma_wait(&mma_bar, phase, st);
+                if (!ok) break;
+                phase ^= 1u;
+                pending = false;
+            }
+            // digits of every entry of the 64-row tile (n columns), 16 loads in flight
+            const int iters = (kOzSub * n + 255) / 256;
+            for (int base = 0; base < iters; base += 16) {
+                unsigned long long vb[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int e = tid + 256 * (base + t);
+                    const int k = e & (kOzSub - 1), j = e >> 6;
+                    const int64_t gr = r0 + k;
+                    vb[t] = (j < n && gr < m && base + t < iters)
+                                ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)j * ldx])
+                                : 0ull;
+                }
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int e = tid + 256 * (base + t);
+                    const int k = e & (kOzSub - 1), j = e >> 6;
+                    if (j < n && base + t < iters) {
+                        float dg[kOzDigits];
+                        digits7(vb[t], colexp[j], dg);
+                        const int off = kmaj_off(j, k);
+#pragma unroll
+                        for (int q = 0; q < kOzDigits; ++q) st_bf16(smem + q * kOzTile, off, dg[q]);
+                    }
+                }
+            }
+            fence_proxy_async_shared();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t b0 = smem_u32(smem);
+#pragma unroll
+                for (int kk = 0; kk < kOzSub / 16; ++kk)
+#pragma unroll
+                    for (int p = 0; p < kOzDigits; ++p)
+#pragma unroll
+                        for (int q = 0; p + q < kOzDigits; ++q) {
+                            const uint32_t acc_on = (sp > 0 || kk > 0 || p > 0) ? 1u : 0u;
+                            tc_mma(tmem + (uint32_t)((p + q) * kOzN), smem_desc(b0 + p * kOzTile + kk * 256, 128, 1024),
+                                   smem_desc(b0 + q * kOzTile + (c0 / 8) * 1024 + kk * 256, 128, 1024), idesc, acc_on);
+                        }
+                tc_commit(&mma_bar);
+            }
+            pending = true;
+        }
+        if (!ok) break;
+        ok = mma_wait(&mma_bar, phase, st);
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc_fence_after();
+        const int ej = colexp[min(my_row, kOzM - 1)];
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+            const int col0 = half * 32 + c16 * 16;
+            float hi[16], lo[16], v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) lo[t] = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kOzDigits; ++d) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + d * kOzN + col0, v);
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float x = __fmul_rn(v[t], w8);
+                    const float sum = __fadd_rn(hi[t], x);
+                    const float bb = __fsub_rn(sum, hi[t]);
+                    const float err = __fadd_rn(__fsub_rn(hi[t], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                    hi[t] = sum;
+                    lo[t] = __fadd_rn(lo[t], err);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int el = colexp[min(c0 + col0 + t, kOzM - 1)];
+                const int be = ej + el - 1035;  // biased exponent of 2^(e_j + e_l - 2058)
+                const double scale = (ej > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
+                const double val = rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
+                acc[c16 * 16 + t] = fma(val, scale, acc[c16 * 16 + t]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (pending) {
+        mma_wait(&mma_bar, phase, st);
+        tc_fence_after();
+    }
+    if (ok && my_row < n) {
+        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int c = c0 + half * 32 + t;
+            if (c < n && my_row <= c) out[my_row + (int64_t)c * n] = acc[t];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// FP64-grade product Q = X T on the tensor cores (the last CholeskyQR pass's
+// apply, T = R_P^{-1}; R_P is within rounding of I once the first pass has
+// made X orthonormal to O(u cond^2), so its explicit inverse is as accurate as
+// substitution).  Row i of X is split relative to its own largest exponent
+// and column l of T relative to its own, seven 8-bit digits each; the digit
+// pairs p + q = d accumulate in tensor memory exactly (K = n <= 64: sums below
+// 2^24) and each output is combined once, scaled by 2^(e_i + e_l).  X is read
+// and overwritten in place, 128 rows per tile.
+// ---------------------------------------------------------------------------
+constexpr int kApM = 128, kApK = 64, kApN = 64, kApDigits = 7;
+constexpr int kApATile = kApM * kApK * 2;  // 16 KB per digit
+constexpr int kApBTile = kApN * kApK * 2;  // 8 KB per digit
+constexpr size_t kApSmem = (size_t)kApDigits * (kApATile + kApBTile);
+
+__global__ void __launch_bounds__(256, 1)
+    k_apply_ozaki(double *X, int64_t ldx, int64_t m, int n, const double *__restrict__ T, int64_t ldt,
+                  int64_t tiles_total, int64_t tiles_per_cta, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *aop = smem;                          // X digits, rows x k
+    unsigned char *bop = smem + kApDigits * kApATile;   // T digits, cols l x k
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int rowexp[kApM];
+    __shared__ int colexp_t[kApN];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int e = tid; e < (int)(kApSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+    }
+    // exponents and digits of T (once per CTA): B tile element (l, k) = T[k][l]
+    if (tid < kApN) {
+        unsigned ex = 0;
+        if (tid < n)
+            for (int k = 0; k <= tid; ++k) ex = max(ex, ((unsigned)__double2hiint(T[k + (int64_t)tid * ldt]) >> 20) & 0x7FFu);
+        colexp_t[tid] = (int)ex;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int k = e % n, l = e / n;
+        const unsigned long long bits = (k <= l) ? (unsigned long long)__double_as_longlong(T[k + (int64_t)l * ldt]) : 0ull;
+        float dg[kApDigits];
+        digits7(bits, colexp_t[l], dg);
+        const int off = kmaj_off(l, k);
+#pragma unroll
+        for (int q = 0; q < kApDigits; ++q) st_bf16(bop + q * kApBTile, off, dg[q]);
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16(kApM, kApN);
+    const int q4 = warp & 3, half = warp >> 2;
+    const int my_row = 32 * q4 + lane;
+
+    uint32_t phase = 0;
+    bool pending = false, ok = true;
+    const int64_t t_begin = blockIdx.x * tiles_per_cta;
+    const int64_t t_end = min(tiles_total, t_begin + tiles_per_cta);
+    for (int64_t tile = t_begin; tile < t_end && ok; ++tile) {
+        const int64_t r0 = tile * kApM;
+        // per-row exponent over the row's n entries (thread per row)
+        if (tid < kApM) {
+            unsigned ex = 0;
+            const int64_t gr = r0 + tid;
+            if (gr < m)
+                for (int k = 0; k < n; ++k) ex = max(ex, ((unsigned)__double2hiint(X[gr + (int64_t)k * ldx]) >> 20) & 0x7FFu);
+            rowexp[tid] = (int)ex;
+        }
+        __syncthreads();
+        // digits of the 128 x n tile, 16 loads in flight per thread
+        const int iters = (kApM * n + 255) / 256;
+        for (int base = 0; base < iters; base += 16) {
+            unsigned long long vb[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int e = tid + 256 * (base + t);
+                const int i = e & (kApM - 1), k = e >> 7;
+                const int64_t gr = r0 + i;
+                vb[t] = (k < n && gr < m && base + t < iters)
+                            ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)k * ldx])
+                            : 0ull;
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int e = tid + 256 * (base + t);
+                const int i = e & (kApM - 1), k = e >> 7;
+                if (k < n && base + t < iters) {
+                    float dg[kApDigits];
+                    digits7(vb[t], rowexp[i], dg);
+                    const int off = kmaj_off(i, k);
+#pragma unroll
+                    for (int q = 0; q < kApDigits; ++q) st_bf16(aop + q * kApATile, off, dg[q]);
+                }
+            }
+        }
+        fence_proxy_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(aop), b0 = smem_u32(bop);
+#pragma unroll
+            for (int kk = 0; kk < kApK / 16; ++kk)
+#pragma unroll
+                for (int p = 0; p < kApDigits; ++p)
+#pragma unroll
+                    for (int q = 0; p + q < kApDigits; ++q) {
+                        const uint32_t acc_on = (kk > 0 || p > 0) ? 1u : 0u;
+                        tc_mma(tmem + (uint32_t)((p + q) * kApN), smem_desc(a0 + p * kApATile + kk * 256, 128, 1024),
+                               smem_desc(b0 + q * kApBTile + kk * 256, 128, 1024), idesc, acc_on);
+                    }
+            tc_commit(&mma_bar);
+        }
+        pending = true;
+        ok = mma_wait(&mma_bar, phase, st);
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc_fence_after();
+        const int ei = rowexp[my_row];
+        const int64_t gr = r0 + my_row;
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+            const int col0 = half * 32 + c16 * 16;
+            float hi[16], lo[16], v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) lo[t] = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kApDigits; ++d) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + d * kApN + col0, v);
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float x = __fmul_rn(v[t], w8);
+                    const float sum = __fadd_rn(hi[t], x);
+                    const float bb = __fsub_rn(sum, hi[t]);
+                    const float err = __fadd_rn(__fsub_rn(hi[t], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                    hi[t] = sum;
+                    lo[t] = __fadd_rn(lo[t], err);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int l = col0 + t;
+                if (l < n && gr < m) {
+                    const int el = colexp_t[l];
+                    const int be = ei + el - 1035;
+                    const double scale = (ei > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
+                    X[gr + (int64_t)l * ldx] = (rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t])) * scale;
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (pending) {
+        mma_wait(&mma_bar, phase, st);
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// T = R^{-1} for upper-triangular R (one CTA; thread c solves R t = e_c by back
+// substitution).
+__global__ void k_tri_inverse(const double *__restrict__ R, int n, int64_t ldr, double *__restrict__ T, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int i = n - 1; i > c; --i) T[i + (int64_t)c * n] = 0.0;
+        T[c + (int64_t)c * n] = 1.0 / R[c + (int64_t)c * ldr];
+        for (int i = c - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int k = i + 1; k <= c; ++k) acc = fma(R[i + (int64_t)k * ldr], T[k + (int64_t)c * n], acc);
+            T[i + (int64_t)c * n] = -acc / R[i + (int64_t)i * ldr];
+        }
+    }
+}
+
 __global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, int, double *, int64_t, RxrStatus *);
 
 // ---------------------------------------------------------------------------
@@ -508,12 +903,52 @@ __global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, i
 // ---------------------------------------------------------------------------
 static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Extra workspace of the split path: the split Gram's per-CTA partial sums
-// (the split sketch reuses the FP64 sketch's partial buffer, which is larger).
+// Extra workspace of the split path: the per-CTA partial sums of the split
+// Gram and of the FP64-grade tensor-core Gram (the split sketch reuses the FP64
+// sketch's partial buffer, which is larger).
+static int64_t ozaki_chunks(int64_t m, int64_t n, int sms)
+{
+    const int64_t gy = cdiv64(n, kOzN);
+    return std::max<int64_t>(1, std::min<int64_t>(cdiv64(m, kOzWin), sms / gy));
+}
+
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
 {
-    const int64_t gx = std::min<int64_t>(sms, cdiv64(m, kGsWin));
+    const int64_t gx = std::max<int64_t>(std::min<int64_t>(sms, cdiv64(m, kGsWin)), ozaki_chunks(m, n, sms));
     return (size_t)gx * n * n * sizeof(double);
+}
+
+// X <- X R^{-1} on the tensor cores through the explicit inverse (n <= 64);
+// T is held in the XR scratch (s x n >= n x n).
+int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
+{
+    if (p.n > kApK) return RXR_ERR_UNSUPPORTED;
+    double *T = p.W;
+    k_tri_inverse<<<1, 128, 0, st>>>(R, (int)p.n, p.n, T, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    const int64_t tiles = cdiv64(p.m, kApM);
+    int64_t gx = std::min<int64_t>(p.sms, tiles);
+    const int64_t tpc = cdiv64(tiles, gx);
+    gx = cdiv64(tiles, tpc);
+    k_apply_ozaki<<<(unsigned)gx, 256, kApSmem, st>>>(X, ldx, p.m, (int)p.n, T, p.n, tiles, tpc, p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
+{
+    if (p.n > kOzM) return RXR_ERR_UNSUPPORTED;
+    const int64_t win_total = cdiv64(p.m, kOzWin);
+    int64_t gx = ozaki_chunks(p.m, p.n, p.sms);
+    const int64_t wpc = cdiv64(win_total, gx);
+    gx = cdiv64(win_total, wpc);
+    const int gy = (int)cdiv64(p.n, kOzN);
+    double *parts = reinterpret_cast<double *>(p.split);
+    k_gram_ozaki<<<dim3((unsigned)gx, gy), 256, kOzSmem, st>>>(X, ldx, p.m, (int)p.n, win_total, wpc, parts, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    const int64_t nn = p.n * p.n;
+    k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(parts, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G, p.n,
+                                                         p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
 cudaError_t set_split_smem()
@@ -521,6 +956,10 @@ cudaError_t set_split_smem()
     cudaError_t e = cudaFuncSetAttribute(k_sketch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGsSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gram_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
     return e;
 }
 

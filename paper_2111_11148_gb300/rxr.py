@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
         "rxr_xr_factor": ([vp, vp, i64, i64, i64, i, vp, i64, vp], i),
         "rxr_precond_gram": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, i, vp], i),
         "rxr_cholesky": ([vp, vp, i64, i64, vp, i64, vp], i),
+        "rxr_gram": ([vp, vp, i64, i64, i64, vp, i64, i, vp], i),
         "rxr_orth_error": ([vp, vp, i64, i64, i64, P(d), vp], i),
         "rxr_resid_error": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, P(d), vp], i),
         "rxr_fp64_peak": ([P(d), vp], i),
@@ -83,7 +84,7 @@ def exported_symbols() -> list[str]:
     return [n for n in ("rxr_create", "rxr_destroy", "rxr_workspace_bytes", "rxr_set_workspace", "rxr_cholqr",
                         "rxr_cholqr_async", "rxr_cholqr_host", "rxr_cholqr_batched", "rxr_last_info",
                         "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_xr_factor", "rxr_precond_gram",
-                        "rxr_cholesky", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
+                        "rxr_cholesky", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
                         "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc")]
 
 
@@ -257,6 +258,13 @@ class Handle:
                                        _ptr(X) if X is not None else None, _ld(X) if X is not None else m,
                                        _ptr(G), _ld(G), _PRECS[prec], _stream(stream)), "rxr_precond_gram")
         return X, G
+
+    def gram(self, X, prec="fp64", stream=None):
+        m, n = X.shape
+        G = empty_colmajor(n, n, device=X.device)
+        _check(load().rxr_gram(self._h, _ptr(X), m, n, _ld(X), _ptr(G), _ld(G), _PRECS[prec], _stream(stream)),
+               "rxr_gram")
+        return G
 
     def cholesky(self, G, stream=None, raise_on_error=True):
         n = G.shape[0]
