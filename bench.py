@@ -38,6 +38,7 @@ WORKLOAD = "rQR-CholeskyQR2 m=2^22 n=64 s=128 kappa=1e10 FP64"
 # dram__bytes_read.sum + dram__bytes_write.sum of one precondition+Gram launch,
 # ncu capture at m = 2^19 scaled by 8 rows-for-rows (profiles/k_subst_gram_precond_m524288_n64.md)
 TRAFFIC_PG = (268.552704e6 + 225.660672e6) * 8
+TRAFFIC_SUBST = None  # filled from an ncu capture of the substitution-only launch
 HBM_GBS = 6795.5  # measured copy bandwidth of this GPU pool (STREAM-style copy)
 
 
@@ -218,6 +219,43 @@ def batched_arm(args, rank: int, world: int, local_rank: int):
     h.close()
 
 
+STAGES = ["sketch", "precond_subst", "pass_subst", "last_apply", "gram1_tensor", "gram2_tensor", "xr_factor"]
+
+
+def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=False):
+    """Time `steps` factorisations (after `warmup`) with CUDA events on the
+    launching stream; then per-stage event times and the accuracy."""
+    import torch
+
+    def step():
+        h.cholqr(A, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=prec, Q=Q, R=R)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0) if sample_clocks else None
+    if clocks:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    clk = clocks.stop() if clocks else None
+    h.set_kernel_timing(True)
+    kms = {k: [] for k in range(len(STAGES))}
+    for _ in range(3):
+        step()
+        for k in range(len(STAGES)):
+            kms[k].append(h.last_kernel_ms(k))
+    h.set_kernel_timing(False)
+    stages = {STAGES[k]: statistics.median(v) for k, v in kms.items() if statistics.median(v) > 0}
+    return {"ms": ms, "stages_ms": stages, "orth": h.orth_error(Q), "resid": h.resid_error(A, Q, R), "clocks": clk}
+
+
 def gpu_arm(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -237,59 +275,23 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
     R = rxr.empty_colmajor(N, N, device=dev)
     h = rxr.Handle(local_rank)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        h.cholqr(A, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=Q, R=R)
-
     peak_fp64 = rxr.fp64_peak_tflops()
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize(dev)
+    warm = max(3, args.warmup)
+
+    # the reported path, timed with clocks sampled; then the other precision
+    other = "fp64" if args.prec == "split" else "split"
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_total = e0.elapsed_time(e1)
-    clk = clocks.stop()
+    main = time_path(h, A, Q, R, args.prec, args, dev, stream, args.steps, warm, sample_clocks=True)
+    ref = None if args.no_compare else time_path(h, A, Q, R, other, args, dev, stream, max(2, args.steps // 2), warm)
+    ms = main["ms"]
     if dist:
-        t = torch.tensor([ms_total], device=dev)
+        t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms = ms_total / args.steps
+        ms = float(t.item())
     value = world * b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9
 
-    # per-kernel device times (events on the launching stream), after the timed region
-    h.set_kernel_timing(True)
-    kms = {k: [] for k in range(4)}
-    for _ in range(3):
-        step()
-        for k in range(4):
-            kms[k].append(h.last_kernel_ms(k))
-    h.set_kernel_timing(False)
-    kmed = {k: statistics.median(v) for k, v in kms.items()}
-    # roofline kernel: the fused precondition + Gram launch (k_subst_gram reading
-    # A, writing X = A R_s^{-1}, accumulating G = X^T X).  Algorithmic FP64 work
-    # per row: n(n-1)/2 substitution FMAs + n scalings + n(n+1)/2 Gram FMAs.
-    pg_flop = (2.0 * N * N + N) * M
-    achieved = pg_flop / (kmed[1] * 1e-3) / 1e12
-    # accuracy of the timed factorisation (GPU Dot2 evaluators)
-    orth = h.orth_error(Q)
-    resid = h.resid_error(A, Q, R)
-
-    # end to end through the host-buffer entry point
-    e2e = None
-    if not args.no_e2e:
-        e2e = e2e_leg(h, A_np, args, world)
-
-    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    e2e = None if args.no_e2e else e2e_leg(h, A_np, args, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -300,11 +302,36 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
         cpu = {"value": b_alg(rows, N, PASSES) / t_or / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"first {rows} of {M} rows of the same A, one full rxr_cholqr (single-threaded C oracle), "
                          f"{t_or:.2f} s"}
-    _emit(args, rank, world, ms, value, peak_fp64, achieved, kmed, orth, resid, e2e, clk, cpu)
+    if rank == 0:
+        _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu)
     h.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def roofline_entry(prec, stages, peak_fp64):
+    """The dominant FP64 launch of the path against the measured DFMA peak.
+    FP64 path: the fused precondition+Gram launch, (2n^2 + n) flop per row.
+    Split path: the FP64 substitution X = A R_s^{-1}, n^2 flop per row (its Gram
+    runs on the tensor cores)."""
+    if prec == "fp64":
+        t = stages.get("precond_subst")
+        flop = (2.0 * N * N + N) * M
+        name = "k_subst_gram (fused precondition + Gram launch)"
+        traffic = TRAFFIC_PG if (M == 2**22 and N == 64) else None
+        hbm_bytes = 16.0 * M * N
+    else:
+        t = stages.get("precond_subst")
+        flop = (1.0 * N * N) * M
+        name = "k_subst_gram (FP64 substitution X = A R_s^-1; its Gram is on the tensor cores)"
+        traffic = TRAFFIC_SUBST if (M == 2**22 and N == 64) else None
+        hbm_bytes = 16.0 * M * N
+    achieved = flop / (t * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp64, "traffic": traffic,
+            "hbm_frac": (hbm_bytes / (t * 1e-3) / 1e9) / HBM_GBS,
+            "peak_kind": "FP64 DFMA pipe, measured by the rxr_fp64_peak calibration kernel in this run"}
 
 
 def e2e_leg(h, A_np, args, world):
@@ -327,32 +354,34 @@ def e2e_leg(h, A_np, args, world):
             "d2h_bytes_per_step": 8 * M * N + 8 * N * N}
 
 
-def _emit(args, rank, world, ms, value, peak_fp64, achieved, kmed, orth, resid, e2e, clk, cpu):
-    launches_per_step = 11 if PASSES == 2 else 9 + 2 * (PASSES - 1)
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f64+bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA, "seed": SEED, "passes": PASSES,
-                       "variant": args.variant, "prec": args.prec,
-                       "l2": f"A ({8 * M * N / 1e9:.1f} GB) larger than L2 (129 MB); no flush needed",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_subst_gram (fused precondition + Gram launch)",
-                         "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s", "frac": achieved / peak_fp64,
-                         "traffic": TRAFFIC_PG if (M == 2**22 and N == 64 and args.prec == "fp64") else None,
-                         "hbm_frac": (16.0 * M * N / (kmed[1] * 1e-3) / 1e9) / HBM_GBS,
-                         "peak_kind": "FP64 DFMA pipe, measured by the rxr_fp64_peak calibration kernel in this run"},
-            "kernels_ms": {"sketch": kmed[0], "precond_gram": kmed[1], "pass_gram": kmed[2], "apply": kmed[3]},
-            "gflops": world * f_alg(M, N, S, PASSES) / (ms * 1e-3) / 1e9,
-            "qr_per_s": world / (ms * 1e-3),
-            "accuracy": {"orth": orth, "resid": resid},
-            "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk,
-            "cpu_baseline": cpu,
+def _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu):
+    launches = {"fp64": 11, "split": 14 if N <= 64 else 13}[args.prec] if PASSES == 2 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f64+bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA, "seed": SEED, "passes": PASSES,
+                   "variant": args.variant, "prec": args.prec,
+                   "l2": f"A ({8 * M * N / 1e9:.1f} GB) larger than L2 (129 MB); no flush needed",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": roofline_entry(args.prec, main["stages_ms"], peak_fp64),
+        "stages_ms": main["stages_ms"],
+        "gflops": world * f_alg(M, N, S, PASSES) / (ms * 1e-3) / 1e9,
+        "qr_per_s": world / (ms * 1e-3),
+        "accuracy": {"orth": main["orth"], "resid": main["resid"]},
+        "e2e": e2e,
+        "gpu_launches": launches * args.steps if launches else None,
+        "clocks": main["clocks"],
+        "cpu_baseline": cpu,
+    }
+    if ref is not None:
+        line["compare"] = {
+            "prec": other, "value": world * b_alg(M, N, PASSES) / (ref["ms"] * 1e-3) / 1e9, "unit": "GB/s",
+            "ms_per_step": ref["ms"], "stages_ms": ref["stages_ms"],
+            "accuracy": {"orth": ref["orth"], "resid": ref["resid"]},
+            "roofline": roofline_entry(other, ref["stages_ms"], peak_fp64),
         }
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -362,7 +391,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--variant", default="qr", choices=["qr", "lu"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--prec", default="split", choices=["fp64", "split"],
+                    help="the reported path; the other precision is timed alongside unless --no-compare")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")

@@ -54,6 +54,11 @@ using namespace rxr;
 // ---------------------------------------------------------------------------
 // Handle
 // ---------------------------------------------------------------------------
+// per-stage event slots: 0 sketch, 1 precondition (+ fused Gram), 2 middle
+// passes (+ fused Gram), 3 last apply, 4 tensor-core first Gram, 5 tensor-core
+// later Gram, 6 XR factorisation of the sketch
+constexpr int kTimers = 7;
+
 struct rxr_ctx {
     int device = 0;
     int sms = 152;
@@ -63,9 +68,9 @@ struct rxr_ctx {
     int *h_status = nullptr;  // pinned, 4 ints
     int last_pass = -1, last_col = -1;
     bool timing = false;
-    cudaEvent_t ev[4][2] = {};
-    float last_ms[4] = {0, 0, 0, 0};
-    bool ev_recorded[4] = {false, false, false, false};
+    cudaEvent_t ev[kTimers][2] = {};
+    float last_ms[kTimers] = {};
+    bool ev_recorded[kTimers] = {};
     // device staging for the _host entry point
     double *dA = nullptr, *dQ = nullptr, *dR = nullptr;
     size_t dA_bytes = 0, dQ_bytes = 0, dR_bytes = 0;
@@ -142,6 +147,34 @@ struct DeviceGuard {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+}  // namespace
+
+namespace rxr {
+// Row chunks for a grid of gx x gy CTAs on `slots` resident CTA slots: the gx
+// (at most max_gx) whose last wave is fullest, preferring fewer chunks, so a
+// grid that overflows one wave by a few CTAs does not pay a second full wave.
+int64_t balanced_chunks(int64_t gy, int64_t slots, int64_t max_gx)
+{
+    max_gx = std::max<int64_t>(1, max_gx);
+    const int64_t lo = std::min(max_gx, std::max<int64_t>(1, slots / gy));
+    const int64_t hi = std::min(max_gx, std::max<int64_t>(lo, 8 * slots / gy));
+    int64_t best = lo;
+    double best_eff = -1.0;
+    for (int64_t gx = lo; gx <= hi; ++gx) {
+        const int64_t ctas = gx * gy;
+        const double eff = (double)ctas / (double)(cdiv(ctas, slots) * slots);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = gx;
+        }
+        if (eff > 0.97) break;
+    }
+    return best;
+}
+}  // namespace rxr
+
+namespace {
+
 constexpr int kSkP = 64, kSkSTile = 128, kSkNTile = 64, kSgP = 128;
 constexpr int kMaxStreamN = RXR_MAX_N;  // n > 128 uses the column-blocked kernels
 constexpr int kNarrowN = 128;            // up to here R lives in shared memory
@@ -162,8 +195,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     const int64_t s_tiles = cdiv(s, kSkSTile), n_tiles = cdiv(n, kSkNTile);
     p.sk_gy = (int)(s_tiles * n_tiles);
     p.sk_panels = cdiv(m, kSkP);
-    int64_t gx = std::max<int64_t>(1, cdiv(2 * (int64_t)sms, p.sk_gy));
-    gx = std::min(std::min(gx, p.sk_panels), std::max<int64_t>(1, max_chunks));
+    int64_t gx = balanced_chunks(p.sk_gy, 2 * (int64_t)sms, std::min(p.sk_panels, std::max<int64_t>(1, max_chunks)));
     p.sk_ppc = cdiv(p.sk_panels, gx);
     p.sk_gx = (int)cdiv(p.sk_panels, p.sk_ppc);
 
@@ -178,8 +210,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
         p.sg_maxt = 3;
         const int64_t nb = cdiv(n, kWB);
         p.gt_gy = (int)(nb * (nb + 1) / 2);
-        int64_t cg = std::max<int64_t>(1, cdiv(2 * (int64_t)sms, p.gt_gy));
-        cg = std::min(cg, panels);
+        int64_t cg = balanced_chunks(p.gt_gy, sms, panels);  // one CTA per SM (128 KB of shared memory)
         p.gt_ppc = cdiv(panels, cg);
         p.gt_gx = (int)cdiv(panels, p.gt_ppc);
     }
@@ -412,19 +443,26 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             Timer t(th, 0, st);
             if (int e = enqueue_sketch(p, A, lda, seed, st)) return e;
         }
-        k_xr_factor<<<1, 512, 0, st>>>(p.Y, (int)p.s, n, p.s, variant, p.W, p.Rs, p.n, p.status);
-        if (launch_ok()) return RXR_ERR_CUDA;
+        {
+            Timer t(th, 6, st);
+            k_xr_factor<<<1, 512, 0, st>>>(p.Y, (int)p.s, n, p.s, variant, p.W, p.Rs, p.n, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        }
     }
     if (cudaMemcpyAsync(p.Racc, p.Rs, (size_t)p.n * p.n * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;
     // step 3: X = A R_s^{-1} into Q, fused with G_1 = X^T X
     {
-        Timer t(th, 1, st);
         // the split Gram covers n <= 128; wider panels keep the FP64 tiled Gram
         if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE && !p.wide) {
-            if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, false, st)) return e;
+            {
+                Timer t(th, 1, st);
+                if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, false, st)) return e;
+            }
+            Timer t(th, 4, st);
             if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
         } else {
+            Timer t(th, 1, st);
             if (int e = enqueue_subst(p, A, lda, p.Rs, variant == RXR_NONE ? 1 : 0, Q, ldq, true,
                                       variant == RXR_NONE, st))
                 return e;
@@ -435,13 +473,19 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         k_factor<<<1, 512, 0, st>>>(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status);
         if (launch_ok()) return RXR_ERR_CUDA;
         const bool last = (pass == passes);
-        Timer t(th, last ? 3 : 2, st);
         // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
         // split path takes that Gram from the tensor cores at FP64 grade
         if (p.prec == RXR_SPLIT_BF16 && !last && !p.wide) {
-            if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, false, false, st)) return e;
+            {
+                Timer t(th, 2, st);
+                if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, false, false, st)) return e;
+            }
+            Timer t(th, 5, st);
             if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
-        } else if (p.prec == RXR_SPLIT_BF16 && last && pass > 1 && p.n <= 64) {
+            continue;
+        }
+        Timer t(th, last ? 3 : 2, st);
+        if (p.prec == RXR_SPLIT_BF16 && last && pass > 1 && p.n <= 64) {
             // the last pass's R_P is within rounding of I: apply its explicit
             // inverse on the tensor cores at FP64 grade
             if (int e = ozaki_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
@@ -490,7 +534,7 @@ int finish_blocking(rxr_handle h, const RxrStatus *d_status, cudaStream_t st)
         h->last_col = h->h_status[2];
     }
     if (h->timing)
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kTimers; ++k)
             if (h->ev_recorded[k]) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, h->ev[k][0], h->ev[k][1]) == cudaSuccess) h->last_ms[k] = ms;
@@ -527,7 +571,7 @@ int rxr_create(rxr_handle *h, int device)
         delete c;
         return RXR_ERR_CUDA;
     }
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kTimers; ++k)
         for (int j = 0; j < 2; ++j) cudaEventCreate(&c->ev[k][j]);
     if (set_kernel_attrs()) {
         cudaFreeHost(c->h_status);
@@ -549,7 +593,7 @@ int rxr_destroy(rxr_handle h)
     if (h->dR) cudaFree(h->dR);
     if (h->eval_buf) cudaFree(h->eval_buf);
     if (h->h_stage) cudaFreeHost(h->h_stage);
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kTimers; ++k)
         for (int j = 0; j < 2; ++j)
             if (h->ev[k][j]) cudaEventDestroy(h->ev[k][j]);
     delete h;
@@ -1092,7 +1136,7 @@ int rxr_fp64_peak(double *tflops, void *stream)
 int rxr_last_kernel_ms(rxr_handle h, int kernel, float *ms)
 {
     if (h == nullptr || ms == nullptr) return -1;
-    if (kernel < 0 || kernel > 3) return -1;
+    if (kernel < 0 || kernel >= kTimers) return -1;
     *ms = h->last_ms[kernel];
     return 0;
 }

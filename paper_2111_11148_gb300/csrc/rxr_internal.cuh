@@ -331,6 +331,7 @@ struct Plan {
 }  // namespace rxr
 
 namespace rxr {
+int64_t balanced_chunks(int64_t gy, int64_t slots, int64_t max_gx);
 // split-precision contractions (split_kernels.cu)
 int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st);
 int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);

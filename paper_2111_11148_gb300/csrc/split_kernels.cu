@@ -967,8 +967,7 @@ int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, c
 {
     const int64_t gy = cdiv64(p.s, kSpM) * cdiv64(p.n, kSpN);
     const int64_t win_total = cdiv64(p.m, kSpWin);
-    int64_t gx = std::max<int64_t>(1, p.sms / gy);
-    gx = std::min(gx, win_total);
+    int64_t gx = balanced_chunks(gy, p.sms, win_total);
     const int64_t wpc = cdiv64(win_total, gx);
     gx = cdiv64(win_total, wpc);
     if (gx > p.sk_gx) return RXR_ERR_NOMEM;  // partial buffer sized by the FP64 plan

@@ -66,21 +66,25 @@ __device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, 
     return true;
 }
 
-// b - sum_{k<j} x[k * xs] r[k * rstride] with four interleaved FMA chains
-// (combined as ((c0 + c1) + (c2 + c3)), a fixed order).
-__device__ __forceinline__ double chain4_dot(const double *x, int xs, const double *r, int rstride, int j, double b)
+// Row-wise substitution x R = b in shared memory with two lanes per row (lane
+// parity h takes the columns k = h mod 2): for each column j both lanes form
+// their partial sums, the pair exchanges them by one shuffle, and the lane
+// that owns column j (j mod 2 = h) writes x_j = (b_j - sum) / R_jj.  Only the
+// owner ever reads x_j again.  x is column-major with leading dimension xs;
+// R is packed by columns (packed = true: column j at j (j + 1) / 2) or square
+// with leading dimension 64.  Every lane of the block must call this.
+__device__ __forceinline__ void pair_substitute(double *x, int xs, const double *r, const double *dinv, int n, int row,
+                                                int h, bool packed)
 {
-    double c0 = b, c1 = 0.0, c2 = 0.0, c3 = 0.0;
-    int k = 0;
-#pragma unroll 2
-    for (; k + 3 < j; k += 4) {
-        c0 = fma(-x[k * xs], r[k * rstride], c0);
-        c1 = fma(-x[(k + 1) * xs], r[(k + 1) * rstride], c1);
-        c2 = fma(-x[(k + 2) * xs], r[(k + 2) * rstride], c2);
-        c3 = fma(-x[(k + 3) * xs], r[(k + 3) * rstride], c3);
+    for (int j = 0; j < n; ++j) {
+        const double *rc = packed ? r + j * (j + 1) / 2 : r + j * 64;
+        const bool owner = (j & 1) == h;
+        double acc = owner ? x[j * xs + row] : 0.0;
+#pragma unroll 4
+        for (int k = h; k < j; k += 2) acc = fma(-x[k * xs + row], rc[k], acc);
+        const double other = __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+        if (owner) x[j * xs + row] = (acc + other) * dinv[j];
     }
-    for (; k < j; ++k) c0 = fma(-x[k * xs], r[k * rstride], c0);
-    return (c0 + c1) + (c2 + c3);
 }
 
 // ---------------------------------------------------------------------------
@@ -341,24 +345,24 @@ __device__ __forceinline__ void subst_gram_body(const CUtensorMap *tmapB, int us
         // substitution, one thread per row: x_j = (b_j - sum_{k<j} x_k R_kj) / R_jj
         // as one FMA chain seeded with b_j (no FP64 operation beyond the
         // n(n-1)/2 FMAs and n multiplications by 1/R_jj)
-        if (!unit_r && threadIdx.x < kSgP) {
-            const int t = threadIdx.x;
+        if (!unit_r) {
             if (n <= 64) {
-                for (int j = 0; j < n; ++j) {
-                    const double *rc = rp + j * (j + 1) / 2;
-                    double accj = xp[j * kSgP + t];
+                // narrow rows run two CTAs per SM: one thread per row, one chain
+                if (threadIdx.x < kSgP) {
+                    const int t = threadIdx.x;
+                    for (int j = 0; j < n; ++j) {
+                        const double *rc = rp + j * (j + 1) / 2;
+                        double accj = xp[j * kSgP + t];
 #pragma unroll 4
-                    for (int k = 0; k < j; ++k) accj = fma(-xp[k * kSgP + t], rc[k], accj);
-                    xp[j * kSgP + t] = accj * dinv[j];
+                        for (int k = 0; k < j; ++k) accj = fma(-xp[k * kSgP + t], rc[k], accj);
+                        xp[j * kSgP + t] = accj * dinv[j];
+                    }
                 }
             } else {
-                // wide rows run one CTA per SM (one warp per scheduler in this
-                // phase): four interleaved chains hide the FMA latency (ncu:
-                // a single chain stalls on the fixed-latency dependency), for
-                // three extra additions per column
-                for (int j = 0; j < n; ++j) {
-                    xp[j * kSgP + t] = chain4_dot(xp + t, kSgP, rp + j * (j + 1) / 2, 1, j, xp[j * kSgP + t]) * dinv[j];
-                }
+                // wide rows fit one CTA per SM; two lanes per row keep two warps
+                // per scheduler busy (ncu: one working warp per scheduler left
+                // the FP64 pipe 27 % idle)
+                pair_substitute(xp, kSgP, rp, dinv, n, threadIdx.x >> 1, threadIdx.x & 1, true);
             }
         }
         __syncthreads();
@@ -504,6 +508,28 @@ __global__ void __launch_bounds__(RXR_THREADS)
 constexpr int kWP = 128;  // rows per panel
 constexpr int kWB = 64;   // column block
 
+// A 128-row x 64-column block of a column-major matrix into shared memory
+// (column-major, leading dimension 128), zeros outside rows < m and columns <
+// ncols; 256 threads, 16 loads in flight per thread.
+__device__ __forceinline__ void load_block_128x64(double *dst, const double *__restrict__ src, int64_t ld, int64_t m,
+                                                  int64_t r0, int c0, int ncols)
+{
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        double v[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = threadIdx.x + 256 * (16 * b + t);
+            const int row = e & 127, col = e >> 7;
+            const int64_t gr = r0 + row;
+            v[t] = (gr < m && c0 + col < ncols) ? src[gr + (int64_t)(c0 + col) * ld] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) dst[threadIdx.x + 256 * (16 * b + t)] = v[t];
+    }
+}
+
+
 __global__ void __launch_bounds__(RXR_THREADS, 1)
     k_subst_wide(const double *__restrict__ src, int64_t lds, int64_t m, int n, const double *__restrict__ R,
                  int64_t ldr, double *dst, int64_t ldd, int64_t panels_total, int64_t panels_per_cta, RxrStatus *st)
@@ -535,11 +561,7 @@ __global__ void __launch_bounds__(RXR_THREADS, 1)
             for (int I = 0; I < J; ++I) {
                 const int cI = I * kWB;
                 __syncthreads();
-                for (int e = tid; e < kWB * kWP; e += blockDim.x) {
-                    const int row = e % kWP, col = e / kWP;
-                    const int64_t gr = r0 + row;
-                    xi[e] = (gr < m) ? dst[gr + (int64_t)(cI + col) * ldd] : 0.0;
-                }
+                load_block_128x64(xi, dst, ldd, m, r0, cI, n);
                 for (int e = tid; e < kWB * kWB; e += blockDim.x) {
                     const int k = e % kWB, c = e / kWB;
                     rb[e] = (c < wJ) ? R[(cI + k) + (int64_t)(cJ + c) * ldr] : 0.0;
@@ -569,10 +591,7 @@ __global__ void __launch_bounds__(RXR_THREADS, 1)
             }
             if (tid < kWB) dv[tid] = (tid < wJ) ? 1.0 / R[(cJ + tid) + (int64_t)(cJ + tid) * ldr] : 0.0;
             __syncthreads();
-            if (tid < kWP) {
-                for (int j = 0; j < wJ; ++j)
-                    ut[j * kWP + tid] = chain4_dot(ut + tid, kWP, rb + j * kWB, 1, j, ut[j * kWP + tid]) * dv[j];
-            }
+            pair_substitute(ut, kWP, rb, dv, wJ, tid >> 1, tid & 1, false);
             __syncthreads();
             for (int e = tid; e < kWB * kWP; e += blockDim.x) {
                 const int row = e % kWP, col = e / kWP;
@@ -612,21 +631,18 @@ __global__ void __launch_bounds__(RXR_THREADS)
     for (int64_t p = p_begin; p < p_end; ++p) {
         const int64_t r0 = p * kWP;
         __syncthreads();
-        for (int e = tid; e < kWB * kWP; e += blockDim.x) {
-            const int row = e % kWP, col = e / kWP;
-            const int64_t gr = r0 + row;
-            xa[e] = (gr < m && cI + col < n) ? X[gr + (int64_t)(cI + col) * ldx] : 0.0;
-            xb[e] = (gr < m && cJ + col < n) ? X[gr + (int64_t)(cJ + col) * ldx] : 0.0;
-        }
+        load_block_128x64(xa, X, ldx, m, r0, cI, n);
+        if (J != I) load_block_128x64(xb, X, ldx, m, r0, cJ, n);
         __syncthreads();
         const int rot = tid & 31;
         for (int i = 0; i < kWP; ++i) {
             const int r = (i + rot) & (kWP - 1);
             double u[4], v[4];
+            const double *xv = (J != I) ? xb : xa;
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 u[a] = xa[(4 * ti + a) * kWP + r];
-                v[a] = xb[(4 * tj + a) * kWP + r];
+                v[a] = xv[(4 * tj + a) * kWP + r];
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
