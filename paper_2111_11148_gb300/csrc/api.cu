@@ -453,14 +453,19 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         return RXR_ERR_CUDA;
     // step 3: X = A R_s^{-1} into Q, fused with G_1 = X^T X
     {
-        // the split Gram covers n <= 128; wider panels keep the FP64 tiled Gram
-        if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE && !p.wide) {
+        // the BF16x3 split Gram covers n <= 128; wider panels take the FP64-grade
+        // tensor-core Gram
+        if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
             {
                 Timer t(th, 1, st);
                 if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, false, st)) return e;
             }
             Timer t(th, 4, st);
-            if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
+            if (p.wide) {
+                if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
+            } else if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) {
+                return e;
+            }
         } else {
             Timer t(th, 1, st);
             if (int e = enqueue_subst(p, A, lda, p.Rs, variant == RXR_NONE ? 1 : 0, Q, ldq, true,
@@ -475,7 +480,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         const bool last = (pass == passes);
         // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
         // split path takes that Gram from the tensor cores at FP64 grade
-        if (p.prec == RXR_SPLIT_BF16 && !last && !p.wide) {
+        if (p.prec == RXR_SPLIT_BF16 && !last) {
             {
                 Timer t(th, 2, st);
                 if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, false, false, st)) return e;
@@ -994,7 +999,7 @@ int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, d
     if (G == nullptr) return -6;
     if (ldg < n) return -7;
     if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -8;
-    if (n > kNarrowN) return RXR_ERR_UNSUPPORTED;
+    if (n > RXR_MAX_N || (n > kNarrowN && prec == RXR_FP64)) return RXR_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     Plan p;
     make_plan(p, m, n, n, prec, h->sms);

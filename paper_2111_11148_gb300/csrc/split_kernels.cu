@@ -519,8 +519,9 @@ constexpr int kOzSub = 64;
 constexpr int kOzM = 128;
 constexpr int kOzN = 64;
 constexpr int kOzDigits = 7;
-constexpr int kOzTile = kOzM * kOzSub * 2;  // 16 KB per digit
-constexpr size_t kOzSmem = (size_t)kOzDigits * kOzTile;
+constexpr int kOzTile = kOzM * kOzSub * 2;   // 16 KB per digit (A operand)
+constexpr int kOzBTile = kOzN * kOzSub * 2;  // 8 KB per digit (separate B operand)
+constexpr size_t kOzSmem = (size_t)kOzDigits * (kOzTile + kOzBTile);
 
 // Seven digits of a 55-bit fixed-point value of x relative to 2^(emax+1),
 // emax = biased exponent of the largest entry of its group: six balanced
@@ -548,17 +549,113 @@ __device__ __forceinline__ void digits7(unsigned long long bits, int emax, float
     dg[0] = (float)T;
 }
 
+// Largest exponent of columns [c0, c0 + ncol) of X over the window rows, one
+// warp per column, into ex[0..ncol).
+__device__ __forceinline__ void window_colexp(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t wr0,
+                                              int c0, int ncol, int *ex)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int col = warp; col < ncol; col += 8) {
+        unsigned e = 0;
+        if (c0 + col < n) {
+            unsigned hv[kOzWin / 32];
+#pragma unroll
+            for (int t = 0; t < kOzWin / 32; ++t) {
+                const int64_t gr = wr0 + lane + 32 * t;
+                hv[t] = (gr < m) ? (unsigned)__double2hiint(X[gr + (int64_t)(c0 + col) * ldx]) : 0u;
+            }
+#pragma unroll
+            for (int t = 0; t < kOzWin / 32; ++t) e = max(e, (hv[t] >> 20) & 0x7FFu);
+        }
+        e = __reduce_max_sync(0xFFFFFFFFu, e);
+        if (lane == 0) ex[col] = (int)e;
+    }
+}
+
+// Digits of columns [c0, c0 + ncol) of a 64-row tile into `ncol`-row operand
+// tiles (one per digit, `tile_bytes` apart), 16 loads in flight per thread.
+__device__ __forceinline__ void tile_digits(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t r0, int c0,
+                                            int ncol, const int *ex, unsigned char *dst, int tile_bytes)
+{
+    const int tid = threadIdx.x;
+    const int iters = (kOzSub * ncol + 255) / 256;
+    for (int base = 0; base < iters; base += 16) {
+        unsigned long long vb[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 256 * (base + t);
+            const int k = e & (kOzSub - 1), j = e >> 6;
+            const int64_t gr = r0 + k;
+            vb[t] = (base + t < iters && j < ncol && c0 + j < n && gr < m)
+                        ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)(c0 + j) * ldx])
+                        : 0ull;
+        }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int e = tid + 256 * (base + t);
+            const int k = e & (kOzSub - 1), j = e >> 6;
+            if (base + t < iters && j < ncol) {
+                float dg[kOzDigits];
+                digits7(vb[t], ex[j], dg);
+                const int off = kmaj_off(j, k);
+#pragma unroll
+                for (int q = 0; q < kOzDigits; ++q) st_bf16(dst + q * tile_bytes, off, dg[q]);
+            }
+        }
+    }
+}
+
+// Output block list: block b covers rows [128 I, 128 I + 128) and columns
+// [64 J, 64 J + 64) of G, for the pairs that meet the upper triangle.
+__host__ __device__ inline int ozaki_blocks(int n)
+{
+    const int nI = (n + kOzM - 1) / kOzM, nJ = (n + kOzN - 1) / kOzN;
+    int cnt = 0;
+    for (int I = 0; I < nI; ++I)
+        for (int J = 0; J < nJ; ++J)
+            if (kOzN * J + kOzN - 1 >= kOzM * I) ++cnt;
+    return cnt;
+}
+
+__device__ __forceinline__ void ozaki_block(int n, int b, int &I, int &J)
+{
+    const int nI = (n + kOzM - 1) / kOzM, nJ = (n + kOzN - 1) / kOzN;
+    for (I = 0; I < nI; ++I)
+        for (J = 0; J < nJ; ++J)
+            if (kOzN * J + kOzN - 1 >= kOzM * I && b-- == 0) return;
+}
+
+// ---------------------------------------------------------------------------
+// FP64-grade Gram on the tensor cores (Ozaki-style exact splitting): for each
+// 128-row window, column j of X is written in fixed point relative to 2^(e_j+1)
+// as seven 8-bit digits (the same digits as the split sketch's A).  The
+// ordered digit pairs (p, q), p + q <= 6, accumulate into seven tensor-memory
+// groups d = p + q; a group holds at most seven pairs of products below 2^14
+// over 128 rows, so every sum stays below 2^24 and the FP32 accumulation is
+// exact.  Per window the groups are combined (weights 2^-8d) and added in FP64
+// with the scale 2^(e_j + e_l).  The result is X^T X to about 2^-53 of
+// |X|^T |X| column-normwise: it serves the CholeskyQR passes that must be
+// FP64-accurate.  grid.y = output blocks of 128 rows x 64 columns of G meeting
+// the upper triangle; the B operand is a view into the A digits when its
+// columns lie inside the block's rows, else digits of its own.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 1)
     k_gram_ozaki(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t win_total, int64_t win_per_cta,
                  double *__restrict__ Gpart, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *aop = smem;
+    unsigned char *bsep = smem + kOzDigits * kOzTile;
     __shared__ __align__(8) uint64_t mma_bar;
     __shared__ uint32_t tmem_base;
-    __shared__ int colexp[kOzM];
+    __shared__ int exA[kOzM];
+    __shared__ int exB[kOzN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int c0 = blockIdx.y * kOzN;
+    int bI, bJ;
+    ozaki_block(n, blockIdx.y, bI, bJ);
+    const int a0c = bI * kOzM, b0c = bJ * kOzN;
+    const bool b_inside = (b0c >= a0c) && (b0c + kOzN <= a0c + kOzM);
 
     for (int e = tid; e < (int)(kOzSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
@@ -572,7 +669,7 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = idesc_bf16(kOzM, kOzN);
     const int q4 = warp & 3, half = warp >> 2;
-    const int my_row = 32 * q4 + lane;  // row j of G
+    const int my_row = 32 * q4 + lane;  // row a0c + my_row of G
     double acc[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = 0.0;
@@ -583,22 +680,8 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t w_end = min(win_total, w_begin + win_per_cta);
     for (int64_t w = w_begin; w < w_end && ok; ++w) {
         const int64_t wr0 = w * kOzWin;
-        // largest exponent of every column in the window: one warp per column
-        for (int col = warp; col < kOzM; col += 8) {
-            unsigned ex = 0;
-            if (col < n) {
-                unsigned hv[kOzWin / 32];
-#pragma unroll
-                for (int t = 0; t < kOzWin / 32; ++t) {
-                    const int64_t gr = wr0 + lane + 32 * t;
-                    hv[t] = (gr < m) ? (unsigned)__double2hiint(X[gr + (int64_t)col * ldx]) : 0u;
-                }
-#pragma unroll
-                for (int t = 0; t < kOzWin / 32; ++t) ex = max(ex, (hv[t] >> 20) & 0x7FFu);
-            }
-            ex = __reduce_max_sync(0xFFFFFFFFu, ex);
-            if (lane == 0) colexp[col] = (int)ex;
-        }
+        window_colexp(X, ldx, m, n, wr0, a0c, kOzM, exA);
+        if (!b_inside) window_colexp(X, ldx, m, n, wr0, b0c, kOzN, exB);
         __syncthreads();
         for (int sp = 0; sp < kOzWin / kOzSub; ++sp) {
             const int64_t r0 = wr0 + sp * kOzSub;
@@ -608,37 +691,15 @@ __global__ void __launch_bounds__(256, 1)
                 phase ^= 1u;
                 pending = false;
             }
-            // digits of every entry of the 64-row tile (n columns), 16 loads in flight
-            const int iters = (kOzSub * n + 255) / 256;
-            for (int base = 0; base < iters; base += 16) {
-                unsigned long long vb[16];
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int e = tid + 256 * (base + t);
-                    const int k = e & (kOzSub - 1), j = e >> 6;
-                    const int64_t gr = r0 + k;
-                    vb[t] = (j < n && gr < m && base + t < iters)
-                                ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)j * ldx])
-                                : 0ull;
-                }
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int e = tid + 256 * (base + t);
-                    const int k = e & (kOzSub - 1), j = e >> 6;
-                    if (j < n && base + t < iters) {
-                        float dg[kOzDigits];
-                        digits7(vb[t], colexp[j], dg);
-                        const int off = kmaj_off(j, k);
-#pragma unroll
-                        for (int q = 0; q < kOzDigits; ++q) st_bf16(smem + q * kOzTile, off, dg[q]);
-                    }
-                }
-            }
+            tile_digits(X, ldx, m, n, r0, a0c, kOzM, exA, aop, kOzTile);
+            if (!b_inside) tile_digits(X, ldx, m, n, r0, b0c, kOzN, exB, bsep, kOzBTile);
             fence_proxy_async_shared();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                const uint32_t b0 = smem_u32(smem);
+                const uint32_t a0 = smem_u32(aop);
+                const uint32_t bb = b_inside ? a0 + ((b0c - a0c) / 8) * 1024 : smem_u32(bsep);
+                const uint32_t bstride = b_inside ? kOzTile : kOzBTile;
 #pragma unroll
                 for (int kk = 0; kk < kOzSub / 16; ++kk)
 #pragma unroll
@@ -646,8 +707,8 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                         for (int q = 0; p + q < kOzDigits; ++q) {
                             const uint32_t acc_on = (sp > 0 || kk > 0 || p > 0) ? 1u : 0u;
-                            tc_mma(tmem + (uint32_t)((p + q) * kOzN), smem_desc(b0 + p * kOzTile + kk * 256, 128, 1024),
-                                   smem_desc(b0 + q * kOzTile + (c0 / 8) * 1024 + kk * 256, 128, 1024), idesc, acc_on);
+                            tc_mma(tmem + (uint32_t)((p + q) * kOzN), smem_desc(a0 + p * kOzTile + kk * 256, 128, 1024),
+                                   smem_desc(bb + q * bstride + kk * 256, 128, 1024), idesc, acc_on);
                         }
                 tc_commit(&mma_bar);
             }
@@ -659,7 +720,7 @@ __global__ void __launch_bounds__(256, 1)
         phase ^= 1u;
         pending = false;
         tc_fence_after();
-        const int ej = colexp[min(my_row, kOzM - 1)];
+        const int ej = exA[my_row];
 #pragma unroll
         for (int c16 = 0; c16 < 2; ++c16) {
             const int col0 = half * 32 + c16 * 16;
@@ -683,7 +744,8 @@ __global__ void __launch_bounds__(256, 1)
             }
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
-                const int el = colexp[min(c0 + col0 + t, kOzM - 1)];
+                const int lc = col0 + t;  // column b0c + lc of G
+                const int el = b_inside ? exA[b0c - a0c + lc] : exB[lc];
                 const int be = ej + el - 1035;  // biased exponent of 2^(e_j + e_l - 2058)
                 const double scale = (ej > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
                 const double val = rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
@@ -697,12 +759,13 @@ __global__ void __launch_bounds__(256, 1)
         mma_wait(&mma_bar, phase, st);
         tc_fence_after();
     }
-    if (ok && my_row < n) {
+    const int gr = a0c + my_row;
+    if (ok && gr < n) {
         double *out = Gpart + (int64_t)blockIdx.x * n * n;
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
-            const int c = c0 + half * 32 + t;
-            if (c < n && my_row <= c) out[my_row + (int64_t)c * n] = acc[t];
+            const int c = b0c + half * 32 + t;
+            if (c < n && gr <= c) out[gr + (int64_t)c * n] = acc[t];
         }
     }
     tc_fence_before();
@@ -908,8 +971,7 @@ static inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // sketch's partial buffer, which is larger).
 static int64_t ozaki_chunks(int64_t m, int64_t n, int sms)
 {
-    const int64_t gy = cdiv64(n, kOzN);
-    return std::max<int64_t>(1, std::min<int64_t>(cdiv64(m, kOzWin), sms / gy));
+    return balanced_chunks(ozaki_blocks((int)n), sms, cdiv64(m, kOzWin));
 }
 
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
@@ -936,12 +998,12 @@ int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaSt
 
 int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
 {
-    if (p.n > kOzM) return RXR_ERR_UNSUPPORTED;
+    if (p.n > RXR_MAX_N) return RXR_ERR_UNSUPPORTED;
     const int64_t win_total = cdiv64(p.m, kOzWin);
     int64_t gx = ozaki_chunks(p.m, p.n, p.sms);
     const int64_t wpc = cdiv64(win_total, gx);
     gx = cdiv64(win_total, wpc);
-    const int gy = (int)cdiv64(p.n, kOzN);
+    const int gy = ozaki_blocks((int)p.n);
     double *parts = reinterpret_cast<double *>(p.split);
     k_gram_ozaki<<<dim3((unsigned)gx, gy), 256, kOzSmem, st>>>(X, ldx, p.m, (int)p.n, win_total, wpc, parts, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;

@@ -84,16 +84,17 @@ def test_split_matches_fp64_factorisation(h):
 
 
 @pytest.mark.parametrize("m,n,kappa", [(1, 1, 1.0), (700, 8, 1e2), (5000, 64, 1e6), (3000, 100, 1e12), (2100, 128, 1e3),
-                                       (129, 65, 1e15)])
+                                       (129, 65, 1e15), (700, 200, 1e8), (600, 512, 1e3)])
 def test_ozaki_gram_is_fp64_grade(h, m, n, kappa):
     # exact 7-digit splitting: G = X^T X to FP64 accuracy, entrywise within the
     # FP64 Gram bound plus the digit truncation 2^-54 * colmax_j * colmax_l * m
     X = usv_matrix(m, n, kappa, seed=m)
     Gs = to_host(h.gram(to_dev(X), prec="split"))
-    Gf = to_host(h.gram(to_dev(X), prec="fp64"))
     Go = o.gram(X)
     cm = np.abs(X).max(axis=0)
     bound = 8 * (m + 2) * U * (np.abs(X).T @ np.abs(X)) + 2.0**-52 * m * np.outer(cm, cm)
     assert np.all(np.abs(Gs - Go) <= bound), np.max(np.abs(Gs - Go) / bound)
-    assert np.all(np.abs(Gf - Go) <= 8 * (m + 2) * U * (np.abs(X).T @ np.abs(X)))
+    if n <= 128:
+        Gf = to_host(h.gram(to_dev(X), prec="fp64"))
+        assert np.all(np.abs(Gf - Go) <= 8 * (m + 2) * U * (np.abs(X).T @ np.abs(X)))
     assert np.array_equal(Gs, Gs.T)
