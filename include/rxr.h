@@ -182,10 +182,12 @@ RXR_API int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int6
 RXR_API int rxr_xr_factor(rxr_handle h, const double *Y, int64_t s, int64_t n, int64_t ldy, int variant, double *Rs,
                   int64_t ldrs, void *stream);
 
-/* X = A R^{-1} by row-wise substitution and G = X^T X (full symmetric n x n,
- * leading dimension ldg >= n), step 3.  X may alias A (ldx == lda); X == NULL
- * computes G only.  prec selects the Gram's arithmetic (the substitution is
- * always FP64). */
+/* X = A R^{-1} and G = X^T X (full symmetric n x n, leading dimension
+ * ldg >= n), step 3.  X may alias A (ldx == lda); X == NULL computes G only
+ * (RXR_FP64).  RXR_FP64: row-wise FP64 substitution fused with the FP64 Gram.
+ * RXR_SPLIT_BF16: right-looking blocked substitution (FP64 diagonal blocks,
+ * trailing updates on the tensor cores at FP64 grade: normwise backward
+ * stable) and the tensor-core Gram (BF16x3 for n <= 128, exact digits above). */
 RXR_API int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *R,
                      int64_t ldr, double *X, int64_t ldx, double *G, int64_t ldg, int prec, void *stream);
 

@@ -458,7 +458,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
             {
                 Timer t(th, 1, st);
-                if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, false, st)) return e;
+                if (int e = blocked_subst_enqueue(const_cast<Plan &>(p), A, lda, p.Rs, p.n, Q, ldq, st)) return e;
             }
             Timer t(th, 4, st);
             if (p.wide) {
@@ -483,7 +483,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         if (p.prec == RXR_SPLIT_BF16 && !last) {
             {
                 Timer t(th, 2, st);
-                if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, false, false, st)) return e;
+                if (int e = blocked_subst_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, p.n, Q, ldq, st)) return e;
             }
             Timer t(th, 5, st);
             if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
@@ -494,6 +494,8 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             // the last pass's R_P is within rounding of I: apply its explicit
             // inverse on the tensor cores at FP64 grade
             if (int e = ozaki_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
+        } else if (p.prec == RXR_SPLIT_BF16) {
+            if (int e = blocked_subst_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, p.n, Q, ldq, st)) return e;
         } else if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) {
             return e;
         }
@@ -976,10 +978,10 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
     // R may have any leading dimension: copy it to the packed n x n buffer
     if (cudaMemcpy2DAsync(p.Rp, n * 8, R, ldr * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;
-    if (prec == RXR_SPLIT_BF16 && !p.wide) {
+    if (prec == RXR_SPLIT_BF16) {
         if (X == nullptr) return RXR_ERR_UNSUPPORTED;
-        if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, false, false, st)) return e;
-        if (int e = split_gram_enqueue(p, X, ldx, st)) return e;
+        if (int e = blocked_subst_enqueue(p, A, lda, p.Rp, p.n, X, ldx, st)) return e;
+        if (int e = p.wide ? ozaki_gram_enqueue(p, X, ldx, st) : split_gram_enqueue(p, X, ldx, st)) return e;
     } else {
         if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, true, false, st)) return e;
     }

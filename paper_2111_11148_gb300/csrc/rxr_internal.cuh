@@ -337,5 +337,7 @@ int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, c
 int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
 int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);
+int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
+                          int64_t ldx, cudaStream_t st);
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
 }  // namespace rxr

@@ -943,6 +943,214 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// ---------------------------------------------------------------------------
+// Trailing update of the blocked substitution, on the tensor cores at FP64
+// grade:  C[:, tc0 : tc0 + N) = B[:, tc0 : tc0 + N) - X[:, xc0 : xc0 + K) R[xc0 : xc0 + K, tc0 : tc0 + N)
+// (B = nullptr: C = + X R-block).  X rows are split relative to their own
+// largest exponent over the K entries, R's block columns relative to theirs,
+// seven 8-bit digits each; K <= 64 keeps every group's integer sum below 2^24
+// (exact).  grid.x = 128-row tiles, grid.y = 64-column tiles of the trailing
+// block.  X's columns are disjoint from C's, so C may alias B and X's matrix.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 1)
+    k_update_ozaki(const double *X, int64_t ldx, int xc0, int K, const double *__restrict__ R, int64_t ldr, int tc0,
+                   int N, const double *B, int64_t ldb, double *C, int64_t ldc, int64_t m, int64_t tiles_total,
+                   int64_t tiles_per_cta, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *aop = smem;
+    unsigned char *bop = smem + kApDigits * kApATile;
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int rowexp[kApM];
+    __shared__ int colexp_t[kApN];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.y * kApN;             // this CTA's columns [tc0 + n0, tc0 + n0 + nw)
+    const int nw = min(kApN, N - n0);
+    const int ksteps = (K + 15) / 16;
+
+    for (int e = tid; e < (int)(kApSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        fence_barrier_init();
+    }
+    // digits of the R block: B tile element (l, k) = R[xc0 + k][tc0 + n0 + l]
+    if (tid < kApN) {
+        unsigned ex = 0;
+        if (tid < nw)
+            for (int k = 0; k < K; ++k)
+                ex = max(ex, ((unsigned)__double2hiint(R[(xc0 + k) + (int64_t)(tc0 + n0 + tid) * ldr]) >> 20) & 0x7FFu);
+        colexp_t[tid] = (int)ex;
+    }
+    __syncthreads();
+    for (int e = tid; e < K * nw; e += blockDim.x) {
+        const int k = e % K, l = e / K;
+        const unsigned long long bits =
+            (unsigned long long)__double_as_longlong(R[(xc0 + k) + (int64_t)(tc0 + n0 + l) * ldr]);
+        float dg[kApDigits];
+        digits7(bits, colexp_t[l], dg);
+        const int off = kmaj_off(l, k);
+#pragma unroll
+        for (int q = 0; q < kApDigits; ++q) st_bf16(bop + q * kApBTile, off, dg[q]);
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16(kApM, kApN);
+    const int q4 = warp & 3, half = warp >> 2;
+    const int my_row = 32 * q4 + lane;
+
+    uint32_t phase = 0;
+    bool pending = false, ok = true;
+    const int64_t t_begin = blockIdx.x * tiles_per_cta;
+    const int64_t t_end = min(tiles_total, t_begin + tiles_per_cta);
+    for (int64_t tile = t_begin; tile < t_end && ok; ++tile) {
+        const int64_t r0 = tile * kApM;
+        if (tid < kApM) {
+            unsigned ex = 0;
+            const int64_t gr = r0 + tid;
+            if (gr < m)
+                for (int k = 0; k < K; ++k)
+                    ex = max(ex, ((unsigned)__double2hiint(X[gr + (int64_t)(xc0 + k) * ldx]) >> 20) & 0x7FFu);
+            rowexp[tid] = (int)ex;
+        }
+        __syncthreads();
+        const int iters = (kApM * K + 255) / 256;
+        for (int base = 0; base < iters; base += 16) {
+            unsigned long long vb[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int e = tid + 256 * (base + t);
+                const int i = e & (kApM - 1), k = e >> 7;
+                const int64_t gr = r0 + i;
+                vb[t] = (base + t < iters && k < K && gr < m)
+                            ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)(xc0 + k) * ldx])
+                            : 0ull;
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int e = tid + 256 * (base + t);
+                const int i = e & (kApM - 1), k = e >> 7;
+                if (base + t < iters && k < K) {
+                    float dg[kApDigits];
+                    digits7(vb[t], rowexp[i], dg);
+                    const int off = kmaj_off(i, k);
+#pragma unroll
+                    for (int q = 0; q < kApDigits; ++q) st_bf16(aop + q * kApATile, off, dg[q]);
+                }
+            }
+        }
+        fence_proxy_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(aop), b0 = smem_u32(bop);
+            for (int kk = 0; kk < ksteps; ++kk)
+#pragma unroll
+                for (int p = 0; p < kApDigits; ++p)
+#pragma unroll
+                    for (int q = 0; p + q < kApDigits; ++q) {
+                        const uint32_t acc_on = (kk > 0 || p > 0) ? 1u : 0u;
+                        tc_mma(tmem + (uint32_t)((p + q) * kApN), smem_desc(a0 + p * kApATile + kk * 256, 128, 1024),
+                               smem_desc(b0 + q * kApBTile + kk * 256, 128, 1024), idesc, acc_on);
+                    }
+            tc_commit(&mma_bar);
+        }
+        pending = true;
+        ok = mma_wait(&mma_bar, phase, st);
+        if (!ok) break;
+        phase ^= 1u;
+        pending = false;
+        tc_fence_after();
+        const int ei = rowexp[my_row];
+        const int64_t gr = r0 + my_row;
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+            const int col0 = half * 32 + c16 * 16;
+            if (col0 >= nw) continue;  // warp-uniform
+            float hi[16], lo[16], v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) lo[t] = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kApDigits; ++d) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + d * kApN + col0, v);
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float x = __fmul_rn(v[t], w8);
+                    const float sum = __fadd_rn(hi[t], x);
+                    const float bb = __fsub_rn(sum, hi[t]);
+                    const float err = __fadd_rn(__fsub_rn(hi[t], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                    hi[t] = sum;
+                    lo[t] = __fadd_rn(lo[t], err);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int l = col0 + t;
+                if (l < nw && gr < m) {
+                    const int el = colexp_t[l];
+                    const int be = ei + el - 1035;
+                    const double scale = (ei > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
+                    const double prod = (rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t])) * scale;
+                    const int64_t cc = tc0 + n0 + l;
+                    C[gr + cc * ldc] = B ? B[gr + cc * ldb] - prod : prod;
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (pending) {
+        mma_wait(&mma_bar, phase, st);
+        tc_fence_after();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// Diagonal block of the blocked substitution, FP64:
+//   X[:, c0 : c0 + b) = B[:, c0 : c0 + b) R[c0 : c0 + b, c0 : c0 + b)^{-1}
+// 256-row tiles, one thread per row, the tile's b columns in shared memory
+// (column-major), the block of R packed and 1 / R_jj in shared memory.  X may
+// alias B.
+constexpr int kSbRows = 256;
+
+__global__ void __launch_bounds__(256)
+    k_solve_block(const double *B, int64_t ldb, double *X, int64_t ldx, const double *__restrict__ R, int64_t ldr,
+                  int c0, int b, int64_t m, int64_t tiles_total, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *xs = reinterpret_cast<double *>(smem_raw);  // [b][kSbRows]
+    double *rb = xs + (int64_t)b * kSbRows;              // packed upper block of R
+    double *dv = rb + b * (b + 1) / 2;
+    const int t = threadIdx.x;
+    for (int j = 0; j < b; ++j)
+        for (int k = t; k <= j; k += blockDim.x) rb[j * (j + 1) / 2 + k] = R[(c0 + k) + (int64_t)(c0 + j) * ldr];
+    for (int j = t; j < b; j += blockDim.x) dv[j] = 1.0 / R[(c0 + j) + (int64_t)(c0 + j) * ldr];
+    for (int64_t tile = blockIdx.x; tile < tiles_total; tile += gridDim.x) {
+        const int64_t i = tile * kSbRows + t;
+        __syncthreads();
+        for (int j = 0; j < b; ++j) xs[j * kSbRows + t] = (i < m) ? B[i + (int64_t)(c0 + j) * ldb] : 0.0;
+        __syncthreads();
+        for (int j = 0; j < b; ++j) {
+            const double *rc = rb + j * (j + 1) / 2;
+            double acc = xs[j * kSbRows + t];
+#pragma unroll 4
+            for (int k = 0; k < j; ++k) acc = fma(-xs[k * kSbRows + t], rc[k], acc);
+            xs[j * kSbRows + t] = acc * dv[j];
+        }
+        if (i < m)
+            for (int j = 0; j < b; ++j) X[i + (int64_t)(c0 + j) * ldx] = xs[j * kSbRows + t];
+    }
+}
+
 // T = R^{-1} for upper-triangular R (one CTA; thread c solves R t = e_c by back
 // substitution).
 __global__ void k_tri_inverse(const double *__restrict__ R, int n, int64_t ldr, double *__restrict__ T, RxrStatus *st)
@@ -996,6 +1204,39 @@ int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaSt
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
+// X = B R^{-1} by right-looking column blocks of width bw: FP64 substitution of
+// each diagonal block, trailing updates on the tensor cores (FP64 grade).
+int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
+                          int64_t ldx, cudaStream_t st)
+{
+    const int n = (int)p.n;
+    const int bw = (n <= 64) ? 16 : (n <= 128 ? 32 : 64);
+    const int64_t tiles = cdiv64(p.m, kApM);
+    const int64_t stiles = cdiv64(p.m, kSbRows);
+    for (int c0 = 0; c0 < n; c0 += bw) {
+        const int b = std::min(bw, n - c0);
+        const double *src = (c0 == 0) ? Bsrc : X;
+        const int64_t lds = (c0 == 0) ? ldb : ldx;
+        const size_t smem = ((size_t)b * kSbRows + b * (b + 1) / 2 + b) * sizeof(double);
+        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / smem));
+        const int sblocks = (int)std::min<int64_t>(stiles, (int64_t)p.sms * per_sm);
+        k_solve_block<<<sblocks, 256, smem, st>>>(src, lds, X, ldx, R, ldr, c0, b, p.m, stiles, p.status);
+        if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+        const int tc0 = c0 + b, N = n - tc0;
+        if (N <= 0) break;
+        const int gy = (int)cdiv64(N, kApN);
+        int64_t gx = balanced_chunks(gy, p.sms, tiles);
+        const int64_t tpc = cdiv64(tiles, gx);
+        gx = cdiv64(tiles, tpc);
+        // the first trailing update reads B (= A) and writes X; later ones work in X
+        k_update_ozaki<<<dim3((unsigned)gx, (unsigned)gy), 256, kApSmem, st>>>(
+            X, ldx, c0, b, R, ldr, tc0, N, (c0 == 0) ? Bsrc : X, (c0 == 0) ? ldb : ldx, X, ldx, p.m, tiles, tpc,
+            p.status);
+        if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    }
+    return 0;
+}
+
 int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
 {
     if (p.n > RXR_MAX_N) return RXR_ERR_UNSUPPORTED;
@@ -1022,6 +1263,10 @@ cudaError_t set_split_smem()
         e = cudaFuncSetAttribute(k_gram_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return e;
 }
 

@@ -98,3 +98,20 @@ def test_ozaki_gram_is_fp64_grade(h, m, n, kappa):
         Gf = to_host(h.gram(to_dev(X), prec="fp64"))
         assert np.all(np.abs(Gf - Go) <= 8 * (m + 2) * U * (np.abs(X).T @ np.abs(X)))
     assert np.array_equal(Gs, Gs.T)
+
+
+@pytest.mark.parametrize("m,n,kappa", [(3000, 64, 1e12), (1000, 17, 1e6), (2500, 128, 1e15), (900, 200, 1e10),
+                                       (700, 512, 1e8), (129, 33, 1e3)])
+def test_blocked_substitution_is_backward_stable(h, m, n, kappa):
+    # split mode solves X R = A by column blocks (FP64 diagonal blocks, tensor-core
+    # trailing updates): the backward error ||X R - A|| / (||X|| ||R||) must stay
+    # at FP64 rounding level however ill-conditioned R is
+    A = usv_matrix(m, n, kappa, seed=n + 1)
+    R = o.rxr_cholqr(A, o.VARIANT_QR, 2 * n, seed=3, passes=1).Rs    # cond(R) ~ kappa
+    X, G = h.precond_gram(to_dev(A), to_dev(R), prec="split")
+    Xg = to_host(X)
+    back = np.linalg.norm(Xg @ R - A) / (np.linalg.norm(Xg) * np.linalg.norm(R))
+    assert back <= 64 * n * U, back
+    Xo = o.trsm_right_upper(A, R)
+    back_o = np.linalg.norm(Xo @ R - A) / (np.linalg.norm(Xo) * np.linalg.norm(R))
+    assert back <= 64 * max(back_o, n * U)
