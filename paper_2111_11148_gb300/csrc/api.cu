@@ -410,6 +410,17 @@ int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, c
     return launch_ok();
 }
 
+// Split-path substitution X = B R^{-1}: up to n = 64 one FP64 pass at ~94 % of
+// the FP64 peak beats four diagonal solves plus three small tensor-core updates
+// (measured 14.6 vs 17.9 ms at m = 2^22); wider panels take the blocked form
+// (n = 128: 125 -> 81 ms at m = 2^23; n = 512: 241 -> 88 ms at m = 2^20).
+int split_subst(const Plan &p, const double *src, int64_t lds, const double *R, double *dst, int64_t ldd,
+                cudaStream_t st)
+{
+    if (p.n <= 64) return enqueue_subst(p, src, lds, R, 0, dst, ldd, false, false, st);
+    return blocked_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
+}
+
 struct Timer {
     rxr_handle h;
     int id;
@@ -458,7 +469,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
             {
                 Timer t(th, 1, st);
-                if (int e = blocked_subst_enqueue(const_cast<Plan &>(p), A, lda, p.Rs, p.n, Q, ldq, st)) return e;
+                if (int e = split_subst(p, A, lda, p.Rs, Q, ldq, st)) return e;
             }
             Timer t(th, 4, st);
             if (p.wide) {
@@ -483,7 +494,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         if (p.prec == RXR_SPLIT_BF16 && !last) {
             {
                 Timer t(th, 2, st);
-                if (int e = blocked_subst_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, p.n, Q, ldq, st)) return e;
+                if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st)) return e;
             }
             Timer t(th, 5, st);
             if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
@@ -495,7 +506,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             // inverse on the tensor cores at FP64 grade
             if (int e = ozaki_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
         } else if (p.prec == RXR_SPLIT_BF16) {
-            if (int e = blocked_subst_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, p.n, Q, ldq, st)) return e;
+            if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st)) return e;
         } else if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) {
             return e;
         }
