@@ -150,6 +150,12 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 }  // namespace
 
 namespace rxr {
+bool encode_tile_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     int box_cols)
+{
+    return encode_2d(map, ptr, rows, cols, ld, box_rows, box_cols);
+}
+
 // Row chunks for a grid of gx x gy CTAs on `slots` resident CTA slots: the gx
 // (at most max_gx) whose last wave is fullest, preferring fewer chunks, so a
 // grid that overflows one wave by a few CTAs does not pay a second full wave.
@@ -410,14 +416,13 @@ int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, c
     return launch_ok();
 }
 
-// Split-path substitution X = B R^{-1}: up to n = 64 one FP64 pass at ~94 % of
-// the FP64 peak beats four diagonal solves plus three small tensor-core updates
-// (measured 14.6 vs 17.9 ms at m = 2^22); wider panels take the blocked form
-// (n = 128: 125 -> 81 ms at m = 2^23; n = 512: 241 -> 88 ms at m = 2^20).
+// Split-path substitution X = B R^{-1}: up to n = 64 one fused pass (FP64
+// diagonal blocks and tensor-core trailing updates on tiles held in shared
+// memory); wider panels take the column-blocked form, one launch per block.
 int split_subst(const Plan &p, const double *src, int64_t lds, const double *R, double *dst, int64_t ldd,
                 cudaStream_t st)
 {
-    if (p.n <= 64) return enqueue_subst(p, src, lds, R, 0, dst, ldd, false, false, st);
+    if (p.n <= 64) return fused_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
     return blocked_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
 }
 
@@ -991,7 +996,7 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
         return RXR_ERR_CUDA;
     if (prec == RXR_SPLIT_BF16) {
         if (X == nullptr) return RXR_ERR_UNSUPPORTED;
-        if (int e = blocked_subst_enqueue(p, A, lda, p.Rp, p.n, X, ldx, st)) return e;
+        if (int e = split_subst(p, A, lda, p.Rp, X, ldx, st)) return e;
         if (int e = p.wide ? ozaki_gram_enqueue(p, X, ldx, st) : split_gram_enqueue(p, X, ldx, st)) return e;
     } else {
         if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, true, false, st)) return e;

@@ -233,6 +233,21 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m
         : "memory");
 }
 
+// 2-D tiled TMA store of a shared-memory box to element coordinates (x = row,
+// y = column); rows past the tensor's extent are not written.  Completion is
+// tracked by the issuing thread's bulk async-group.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *smem_src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)map),
+                 "r"(x), "r"(y), "r"(smem_u32(smem_src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of every committed store have been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Block-wide helpers
 // ---------------------------------------------------------------------------
@@ -339,5 +354,11 @@ int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);
 int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                           int64_t ldx, cudaStream_t st);
+int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
+                        int64_t ldx, cudaStream_t st);
+// 2-D tensor map of a column-major FP64 matrix (api.cu); false where TMA's
+// alignment rules are not met
+bool encode_tile_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     int box_cols);
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
 }  // namespace rxr

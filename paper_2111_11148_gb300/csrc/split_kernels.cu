@@ -1151,6 +1151,365 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused blocked substitution X = B R^{-1} for n <= 64, one pass over B.
+// The CTA runs two independent groups of four warps; each group walks its own
+// stream of 128-row tiles of B (TMA load into the group's shared-memory tile,
+// TMA store back), so that one group's loads, tensor-core waits and epilogues
+// overlap the other group's FP64 work and every scheduler holds two warps
+// issuing FP64.  A tile is solved in shared memory by column blocks of 16:
+//   * the diagonal block by FP64 row substitution, one thread per row,
+//     right-looking inside the block (for every column the same FMA sequence
+//     as the plain substitution: seeded with b_j, k ascending, times 1/R_jj);
+//   * the trailing columns receive -X_blk R_blk from the tensor cores at FP64
+//     grade: each row of X_blk is written as seven 8-bit digits relative to its
+//     own largest exponent, each column of R_blk relative to its own, and the
+//     digit pairs p + q = d accumulate in tensor-memory group d (K = 16:
+//     every group sum is an integer below 2^24, exact in FP32); each output
+//     combines its seven groups once and is subtracted in FP64.
+// The same thread owns a row in the solve and in the epilogue (tensor-memory
+// lane = row), so a tile's rows never cross threads.  dst may equal src: a
+// tile is read completely before it is written, and only by its own group.
+// ---------------------------------------------------------------------------
+constexpr int kFuM = 128, kFuBw = 16, kFuMaxN = 64, kFuDigits = 7;
+constexpr int kFuATile = kFuM * kFuBw * 2;  // bytes of one digit plane of X_blk (4 KB)
+constexpr int kFuChunk = 32;                // trailing columns per tensor-core round
+constexpr int kFuGroupTmem = 256;           // tensor-memory columns per warp group (7 x 32 used)
+
+__host__ __device__ inline int fu_blocks(int n) { return (n + kFuBw - 1) / kFuBw; }
+// trailing columns after block c, padded to the MMA's N granularity (16)
+__host__ __device__ inline int fu_npad(int n, int c)
+{
+    const int N = n - kFuBw * (c + 1);
+    return N > 0 ? (N + 15) & ~15 : 0;
+}
+// byte offset of block c's R digits, and its first column-exponent slot
+__host__ __device__ inline int fu_bdig_off(int n, int c)
+{
+    int off = 0;
+    for (int q = 0; q < c; ++q) off += kFuDigits * fu_npad(n, q) * kFuBw * 2;
+    return off;
+}
+__host__ __device__ inline int fu_cbase(int n, int c)
+{
+    int off = 0;
+    for (int q = 0; q < c; ++q) off += fu_npad(n, q);
+    return off;
+}
+__host__ __device__ inline size_t fu_smem_bytes(int n)
+{
+    const int nb = fu_blocks(n);
+    return 2 * (size_t)kFuM * n * 8 + 2 * (size_t)kFuDigits * kFuATile + (size_t)fu_bdig_off(n, nb) +
+           (size_t)nb * (kFuBw * kFuBw + kFuBw) * 8;
+}
+
+// Byte offset of element (row, k) in a K-major, no-swizzle operand tile with
+// K = 16 (two core matrices of 128 bytes along K per 8-row group).
+__device__ __forceinline__ int kmaj16_off(int row, int k)
+{
+    return (row & 7) * 16 + (row >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
+}
+
+// Eight BF16 values (exact small integers) packed for one 16-byte store.
+__device__ __forceinline__ uint4 pack_bf16x8(const float *v)
+{
+    uint4 r;
+    r.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[0])) |
+          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[1])) << 16);
+    r.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2])) |
+          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[3])) << 16);
+    r.z = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[4])) |
+          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[5])) << 16);
+    r.w = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[6])) |
+          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[7])) << 16);
+    return r;
+}
+
+// f * 2^(be - 1023) as a double, built on the integer pipes (exact: f is
+// normal and the result's exponent stays in range; results below the normal
+// range are flushed to zero, above it they become infinite).
+__device__ __forceinline__ double f2d_pow2(float f, int be)
+{
+    const uint32_t u = __float_as_uint(f);
+    const int e8 = (int)((u >> 23) & 0xFFu);
+    const int e = e8 - 127 + be;
+    if (e8 == 0 || e <= 0) return 0.0;
+    const uint32_t sign = u & 0x80000000u;
+    if (e >= 2047) return __hiloint2double((int)(sign | 0x7FF00000u), 0);
+    return __hiloint2double((int)(sign | ((uint32_t)e << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+}
+
+// 16 tensor-memory columns into registers without waiting (tcgen05.wait::ld
+// must follow before the values are used).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Barrier of one 128-thread warp group (named barrier 1 + g), and the same
+// barrier returning the OR of a predicate over the group.
+__device__ __forceinline__ void group_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory"); }
+__device__ __forceinline__ bool group_or(int g, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(g + 1)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_subst_fused(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst, int use_tma,
+                  const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
+                  const double *__restrict__ R, int64_t ldr, int64_t tiles_total, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nb = fu_blocks(n);
+    const size_t tile_bytes = (size_t)kFuM * n * 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp >> 2;        // warp group
+    const int row = tid & (kFuM - 1);  // this thread's row of the group's tile (= tensor-memory lane)
+    double *xs = reinterpret_cast<double *>(smem + g * tile_bytes);
+    unsigned char *adig_all = smem + 2 * tile_bytes;         // [2 groups][7][128 x 16] X_blk digits
+    unsigned char *adig = adig_all + g * kFuDigits * kFuATile;
+    unsigned char *bdig = adig_all + 2 * kFuDigits * kFuATile;  // R digits per block [7][Npad x 16]
+    double *rdg = reinterpret_cast<double *>(bdig + fu_bdig_off(n, nb));  // [nb][16 x 16]: r(k, j) at j*16 + k
+    double *dvs = rdg + nb * kFuBw * kFuBw;                                 // 1 / R_jj, zero past n
+    __shared__ __align__(8) uint64_t full_bar[2];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int colexp[2 * kFuMaxN];
+
+    // --- per-CTA setup: R's diagonal blocks, 1 / R_jj and the digits of R's
+    // off-diagonal blocks (the same for every tile)
+    {
+        const int zbytes = 2 * kFuDigits * kFuATile + fu_bdig_off(n, nb);
+        for (int e = tid; e < zbytes / 16; e += blockDim.x)
+            reinterpret_cast<uint4 *>(adig_all)[e] = make_uint4(0, 0, 0, 0);
+    }
+    for (int e = tid; e < nb * kFuBw * kFuBw; e += blockDim.x) {
+        const int c = e / (kFuBw * kFuBw), j = (e / kFuBw) % kFuBw, k = e % kFuBw;
+        const int gk = kFuBw * c + k, gj = kFuBw * c + j;
+        rdg[e] = (k < j && gj < n) ? R[gk + (int64_t)gj * ldr] : 0.0;
+    }
+    for (int e = tid; e < nb * kFuBw; e += blockDim.x) dvs[e] = (e < n) ? 1.0 / R[e + (int64_t)e * ldr] : 0.0;
+    for (int c = 0; c + 1 < nb; ++c) {
+        const int Nc = n - kFuBw * (c + 1);
+        for (int l = tid; l < Nc; l += blockDim.x) {
+            unsigned ex = 0;
+            for (int k = 0; k < kFuBw; ++k)
+                ex = max(ex, ((unsigned)__double2hiint(R[(kFuBw * c + k) + (int64_t)(kFuBw * (c + 1) + l) * ldr]) >> 20) &
+                                 0x7FFu);
+            colexp[fu_cbase(n, c) + l] = (int)ex;
+        }
+    }
+    if (tid == 0) {
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    for (int c = 0; c + 1 < nb; ++c) {
+        const int Nc = n - kFuBw * (c + 1), Np = fu_npad(n, c);
+        unsigned char *bd = bdig + fu_bdig_off(n, c);
+        for (int l = tid; l < Nc; l += blockDim.x) {
+            const int ex = colexp[fu_cbase(n, c) + l];
+            for (int k0 = 0; k0 < kFuBw; k0 += 8) {
+                float dg[8][kFuDigits];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    digits7((unsigned long long)__double_as_longlong(
+                                R[(kFuBw * c + k0 + k) + (int64_t)(kFuBw * (c + 1) + l) * ldr]),
+                            ex, dg[k]);
+#pragma unroll
+                for (int q = 0; q < kFuDigits; ++q) {
+                    float v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = dg[k][q];
+                    *reinterpret_cast<uint4 *>(bd + q * Np * kFuBw * 2 + kmaj16_off(l, k0)) = pack_bf16x8(v);
+                }
+            }
+        }
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    fence_proxy_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base + (uint32_t)(g * kFuGroupTmem) + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t tmem_mma = tmem_base + (uint32_t)(g * kFuGroupTmem);
+    const bool leader = (row == 0);  // issues this group's TMA copies and MMAs
+
+    // --- this group's tile stream: tiles 2 * blockIdx.x + g, + 2 * gridDim.x, ...
+    uint32_t loads = 0, mphase = 0;  // TMA loads consumed; tensor-core commits consumed
+    bool ok = true, load_pending = false, mma_pending = false;
+    const int64_t stride = 2 * (int64_t)gridDim.x;
+    for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < tiles_total && ok; tile += stride) {
+        const int64_t r0 = tile * kFuM;
+        if (use_tma) {
+            if (leader) {
+                bulk_wait_read_all();  // the previous tile's store has left shared memory
+                mbar_arrive_expect_tx(&full_bar[g], (uint32_t)tile_bytes);
+                tma_load_2d(xs, &tm_src, (int)r0, 0, &full_bar[g]);
+            }
+            load_pending = true;
+            const bool got = mbar_wait_bounded(&full_bar[g], loads & 1u, st);
+            ok = !group_or(g, !got);
+            if (!ok) break;
+            load_pending = false;
+            ++loads;
+        } else {
+            for (int e = row; e < kFuM * n; e += kFuM) {
+                const int rr = e & (kFuM - 1), col = e >> 7;
+                xs[e] = (r0 + rr < m) ? src[r0 + rr + (int64_t)col * lds] : 0.0;
+            }
+            group_bar(g);
+        }
+        for (int c = 0; c < nb && ok; ++c) {
+            const int c16 = kFuBw * c;
+            const int Nc = n - c16 - kFuBw;  // trailing columns after this block
+            int ei;
+            {
+                const double *rb = rdg + c * kFuBw * kFuBw;
+                const double *dvb = dvs + c16;
+                double v[kFuBw];
+#pragma unroll
+                for (int j = 0; j < kFuBw; ++j) v[j] = (c16 + j < n) ? xs[(c16 + j) * kFuM + row] : 0.0;
+#pragma unroll
+                for (int k = 0; k < kFuBw; ++k) {
+                    v[k] *= dvb[k];
+#pragma unroll
+                    for (int j = k + 1; j < kFuBw; ++j) v[j] = fma(-v[k], rb[j * kFuBw + k], v[j]);
+                }
+                unsigned ex = 0;
+#pragma unroll
+                for (int j = 0; j < kFuBw; ++j) {
+                    if (c16 + j < n) xs[(c16 + j) * kFuM + row] = v[j];
+                    ex = max(ex, ((unsigned)__double2hiint(v[j]) >> 20) & 0x7FFu);
+                }
+                ei = (int)ex;
+                if (Nc > 0) {
+#pragma unroll
+                    for (int j0 = 0; j0 < kFuBw; j0 += 8) {
+                        float dg[8][kFuDigits];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            digits7((unsigned long long)__double_as_longlong(v[j0 + j]), ei, dg[j]);
+#pragma unroll
+                        for (int q = 0; q < kFuDigits; ++q) {
+                            float w[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) w[j] = dg[j][q];
+                            *reinterpret_cast<uint4 *>(adig + q * kFuATile + kmaj16_off(row, j0)) = pack_bf16x8(w);
+                        }
+                    }
+                }
+            }
+            if (Nc <= 0) break;
+            const int Np = fu_npad(n, c);
+            const int cb = fu_cbase(n, c);
+            const unsigned char *bd = bdig + fu_bdig_off(n, c);
+            // trailing columns in rounds of at most 32 (7 groups x 32 tensor-memory columns)
+            for (int n0 = 0; n0 < Np && ok; n0 += kFuChunk) {
+                const int nw = min(kFuChunk, Np - n0);
+                fence_proxy_async_shared();
+                tc_fence_before();
+                group_bar(g);
+                if (leader) {
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(adig), b0 = smem_u32(bd) + (uint32_t)(n0 * kFuBw * 2);
+                    const uint32_t idesc = idesc_bf16(kFuM, nw);
+#pragma unroll
+                    for (int p = 0; p < kFuDigits; ++p)
+#pragma unroll
+                        for (int q = 0; p + q < kFuDigits; ++q)
+                            tc_mma(tmem_mma + (uint32_t)((p + q) * kFuChunk), smem_desc(a0 + p * kFuATile, 128, 256),
+                                   smem_desc(b0 + q * Np * kFuBw * 2, 128, 256), idesc, p > 0 ? 1u : 0u);
+                    tc_commit(&mma_bar[g]);
+                }
+                mma_pending = true;
+                const bool got = mbar_wait_bounded(&mma_bar[g], mphase, st);
+                ok = !group_or(g, !got);
+                if (!ok) break;
+                mphase ^= 1u;
+                mma_pending = false;
+                tc_fence_after();
+                // epilogue: this thread's row, 16 columns at a time
+                for (int h0 = 0; h0 < nw; h0 += 16) {
+                    uint32_t gv[kFuDigits][16];
+#pragma unroll
+                    for (int d = 0; d < kFuDigits; ++d) tmem_ld16_issue(tmem + d * kFuChunk + h0, gv[d]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        float hi = __uint_as_float(gv[0][t]), lo = 0.0f;
+#pragma unroll
+                        for (int d = 1; d < kFuDigits; ++d) {
+                            const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+                            const float x = __fmul_rn(__uint_as_float(gv[d][t]), w8);
+                            const float sum = __fadd_rn(hi, x);
+                            const float bb = __fsub_rn(sum, hi);
+                            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                            hi = sum;
+                            lo = __fadd_rn(lo, err);
+                        }
+                        const int l = n0 + h0 + t;
+                        if (l < Nc) {
+                            const int el = colexp[cb + l];
+                            const int be = ei + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
+                            if (ei > 0 && el > 0 && be > 0 && be < 2047) {
+                                double *xp = xs + (c16 + kFuBw + l) * kFuM + row;
+                                *xp = (*xp - f2d_pow2(hi, be)) - f2d_pow2(lo, be);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+            }
+        }
+        if (!ok) break;
+        if (use_tma) {
+            fence_proxy_async_shared();
+            group_bar(g);
+            if (leader) {
+                tma_store_2d(&tm_dst, (int)r0, 0, xs);
+                bulk_commit();
+            }
+        } else {
+            group_bar(g);
+            for (int e = row; e < kFuM * n; e += kFuM) {
+                const int rr = e & (kFuM - 1), col = e >> 7;
+                if (r0 + rr < m) dst[r0 + rr + (int64_t)col * ldd] = xs[e];
+            }
+            group_bar(g);
+        }
+    }
+    // drain this group's tensor-core work, TMA load and stores (bounded waits)
+    if (mma_pending) {
+        mbar_wait_bounded(&mma_bar[g], mphase, st);
+        tc_fence_after();
+    }
+    if (leader && use_tma) {
+        if (load_pending) mbar_wait_bounded(&full_bar[g], loads & 1u, st);
+        bulk_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
 // T = R^{-1} for upper-triangular R (one CTA; thread c solves R t = e_c by back
 // substitution).
 __global__ void k_tri_inverse(const double *__restrict__ R, int n, int64_t ldr, double *__restrict__ T, RxrStatus *st)
@@ -1237,6 +1596,22 @@ int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double
     return 0;
 }
 
+// X = B R^{-1} for n <= 64 in one pass over B (k_subst_fused); X may equal B.
+int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
+                        int64_t ldx, cudaStream_t st)
+{
+    if (p.n > kFuMaxN) return RXR_ERR_UNSUPPORTED;
+    const int n = (int)p.n;
+    CUtensorMap ms, md;
+    const int use_tma =
+        (encode_tile_map(&ms, Bsrc, p.m, n, ldb, kFuM, n) && encode_tile_map(&md, X, p.m, n, ldx, kFuM, n)) ? 1 : 0;
+    const int64_t tiles = cdiv64(p.m, kFuM);
+    const int gx = (int)std::min<int64_t>(p.sms, cdiv64(tiles, 2));  // two tile streams per CTA
+    k_subst_fused<<<gx, 256, fu_smem_bytes(n), st>>>(ms, md, use_tma, Bsrc, ldb, X, ldx, p.m, n, R, ldr, tiles,
+                                                      p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
 int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
 {
     if (p.n > RXR_MAX_N) return RXR_ERR_UNSUPPORTED;
@@ -1267,6 +1642,9 @@ cudaError_t set_split_smem()
         e = cudaFuncSetAttribute(k_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_solve_block, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_subst_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fu_smem_bytes(kFuMaxN));
     return e;
 }
 

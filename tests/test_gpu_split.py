@@ -115,3 +115,31 @@ def test_blocked_substitution_is_backward_stable(h, m, n, kappa):
     Xo = o.trsm_right_upper(A, R)
     back_o = np.linalg.norm(Xo @ R - A) / (np.linalg.norm(Xo) * np.linalg.norm(R))
     assert back <= 64 * max(back_o, n * U)
+
+
+@pytest.mark.parametrize("m,n,kappa", [(1, 1, 1.0), (130, 16, 1e4), (4097, 48, 1e13), (1000, 63, 1e9),
+                                       (128 * 152 * 2 + 77, 64, 1e11)])
+def test_fused_substitution_edges(h, m, n, kappa):
+    # the fused kernel (n <= 64): one block, whole blocks, a narrow last block,
+    # a ragged last tile and more tiles than CTAs; backward error at FP64
+    # rounding level, and an even leading dimension (TMA) must give the same
+    # bits as an odd one (plain loads and stores)
+    A = usv_matrix(m, n, kappa, seed=m + n)
+    R = o.rxr_cholqr(A, o.VARIANT_QR, 2 * n, seed=5, passes=1).Rs
+    X, _ = h.precond_gram(to_dev(A), to_dev(R), prec="split")
+    Xg = to_host(X)
+    back = np.linalg.norm(Xg @ R - A) / max(np.linalg.norm(Xg) * np.linalg.norm(R), 1e-300)
+    assert back <= 64 * n * U, back
+    Xodd, _ = h.precond_gram(to_dev(A, ld=m + 1), to_dev(R), X=rxr.empty_colmajor(m, n, ld=m + 1), prec="split")
+    assert np.array_equal(to_host(Xodd), Xg)
+
+
+def test_fused_substitution_first_block_is_plain_substitution(h):
+    # the first 16 columns see no trailing update: they must equal the FP64
+    # path's substitution bit for bit (same FMA order, same 1 / R_jj)
+    m, n = 3000, 40
+    A = usv_matrix(m, n, 1e8, seed=9)
+    R = o.rxr_cholqr(A, o.VARIANT_QR, 2 * n, seed=1, passes=1).Rs
+    Xs, _ = h.precond_gram(to_dev(A), to_dev(R), prec="split")
+    Xf, _ = h.precond_gram(to_dev(A), to_dev(R), prec="fp64")
+    assert np.array_equal(to_host(Xs)[:, :16], to_host(Xf)[:, :16])
