@@ -419,10 +419,15 @@ int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, c
 // Split-path substitution X = B R^{-1}: up to n = 64 one fused pass (FP64
 // diagonal blocks and tensor-core trailing updates on tiles held in shared
 // memory); wider panels take the column-blocked form, one launch per block.
+// colexp_out (n <= 64, nullable): also record the column exponents of X for
+// the FP64-grade Gram that follows.
 int split_subst(const Plan &p, const double *src, int64_t lds, const double *R, double *dst, int64_t ldd,
-                cudaStream_t st)
+                cudaStream_t st, int *colexp_out = nullptr)
 {
-    if (p.n <= 64) return fused_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
+    if (p.n <= 64) {
+        if (colexp_out && cudaMemsetAsync(colexp_out, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+        return fused_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, colexp_out, st);
+    }
     return blocked_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
 }
 
@@ -497,12 +502,13 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
         // split path takes that Gram from the tensor cores at FP64 grade
         if (p.prec == RXR_SPLIT_BF16 && !last) {
+            int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
             {
                 Timer t(th, 2, st);
-                if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st)) return e;
+                if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st, cx)) return e;
             }
             Timer t(th, 5, st);
-            if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
+            if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st, cx != nullptr)) return e;
             continue;
         }
         Timer t(th, last ? 3 : 2, st);

@@ -350,12 +350,15 @@ int64_t balanced_chunks(int64_t gy, int64_t slots, int64_t max_gx);
 // split-precision contractions (split_kernels.cu)
 int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st);
 int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
-int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
+// colexp_ready: the column exponents of X (n <= 64) are already in
+// split_colexp(p), written by the substitution that produced X
+int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, bool colexp_ready = false);
+int *split_colexp(const Plan &p);
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);
 int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                           int64_t ldx, cudaStream_t st);
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                        int64_t ldx, cudaStream_t st);
+                        int64_t ldx, int *colexp_out, cudaStream_t st);
 // 2-D tensor map of a column-major FP64 matrix (api.cu); false where TMA's
 // alignment rules are not met
 bool encode_tile_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,

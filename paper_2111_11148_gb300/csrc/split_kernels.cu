@@ -132,224 +132,7 @@ constexpr int kSpDigits = 7; // balanced 8-bit digits of A
 constexpr int kSpZ = 2;      // 8-bit pieces of 4096 z'
 constexpr int kSpB = kSpN * kSpSub * 2;  // bytes of one B tile (8 KB)
 constexpr int kSpA = kSpM * kSpSub * 2;  // bytes of one A tile (16 KB)
-constexpr size_t kSpSmem = (size_t)kSpDigits * kSpB + (size_t)kSpZ * kSpA;
 
-__global__ void __launch_bounds__(256, 1)
-    k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed,
-                   int64_t win_total, int64_t win_per_cta, double *__restrict__ Ypart, RxrStatus *st)
-{
-    if (rxr_failed(st)) return;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *bop = smem;                   // kSpDigits tiles, N x K
-    unsigned char *aop = smem + kSpDigits * kSpB; // kSpZ tiles, M x K
-    __shared__ __align__(8) uint64_t mma_bar;
-    __shared__ uint32_t tmem_base;
-    __shared__ int colexp[kSpN];
-    __shared__ int bad_flag;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_tiles = (n + kSpN - 1) / kSpN;
-    const int si = blockIdx.y / n_tiles, ni = blockIdx.y % n_tiles;
-    const int s0 = si * kSpM, c0 = ni * kSpN;
-    const int sw = min(kSpM, s - s0), nw = min(kSpN, n - c0);
-    const int kcount = (sw + 3) / 4;
-
-    for (int e = tid; e < (int)(kSpSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) {
-        bad_flag = 0;
-        mbar_init(&mma_bar, 1);
-        fence_barrier_init();
-    }
-    if (warp == 0) tmem_alloc(&tmem_base, 512);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = idesc_bf16(kSpM, kSpN);
-
-    // epilogue ownership: tensor-memory lane quarter (warp % 4) = sketch rows,
-    // column half (warp / 4)
-    const int q4 = warp & 3, half = warp >> 2;
-    const int my_row = 32 * q4 + lane;
-    double acc[32];
-#pragma unroll
-    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
-
-    uint32_t phase = 0;
-    bool pending = false, ok = true;
-    const int64_t w_begin = blockIdx.x * win_per_cta;
-    const int64_t w_end = min(win_total, w_begin + win_per_cta);
-    for (int64_t w = w_begin; w < w_end && ok; ++w) {
-        const int64_t wr0 = w * kSpWin;
-        // 1. largest exponent of each column in the window (integer pipes)
-        // one warp per column, 16 loads in flight per lane
-        for (int col = warp; col < kSpN; col += 8) {
-            unsigned ex = 0;
-            if (col < nw) {
-                const double *colp = A + (int64_t)(c0 + col) * lda + wr0;
-                unsigned hv[kSpWin / 32];
-#pragma unroll
-                for (int t = 0; t < kSpWin / 32; ++t) {
-                    const int64_t gr = wr0 + lane + 32 * t;
-                    hv[t] = (gr < m) ? (unsigned)__double2hiint(colp[lane + 32 * t]) : 0u;
-                }
-#pragma unroll
-                for (int t = 0; t < kSpWin / 32; ++t) ex = max(ex, (hv[t] >> 20) & 0x7FFu);
-            }
-            ex = __reduce_max_sync(0xFFFFFFFFu, ex);
-            if (lane == 0) {
-                colexp[col] = (int)ex;
-                if (ex == 0x7FFu) bad_flag = 1;
-            }
-        }
-        __syncthreads();
-        // 2. eight operand tiles of 64 rows
-        for (int sp = 0; sp < kSpWin / kSpSub; ++sp) {
-            const int64_t r0 = wr0 + sp * kSpSub;
-            if (pending) {
-                ok = mma_wait(&mma_bar, phase, st);
-                if (!ok) break;
-                phase ^= 1u;
-                pending = false;
-            }
-            // digits of A: element (row k, column j) -> B tile (j, k); the
-            // thread's 16 elements are loaded first (all in flight together)
-            unsigned long long vbits[kSpSub * kSpN / 256];
-#pragma unroll
-            for (int t = 0; t < kSpSub * kSpN / 256; ++t) {
-                const int e = tid + 256 * t;
-                const int k = e & (kSpSub - 1), j = e >> 6;
-                const int64_t gr = r0 + k;
-                vbits[t] = (j < nw && gr < m) ? (unsigned long long)__double_as_longlong(A[gr + (int64_t)(c0 + j) * lda])
-                                              : 0ull;
-            }
-#pragma unroll
-            for (int t = 0; t < kSpSub * kSpN / 256; ++t) {
-                const int e = tid + 256 * t;
-                const int k = e & (kSpSub - 1), j = e >> 6;
-                long long T = 0;
-                {
-                    const unsigned long long bits = vbits[t];
-                    const int ea = (int)((bits >> 52) & 0x7FF);
-                    if (ea > 0 && ea < 0x7FF) {
-                        // T = a / 2^(e_j + 1) * 2^55, |T| < 2^55 (rounded to an integer)
-                        const long long m53 = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-                        const int sh = colexp[j] - ea;  // >= 0
-                        if (sh <= 2)
-                            T = m53 << (2 - sh);
-                        else if (sh < 56)
-                            T = (m53 + (1ll << (sh - 3))) >> (sh - 2);
-                        if (bits >> 63) T = -T;
-                    }
-                }
-                // six balanced digits in [-128, 127] from the bottom; the rest,
-                // |T / 2^48| rounded, is the top digit and lies in [-128, 128]
-#pragma unroll
-                for (int q = kSpDigits - 1; q >= 1; --q) {
-                    const long long d = ((T + 128) & 255) - 128;
-                    T = (T - d) >> 8;
-                    st_bf16(bop + q * kSpB, kmaj_off(j, k), (float)d);
-                }
-                st_bf16(bop, kmaj_off(j, k), (float)T);
-            }
-            // Omega' pieces: A tile (sketch row r, k)
-            for (int c = tid; c < kSpSub * kcount; c += blockDim.x) {
-                const int k = c / kcount, kk = c % kcount;
-                float z[4];
-                rxr_normal4(seed, (uint64_t)(r0 + k), (uint32_t)(s0 / 4 + kk), 0u, z);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int r = 4 * kk + t;
-                    if (r < sw) {
-                        const int q = __float2int_rn(__fmul_rn(z[t], 4096.0f));
-                        const int z0 = (q + 128) >> 8;
-                        const int z1 = q - (z0 << 8);
-                        const int off = kmaj_off(r, k);
-                        st_bf16(aop, off, (float)z0);
-                        st_bf16(aop + kSpA, off, (float)z1);
-                    }
-                }
-            }
-            fence_proxy_async_shared();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t a0 = smem_u32(aop), b0 = smem_u32(bop);
-#pragma unroll
-                for (int kk = 0; kk < kSpSub / 16; ++kk) {
-#pragma unroll
-                    for (int p = 0; p < kSpZ; ++p)
-#pragma unroll
-                        for (int q = 0; q + p < kSpDigits; ++q) {
-                            const uint32_t acc_on = (sp > 0 || kk > 0 || p > 0) ? 1u : 0u;
-                            tc_mma(tmem + (uint32_t)((p + q) * kSpN),
-                                   smem_desc(a0 + p * kSpA + kk * 256, 128, 1024),
-                                   smem_desc(b0 + q * kSpB + kk * 256, 128, 1024), idesc, acc_on);
-                        }
-                }
-                tc_commit(&mma_bar);
-            }
-            pending = true;
-        }
-        if (!ok) break;
-        // 3. drain the window: combine the seven weights in FP32 pairs, add in FP64
-        ok = mma_wait(&mma_bar, phase, st);
-        if (!ok) break;
-        phase ^= 1u;
-        pending = false;
-        tc_fence_after();
-#pragma unroll
-        for (int c16 = 0; c16 < 2; ++c16) {
-            const int col0 = half * 32 + c16 * 16;
-            float hi[16], lo[16], v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
-#pragma unroll
-            for (int t = 0; t < 16; ++t) lo[t] = 0.0f;
-#pragma unroll
-            for (int d = 1; d < kSpDigits; ++d) {
-                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + d * kSpN + col0, v);
-                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);  // 2^-8d
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const float x = __fmul_rn(v[t], w8);
-                    const float sum = __fadd_rn(hi[t], x);
-                    const float bb = __fsub_rn(sum, hi[t]);
-                    const float err = __fadd_rn(__fsub_rn(hi[t], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
-                    hi[t] = sum;
-                    lo[t] = __fadd_rn(lo[t], err);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int ce = colexp[min(col0 + t, kSpN - 1)];
-                const double scale = (ce > 10) ? __hiloint2double((ce - 10) << 20, 0) : 0.0;  // 2^(e_j - 1033)
-                const double val = rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
-                acc[c16 * 16 + t] = fma(val, scale, acc[c16 * 16 + t]);
-            }
-        }
-        tc_fence_before();
-        __syncthreads();
-    }
-    // an abandoned wait may leave tensor-core work in flight: wait for it once
-    // more (bounded) before releasing tensor memory
-    if (pending) {
-        mma_wait(&mma_bar, phase, st);
-        tc_fence_after();
-    }
-    if (bad_flag) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
-    if (ok) {
-        double *out = Ypart + (int64_t)blockIdx.x * s * n;
-        const int r = s0 + my_row;
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const int c = c0 + half * 32 + t;
-            if (my_row < sw && c < c0 + nw) out[r + (int64_t)c * s] = acc[t];
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 512);
-}
 
 // ---------------------------------------------------------------------------
 // Split Gram
@@ -527,7 +310,13 @@ constexpr size_t kOzSmem = (size_t)kOzDigits * (kOzTile + kOzBTile);
 // emax = biased exponent of the largest entry of its group: six balanced
 // digits in [-128, 127] from the bottom, the rest (in [-128, 128]) on top.
 // Digit q has weight 2^(emax - 1029 - 8q).
-__device__ __forceinline__ void digits7(unsigned long long bits, int emax, float dg[kOzDigits])
+// The 55-bit fixed-point integer T of an FP64 value relative to 2^(emax + 1)
+// (rounded to nearest; zero for zeros, subnormals and non-finite values),
+// returned in offset form U = T + 0x808080808080: because T = sum_q alpha_q
+// 256^(6-q) with balanced digits alpha_1..6 in [-128, 127], byte k of U is
+// alpha_(6-k) + 128 (k = 0..5) and U >> 48 (arithmetic) is alpha_0: the
+// carries of the offset do the balancing.
+__device__ __forceinline__ unsigned long long digits_offset(unsigned long long bits, int emax)
 {
     long long T = 0;
     const int ea = (int)((bits >> 52) & 0x7FF);
@@ -540,13 +329,25 @@ __device__ __forceinline__ void digits7(unsigned long long bits, int emax, float
             T = (m53 + (1ll << (sh - 3))) >> (sh - 2);
         if (bits >> 63) T = -T;
     }
+    return (unsigned long long)(T + 0x808080808080ll);
+}
+
+// FP32 bit pattern of digit q of offset form U (an integer in [-128, 128]:
+// exact, and its upper 16 bits are its BF16 encoding).
+__device__ __forceinline__ uint32_t digit_bits(unsigned long long U, int q)
+{
+    const uint32_t b = (q == 0) ? (uint32_t)((int)((long long)U >> 48) + 128)
+                                : (uint32_t)(U >> (8 * (6 - q))) & 0xFFu;
+    return __float_as_uint(__fadd_rn(__uint_as_float(0x4B000000u | b), -8388736.0f));  // 2^23 + b - (2^23 + 128)
+}
+
+// Seven balanced 8-bit digits alpha_0..alpha_6 of the value (alpha_0 may be
+// +-128), as floats.
+__device__ __forceinline__ void digits7(unsigned long long bits, int emax, float dg[kOzDigits])
+{
+    const unsigned long long U = digits_offset(bits, emax);
 #pragma unroll
-    for (int q = kOzDigits - 1; q >= 1; --q) {
-        const long long d = ((T + 128) & 255) - 128;
-        T = (T - d) >> 8;
-        dg[q] = (float)d;
-    }
-    dg[0] = (float)T;
+    for (int q = 0; q < kOzDigits; ++q) dg[q] = __uint_as_float(digit_bits(U, q));
 }
 
 // Largest exponent of columns [c0, c0 + ncol) of X over the window rows, one
@@ -1210,18 +1011,16 @@ __device__ __forceinline__ int kmaj16_off(int row, int k)
     return (row & 7) * 16 + (row >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
 }
 
-// Eight BF16 values (exact small integers) packed for one 16-byte store.
+// Eight BF16 values packed for one 16-byte store.  The values are integers
+// of at most eight significant bits, so each BF16 is the upper half of its
+// FP32 encoding (no rounding).
 __device__ __forceinline__ uint4 pack_bf16x8(const float *v)
 {
     uint4 r;
-    r.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[0])) |
-          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[1])) << 16);
-    r.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2])) |
-          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[3])) << 16);
-    r.z = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[4])) |
-          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[5])) << 16);
-    r.w = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[6])) |
-          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[7])) << 16);
+    r.x = __byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632);
+    r.y = __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632);
+    r.z = __byte_perm(__float_as_uint(v[4]), __float_as_uint(v[5]), 0x7632);
+    r.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
     return r;
 }
 
@@ -1270,7 +1069,7 @@ __device__ __forceinline__ bool group_or(int g, bool v)
 __global__ void __launch_bounds__(256, 1)
     k_subst_fused(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst, int use_tma,
                   const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
-                  const double *__restrict__ R, int64_t ldr, int64_t tiles_total, RxrStatus *st)
+                  const double *__restrict__ R, int64_t ldr, int64_t tiles_total, int *colexp_out, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1289,6 +1088,7 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ __align__(8) uint64_t mma_bar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int colexp[2 * kFuMaxN];
+    __shared__ int out_exp[kFuMaxN];  // largest exponent per column of the tiles written
 
     // --- per-CTA setup: R's diagonal blocks, 1 / R_jj and the digits of R's
     // off-diagonal blocks (the same for every tile)
@@ -1303,6 +1103,7 @@ __global__ void __launch_bounds__(256, 1)
         rdg[e] = (k < j && gj < n) ? R[gk + (int64_t)gj * ldr] : 0.0;
     }
     for (int e = tid; e < nb * kFuBw; e += blockDim.x) dvs[e] = (e < n) ? 1.0 / R[e + (int64_t)e * ldr] : 0.0;
+    if (tid < kFuMaxN) out_exp[tid] = 0;
     for (int c = 0; c + 1 < nb; ++c) {
         const int Nc = n - kFuBw * (c + 1);
         for (int l = tid; l < Nc; l += blockDim.x) {
@@ -1480,6 +1281,15 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
         if (!ok) break;
+        if (colexp_out != nullptr) {
+            // column exponents of the finished tile (this thread's row), max over
+            // the warp's 32 rows, then over the CTA in shared memory
+            for (int jj = 0; jj < n; ++jj) {
+                unsigned e = ((unsigned)__double2hiint(xs[jj * kFuM + row]) >> 20) & 0x7FFu;
+                e = __reduce_max_sync(0xFFFFFFFFu, e);
+                if (lane == 0 && e > 0) atomicMax(&out_exp[jj], (int)e);
+            }
+        }
         if (use_tma) {
             fence_proxy_async_shared();
             group_bar(g);
@@ -1507,7 +1317,702 @@ __global__ void __launch_bounds__(256, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (colexp_out != nullptr && tid < n && out_exp[tid] > 0) atomicMax(colexp_out + tid, out_exp[tid]);
     if (warp == 0) tmem_dealloc(tmem_base, 512);
+}
+
+// One exact window of k_gram_oz64 folded into the FP64 accumulators of this
+// thread: tensor-memory lane 32 q4 + lane, columns 32 half .. + 31 of the seven
+// accumulator blocks, combined with weights 2^-8d in FP32 pairs (exact: hi +
+// lo carries every bit of the sums) and added in FP64.
+__device__ __forceinline__ void gram64_drain(uint32_t tmem, int q4, int half, double acc[32])
+{
+#pragma unroll
+    for (int c16 = 0; c16 < 2; ++c16) {
+        uint32_t g[kOzDigits][16];
+#pragma unroll
+        for (int d = 0; d < kOzDigits; ++d)
+            tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + 32 * half + 16 * c16, g[d]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            float hi = __uint_as_float(g[0][t]), lo = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kOzDigits; ++d) {
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+                const float x = __fmul_rn(__uint_as_float(g[d][t]), w8);
+                const float sum = __fadd_rn(hi, x);
+                const float bb = __fsub_rn(sum, hi);
+                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                hi = sum;
+                lo = __fadd_rn(lo, err);
+            }
+            acc[16 * c16 + t] += rxr_f2d_exact(hi) + rxr_f2d_exact(lo);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64-grade Gram G = X^T X for n <= 64 on the tensor cores.  Column j of X is
+// written as seven 8-bit digits relative to 2^(e_j + 1), e_j the largest
+// exponent of the column over all m rows (so the scale of every product is
+// fixed and tensor-memory sums stay integers across row blocks).  The digit
+// planes X_0 .. X_6 (64 columns x 64 rows each, K-major) are followed by a zero
+// plane X_7, so that a 128-row A operand starting at plane p is the stack
+// [X_p; X_{p+1}]: one MMA with B = X_q forms the digit products (p, q) in
+// tensor-memory lanes 0-63 and (p + 1, q) in lanes 64-127.  Sixteen stacks
+// (p even) cover all 28 products with p + q <= 6; accumulator block d = p + q
+// holds weight group d in its upper lanes and group d + 1 in its lower lanes.
+// Every accumulator sums at most four products below 2^14 per row, so a
+// window of 256 rows keeps it an integer below 2^24 (exact in FP32); after
+// each window the groups are combined (weights 2^-8d) and added in FP64, and
+// the fixed scale 2^(e_i + e_j - 2058) is applied once at the end.  Operand
+// buffers of 64 rows alternate so that the digits of one are written while
+// the tensor core reads the other.
+// ---------------------------------------------------------------------------
+constexpr int kG6Rows = 64;                     // rows of X per operand buffer (K = 4 x 16)
+constexpr int kG6Window = 4;                    // buffers per exact accumulation window (256 rows)
+constexpr int kG6Plane = 64 * kG6Rows * 2;      // one digit plane, 8 KB
+constexpr int kG6Planes = 8;                    // X_0 .. X_6 and the zero plane
+constexpr int kG6Buf = kG6Planes * kG6Plane;    // 64 KB per buffer
+constexpr size_t kG6Smem = 2 * (size_t)kG6Buf;  // 128 KB
+
+// Largest exponent field of each column over all rows: atomicMax into
+// colexp[0 .. n) (zeroed by the caller).  grid.y = column.
+__global__ void k_colexp(const double *__restrict__ X, int64_t ldx, int64_t m, int *colexp, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    const int col = blockIdx.y;
+    unsigned e = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+        e = max(e, ((unsigned)__double2hiint(X[r + (int64_t)col * ldx]) >> 20) & 0x7FFu);
+    e = __reduce_max_sync(0xFFFFFFFFu, e);
+    if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(colexp + col, (int)e);
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_gram_oz64(const double *__restrict__ X, int64_t ldx, int64_t m, int n, const int *__restrict__ colexp_g,
+                int64_t bufs_total, int64_t bufs_per_cta, double *__restrict__ Gpart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int cex[64];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int j = tid >> 2, rq = tid & 3;  // column of X and 16-row quarter of each buffer this thread converts
+
+    for (int e = tid; e < (int)(kG6Smem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid < 64) cex[tid] = (tid < n) ? colexp_g[tid] : 0;
+    if (tid == 0) {
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int ej = cex[j];
+    const bool has_col = j < n;
+
+    // epilogue role: tensor-memory lane quarter q4 (rows of G: lanes 0-63 the
+    // upper halves of the stacks, 64-127 the lower), 32 columns of G per half;
+    // the quarter of rows 32-63 has nothing on or above the diagonal in the
+    // first 32 columns
+    const int q4 = warp & 3, half = warp >> 2;
+    const bool skip_epi = (q4 & 1) && half == 0;
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+
+    const int64_t b_begin = blockIdx.x * bufs_per_cta;
+    const int64_t b_end = min(bufs_total, b_begin + bufs_per_cta);
+    const double *xcol = X + (int64_t)j * ldx;
+    double vn[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t r = b_begin * kG6Rows + 16 * rq + i;
+        vn[i] = (has_col && b_begin < b_end && r < m) ? xcol[r] : 0.0;
+    }
+    // Waits are per thread and bounded; a wait that gives up records a timeout
+    // in the status and the kernel runs to its end (bounded loop) without
+    // publishing its sums, so no thread is ever left at a barrier.
+    bool ok = true;
+    int it = 0;
+    // descriptors of buffer 0, plane 0: the start-address field (bits 0-13, in
+    // 16-byte units) takes plain offsets (shared memory stays below 256 KB)
+    const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
+    for (int64_t b = b_begin; b < b_end; ++b, ++it) {
+        const int buf = it & 1;
+        unsigned char *base = smem + buf * kG6Buf;
+        double v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = vn[i];
+        if (b + 1 < b_end) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int64_t r = (b + 1) * kG6Rows + 16 * rq + i;
+                vn[i] = (has_col && r < m) ? xcol[r] : 0.0;
+            }
+        }
+        // the MMAs issued two buffers ago read this buffer
+        if (it >= 2) ok &= mbar_wait_bounded(&mma_bar[buf], ((it - 2) >> 1) & 1, st);
+        if (has_col) {
+#pragma unroll
+            for (int g8 = 0; g8 < 2; ++g8) {
+                unsigned long long U[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[8 * g8 + r]), ej);
+#pragma unroll
+                for (int q = 0; q < kOzDigits; ++q) {
+                    uint4 w;
+                    w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
+                    w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
+                    w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
+                    w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+                    *reinterpret_cast<uint4 *>(base + q * kG6Plane + kmaj_off(j, 16 * rq + 8 * g8)) = w;
+                }
+            }
+        }
+        const bool first_of_window = (it % kG6Window) == 0;
+        if (first_of_window && it > 0) {
+            // the previous window is complete once its last buffer's MMAs are:
+            // fold its tensor-memory sums into the FP64 accumulators
+            ok &= mbar_wait_bounded(&mma_bar[buf ^ 1], ((it - 1) >> 1) & 1, st);
+            tc_fence_after();
+            if (!skip_epi) gram64_drain(tmem, q4, half, acc);
+        }
+        fence_proxy_async_shared();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t dbuf = desc0 + (uint64_t)(buf * (kG6Buf >> 4));
+            constexpr uint32_t idesc = idesc_bf16(128, 64);
+            constexpr int kP[16] = {0, 2, 4, 6, 0, 2, 4, 0, 2, 4, 0, 2, 0, 2, 0, 0};
+            constexpr int kQ[16] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 4, 4, 5, 6};
+#pragma unroll
+            for (int kk = 0; kk < kG6Rows / 16; ++kk)
+#pragma unroll
+                for (int x = 0; x < 16; ++x) {
+                    // the first MMA into each block (x < 7 lists blocks 0, 2, 4, 6, 1, 3, 5) starts the window
+                    const uint32_t acc_on = (!first_of_window || kk > 0 || x >= 7) ? 1u : 0u;
+                    tc_mma(tmem + (uint32_t)((kP[x] + kQ[x]) * 64),
+                           dbuf + (uint64_t)((kP[x] * kG6Plane + kk * 256) >> 4),
+                           dbuf + (uint64_t)((kQ[x] * kG6Plane + kk * 256) >> 4), idesc, acc_on);
+                }
+            tc_commit(&mma_bar[buf]);
+        }
+    }
+    // last window
+    if (it > 0) {
+        ok &= mbar_wait_bounded(&mma_bar[(it - 1) & 1], ((it - 1) >> 1) & 1, st);
+        tc_fence_after();
+        if (!skip_epi) gram64_drain(tmem, q4, half, acc);
+    }
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_before();
+    __syncthreads();
+    // G[i][j] = 2^(e_i + e_j - 2058) (upper-lane sum + 2^-8 lower-lane sum):
+    // the lower lanes hand their sums over through shared memory
+    double *low = reinterpret_cast<double *>(smem);  // [64][64], i + 64 j
+    const int gi = 32 * (q4 & 1) + lane;
+    if (q4 >= 2 && !skip_epi) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) low[gi + 64 * (32 * half + t)] = acc[t];
+    }
+    __syncthreads();
+    if (ok && q4 < 2 && !skip_epi && gi < n) {
+        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+        const int ei = cex[gi];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int gj = 32 * half + t;
+            if (gj < n && gi <= gj) {
+                const int e = ei + cex[gj] - 2058;
+                const double v = acc[t] + ldexp(low[gi + 64 * gj], -8);
+                out[gi + (int64_t)gj * n] = (ei > 0 && cex[gj] > 0) ? ldexp(v, e) : 0.0;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// FP64-grade product Q = X T on the tensor cores for n <= 64 (the last
+// CholeskyQR pass's apply, T = R_P^{-1}), in place.  A CTA walks 128-row
+// tiles of X: one TMA load per tile into shared memory (the next tile's load
+// is issued as soon as the current tile's digits are all written), each row
+// of X written as seven 8-bit digits relative to its own largest exponent,
+// each column of T relative to its own (digits of T built once per CTA).  The
+// digit products p + q = d accumulate in tensor-memory group d over K = n
+// (at most seven pairs of products below 2^14 per row: exact in FP32); the
+// X digits are produced one 16-column K-step at a time into two alternating
+// buffers, so the tensor core works on one K-step while the next is written.
+// The epilogue combines the seven groups of each output and writes Q with one
+// FP64 addition.
+// ---------------------------------------------------------------------------
+constexpr int kAqM = 128;
+constexpr int kAqPlane = kAqM * 16 * 2;  // one X digit plane of a K-step (4 KB)
+constexpr int kAqTPlane = 64 * 64 * 2;   // one T digit plane (8 KB), K-major, K = 64
+__host__ __device__ inline size_t aq_smem_bytes(int n)
+{
+    return (size_t)kAqM * n * 8 + 2 * (size_t)kOzDigits * kAqPlane + (size_t)kOzDigits * kAqTPlane;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_apply_oz64(const __grid_constant__ CUtensorMap tm_x, int use_tma, double *X, int64_t ldx, int64_t m, int n,
+                 const double *__restrict__ T, int64_t ldt, int64_t tiles_total, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const size_t tile_bytes = (size_t)kAqM * n * 8;
+    double *xs = reinterpret_cast<double *>(smem);            // [n][128]
+    unsigned char *adig = smem + tile_bytes;                  // [2][7][128 x 16]
+    unsigned char *tdig = adig + 2 * kOzDigits * kAqPlane;    // [7][64 x 64]
+    __shared__ __align__(8) uint64_t full_bar;
+    __shared__ __align__(8) uint64_t abar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int colexp_t[64];
+    __shared__ int pexp[2][kAqM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (kAqM - 1), h = tid >> 7;  // digit role: row of the tile, 8-column half of a K-step
+
+    for (int e = tid; e < (int)((2 * kOzDigits * kAqPlane + kOzDigits * kAqTPlane) / 16); e += blockDim.x)
+        reinterpret_cast<uint4 *>(adig)[e] = make_uint4(0, 0, 0, 0);
+    if (tid < 64) {
+        unsigned ex = 0;
+        if (tid < n)
+            for (int k = 0; k <= tid; ++k) ex = max(ex, ((unsigned)__double2hiint(T[k + (int64_t)tid * ldt]) >> 20) & 0x7FFu);
+        colexp_t[tid] = (int)ex;
+    }
+    if (tid == 0) {
+        mbar_init(&full_bar, 1);
+        mbar_init(&abar[0], 1);
+        mbar_init(&abar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    // digits of T: B operand element (l, k) = T[k][l] (zero below the diagonal)
+    for (int e = tid; e < n * 8; e += blockDim.x) {
+        const int l = e >> 3, k0 = 8 * (e & 7);
+        unsigned long long U[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int k = k0 + r;
+            const unsigned long long bits =
+                (k <= l && k < n) ? (unsigned long long)__double_as_longlong(T[k + (int64_t)l * ldt]) : 0ull;
+            U[r] = digits_offset(bits, colexp_t[l]);
+        }
+#pragma unroll
+        for (int q = 0; q < kOzDigits; ++q) {
+            uint4 w;
+            w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
+            w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
+            w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
+            w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+            *reinterpret_cast<uint4 *>(tdig + q * kAqTPlane + kmaj_off(l, k0)) = w;
+        }
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    fence_proxy_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint64_t da0 = smem_desc(smem_u32(adig), 128, 256);   // X digits, K = 16 per plane
+    const uint64_t dt0 = smem_desc(smem_u32(tdig), 128, 1024);  // T digits, K = 64
+    constexpr uint32_t idesc = idesc_bf16(kAqM, 64);
+    const int nk = (n + 15) / 16;
+
+    if (use_tma && tid == 0 && (int64_t)blockIdx.x < tiles_total) {
+        mbar_arrive_expect_tx(&full_bar, (uint32_t)tile_bytes);
+        tma_load_2d(xs, &tm_x, (int)(blockIdx.x * kAqM), 0, &full_bar);
+    }
+    // Waits are per thread and bounded; one that gives up records a timeout and
+    // the loop runs to its end without further effect on the result's status.
+    bool ok = true;
+    uint32_t loads = 0, ksteps = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles_total; tile += gridDim.x) {
+        const int64_t r0 = tile * kAqM;
+        if (use_tma) {
+            ok &= mbar_wait_bounded(&full_bar, loads & 1u, st);
+            ++loads;
+        } else {
+            for (int e = tid; e < kAqM * n; e += blockDim.x) {
+                const int rr = e & (kAqM - 1), col = e >> 7;
+                xs[e] = (r0 + rr < m) ? X[r0 + rr + (int64_t)col * ldx] : 0.0;
+            }
+            __syncthreads();
+        }
+        // largest exponent of each row (two threads per row, 32 columns each)
+        {
+            unsigned ex = 0;
+            for (int c = 32 * h; c < min(n, 32 * h + 32); ++c)
+                ex = max(ex, ((unsigned)__double2hiint(xs[c * kAqM + row]) >> 20) & 0x7FFu);
+            pexp[h][row] = (int)ex;
+        }
+        __syncthreads();
+        const int ei = max(pexp[0][row], pexp[1][row]);
+        for (int kk = 0; kk < nk; ++kk, ++ksteps) {
+            const int buf = ksteps & 1;
+            // the MMAs of two K-steps ago read this buffer
+            if (ksteps >= 2) ok &= mbar_wait_bounded(&abar[buf], ((ksteps - 2) >> 1) & 1, st);
+            {
+                unsigned long long U[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int c = 16 * kk + 8 * h + r;
+                    U[r] = digits_offset(c < n ? (unsigned long long)__double_as_longlong(xs[c * kAqM + row]) : 0ull, ei);
+                }
+                unsigned char *plane = adig + buf * kOzDigits * kAqPlane;
+#pragma unroll
+                for (int q = 0; q < kOzDigits; ++q) {
+                    uint4 w;
+                    w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
+                    w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
+                    w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
+                    w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+                    *reinterpret_cast<uint4 *>(plane + q * kAqPlane + kmaj16_off(row, 8 * h)) = w;
+                }
+            }
+            fence_proxy_async_shared();
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                // every read of this tile's X is done: fetch the next tile
+                if (kk == nk - 1 && use_tma && tile + gridDim.x < tiles_total) {
+                    mbar_arrive_expect_tx(&full_bar, (uint32_t)tile_bytes);
+                    tma_load_2d(xs, &tm_x, (int)((tile + gridDim.x) * kAqM), 0, &full_bar);
+                }
+                const uint64_t da = da0 + (uint64_t)((buf * kOzDigits * kAqPlane) >> 4);
+#pragma unroll
+                for (int p = 0; p < kOzDigits; ++p)
+#pragma unroll
+                    for (int q = 0; p + q < kOzDigits; ++q)
+                        tc_mma(tmem + (uint32_t)((p + q) * 64), da + (uint64_t)((p * kAqPlane) >> 4),
+                               dt0 + (uint64_t)((q * kAqTPlane + kk * 256) >> 4), idesc, (kk > 0 || p > 0) ? 1u : 0u);
+                tc_commit(&abar[buf]);
+            }
+        }
+        // the tile's last K-step completes after all earlier ones
+        ok &= mbar_wait_bounded(&abar[(ksteps - 1) & 1], ((ksteps - 1) >> 1) & 1, st);
+        tc_fence_after();
+        {
+            const int q4 = warp & 3, half = warp >> 2;
+            const int erow = 32 * q4 + lane;
+            const int er = max(pexp[0][erow], pexp[1][erow]);
+            const int64_t gr = r0 + erow;
+#pragma unroll
+            for (int c16 = 0; c16 < 2; ++c16) {
+                const int col0 = 32 * half + 16 * c16;
+                if (col0 >= n) continue;  // warp-uniform
+                uint32_t g[kOzDigits][16];
+#pragma unroll
+                for (int d = 0; d < kOzDigits; ++d)
+                    tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + col0, g[d]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    float hi = __uint_as_float(g[0][t]), lo = 0.0f;
+#pragma unroll
+                    for (int d = 1; d < kOzDigits; ++d) {
+                        const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+                        const float x = __fmul_rn(__uint_as_float(g[d][t]), w8);
+                        const float sum = __fadd_rn(hi, x);
+                        const float bb = __fsub_rn(sum, hi);
+                        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                        hi = sum;
+                        lo = __fadd_rn(lo, err);
+                    }
+                    const int l = col0 + t;
+                    if (l < n && gr < m) {
+                        const int el = colexp_t[l];
+                        const int be = er + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
+                        X[gr + (int64_t)l * ldx] = (er > 0 && el > 0) ? f2d_pow2(hi, be) + f2d_pow2(lo, be) : 0.0;
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    // drain: a load still in flight after a timeout (bounded)
+    if (tid == 0 && use_tma && !ok) mbar_wait_bounded(&full_bar, loads & 1u, st);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// T = R^{-1} for upper-triangular R, n <= 64, one CTA of 1024 threads with R
+// and T in shared memory.  16 lanes per column c solve R t = e_c by back
+// substitution: row i takes the dot product of R's row i with the entries of
+// t already known, split over the 16 lanes and reduced in a fixed order by
+// shuffles, times 1 / R_ii (precomputed).
+__global__ void __launch_bounds__(1024) k_tri_inverse64(const double *__restrict__ R, int n, int64_t ldr,
+                                                         double *__restrict__ T, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double rs[64 * 65];  // R[i][k] at i * 65 + k
+    __shared__ double ts[64 * 65];  // T[k][c] at c * 65 + k
+    __shared__ double dinv[64];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int i = e % n, k = e / n;
+        rs[i * 65 + k] = R[i + (int64_t)k * ldr];
+        ts[k * 65 + i] = 0.0;
+    }
+    if (tid < n) dinv[tid] = 1.0 / R[tid + (int64_t)tid * ldr];
+    __syncthreads();
+    const int c = tid >> 4, sl = tid & 15;  // column, lane within the column's 16
+    double *tc = ts + c * 65;
+    if (c < n && sl == 0) tc[c] = dinv[c];
+    __syncwarp();
+    for (int i = n - 2; i >= 0; --i) {
+        double part = 0.0;
+        if (c < n && c > i)
+            for (int k = i + 1 + sl; k <= c; k += 16) part = fma(rs[i * 65 + k], tc[k], part);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        if (c < n && c > i && sl == 0) tc[i] = -part * dinv[i];
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int k = e % n, cc = e / n;
+        T[k + (int64_t)cc * n] = ts[cc * 65 + k];
+    }
+}
+
+// One exact window of the split sketch folded into this thread's FP64
+// accumulators (tensor-memory lane 32 q4 + lane, columns 32 half .. + 31):
+// weights 2^-8d combined in FP32 pairs, added in FP64 without the column
+// scale.
+__device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int half, double acc[32])
+{
+#pragma unroll
+    for (int c16 = 0; c16 < 2; ++c16) {
+        uint32_t g[kSpDigits][16];
+#pragma unroll
+        for (int d = 0; d < kSpDigits; ++d)
+            tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * kSpN + 32 * half + 16 * c16, g[d]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            float hi = __uint_as_float(g[0][t]), lo = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kSpDigits; ++d) {
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+                const float x = __fmul_rn(__uint_as_float(g[d][t]), w8);
+                const float sum = __fadd_rn(hi, x);
+                const float bb = __fsub_rn(sum, hi);
+                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                hi = sum;
+                lo = __fadd_rn(lo, err);
+            }
+            acc[16 * c16 + t] += rxr_f2d_exact(hi) + rxr_f2d_exact(lo);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Split sketch Y' = Omega' A (see the file header).  grid.y = (s-tile,
+// n-tile) output tiles of 128 x 64; grid.x = row chunks.  Column j of A is
+// cut into seven digits relative to 2^(e_j + 1), e_j its largest exponent over
+// all rows (from k_colexp), so the scale of every product is fixed.  Operand
+// tiles of 64 rows alternate between two buffers: the Omega' pieces and A
+// digits of one are written while the tensor core reads the other (A's next
+// rows are already in registers).  Every 512 rows the seven tensor-memory
+// groups (each an exact integer below 2^24: at most two pairs of products
+// below 2^14 per row) are combined in FP32 pairs and added in FP64; the fixed
+// scale 2^(e_j - 1033) is applied once at the end.
+// ---------------------------------------------------------------------------
+constexpr int kSpBuf = kSpDigits * kSpB + kSpZ * kSpA;  // 88 KB per buffer
+constexpr size_t kSpSmem2 = 2 * (size_t)kSpBuf;
+
+__global__ void __launch_bounds__(256, 1)
+    k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed,
+                   const int *__restrict__ colexp_g, int64_t subs_total, int64_t subs_per_cta,
+                   double *__restrict__ Ypart, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int cex[kSpN];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = (n + kSpN - 1) / kSpN;
+    const int si = blockIdx.y / n_tiles, ni = blockIdx.y % n_tiles;
+    const int s0 = si * kSpM, c0 = ni * kSpN;
+    const int sw = min(kSpM, s - s0), nw = min(kSpN, n - c0);
+
+    for (int e = tid; e < (int)(kSpSmem2 / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    if (tid < kSpN) {
+        cex[tid] = (tid < nw) ? colexp_g[c0 + tid] : 0;
+        if (tid < nw && cex[tid] == 0x7FF) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+    }
+    if (tid == 0) {
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = idesc_bf16(kSpM, kSpN);
+    const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
+
+    // roles: A digits -> column j, rows 16 rq .. + 15 of each 64-row tile;
+    // Omega' -> sketch rows 4 kq .. + 3, data rows 8 warp .. + 7
+    const int j = tid >> 2, rq = tid & 3;
+    const int kq = lane;
+    const bool has_col = j < nw;
+    const int ej = cex[j];
+    const double *acol = A + (int64_t)(c0 + j) * lda;
+    // epilogue: tensor-memory lane quarter (sketch rows), column half
+    const int q4 = warp & 3, half = warp >> 2;
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+
+    const int64_t b_begin = blockIdx.x * subs_per_cta;
+    const int64_t b_end = min(subs_total, b_begin + subs_per_cta);
+    double vn[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t r = b_begin * kSpSub + 16 * rq + i;
+        vn[i] = (has_col && b_begin < b_end && r < m) ? acol[r] : 0.0;
+    }
+    // Waits are per thread and bounded; one that gives up records a timeout
+    // and the loop runs to its end without publishing the sums.
+    bool ok = true;
+    int it = 0;
+    constexpr int kWinSubs = kSpWin / kSpSub;
+    for (int64_t b = b_begin; b < b_end; ++b, ++it) {
+        const int buf = it & 1;
+        unsigned char *bop = smem + buf * kSpBuf;  // A digits: kSpDigits planes, N x K
+        unsigned char *aop = bop + kSpDigits * kSpB;  // Omega' pieces: kSpZ planes, M x K
+        const int64_t r0 = b * kSpSub;
+        double v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = vn[i];
+        if (b + 1 < b_end) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int64_t r = (b + 1) * kSpSub + 16 * rq + i;
+                vn[i] = (has_col && r < m) ? acol[r] : 0.0;
+            }
+        }
+        if (it >= 2) ok &= mbar_wait_bounded(&mma_bar[buf], ((it - 2) >> 1) & 1, st);
+        // Omega' on the 2^-12 grid: 4096 z' = 256 zeta0 + zeta1 (round to nearest
+        // even by the 1.5 * 2^23 addition, as rint), both pieces exact in BF16
+        if (4 * kq < sw) {
+            float z[8][4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                rxr_normal4(seed, (uint64_t)(r0 + 8 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
+#pragma unroll
+            for (int t4 = 0; t4 < 4; ++t4) {
+                uint32_t p0[8], p1[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int q = (int)(__float_as_uint(__fadd_rn(__fmul_rn(z[i][t4], 4096.0f), 12582912.0f)) & 0x7FFFFFu) -
+                                  0x400000;
+                    const int z0 = (q + 128) >> 8;
+                    const int z1 = q - (z0 << 8);
+                    p0[i] = __float_as_uint(__fadd_rn(__uint_as_float(0x4B000000u | (uint32_t)(z0 + 128)), -8388736.0f));
+                    p1[i] = __float_as_uint(__fadd_rn(__uint_as_float(0x4B000000u | (uint32_t)(z1 + 128)), -8388736.0f));
+                }
+                const int r = 4 * kq + t4;
+                if (r < sw) {
+                    uint4 w0, w1;
+                    w0.x = __byte_perm(p0[0], p0[1], 0x7632);
+                    w0.y = __byte_perm(p0[2], p0[3], 0x7632);
+                    w0.z = __byte_perm(p0[4], p0[5], 0x7632);
+                    w0.w = __byte_perm(p0[6], p0[7], 0x7632);
+                    w1.x = __byte_perm(p1[0], p1[1], 0x7632);
+                    w1.y = __byte_perm(p1[2], p1[3], 0x7632);
+                    w1.z = __byte_perm(p1[4], p1[5], 0x7632);
+                    w1.w = __byte_perm(p1[6], p1[7], 0x7632);
+                    *reinterpret_cast<uint4 *>(aop + kmaj_off(r, 8 * warp)) = w0;
+                    *reinterpret_cast<uint4 *>(aop + kSpA + kmaj_off(r, 8 * warp)) = w1;
+                }
+            }
+        }
+        // digits of A: element (row k, column j) -> B tile (j, k)
+        if (has_col) {
+#pragma unroll
+            for (int g8 = 0; g8 < 2; ++g8) {
+                unsigned long long U[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[8 * g8 + r]), ej);
+#pragma unroll
+                for (int q = 0; q < kSpDigits; ++q) {
+                    uint4 w;
+                    w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
+                    w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
+                    w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
+                    w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+                    *reinterpret_cast<uint4 *>(bop + q * kSpB + kmaj_off(j, 16 * rq + 8 * g8)) = w;
+                }
+            }
+        }
+        const bool first_of_window = (it % kWinSubs) == 0;
+        if (first_of_window && it > 0) {
+            ok &= mbar_wait_bounded(&mma_bar[buf ^ 1], ((it - 1) >> 1) & 1, st);
+            tc_fence_after();
+            sketch_drain(tmem, q4, half, acc);
+        }
+        fence_proxy_async_shared();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t db = desc0 + (uint64_t)((buf * kSpBuf) >> 4);
+            const uint64_t da = db + (uint64_t)((kSpDigits * kSpB) >> 4);
+#pragma unroll
+            for (int kk = 0; kk < kSpSub / 16; ++kk)
+#pragma unroll
+                for (int p = 0; p < kSpZ; ++p)
+#pragma unroll
+                    for (int q = 0; q + p < kSpDigits; ++q) {
+                        const uint32_t acc_on = (!first_of_window || kk > 0 || p > 0) ? 1u : 0u;
+                        tc_mma(tmem + (uint32_t)((p + q) * kSpN), da + (uint64_t)((p * kSpA + kk * 256) >> 4),
+                               db + (uint64_t)((q * kSpB + kk * 256) >> 4), idesc, acc_on);
+                    }
+            tc_commit(&mma_bar[buf]);
+        }
+    }
+    if (it > 0) {
+        ok &= mbar_wait_bounded(&mma_bar[(it - 1) & 1], ((it - 1) >> 1) & 1, st);
+        tc_fence_after();
+        sketch_drain(tmem, q4, half, acc);
+    }
+    ok = __syncthreads_and(ok) != 0;
+    if (ok) {
+        double *out = Ypart + (int64_t)blockIdx.x * s * n;
+        const int my_row = 32 * q4 + lane;
+        const int r = s0 + my_row;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int cl = half * 32 + t;
+            if (my_row < sw && cl < nw) {
+                const int ce = cex[cl];
+                out[r + (int64_t)(c0 + cl) * s] = (ce > 0) ? ldexp(acc[t], ce - 1033) : 0.0;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // T = R^{-1} for upper-triangular R (one CTA; thread c solves R t = e_c by back
@@ -1541,10 +2046,22 @@ static int64_t ozaki_chunks(int64_t m, int64_t n, int sms)
     return balanced_chunks(ozaki_blocks((int)n), sms, cdiv64(m, kOzWin));
 }
 
-size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
+static size_t split_partial_bytes(int64_t m, int64_t n, int sms)
 {
     const int64_t gx = std::max<int64_t>(std::min<int64_t>(sms, cdiv64(m, kGsWin)), ozaki_chunks(m, n, sms));
-    return (size_t)gx * n * n * sizeof(double);
+    return ((size_t)gx * n * n * sizeof(double) + 255) & ~(size_t)255;
+}
+
+// partial sums, then a column-exponent array (int[512]: the split sketch's
+// columns of A, later the n <= 64 Gram's columns of X)
+size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
+{
+    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int);
+}
+
+int *split_colexp(const Plan &p)
+{
+    return reinterpret_cast<int *>(p.split + split_partial_bytes(p.m, p.n, p.sms));
 }
 
 // X <- X R^{-1} on the tensor cores through the explicit inverse (n <= 64);
@@ -1553,6 +2070,17 @@ int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaSt
 {
     if (p.n > kApK) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
+    if (p.n <= 64) {
+        k_tri_inverse64<<<1, 1024, 0, st>>>(R, (int)p.n, p.n, T, p.status);
+        if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+        const int n = (int)p.n;
+        CUtensorMap mx;
+        const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
+        const int64_t tiles = cdiv64(p.m, kAqM);
+        const int gx = (int)std::min<int64_t>(p.sms, tiles);
+        k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, p.status);
+        return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+    }
     k_tri_inverse<<<1, 128, 0, st>>>(R, (int)p.n, p.n, T, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t tiles = cdiv64(p.m, kApM);
@@ -1598,7 +2126,7 @@ int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double
 
 // X = B R^{-1} for n <= 64 in one pass over B (k_subst_fused); X may equal B.
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                        int64_t ldx, cudaStream_t st)
+                        int64_t ldx, int *colexp_out, cudaStream_t st)
 {
     if (p.n > kFuMaxN) return RXR_ERR_UNSUPPORTED;
     const int n = (int)p.n;
@@ -1608,13 +2136,33 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
     const int64_t tiles = cdiv64(p.m, kFuM);
     const int gx = (int)std::min<int64_t>(p.sms, cdiv64(tiles, 2));  // two tile streams per CTA
     k_subst_fused<<<gx, 256, fu_smem_bytes(n), st>>>(ms, md, use_tma, Bsrc, ldb, X, ldx, p.m, n, R, ldr, tiles,
-                                                      p.status);
+                                                      colexp_out, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
-int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
+int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, bool colexp_ready)
 {
     if (p.n > RXR_MAX_N) return RXR_ERR_UNSUPPORTED;
+    if (p.n <= 64) {
+        int *cx = split_colexp(p);
+        if (!colexp_ready) {
+            if (cudaMemsetAsync(cx, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+            const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
+            k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(X, ldx, p.m, cx, p.status);
+            if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+        }
+        const int64_t total = cdiv64(p.m, kG6Rows);
+        int64_t gx = std::min<int64_t>(p.sms, total);
+        const int64_t bpc = cdiv64(total, gx);
+        gx = cdiv64(total, bpc);
+        double *parts = reinterpret_cast<double *>(p.split);
+        k_gram_oz64<<<(unsigned)gx, 256, kG6Smem, st>>>(X, ldx, p.m, (int)p.n, cx, total, bpc, parts, p.status);
+        if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+        const int64_t nn = p.n * p.n;
+        k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(parts, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G,
+                                                             p.n, p.status);
+        return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+    }
     const int64_t win_total = cdiv64(p.m, kOzWin);
     int64_t gx = ozaki_chunks(p.m, p.n, p.sms);
     const int64_t wpc = cdiv64(win_total, gx);
@@ -1631,7 +2179,7 @@ int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)
 
 cudaError_t set_split_smem()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sketch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpSmem2);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGsSmem);
     if (e == cudaSuccess)
@@ -1645,19 +2193,29 @@ cudaError_t set_split_smem()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_subst_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fu_smem_bytes(kFuMaxN));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gram_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kG6Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)aq_smem_bytes(64));
     return e;
 }
 
 int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st)
 {
+    // column exponents of A over all rows (the digit scale of each column)
+    int *cx = split_colexp(p);
+    if (cudaMemsetAsync(cx, 0, (size_t)p.n * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+    const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
+    k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(A, lda, p.m, cx, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t gy = cdiv64(p.s, kSpM) * cdiv64(p.n, kSpN);
-    const int64_t win_total = cdiv64(p.m, kSpWin);
-    int64_t gx = balanced_chunks(gy, p.sms, win_total);
-    const int64_t wpc = cdiv64(win_total, gx);
-    gx = cdiv64(win_total, wpc);
+    const int64_t subs_total = cdiv64(p.m, kSpSub);
+    int64_t gx = balanced_chunks(gy, p.sms, cdiv64(p.m, kSpWin));
+    const int64_t spc = cdiv64(subs_total, gx);
+    gx = cdiv64(subs_total, spc);
     if (gx > p.sk_gx) return RXR_ERR_NOMEM;  // partial buffer sized by the FP64 plan
-    k_sketch_split<<<dim3((unsigned)gx, (unsigned)gy), 256, kSpSmem, st>>>(A, lda, p.m, (int)p.n, (int)p.s, seed,
-                                                                         win_total, wpc, p.Ypart, p.status);
+    k_sketch_split<<<dim3((unsigned)gx, (unsigned)gy), 256, kSpSmem2, st>>>(A, lda, p.m, (int)p.n, (int)p.s, seed, cx,
+                                                                          subs_total, spc, p.Ypart, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t sn = p.s * p.n;
     k_reduce_parts<<<(int)cdiv64(sn, 256), 256, 0, st>>>(p.Ypart, (int)gx, sn, (int)p.s, (int)p.n,

@@ -143,3 +143,20 @@ def test_fused_substitution_first_block_is_plain_substitution(h):
     Xs, _ = h.precond_gram(to_dev(A), to_dev(R), prec="split")
     Xf, _ = h.precond_gram(to_dev(A), to_dev(R), prec="fp64")
     assert np.array_equal(to_host(Xs)[:, :16], to_host(Xf)[:, :16])
+
+
+@pytest.mark.parametrize("m,n", [(64 * 152 * 5 + 13, 64), (4100, 33), (300, 1)])
+def test_ozaki_gram_column_scales(h, m, n):
+    # columns scaled across the whole FP64 range, one column zero: the Gram must
+    # stay FP64-grade column-normwise (the digit scale of each column is its own
+    # largest exponent over all rows)
+    rng = np.random.default_rng(m)
+    X = usv_matrix(m, n, 1e4, seed=m + 1) * np.ldexp(1.0, rng.integers(-400, 400, size=n))[None, :]
+    if n > 2:
+        X[:, 2] = 0.0
+    Gs = to_host(h.gram(to_dev(X), prec="split"))
+    Go = o.gram(X)
+    cm = np.abs(X).max(axis=0)
+    bound = 8 * (m + 2) * U * (np.abs(X).T @ np.abs(X)) + 2.0**-52 * m * np.outer(cm, cm)
+    assert np.all(np.abs(Gs - Go) <= bound), np.nanmax(np.abs(Gs - Go) / np.where(bound > 0, bound, 1))
+    assert np.array_equal(Gs, Gs.T)
