@@ -310,11 +310,39 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
+def subst_fp64_flop_per_row(n, bw, sub_ops):
+    """FP64 flop a blocked substitution issues per row: the diagonal-block
+    solves (bw (bw - 1) / 2 FMAs per block, 2 flop each), the n multiplications
+    by 1 / R_jj, and sub_ops FP64 operations per trailing output per block (the
+    subtraction of the tensor-core update)."""
+    flop, c0 = 0.0, 0
+    while c0 < n:
+        b = min(bw, n - c0)
+        flop += b * (b - 1) + sub_ops * (n - c0 - b)
+        c0 += b
+    return flop + n
+
+
+def launches_per_step(prec, n):
+    """Kernels one CholeskyQR2 factorisation launches (P = 2)."""
+    if prec == "fp64":
+        # sketch, reduce, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
+        return 11 if n <= 128 else 13
+    if n <= 64:
+        # colexp, sketch, reduce, XR, 2 x (fused substitution, Gram, reduce, factor), inverse, apply, copy
+        return 15
+    bw = 32 if n <= 128 else 64
+    blocked = 2 * ((n + bw - 1) // bw) - 1  # diagonal solves + trailing updates
+    return 4 + 3 * blocked + 2 * 2 + 2 + 1
+
+
 def roofline_entry(prec, stages, peak_fp64):
-    """The dominant FP64 launch of the path against the measured DFMA peak.
+    """The dominant FP64 launch of the path against the measured DFMA peak,
+    counting the FP64 flop that launch actually issues.
     FP64 path: the fused precondition+Gram launch, (2n^2 + n) flop per row.
-    Split path: the FP64 substitution X = A R_s^{-1}, n^2 flop per row (its Gram
-    runs on the tensor cores)."""
+    Split path: the substitution X = A R_s^{-1}; its trailing updates run on the
+    tensor cores, so only its diagonal-block solves and the FP64 subtractions
+    of the updates are FP64 work."""
     if prec == "fp64":
         t = stages.get("precond_subst")
         flop = (2.0 * N * N + N) * M
@@ -323,16 +351,14 @@ def roofline_entry(prec, stages, peak_fp64):
         hbm_bytes = 16.0 * M * N
     elif N <= 64:
         t = stages.get("precond_subst")
-        flop = (1.0 * N * N) * M
-        name = "k_subst_gram (FP64 substitution X = A R_s^-1; its Gram is on the tensor cores)"
+        flop = subst_fp64_flop_per_row(N, 16, 2) * M
+        name = "k_subst_fused (FP64 16-column diagonal solves + FP64 subtraction of tcgen05 updates)"
         traffic = TRAFFIC_SUBST if (M == 2**22 and N == 64) else None
         hbm_bytes = 16.0 * M * N
     else:
-        # blocked substitution: FP64 diagonal blocks + tensor-core trailing updates;
-        # achieved counts the n^2 FP64-equivalent flop, so frac can exceed 1
         t = stages.get("precond_subst")
-        flop = (1.0 * N * N) * M
-        name = "blocked substitution X = A R_s^-1 (FP64 diagonal blocks, tcgen05 updates), FP64-equivalent flop"
+        flop = subst_fp64_flop_per_row(N, 32 if N <= 128 else 64, 3) * M
+        name = "k_solve_block + k_update_ozaki (blocked substitution: FP64 diagonal blocks, tcgen05 updates)"
         traffic = None
         hbm_bytes = 16.0 * M * N
     achieved = flop / (t * 1e-3) / 1e12
@@ -363,7 +389,7 @@ def e2e_leg(h, A_np, args, world):
 
 
 def _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu):
-    launches = {"fp64": 11, "split": 14 if N <= 64 else 13}[args.prec] if PASSES == 2 else None
+    launches = launches_per_step(args.prec, N) if PASSES == 2 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -474,16 +474,20 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         return RXR_ERR_CUDA;
     // step 3: X = A R_s^{-1} into Q, fused with G_1 = X^T X
     {
-        // the BF16x3 split Gram covers n <= 128; wider panels take the FP64-grade
-        // tensor-core Gram
+        // the first Gram on the tensor cores: FP64-grade stacked digits for
+        // n <= 64, BF16x3 for 64 < n <= 128, FP64-grade 128 x 64 blocks above
         if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
+            // n <= 64: the substitution records X's column exponents and the
+            // FP64-grade stacked-digit Gram (faster than the BF16x3 one here)
+            // follows
+            int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
             {
                 Timer t(th, 1, st);
-                if (int e = split_subst(p, A, lda, p.Rs, Q, ldq, st)) return e;
+                if (int e = split_subst(p, A, lda, p.Rs, Q, ldq, st, cx)) return e;
             }
             Timer t(th, 4, st);
-            if (p.wide) {
-                if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) return e;
+            if (p.wide || cx) {
+                if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st, cx != nullptr)) return e;
             } else if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) {
                 return e;
             }
@@ -1002,8 +1006,10 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
         return RXR_ERR_CUDA;
     if (prec == RXR_SPLIT_BF16) {
         if (X == nullptr) return RXR_ERR_UNSUPPORTED;
-        if (int e = split_subst(p, A, lda, p.Rp, X, ldx, st)) return e;
-        if (int e = p.wide ? ozaki_gram_enqueue(p, X, ldx, st) : split_gram_enqueue(p, X, ldx, st)) return e;
+        int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
+        if (int e = split_subst(p, A, lda, p.Rp, X, ldx, st, cx)) return e;
+        if (int e = (p.wide || cx) ? ozaki_gram_enqueue(p, X, ldx, st, cx != nullptr) : split_gram_enqueue(p, X, ldx, st))
+            return e;
     } else {
         if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, true, false, st)) return e;
     }

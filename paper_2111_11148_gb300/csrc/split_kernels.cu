@@ -1155,6 +1155,7 @@ __global__ void __launch_bounds__(256, 1)
 
     // --- this group's tile stream: tiles 2 * blockIdx.x + g, + 2 * gridDim.x, ...
     uint32_t loads = 0, mphase = 0;  // TMA loads consumed; tensor-core commits consumed
+    unsigned cmax_lo = 0, cmax_hi = 0;  // largest exponent of columns lane and lane + 32 (colexp_out)
     bool ok = true, load_pending = false, mma_pending = false;
     const int64_t stride = 2 * (int64_t)gridDim.x;
     for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < tiles_total && ok; tile += stride) {
@@ -1198,7 +1199,19 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                 for (int j = 0; j < kFuBw; ++j) {
                     if (c16 + j < n) xs[(c16 + j) * kFuM + row] = v[j];
-                    ex = max(ex, ((unsigned)__double2hiint(v[j]) >> 20) & 0x7FFu);
+                    const unsigned ej = ((unsigned)__double2hiint(v[j]) >> 20) & 0x7FFu;
+                    ex = max(ex, ej);
+                    if (colexp_out != nullptr) {
+                        // these columns are final: the warp's largest exponent per
+                        // column is kept by lane (column mod 32)
+                        const unsigned w = __reduce_max_sync(0xFFFFFFFFu, ej);
+                        if (((c16 + j) & 31) == lane) {
+                            if (c16 + j < 32)
+                                cmax_lo = max(cmax_lo, w);
+                            else
+                                cmax_hi = max(cmax_hi, w);
+                        }
+                    }
                 }
                 ei = (int)ex;
                 if (Nc > 0) {
@@ -1281,15 +1294,6 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
         if (!ok) break;
-        if (colexp_out != nullptr) {
-            // column exponents of the finished tile (this thread's row), max over
-            // the warp's 32 rows, then over the CTA in shared memory
-            for (int jj = 0; jj < n; ++jj) {
-                unsigned e = ((unsigned)__double2hiint(xs[jj * kFuM + row]) >> 20) & 0x7FFu;
-                e = __reduce_max_sync(0xFFFFFFFFu, e);
-                if (lane == 0 && e > 0) atomicMax(&out_exp[jj], (int)e);
-            }
-        }
         if (use_tma) {
             fence_proxy_async_shared();
             group_bar(g);
@@ -1314,6 +1318,10 @@ __global__ void __launch_bounds__(256, 1)
     if (leader && use_tma) {
         if (load_pending) mbar_wait_bounded(&full_bar[g], loads & 1u, st);
         bulk_wait_all();
+    }
+    if (colexp_out != nullptr) {
+        if (cmax_lo > 0) atomicMax(&out_exp[lane], (int)cmax_lo);
+        if (cmax_hi > 0) atomicMax(&out_exp[lane + 32], (int)cmax_hi);
     }
     tc_fence_before();
     __syncthreads();
@@ -1749,44 +1757,41 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// T = R^{-1} for upper-triangular R, n <= 64, one CTA of 1024 threads with R
-// and T in shared memory.  16 lanes per column c solve R t = e_c by back
-// substitution: row i takes the dot product of R's row i with the entries of
-// t already known, split over the 16 lanes and reduced in a fixed order by
-// shuffles, times 1 / R_ii (precomputed).
-__global__ void __launch_bounds__(1024) k_tri_inverse64(const double *__restrict__ R, int n, int64_t ldr,
-                                                         double *__restrict__ T, RxrStatus *st)
+// T = R^{-1} for upper-triangular R, n <= 64: CTA c (one warp) solves
+// R t = e_c by column-oriented back substitution.  Lane l holds rows l and
+// l + 32 of t; for k = c, c - 1, ..., 0 the owner of row k forms
+// t_k = s_k / R_kk (times the precomputed reciprocal), one shuffle broadcasts
+// it, and every lane updates its rows i < k: s_i -= R_ik t_k (k descending, a
+// fixed order).  R's leading c + 1 columns are staged in shared memory.  One
+// warp per SM keeps the FP64 pipe free of contention: the chain of
+// dependent operations, not FP64 throughput, sets the time.
+__global__ void __launch_bounds__(32) k_tri_inverse64(const double *__restrict__ R, int n, int64_t ldr,
+                                                       double *__restrict__ T, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
-    __shared__ double rs[64 * 65];  // R[i][k] at i * 65 + k
-    __shared__ double ts[64 * 65];  // T[k][c] at c * 65 + k
-    __shared__ double dinv[64];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < n * n; e += blockDim.x) {
-        const int i = e % n, k = e / n;
-        rs[i * 65 + k] = R[i + (int64_t)k * ldr];
-        ts[k * 65 + i] = 0.0;
+    __shared__ double rs[64 * 64];  // R[i][k] at k * 64 + i
+    const int c = blockIdx.x, lane = threadIdx.x;
+    for (int k = 0; k <= c; ++k) {
+        rs[k * 64 + lane] = (lane <= k) ? R[lane + (int64_t)k * ldr] : 0.0;
+        if (lane + 32 < n) rs[k * 64 + lane + 32] = (lane + 32 <= k) ? R[lane + 32 + (int64_t)k * ldr] : 0.0;
     }
-    if (tid < n) dinv[tid] = 1.0 / R[tid + (int64_t)tid * ldr];
-    __syncthreads();
-    const int c = tid >> 4, sl = tid & 15;  // column, lane within the column's 16
-    double *tc = ts + c * 65;
-    if (c < n && sl == 0) tc[c] = dinv[c];
+    const double d0 = (lane < n) ? 1.0 / R[lane + (int64_t)lane * ldr] : 0.0;
+    const double d1 = (lane + 32 < n) ? 1.0 / R[(lane + 32) + (int64_t)(lane + 32) * ldr] : 0.0;
     __syncwarp();
-    for (int i = n - 2; i >= 0; --i) {
-        double part = 0.0;
-        if (c < n && c > i)
-            for (int k = i + 1 + sl; k <= c; k += 16) part = fma(rs[i * 65 + k], tc[k], part);
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-        if (c < n && c > i && sl == 0) tc[i] = -part * dinv[i];
-        __syncwarp();
+    double s0 = (lane == c) ? 1.0 : 0.0, s1 = (lane + 32 == c) ? 1.0 : 0.0;
+    for (int k = c; k >= 0; --k) {
+        const double own = (k < 32) ? s0 * d0 : s1 * d1;  // right only in the owner lane
+        const double tk = __shfl_sync(0xFFFFFFFFu, own, k & 31);
+        if (k < 32) {
+            if (lane == k) s0 = tk;
+        } else if (lane == k - 32) {
+            s1 = tk;
+        }
+        if (lane < k) s0 = fma(-rs[k * 64 + lane], tk, s0);
+        if (lane + 32 < k) s1 = fma(-rs[k * 64 + lane + 32], tk, s1);
     }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += blockDim.x) {
-        const int k = e % n, cc = e / n;
-        T[k + (int64_t)cc * n] = ts[cc * 65 + k];
-    }
+    if (lane < n) T[lane + (int64_t)c * n] = (lane <= c) ? s0 : 0.0;
+    if (lane + 32 < n) T[lane + 32 + (int64_t)c * n] = (lane + 32 <= c) ? s1 : 0.0;
 }
 
 // One exact window of the split sketch folded into this thread's FP64
@@ -2071,7 +2076,7 @@ int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaSt
     if (p.n > kApK) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
     if (p.n <= 64) {
-        k_tri_inverse64<<<1, 1024, 0, st>>>(R, (int)p.n, p.n, T, p.status);
+        k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
         if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
         const int n = (int)p.n;
         CUtensorMap mx;
