@@ -215,10 +215,14 @@ RXR_API int rxr_resid_error(rxr_handle h, const double *A, int64_t m, int64_t n,
  * roofline.  Blocking. */
 RXR_API int rxr_fp64_peak(double *tflops, void *stream);
 
-/* Device time in milliseconds of the most recent launch of `kernel` made by
- * a blocking or host call on this handle, measured with CUDA events on the
- * launching stream (kernel: 0 sketch, 1 precondition+Gram, 2 pass-2 Gram,
- * 3 Q apply).  Returns -1 for an unknown kernel id. */
+/* Device time in milliseconds of one stage of the most recent blocking or
+ * host factorisation on this handle, measured with CUDA events on the
+ * launching stream.  Stage ids: 0 sketch (with its reduction), 1
+ * preconditioning substitution X = A R_s^{-1} (FP64 path: with its Gram),
+ * 2 substitution of a middle CholeskyQR pass (FP64 path: with the next
+ * Gram), 3 last pass's Q formation, 4 first Gram on the tensor cores, 5 later
+ * Gram on the tensor cores, 6 XR factorisation of the sketch.  A stage the
+ * last call did not run reads 0.  Returns -1 for an unknown stage id. */
 RXR_API int rxr_last_kernel_ms(rxr_handle h, int kernel, float *ms);
 
 /* Enable or disable the per-kernel events of rxr_last_kernel_ms (off by default). */

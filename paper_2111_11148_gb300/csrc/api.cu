@@ -567,13 +567,16 @@ int finish_blocking(rxr_handle h, const RxrStatus *d_status, cudaStream_t st)
         h->last_col = h->h_status[2];
     }
     if (h->timing)
-        for (int k = 0; k < kTimers; ++k)
-            if (h->ev_recorded[k]) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, h->ev[k][0], h->ev[k][1]) == cudaSuccess) h->last_ms[k] = ms;
-                else (void)cudaGetLastError();
-                h->ev_recorded[k] = false;
+        for (int k = 0; k < kTimers; ++k) {
+            // a stage the last call did not run reads 0
+            float ms = 0.f;
+            if (h->ev_recorded[k] && cudaEventElapsedTime(&ms, h->ev[k][0], h->ev[k][1]) != cudaSuccess) {
+                (void)cudaGetLastError();
+                ms = 0.f;
             }
+            h->last_ms[k] = ms;
+            h->ev_recorded[k] = false;
+        }
     return code;
 }
 

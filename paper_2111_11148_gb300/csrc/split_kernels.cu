@@ -574,175 +574,12 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// ---------------------------------------------------------------------------
-// FP64-grade product Q = X T on the tensor cores (the last CholeskyQR pass's
-// apply, T = R_P^{-1}; R_P is within rounding of I once the first pass has
-// made X orthonormal to O(u cond^2), so its explicit inverse is as accurate as
-// substitution).  Row i of X is split relative to its own largest exponent
-// and column l of T relative to its own, seven 8-bit digits each; the digit
-// pairs p + q = d accumulate in tensor memory exactly (K = n <= 64: sums below
-// 2^24) and each output is combined once, scaled by 2^(e_i + e_l).  X is read
-// and overwritten in place, 128 rows per tile.
-// ---------------------------------------------------------------------------
+// operand tiles of the blocked substitution's trailing update (k_update_ozaki)
 constexpr int kApM = 128, kApK = 64, kApN = 64, kApDigits = 7;
 constexpr int kApATile = kApM * kApK * 2;  // 16 KB per digit
 constexpr int kApBTile = kApN * kApK * 2;  // 8 KB per digit
 constexpr size_t kApSmem = (size_t)kApDigits * (kApATile + kApBTile);
 
-__global__ void __launch_bounds__(256, 1)
-    k_apply_ozaki(double *X, int64_t ldx, int64_t m, int n, const double *__restrict__ T, int64_t ldt,
-                  int64_t tiles_total, int64_t tiles_per_cta, RxrStatus *st)
-{
-    if (rxr_failed(st)) return;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *aop = smem;                          // X digits, rows x k
-    unsigned char *bop = smem + kApDigits * kApATile;   // T digits, cols l x k
-    __shared__ __align__(8) uint64_t mma_bar;
-    __shared__ uint32_t tmem_base;
-    __shared__ int rowexp[kApM];
-    __shared__ int colexp_t[kApN];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    for (int e = tid; e < (int)(kApSmem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) {
-        mbar_init(&mma_bar, 1);
-        fence_barrier_init();
-    }
-    // exponents and digits of T (once per CTA): B tile element (l, k) = T[k][l]
-    if (tid < kApN) {
-        unsigned ex = 0;
-        if (tid < n)
-            for (int k = 0; k <= tid; ++k) ex = max(ex, ((unsigned)__double2hiint(T[k + (int64_t)tid * ldt]) >> 20) & 0x7FFu);
-        colexp_t[tid] = (int)ex;
-    }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += blockDim.x) {
-        const int k = e % n, l = e / n;
-        const unsigned long long bits = (k <= l) ? (unsigned long long)__double_as_longlong(T[k + (int64_t)l * ldt]) : 0ull;
-        float dg[kApDigits];
-        digits7(bits, colexp_t[l], dg);
-        const int off = kmaj_off(l, k);
-#pragma unroll
-        for (int q = 0; q < kApDigits; ++q) st_bf16(bop + q * kApBTile, off, dg[q]);
-    }
-    if (warp == 0) tmem_alloc(&tmem_base, 512);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = idesc_bf16(kApM, kApN);
-    const int q4 = warp & 3, half = warp >> 2;
-    const int my_row = 32 * q4 + lane;
-
-    uint32_t phase = 0;
-    bool pending = false, ok = true;
-    const int64_t t_begin = blockIdx.x * tiles_per_cta;
-    const int64_t t_end = min(tiles_total, t_begin + tiles_per_cta);
-    for (int64_t tile = t_begin; tile < t_end && ok; ++tile) {
-        const int64_t r0 = tile * kApM;
-        // per-row exponent over the row's n entries (thread per row)
-        if (tid < kApM) {
-            unsigned ex = 0;
-            const int64_t gr = r0 + tid;
-            if (gr < m)
-                for (int k = 0; k < n; ++k) ex = max(ex, ((unsigned)__double2hiint(X[gr + (int64_t)k * ldx]) >> 20) & 0x7FFu);
-            rowexp[tid] = (int)ex;
-        }
-        __syncthreads();
-        // digits of the 128 x n tile, 16 loads in flight per thread
-        const int iters = (kApM * n + 255) / 256;
-        for (int base = 0; base < iters; base += 16) {
-            unsigned long long vb[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int e = tid + 256 * (base + t);
-                const int i = e & (kApM - 1), k = e >> 7;
-                const int64_t gr = r0 + i;
-                vb[t] = (k < n && gr < m && base + t < iters)
-                            ? (unsigned long long)__double_as_longlong(X[gr + (int64_t)k * ldx])
-                            : 0ull;
-            }
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int e = tid + 256 * (base + t);
-                const int i = e & (kApM - 1), k = e >> 7;
-                if (k < n && base + t < iters) {
-                    float dg[kApDigits];
-                    digits7(vb[t], rowexp[i], dg);
-                    const int off = kmaj_off(i, k);
-#pragma unroll
-                    for (int q = 0; q < kApDigits; ++q) st_bf16(aop + q * kApATile, off, dg[q]);
-                }
-            }
-        }
-        fence_proxy_async_shared();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(aop), b0 = smem_u32(bop);
-#pragma unroll
-            for (int kk = 0; kk < kApK / 16; ++kk)
-#pragma unroll
-                for (int p = 0; p < kApDigits; ++p)
-#pragma unroll
-                    for (int q = 0; p + q < kApDigits; ++q) {
-                        const uint32_t acc_on = (kk > 0 || p > 0) ? 1u : 0u;
-                        tc_mma(tmem + (uint32_t)((p + q) * kApN), smem_desc(a0 + p * kApATile + kk * 256, 128, 1024),
-                               smem_desc(b0 + q * kApBTile + kk * 256, 128, 1024), idesc, acc_on);
-                    }
-            tc_commit(&mma_bar);
-        }
-        pending = true;
-        ok = mma_wait(&mma_bar, phase, st);
-        if (!ok) break;
-        phase ^= 1u;
-        pending = false;
-        tc_fence_after();
-        const int ei = rowexp[my_row];
-        const int64_t gr = r0 + my_row;
-#pragma unroll
-        for (int c16 = 0; c16 < 2; ++c16) {
-            const int col0 = half * 32 + c16 * 16;
-            float hi[16], lo[16], v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
-#pragma unroll
-            for (int t = 0; t < 16; ++t) lo[t] = 0.0f;
-#pragma unroll
-            for (int d = 1; d < kApDigits; ++d) {
-                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + d * kApN + col0, v);
-                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
-#pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const float x = __fmul_rn(v[t], w8);
-                    const float sum = __fadd_rn(hi[t], x);
-                    const float bb = __fsub_rn(sum, hi[t]);
-                    const float err = __fadd_rn(__fsub_rn(hi[t], __fsub_rn(sum, bb)), __fsub_rn(x, bb));
-                    hi[t] = sum;
-                    lo[t] = __fadd_rn(lo[t], err);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int l = col0 + t;
-                if (l < n && gr < m) {
-                    const int el = colexp_t[l];
-                    const int be = ei + el - 1035;
-                    const double scale = (ei > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
-                    X[gr + (int64_t)l * ldx] = (rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t])) * scale;
-                }
-            }
-        }
-        tc_fence_before();
-        __syncthreads();
-    }
-    if (pending) {
-        mma_wait(&mma_bar, phase, st);
-        tc_fence_after();
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 512);
-}
 
 // ---------------------------------------------------------------------------
 // Trailing update of the blocked substitution, on the tensor cores at FP64
@@ -2020,21 +1857,6 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// T = R^{-1} for upper-triangular R (one CTA; thread c solves R t = e_c by back
-// substitution).
-__global__ void k_tri_inverse(const double *__restrict__ R, int n, int64_t ldr, double *__restrict__ T, RxrStatus *st)
-{
-    if (rxr_failed(st)) return;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int i = n - 1; i > c; --i) T[i + (int64_t)c * n] = 0.0;
-        T[c + (int64_t)c * n] = 1.0 / R[c + (int64_t)c * ldr];
-        for (int i = c - 1; i >= 0; --i) {
-            double acc = 0.0;
-            for (int k = i + 1; k <= c; ++k) acc = fma(R[i + (int64_t)k * ldr], T[k + (int64_t)c * n], acc);
-            T[i + (int64_t)c * n] = -acc / R[i + (int64_t)i * ldr];
-        }
-    }
-}
 
 __global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, int, double *, int64_t, RxrStatus *);
 
@@ -2073,26 +1895,16 @@ int *split_colexp(const Plan &p)
 // T is held in the XR scratch (s x n >= n x n).
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
 {
-    if (p.n > kApK) return RXR_ERR_UNSUPPORTED;
+    if (p.n > 64) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
-    if (p.n <= 64) {
-        k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
-        if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
-        const int n = (int)p.n;
-        CUtensorMap mx;
-        const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
-        const int64_t tiles = cdiv64(p.m, kAqM);
-        const int gx = (int)std::min<int64_t>(p.sms, tiles);
-        k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, p.status);
-        return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
-    }
-    k_tri_inverse<<<1, 128, 0, st>>>(R, (int)p.n, p.n, T, p.status);
+    k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
-    const int64_t tiles = cdiv64(p.m, kApM);
-    int64_t gx = std::min<int64_t>(p.sms, tiles);
-    const int64_t tpc = cdiv64(tiles, gx);
-    gx = cdiv64(tiles, tpc);
-    k_apply_ozaki<<<(unsigned)gx, 256, kApSmem, st>>>(X, ldx, p.m, (int)p.n, T, p.n, tiles, tpc, p.status);
+    const int n = (int)p.n;
+    CUtensorMap mx;
+    const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
+    const int64_t tiles = cdiv64(p.m, kAqM);
+    const int gx = (int)std::min<int64_t>(p.sms, tiles);
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
@@ -2189,8 +2001,6 @@ cudaError_t set_split_smem()
         e = cudaFuncSetAttribute(k_gram_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGsSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gram_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_apply_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_update_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApSmem);
     if (e == cudaSuccess)
