@@ -108,7 +108,7 @@ PFN_encodeTiled get_encode()
 // rules are not met (16-byte aligned base, ld * 8 a multiple of 16, box sizes
 // in range); the kernels then stage panels with plain coalesced loads.
 bool encode_2d(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-               int box_cols)
+               int box_cols, bool swizzle128 = false)
 {
     memset(map, 0, sizeof(*map));
     PFN_encodeTiled enc = get_encode();
@@ -121,7 +121,8 @@ bool encode_2d(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, in
     cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(ptr), gdim, gstride, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -151,9 +152,10 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 namespace rxr {
 bool encode_tile_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-                     int box_cols)
+                     int box_cols, bool swizzle128)
 {
-    return encode_2d(map, ptr, rows, cols, ld, box_rows, box_cols);
+    if (swizzle128 && box_rows * 8 > 128) return false;  // the swizzle span is one 128-byte row of the box
+    return encode_2d(map, ptr, rows, cols, ld, box_rows, box_cols, swizzle128);
 }
 
 // Row chunks for a grid of gx x gy CTAs on `slots` resident CTA slots: the gx

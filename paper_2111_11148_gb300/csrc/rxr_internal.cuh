@@ -200,6 +200,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
 {
     uint32_t ok;
@@ -360,8 +365,9 @@ int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                         int64_t ldx, int *colexp_out, cudaStream_t st);
 // 2-D tensor map of a column-major FP64 matrix (api.cu); false where TMA's
-// alignment rules are not met
+// alignment rules are not met.  swizzle128: 128-byte swizzle (box_rows <= 16;
+// in shared memory, 16-byte chunk c of box column j sits at chunk c ^ (j mod 8))
 bool encode_tile_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-                     int box_cols);
+                     int box_cols, bool swizzle128 = false);
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
 }  // namespace rxr

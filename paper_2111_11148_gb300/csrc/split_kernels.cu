@@ -26,6 +26,7 @@
 //   (Theorem 3.4) and the error of G only perturbs R_1, which the second, FP64
 //   CholeskyQR pass corrects (Algorithm 2).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -53,6 +54,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16 with FP16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
@@ -348,6 +355,52 @@ __device__ __forceinline__ void digits7(unsigned long long bits, int emax, float
     const unsigned long long U = digits_offset(bits, emax);
 #pragma unroll
     for (int q = 0; q < kOzDigits; ++q) dg[q] = __uint_as_float(digit_bits(U, q));
+}
+
+// Digit q of two offset forms as one packed FP16 pair (value a in the low
+// half): 0x6400 | (digit + 128) encodes the FP16 number 1024 + digit + 128
+// (exact: at most 9 bits over 2^10), so one packed subtraction of 1152 leaves
+// the digits themselves, exact in FP16.
+__device__ __forceinline__ uint32_t digit_pair_f16(unsigned long long Ua, unsigned long long Ub, int q)
+{
+    uint32_t w;
+    if (q == 0) {
+        const uint32_t ta = (uint32_t)((int)((long long)Ua >> 48) + 128);
+        const uint32_t tb = (uint32_t)((int)((long long)Ub >> 48) + 128);
+        w = ta | (tb << 16) | 0x64006400u;
+    } else {
+        const int k = 6 - q, kb = k & 3;  // byte k of U: digit q + 128
+        const uint32_t wa = (k < 4) ? (uint32_t)Ua : (uint32_t)(Ua >> 32);
+        const uint32_t wb = (k < 4) ? (uint32_t)Ub : (uint32_t)(Ub >> 32);
+        w = (__byte_perm(wa, wb, (uint32_t)(kb | ((4 + kb) << 8))) & 0x00FF00FFu) | 0x64006400u;
+    }
+    const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&w), __half2half2(__ushort_as_half((unsigned short)0x6480u)));
+    return *reinterpret_cast<const uint32_t *>(&r);
+}
+
+// Digit plane q of eight consecutive K elements (offset forms U[0..7]) as one
+// 16-byte FP16 store.
+__device__ __forceinline__ uint4 pack_plane_f16(const unsigned long long U[8], int q)
+{
+    uint4 w;
+    w.x = digit_pair_f16(U[0], U[1], q);
+    w.y = digit_pair_f16(U[2], U[3], q);
+    w.z = digit_pair_f16(U[4], U[5], q);
+    w.w = digit_pair_f16(U[6], U[7], q);
+    return w;
+}
+
+// Eight small integers t[i] + 128 in [0, 256] (i = 0..7) as FP16 t[i].
+__device__ __forceinline__ uint4 pack_int8x_f16(const uint32_t t[8])
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t v = t[2 * i] | (t[2 * i + 1] << 16) | 0x64006400u;
+        const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&v), __half2half2(__ushort_as_half((unsigned short)0x6480u)));
+        w[i] = *reinterpret_cast<const uint32_t *>(&r);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Largest exponent of columns [c0, c0 + ncol) of X over the window rows, one
@@ -848,18 +901,6 @@ __device__ __forceinline__ int kmaj16_off(int row, int k)
     return (row & 7) * 16 + (row >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
 }
 
-// Eight BF16 values packed for one 16-byte store.  The values are integers
-// of at most eight significant bits, so each BF16 is the upper half of its
-// FP32 encoding (no rounding).
-__device__ __forceinline__ uint4 pack_bf16x8(const float *v)
-{
-    uint4 r;
-    r.x = __byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632);
-    r.y = __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632);
-    r.z = __byte_perm(__float_as_uint(v[4]), __float_as_uint(v[5]), 0x7632);
-    r.w = __byte_perm(__float_as_uint(v[6]), __float_as_uint(v[7]), 0x7632);
-    return r;
-}
 
 // f * 2^(be - 1023) as a double, built on the integer pipes (exact: f is
 // normal and the result's exponent stays in range; results below the normal
@@ -965,19 +1006,15 @@ __global__ void __launch_bounds__(256, 1)
         for (int l = tid; l < Nc; l += blockDim.x) {
             const int ex = colexp[fu_cbase(n, c) + l];
             for (int k0 = 0; k0 < kFuBw; k0 += 8) {
-                float dg[8][kFuDigits];
+                unsigned long long U[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
-                    digits7((unsigned long long)__double_as_longlong(
-                                R[(kFuBw * c + k0 + k) + (int64_t)(kFuBw * (c + 1) + l) * ldr]),
-                            ex, dg[k]);
+                    U[k] = digits_offset((unsigned long long)__double_as_longlong(
+                                             R[(kFuBw * c + k0 + k) + (int64_t)(kFuBw * (c + 1) + l) * ldr]),
+                                         ex);
 #pragma unroll
-                for (int q = 0; q < kFuDigits; ++q) {
-                    float v[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] = dg[k][q];
-                    *reinterpret_cast<uint4 *>(bd + q * Np * kFuBw * 2 + kmaj16_off(l, k0)) = pack_bf16x8(v);
-                }
+                for (int q = 0; q < kFuDigits; ++q)
+                    *reinterpret_cast<uint4 *>(bd + q * Np * kFuBw * 2 + kmaj16_off(l, k0)) = pack_plane_f16(U, q);
             }
         }
     }
@@ -1054,17 +1091,12 @@ __global__ void __launch_bounds__(256, 1)
                 if (Nc > 0) {
 #pragma unroll
                     for (int j0 = 0; j0 < kFuBw; j0 += 8) {
-                        float dg[8][kFuDigits];
+                        unsigned long long U[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            digits7((unsigned long long)__double_as_longlong(v[j0 + j]), ei, dg[j]);
+                        for (int j = 0; j < 8; ++j) U[j] = digits_offset((unsigned long long)__double_as_longlong(v[j0 + j]), ei);
 #pragma unroll
-                        for (int q = 0; q < kFuDigits; ++q) {
-                            float w[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) w[j] = dg[j][q];
-                            *reinterpret_cast<uint4 *>(adig + q * kFuATile + kmaj16_off(row, j0)) = pack_bf16x8(w);
-                        }
+                        for (int q = 0; q < kFuDigits; ++q)
+                            *reinterpret_cast<uint4 *>(adig + q * kFuATile + kmaj16_off(row, j0)) = pack_plane_f16(U, q);
                     }
                 }
             }
@@ -1081,7 +1113,7 @@ __global__ void __launch_bounds__(256, 1)
                 if (leader) {
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(adig), b0 = smem_u32(bd) + (uint32_t)(n0 * kFuBw * 2);
-                    const uint32_t idesc = idesc_bf16(kFuM, nw);
+                    const uint32_t idesc = idesc_f16(kFuM, nw);
 #pragma unroll
                     for (int p = 0; p < kFuDigits; ++p)
 #pragma unroll
@@ -1166,35 +1198,49 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) tmem_dealloc(tmem_base, 512);
 }
 
-// One exact window of k_gram_oz64 folded into the FP64 accumulators of this
-// thread: tensor-memory lane 32 q4 + lane, columns 32 half .. + 31 of the seven
-// accumulator blocks, combined with weights 2^-8d in FP32 pairs (exact: hi +
-// lo carries every bit of the sums) and added in FP64.
-__device__ __forceinline__ void gram64_drain(uint32_t tmem, int q4, int half, double acc[32])
+// One exact window of k_gram_oz64, read out of tensor memory: lane 32 q4 +
+// lane, columns 32 half .. + 31 of the seven accumulator blocks, combined with
+// weights 2^-8d into FP32 pairs (TwoSum; hi + lo carries the window's sum to
+// about 2^-48 of it).  Eight columns per tensor-memory load keep the register
+// footprint small.
+__device__ __forceinline__ void gram64_read(uint32_t tmem, int q4, int half, float hi[32], float lo[32])
 {
 #pragma unroll
-    for (int c16 = 0; c16 < 2; ++c16) {
-        uint32_t g[kOzDigits][16];
+    for (int c8 = 0; c8 < 4; ++c8) {
+        uint32_t g[kOzDigits][8];
 #pragma unroll
-        for (int d = 0; d < kOzDigits; ++d)
-            tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + 32 * half + 16 * c16, g[d]);
+        for (int d = 0; d < kOzDigits; ++d) {
+            const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + 32 * half + 8 * c8;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(g[d][0]), "=r"(g[d][1]), "=r"(g[d][2]), "=r"(g[d][3]), "=r"(g[d][4]), "=r"(g[d][5]),
+                           "=r"(g[d][6]), "=r"(g[d][7])
+                         : "r"(ta)
+                         : "memory");
+        }
         tmem_wait_ld();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            float hi = __uint_as_float(g[0][t]), lo = 0.0f;
+        for (int t = 0; t < 8; ++t) {
+            float h = __uint_as_float(g[0][t]), l = 0.0f;
 #pragma unroll
             for (int d = 1; d < kOzDigits; ++d) {
                 const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
                 const float x = __fmul_rn(__uint_as_float(g[d][t]), w8);
-                const float sum = __fadd_rn(hi, x);
-                const float bb = __fsub_rn(sum, hi);
-                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
-                hi = sum;
-                lo = __fadd_rn(lo, err);
+                const float sum = __fadd_rn(h, x);
+                const float bb = __fsub_rn(sum, h);
+                const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                h = sum;
+                l = __fadd_rn(l, err);
             }
-            acc[16 * c16 + t] += rxr_f2d_exact(hi) + rxr_f2d_exact(lo);
+            hi[8 * c8 + t] = h;
+            lo[8 * c8 + t] = l;
         }
     }
+}
+
+__device__ __forceinline__ void gram64_accumulate(const float hi[32], const float lo[32], double acc[32])
+{
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] += rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1220,7 +1266,8 @@ constexpr int kG6Window = 4;                    // buffers per exact accumulatio
 constexpr int kG6Plane = 64 * kG6Rows * 2;      // one digit plane, 8 KB
 constexpr int kG6Planes = 8;                    // X_0 .. X_6 and the zero plane
 constexpr int kG6Buf = kG6Planes * kG6Plane;    // 64 KB per buffer
-constexpr size_t kG6Smem = 2 * (size_t)kG6Buf;  // 128 KB
+constexpr int kG6Stage = kG6Rows * 64 * 8;      // 32 KB: X's 64 rows x 64 columns, four swizzled TMA boxes
+constexpr size_t kG6Smem = 2 * (size_t)kG6Buf + 2 * (size_t)kG6Stage;  // 192 KB
 
 // Largest exponent field of each column over all rows: atomicMax into
 // colexp[0 .. n) (zeroed by the caller).  grid.y = column.
@@ -1235,23 +1282,39 @@ __global__ void k_colexp(const double *__restrict__ X, int64_t ldx, int64_t m, i
     if ((threadIdx.x & 31) == 0 && e > 0) atomicMax(colexp + col, (int)e);
 }
 
-__global__ void __launch_bounds__(256, 1)
-    k_gram_oz64(const double *__restrict__ X, int64_t ldx, int64_t m, int n, const int *__restrict__ colexp_g,
-                int64_t bufs_total, int64_t bufs_per_cta, double *__restrict__ Gpart, RxrStatus *st)
+// All eight warps load rows and write digits; six of them drain tensor memory
+// (two quarters have nothing on or above the diagonal), and lane 0 of warp 3,
+// one that never drains, also issues the MMAs.
+constexpr int kG6Producers = 256;
+constexpr int kG6MmaWarp = 3;
+
+__global__ void __launch_bounds__(kG6Producers, 1)
+    k_gram_oz64(const __grid_constant__ CUtensorMap tm_x, int use_tma, const double *__restrict__ X, int64_t ldx,
+                int64_t m, int n, const int *__restrict__ colexp_g, int64_t bufs_total, int64_t bufs_per_cta,
+                double *__restrict__ Gpart, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ __align__(8) uint64_t ready[2];  // producers -> MMA thread: digits of a buffer written (256 arrivals)
+    __shared__ __align__(8) uint64_t done[2];   // MMA thread -> producers: a buffer's MMAs completed (commit)
+    __shared__ __align__(8) uint64_t tfree;     // producers -> MMA thread: a window's accumulators read (256)
+    __shared__ __align__(8) uint64_t full[2];   // TMA -> producers: a staging slot holds its 64 rows of X
     __shared__ uint32_t tmem_base;
     __shared__ int cex[64];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int j = tid >> 2, rq = tid & 3;  // column of X and 16-row quarter of each buffer this thread converts
+    const bool producer = true;
+    const bool mma_thread = (warp == kG6MmaWarp && lane == 0);
 
     for (int e = tid; e < (int)(kG6Smem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
     if (tid < 64) cex[tid] = (tid < n) ? colexp_g[tid] : 0;
     if (tid == 0) {
-        mbar_init(&mma_bar[0], 1);
-        mbar_init(&mma_bar[1], 1);
+        mbar_init(&ready[0], kG6Producers);
+        mbar_init(&ready[1], kG6Producers);
+        mbar_init(&done[0], 1);
+        mbar_init(&done[1], 1);
+        mbar_init(&tfree, kG6Producers);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
         fence_barrier_init();
     }
     if (warp == 0) tmem_alloc(&tmem_base, 512);
@@ -1259,117 +1322,142 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const int ej = cex[j];
-    const bool has_col = j < n;
+    const int64_t b_begin = blockIdx.x * bufs_per_cta;
+    const int64_t b_end = min(bufs_total, b_begin + bufs_per_cta);
+    const int nbufs = (b_end > b_begin) ? (int)(b_end - b_begin) : 0;
+    // Waits are per thread and bounded; one that gives up records a timeout in
+    // the status and the thread carries on (every arrival still happens), so
+    // no thread is left waiting and the sums are not published.
+    bool ok = true;
 
     // epilogue role: tensor-memory lane quarter q4 (rows of G: lanes 0-63 the
     // upper halves of the stacks, 64-127 the lower), 32 columns of G per half;
     // the quarter of rows 32-63 has nothing on or above the diagonal in the
     // first 32 columns
-    const int q4 = warp & 3, half = warp >> 2;
+    const int q4 = warp & 3, half = (warp >> 2) & 1;
     const bool skip_epi = (q4 & 1) && half == 0;
     double acc[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = 0.0;
 
-    const int64_t b_begin = blockIdx.x * bufs_per_cta;
-    const int64_t b_end = min(bufs_total, b_begin + bufs_per_cta);
-    const double *xcol = X + (int64_t)j * ldx;
-    double vn[16];
+    if (producer) {
+        const int j = tid >> 2, rq = tid & 3;  // column of X and 16-row quarter of each buffer this thread converts
+        const int ej = cex[j];
+        const bool has_col = j < n;
+        const double *xcol = X + (int64_t)j * ldx;
+        const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
+        constexpr uint32_t idesc = idesc_f16(128, 64);
+        constexpr int kP[16] = {0, 2, 4, 6, 0, 2, 4, 0, 2, 4, 0, 2, 0, 2, 0, 0};
+        constexpr int kQ[16] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 4, 4, 5, 6};
+        unsigned char *stage = smem + 2 * kG6Buf;  // [2 slots][4 boxes of 16 rows x 64 columns]
+        // X's rows of buffer it: four 16-row x 64-column boxes (128-byte swizzle)
+        auto issue_load = [&](int it_load) {
+            unsigned char *slot = stage + (it_load & 1) * kG6Stage;
+            mbar_arrive_expect_tx(&full[it_load & 1], (uint32_t)kG6Stage);
+            const int r0 = (int)((b_begin + it_load) * kG6Rows);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int64_t r = b_begin * kG6Rows + 16 * rq + i;
-        vn[i] = (has_col && b_begin < b_end && r < m) ? xcol[r] : 0.0;
-    }
-    // Waits are per thread and bounded; a wait that gives up records a timeout
-    // in the status and the kernel runs to its end (bounded loop) without
-    // publishing its sums, so no thread is ever left at a barrier.
-    bool ok = true;
-    int it = 0;
-    // descriptors of buffer 0, plane 0: the start-address field (bits 0-13, in
-    // 16-byte units) takes plain offsets (shared memory stays below 256 KB)
-    const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
-    for (int64_t b = b_begin; b < b_end; ++b, ++it) {
-        const int buf = it & 1;
-        unsigned char *base = smem + buf * kG6Buf;
-        double v[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = vn[i];
-        if (b + 1 < b_end) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int64_t r = (b + 1) * kG6Rows + 16 * rq + i;
-                vn[i] = (has_col && r < m) ? xcol[r] : 0.0;
-            }
+            for (int q = 0; q < 4; ++q) tma_load_2d(slot + q * (kG6Stage / 4), &tm_x, r0 + 16 * q, 0, &full[it_load & 1]);
+        };
+        if (use_tma && mma_thread) {
+            if (nbufs > 0) issue_load(0);
+            if (nbufs > 1) issue_load(1);
         }
-        // the MMAs issued two buffers ago read this buffer
-        if (it >= 2) ok &= mbar_wait_bounded(&mma_bar[buf], ((it - 2) >> 1) & 1, st);
-        if (has_col) {
+        for (int it = 0; it < nbufs; ++it) {
+            const int64_t b = b_begin + it;
+            const int buf = it & 1;
+            unsigned char *base = smem + buf * kG6Buf;
+            if (use_tma) ok &= mbar_wait_bounded(&full[buf], (it >> 1) & 1, st);
+            // the MMAs issued two buffers ago read this digit buffer
+            if (it >= 2) ok &= mbar_wait_bounded(&done[buf], ((it - 2) >> 1) & 1, st);
+            if (has_col) {
+                const unsigned char *box = stage + buf * kG6Stage + rq * (kG6Stage / 4) + j * 128;
 #pragma unroll
-            for (int g8 = 0; g8 < 2; ++g8) {
-                unsigned long long U[8];
+                for (int g8 = 0; g8 < 2; ++g8) {
+                    // eight rows of column j: swizzled 16-byte chunks 4 g8 .. 4 g8 + 3 of the box
+                    double v[8];
+                    if (use_tma) {
 #pragma unroll
-                for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[8 * g8 + r]), ej);
+                        for (int c = 0; c < 4; ++c) {
+                            const double2 w = *reinterpret_cast<const double2 *>(box + (((4 * g8 + c) ^ (j & 7)) << 4));
+                            v[2 * c] = w.x;
+                            v[2 * c + 1] = w.y;
+                        }
+                    } else {
 #pragma unroll
-                for (int q = 0; q < kOzDigits; ++q) {
-                    uint4 w;
-                    w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
-                    w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
-                    w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
-                    w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
-                    *reinterpret_cast<uint4 *>(base + q * kG6Plane + kmaj_off(j, 16 * rq + 8 * g8)) = w;
+                        for (int i = 0; i < 8; ++i) {
+                            const int64_t r = b * kG6Rows + 16 * rq + 8 * g8 + i;
+                            v[i] = (r < m) ? xcol[r] : 0.0;
+                        }
+                    }
+                    unsigned long long U[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[r]), ej);
+#pragma unroll
+                    for (int q = 0; q < kOzDigits; ++q)
+                        *reinterpret_cast<uint4 *>(base + q * kG6Plane + kmaj_off(j, 16 * rq + 8 * g8)) =
+                            pack_plane_f16(U, q);
                 }
             }
-        }
-        const bool first_of_window = (it % kG6Window) == 0;
-        if (first_of_window && it > 0) {
-            // the previous window is complete once its last buffer's MMAs are:
-            // fold its tensor-memory sums into the FP64 accumulators
-            ok &= mbar_wait_bounded(&mma_bar[buf ^ 1], ((it - 1) >> 1) & 1, st);
-            tc_fence_after();
-            if (!skip_epi) gram64_drain(tmem, q4, half, acc);
-        }
-        fence_proxy_async_shared();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint64_t dbuf = desc0 + (uint64_t)(buf * (kG6Buf >> 4));
-            constexpr uint32_t idesc = idesc_bf16(128, 64);
-            constexpr int kP[16] = {0, 2, 4, 6, 0, 2, 4, 0, 2, 4, 0, 2, 0, 2, 0, 0};
-            constexpr int kQ[16] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 4, 4, 5, 6};
+            fence_proxy_async_shared();
+            mbar_arrive(&ready[buf]);
+            if ((it % kG6Window) == 0 && it > 0) {
+                // the previous window is complete once its last buffer's MMAs
+                // are: read its sums into FP32 pairs, release tensor memory,
+                // then add them in FP64
+                ok &= mbar_wait_bounded(&done[buf ^ 1], ((it - 1) >> 1) & 1, st);
+                tc_fence_after();
+                float hi[32], lo[32];
+                if (!skip_epi) gram64_read(tmem, q4, half, hi, lo);
+                tc_fence_before();
+                mbar_arrive(&tfree);
+                if (!skip_epi) gram64_accumulate(hi, lo, acc);
+            }
+            if (mma_thread) {
+                // every producer's digits of this buffer (and, at a window start,
+                // every read of the last window's sums) are in: issue its MMAs
+                const bool first_of_window = (it % kG6Window) == 0;
+                ok &= mbar_wait_bounded(&ready[buf], (it >> 1) & 1, st);
+                // every producer has read staging slot `buf`: refill it
+                if (use_tma && it + 2 < nbufs) issue_load(it + 2);
+                if (first_of_window && it > 0) ok &= mbar_wait_bounded(&tfree, ((it / kG6Window) - 1) & 1, st);
+                tc_fence_after();
+                const uint64_t dbuf = desc0 + (uint64_t)(buf * (kG6Buf >> 4));
 #pragma unroll
-            for (int kk = 0; kk < kG6Rows / 16; ++kk)
+                for (int kk = 0; kk < kG6Rows / 16; ++kk)
 #pragma unroll
-                for (int x = 0; x < 16; ++x) {
-                    // the first MMA into each block (x < 7 lists blocks 0, 2, 4, 6, 1, 3, 5) starts the window
-                    const uint32_t acc_on = (!first_of_window || kk > 0 || x >= 7) ? 1u : 0u;
-                    tc_mma(tmem + (uint32_t)((kP[x] + kQ[x]) * 64),
-                           dbuf + (uint64_t)((kP[x] * kG6Plane + kk * 256) >> 4),
-                           dbuf + (uint64_t)((kQ[x] * kG6Plane + kk * 256) >> 4), idesc, acc_on);
-                }
-            tc_commit(&mma_bar[buf]);
+                    for (int x = 0; x < 16; ++x) {
+                        // the first MMA into each block (x < 7 lists blocks 0, 2, 4, 6, 1, 3, 5) starts the window
+                        const uint32_t acc_on = (!first_of_window || kk > 0 || x >= 7) ? 1u : 0u;
+                        tc_mma(tmem + (uint32_t)((kP[x] + kQ[x]) * 64),
+                               dbuf + (uint64_t)((kP[x] * kG6Plane + kk * 256) >> 4),
+                               dbuf + (uint64_t)((kQ[x] * kG6Plane + kk * 256) >> 4), idesc, acc_on);
+                    }
+                tc_commit(&done[buf]);
+            }
         }
-    }
-    // last window
-    if (it > 0) {
-        ok &= mbar_wait_bounded(&mma_bar[(it - 1) & 1], ((it - 1) >> 1) & 1, st);
-        tc_fence_after();
-        if (!skip_epi) gram64_drain(tmem, q4, half, acc);
+        // last window
+        if (nbufs > 0) {
+            ok &= mbar_wait_bounded(&done[(nbufs - 1) & 1], ((nbufs - 1) >> 1) & 1, st);
+            tc_fence_after();
+            float hi[32], lo[32];
+            if (!skip_epi) {
+                gram64_read(tmem, q4, half, hi, lo);
+                gram64_accumulate(hi, lo, acc);
+            }
+        }
     }
     ok = __syncthreads_and(ok) != 0;
     tc_fence_before();
-    __syncthreads();
     // G[i][j] = 2^(e_i + e_j - 2058) (upper-lane sum + 2^-8 lower-lane sum):
     // the lower lanes hand their sums over through shared memory
     double *low = reinterpret_cast<double *>(smem);  // [64][64], i + 64 j
     const int gi = 32 * (q4 & 1) + lane;
-    if (q4 >= 2 && !skip_epi) {
+    if (producer && q4 >= 2 && !skip_epi) {
 #pragma unroll
         for (int t = 0; t < 32; ++t) low[gi + 64 * (32 * half + t)] = acc[t];
     }
     __syncthreads();
-    if (ok && q4 < 2 && !skip_epi && gi < n) {
+    if (ok && producer && q4 < 2 && !skip_epi && gi < n) {
         double *out = Gpart + (int64_t)blockIdx.x * n * n;
         const int ei = cex[gi];
 #pragma unroll
@@ -1455,11 +1543,7 @@ __global__ void __launch_bounds__(256, 1)
         }
 #pragma unroll
         for (int q = 0; q < kOzDigits; ++q) {
-            uint4 w;
-            w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
-            w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
-            w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
-            w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+            const uint4 w = pack_plane_f16(U, q);
             *reinterpret_cast<uint4 *>(tdig + q * kAqTPlane + kmaj_off(l, k0)) = w;
         }
     }
@@ -1471,7 +1555,7 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t tmem = tmem_base;
     const uint64_t da0 = smem_desc(smem_u32(adig), 128, 256);   // X digits, K = 16 per plane
     const uint64_t dt0 = smem_desc(smem_u32(tdig), 128, 1024);  // T digits, K = 64
-    constexpr uint32_t idesc = idesc_bf16(kAqM, 64);
+    constexpr uint32_t idesc = idesc_f16(kAqM, 64);
     const int nk = (n + 15) / 16;
 
     if (use_tma && tid == 0 && (int64_t)blockIdx.x < tiles_total) {
@@ -1517,11 +1601,7 @@ __global__ void __launch_bounds__(256, 1)
                 unsigned char *plane = adig + buf * kOzDigits * kAqPlane;
 #pragma unroll
                 for (int q = 0; q < kOzDigits; ++q) {
-                    uint4 w;
-                    w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
-                    w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
-                    w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
-                    w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+                    const uint4 w = pack_plane_f16(U, q);
                     *reinterpret_cast<uint4 *>(plane + q * kAqPlane + kmaj16_off(row, 8 * h)) = w;
                 }
             }
@@ -1709,7 +1789,7 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    constexpr uint32_t idesc = idesc_bf16(kSpM, kSpN);
+    constexpr uint32_t idesc = idesc_f16(kSpM, kSpN);
     const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
 
     // roles: A digits -> column j, rows 16 rq .. + 15 of each 64-row tile;
@@ -1755,7 +1835,7 @@ __global__ void __launch_bounds__(256, 1)
         }
         if (it >= 2) ok &= mbar_wait_bounded(&mma_bar[buf], ((it - 2) >> 1) & 1, st);
         // Omega' on the 2^-12 grid: 4096 z' = 256 zeta0 + zeta1 (round to nearest
-        // even by the 1.5 * 2^23 addition, as rint), both pieces exact in BF16
+        // even by the 1.5 * 2^23 addition, as rint), both pieces exact in FP16
         if (4 * kq < sw) {
             float z[8][4];
 #pragma unroll
@@ -1763,29 +1843,20 @@ __global__ void __launch_bounds__(256, 1)
                 rxr_normal4(seed, (uint64_t)(r0 + 8 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
 #pragma unroll
             for (int t4 = 0; t4 < 4; ++t4) {
-                uint32_t p0[8], p1[8];
+                uint32_t p0[8], p1[8];  // zeta + 128, in [0, 256]
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int q = (int)(__float_as_uint(__fadd_rn(__fmul_rn(z[i][t4], 4096.0f), 12582912.0f)) & 0x7FFFFFu) -
                                   0x400000;
                     const int z0 = (q + 128) >> 8;
                     const int z1 = q - (z0 << 8);
-                    p0[i] = __float_as_uint(__fadd_rn(__uint_as_float(0x4B000000u | (uint32_t)(z0 + 128)), -8388736.0f));
-                    p1[i] = __float_as_uint(__fadd_rn(__uint_as_float(0x4B000000u | (uint32_t)(z1 + 128)), -8388736.0f));
+                    p0[i] = (uint32_t)(z0 + 128);
+                    p1[i] = (uint32_t)(z1 + 128);
                 }
                 const int r = 4 * kq + t4;
                 if (r < sw) {
-                    uint4 w0, w1;
-                    w0.x = __byte_perm(p0[0], p0[1], 0x7632);
-                    w0.y = __byte_perm(p0[2], p0[3], 0x7632);
-                    w0.z = __byte_perm(p0[4], p0[5], 0x7632);
-                    w0.w = __byte_perm(p0[6], p0[7], 0x7632);
-                    w1.x = __byte_perm(p1[0], p1[1], 0x7632);
-                    w1.y = __byte_perm(p1[2], p1[3], 0x7632);
-                    w1.z = __byte_perm(p1[4], p1[5], 0x7632);
-                    w1.w = __byte_perm(p1[6], p1[7], 0x7632);
-                    *reinterpret_cast<uint4 *>(aop + kmaj_off(r, 8 * warp)) = w0;
-                    *reinterpret_cast<uint4 *>(aop + kSpA + kmaj_off(r, 8 * warp)) = w1;
+                    *reinterpret_cast<uint4 *>(aop + kmaj_off(r, 8 * warp)) = pack_int8x_f16(p0);
+                    *reinterpret_cast<uint4 *>(aop + kSpA + kmaj_off(r, 8 * warp)) = pack_int8x_f16(p1);
                 }
             }
         }
@@ -1798,11 +1869,7 @@ __global__ void __launch_bounds__(256, 1)
                 for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[8 * g8 + r]), ej);
 #pragma unroll
                 for (int q = 0; q < kSpDigits; ++q) {
-                    uint4 w;
-                    w.x = __byte_perm(digit_bits(U[0], q), digit_bits(U[1], q), 0x7632);
-                    w.y = __byte_perm(digit_bits(U[2], q), digit_bits(U[3], q), 0x7632);
-                    w.z = __byte_perm(digit_bits(U[4], q), digit_bits(U[5], q), 0x7632);
-                    w.w = __byte_perm(digit_bits(U[6], q), digit_bits(U[7], q), 0x7632);
+                    const uint4 w = pack_plane_f16(U, q);
                     *reinterpret_cast<uint4 *>(bop + q * kSpB + kmaj_off(j, 16 * rq + 8 * g8)) = w;
                 }
             }
@@ -1973,7 +2040,10 @@ int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, b
         const int64_t bpc = cdiv64(total, gx);
         gx = cdiv64(total, bpc);
         double *parts = reinterpret_cast<double *>(p.split);
-        k_gram_oz64<<<(unsigned)gx, 256, kG6Smem, st>>>(X, ldx, p.m, (int)p.n, cx, total, bpc, parts, p.status);
+        CUtensorMap mx;
+        const int use_tma = encode_tile_map(&mx, X, p.m, p.n, ldx, 16, 64, true) ? 1 : 0;
+        k_gram_oz64<<<(unsigned)gx, kG6Producers, kG6Smem, st>>>(mx, use_tma, X, ldx, p.m, (int)p.n, cx, total, bpc,
+                                                                 parts, p.status);
         if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
         const int64_t nn = p.n * p.n;
         k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(parts, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G,
