@@ -347,6 +347,7 @@ int set_kernel_attrs()
         set_split_smem(),
         set_batched_smem(big),
         set_wide_smem(),
+        set_small_smem(),
     };
     for (cudaError_t e : es)
         if (e != cudaSuccess) {
@@ -468,7 +469,8 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         }
         {
             Timer t(th, 6, st);
-            k_xr_factor<<<1, 512, 0, st>>>(p.Y, (int)p.s, n, p.s, variant, p.W, p.Rs, p.n, p.status);
+            k_xr_factor<<<1, 512, xr_smem_bytes(p.s, p.n), st>>>(p.Y, (int)p.s, n, p.s, variant, p.W, p.Rs, p.n,
+                                                                 p.status);
             if (launch_ok()) return RXR_ERR_CUDA;
         }
     }
@@ -502,7 +504,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     }
     // step 4: CholeskyQR passes on X
     for (int pass = 1; pass <= passes; ++pass) {
-        k_factor<<<1, 512, 0, st>>>(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status);
+        k_factor<<<1, 512, factor_smem_bytes(p.n), st>>>(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status);
         if (launch_ok()) return RXR_ERR_CUDA;
         const bool last = (pass == passes);
         // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
@@ -979,7 +981,7 @@ int rxr_xr_factor(rxr_handle h, const double *Y, int64_t s, int64_t n, int64_t l
     bind_plan(p, h->ws);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
-    k_xr_factor<<<1, 512, 0, st>>>(Y, (int)s, (int)n, ldy, variant, p.W, Rs, ldrs, p.status);
+    k_xr_factor<<<1, 512, xr_smem_bytes(s, n), st>>>(Y, (int)s, (int)n, ldy, variant, p.W, Rs, ldrs, p.status);
     if (launch_ok()) return RXR_ERR_CUDA;
     return finish_blocking(h, p.status, st);
 }
@@ -1068,7 +1070,7 @@ int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *
     bind_plan(p, h->ws);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
-    k_factor<<<1, 512, 0, st>>>(G, (int)n, ldg, p.Rp, p.Racc, p.C, 1, 0, p.status);
+    k_factor<<<1, 512, factor_smem_bytes(n), st>>>(G, (int)n, ldg, p.Rp, p.Racc, p.C, 1, 0, p.status);
     if (launch_ok()) return RXR_ERR_CUDA;
     if (cudaMemcpy2DAsync(R, ldr * 8, p.Rp, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;

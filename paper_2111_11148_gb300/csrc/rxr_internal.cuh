@@ -370,4 +370,8 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
 bool encode_tile_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                      int box_cols, bool swizzle128 = false);
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
+// dynamic shared memory of the one-CTA factorisations (small_kernels.cu)
+size_t xr_smem_bytes(int64_t s, int64_t n);
+size_t factor_smem_bytes(int64_t n);
+cudaError_t set_small_smem();
 }  // namespace rxr

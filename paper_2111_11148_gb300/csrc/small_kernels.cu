@@ -18,6 +18,8 @@
 namespace rxr {
 
 constexpr int kSmallThreads = 512;
+constexpr int64_t kXrSmemDoubles = 26624;  // 208 KB: the sketch's working copy in shared memory up to here
+constexpr int kFactorSmemN = 64;           // C, R_p, R_acc in shared memory (96 KB) up to here
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
@@ -175,11 +177,20 @@ __device__ __forceinline__ void xr_body(const double *__restrict__ Y, int s, int
     if (tid == 0 && sh_bad) rxr_fail(st, RXR_ERR_SKETCH_SINGULAR, 0, -1);
 }
 
+// The working copy of Y lives in shared memory when it fits (dynamic size
+// s * n * 8 bytes, launched by xr_smem_bytes), else in the global scratch W.
 __global__ void __launch_bounds__(kSmallThreads)
     k_xr_factor(const double *__restrict__ Y, int s, int n, int64_t ldy, int variant, double *__restrict__ W,
                 double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
 {
-    xr_body(Y, s, n, ldy, variant, W, Rs, ldrs, st);
+    extern __shared__ double xr_smem[];
+    const bool in_smem = (int64_t)s * n <= kXrSmemDoubles;
+    xr_body(Y, s, n, ldy, variant, in_smem ? xr_smem : W, Rs, ldrs, st);
+}
+
+size_t xr_smem_bytes(int64_t s, int64_t n)
+{
+    return (s * n <= kXrSmemDoubles) ? (size_t)(s * n) * sizeof(double) : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -242,11 +253,35 @@ __device__ __forceinline__ void factor_body(const double *__restrict__ G, int n,
     for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) Racc[e] = C[e];
 }
 
+// n <= 64: C, R_p and R_acc are worked on in shared memory (3 n^2 doubles,
+// launched by factor_smem_bytes) and R_p, R_acc written back at the end.
 __global__ void __launch_bounds__(kSmallThreads)
     k_factor(const double *__restrict__ G, int n, int64_t ldg, double *__restrict__ Rp, double *__restrict__ Racc,
              double *__restrict__ C, int pass, int update_racc, RxrStatus *st)
 {
-    factor_body(G, n, ldg, Rp, Racc, C, pass, update_racc, st);
+    if (n > kFactorSmemN) {
+        factor_body(G, n, ldg, Rp, Racc, C, pass, update_racc, st);
+        return;
+    }
+    if (rxr_failed(st)) return;
+    extern __shared__ double fac_smem[];
+    const int nn = n * n;
+    double *Cs = fac_smem, *Rps = fac_smem + nn, *Ras = fac_smem + 2 * nn;
+    if (update_racc)
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) Ras[e] = Racc[e];
+    __syncthreads();
+    factor_body(G, n, ldg, Rps, Ras, Cs, pass, update_racc, st);
+    __syncthreads();
+    if (rxr_failed(st)) return;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        Rp[e] = Rps[e];
+        if (update_racc) Racc[e] = Ras[e];
+    }
+}
+
+size_t factor_smem_bytes(int64_t n)
+{
+    return (n <= kFactorSmemN) ? (size_t)(3 * n * n) * sizeof(double) : 0;
 }
 
 // Batched forms of the one-CTA steps: block k serves problem k.  The XR step
@@ -476,6 +511,16 @@ __global__ void __launch_bounds__(256) k_fp64_peak(double *out, int iters, doubl
 #pragma unroll
     for (int c = 0; c < 8; ++c) s += acc[c];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t set_small_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_xr_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kXrSmemDoubles * sizeof(double)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(3 * kFactorSmemN * kFactorSmemN * sizeof(double)));
+    return e;
 }
 
 }  // namespace rxr
