@@ -333,7 +333,10 @@ def launches_per_step(prec, n):
     if n <= 64:
         # colexp, sketch, reduce, XR, 2 x (fused substitution, Gram, reduce, factor), inverse, apply, copy
         return 15
-    bw = 32 if n <= 128 else 64
+    if n <= 128:
+        # colexp, sketch, reduce, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
+        return 4 + 3 * 2 + 2 * 2 + 2 + 1
+    bw = 64
     blocked = 2 * ((n + bw - 1) // bw) - 1  # diagonal solves + trailing updates
     return 4 + 3 * blocked + 2 * 2 + 2 + 1
 
@@ -351,15 +354,16 @@ def roofline_entry(prec, stages, peak_fp64):
         name = "k_subst_gram (fused precondition + Gram launch)"
         traffic = TRAFFIC_PG if (M == 2**22 and N == 64) else None
         hbm_bytes = 16.0 * M * N
-    elif N <= 64:
+    elif N <= 128:
         t = stages.get("precond_subst")
         flop = subst_fp64_flop_per_row(N, 16, 2) * M
-        name = "k_subst_fused (FP64 16-column diagonal solves + FP64 subtraction of tcgen05 updates)"
+        name = ("k_subst_fused" if N <= 64 else "k_subst_fused128") + \
+            " (FP64 16-column diagonal solves + FP64 subtraction of tcgen05 updates)"
         traffic = TRAFFIC_SUBST if (M == 2**22 and N == 64) else None
         hbm_bytes = 16.0 * M * N
     else:
         t = stages.get("precond_subst")
-        flop = subst_fp64_flop_per_row(N, 32 if N <= 128 else 64, 3) * M
+        flop = subst_fp64_flop_per_row(N, 64, 3) * M
         name = "k_solve_block + k_update_ozaki (blocked substitution: FP64 diagonal blocks, tcgen05 updates)"
         traffic = None
         hbm_bytes = 16.0 * M * N

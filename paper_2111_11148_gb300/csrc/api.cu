@@ -431,6 +431,7 @@ int split_subst(const Plan &p, const double *src, int64_t lds, const double *R, 
         if (colexp_out && cudaMemsetAsync(colexp_out, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
         return fused_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, colexp_out, st);
     }
+    if (p.n <= 128) return fused128_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
     return blocked_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
 }
 

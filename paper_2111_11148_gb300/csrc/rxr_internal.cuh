@@ -238,6 +238,16 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m
         : "memory");
 }
 
+// 1-D bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load_1d(void *smem_dst, const void *gsrc, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(smem_dst)),
+                 "l"((uint64_t)gsrc), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 2-D tiled TMA store of a shared-memory box to element coordinates (x = row,
 // y = column); rows past the tensor's extent are not written.  Completion is
 // tracked by the issuing thread's bulk async-group.
@@ -364,6 +374,8 @@ int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double
                           int64_t ldx, cudaStream_t st);
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                         int64_t ldx, int *colexp_out, cudaStream_t st);
+int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
+                           int64_t ldx, cudaStream_t st);
 // 2-D tensor map of a column-major FP64 matrix (api.cu); false where TMA's
 // alignment rules are not met.  swizzle128: 128-byte swizzle (box_rows <= 16;
 // in shared memory, 16-byte chunk c of box column j sits at chunk c ^ (j mod 8))

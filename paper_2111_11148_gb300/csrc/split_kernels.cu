@@ -357,6 +357,20 @@ __device__ __forceinline__ void digits7(unsigned long long bits, int emax, float
     for (int q = 0; q < kOzDigits; ++q) dg[q] = __uint_as_float(digit_bits(U, q));
 }
 
+// f * 2^(be - 1023) as a double, built on the integer pipes (exact: f is
+// normal and the result's exponent stays in range; results below the normal
+// range are flushed to zero, above it they become infinite).
+__device__ __forceinline__ double f2d_pow2(float f, int be)
+{
+    const uint32_t u = __float_as_uint(f);
+    const int e8 = (int)((u >> 23) & 0xFFu);
+    const int e = e8 - 127 + be;
+    if (e8 == 0 || e <= 0) return 0.0;
+    const uint32_t sign = u & 0x80000000u;
+    if (e >= 2047) return __hiloint2double((int)(sign | 0x7FF00000u), 0);
+    return __hiloint2double((int)(sign | ((uint32_t)e << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+}
+
 // Digit q of two offset forms as one packed FP16 pair (value a in the low
 // half): 0x6400 | (digit + 128) encodes the FP16 number 1024 + digit + 128
 // (exact: at most 9 bits over 2^10), so one packed subtraction of 1152 leaves
@@ -902,19 +916,6 @@ __device__ __forceinline__ int kmaj16_off(int row, int k)
 }
 
 
-// f * 2^(be - 1023) as a double, built on the integer pipes (exact: f is
-// normal and the result's exponent stays in range; results below the normal
-// range are flushed to zero, above it they become infinite).
-__device__ __forceinline__ double f2d_pow2(float f, int be)
-{
-    const uint32_t u = __float_as_uint(f);
-    const int e8 = (int)((u >> 23) & 0xFFu);
-    const int e = e8 - 127 + be;
-    if (e8 == 0 || e <= 0) return 0.0;
-    const uint32_t sign = u & 0x80000000u;
-    if (e >= 2047) return __hiloint2double((int)(sign | 0x7FF00000u), 0);
-    return __hiloint2double((int)(sign | ((uint32_t)e << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
-}
 
 // 16 tensor-memory columns into registers without waiting (tcgen05.wait::ld
 // must follow before the values are used).
@@ -1241,6 +1242,279 @@ __device__ __forceinline__ void gram64_accumulate(const float hi[32], const floa
 {
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] += rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
+}
+
+// ---------------------------------------------------------------------------
+// Fused blocked substitution X = B R^{-1} for 64 < n <= 128, one pass over B.
+// Same scheme as k_subst_fused (16-column FP64 diagonal solves, FP64-grade
+// tensor-core trailing updates, 128-row tiles resident in shared memory), with
+// one tile per CTA (a 128 x 128 FP64 tile is 128 KB).  R's per-block data no
+// longer fits in shared memory at once: k_rprep128 lays it out in global
+// memory, one contiguous record per column block (FP16 digits of the
+// off-diagonal block, their column exponents, the diagonal block, 1 / R_jj),
+// and the CTA streams the records through two shared-memory slots by 1-D bulk
+// copies, one block ahead.  The trailing update runs in rounds of up to 64
+// columns (7 groups x 64 tensor-memory columns).
+// ---------------------------------------------------------------------------
+constexpr int kF2MaxN = 128;
+constexpr int kF2Slot = 28672;  // largest record (n = 128, block 0): 7 x 112 x 32 + 112 x 4 + 2048 + 128 bytes
+
+__host__ __device__ inline int f2_rec_bytes(int n, int c)
+{
+    const int Np = fu_npad(n, c);
+    return kFuDigits * Np * kFuBw * 2 + Np * 4 + kFuBw * kFuBw * 8 + kFuBw * 8;
+}
+__host__ __device__ inline int f2_rec_off(int n, int c)
+{
+    int off = 0;
+    for (int q = 0; q < c; ++q) off += f2_rec_bytes(n, q);
+    return off;
+}
+__host__ __device__ inline size_t f2_smem_bytes(int n)
+{
+    return (size_t)kFuM * n * 8 + (size_t)kFuDigits * kFuATile + 2 * (size_t)kF2Slot;
+}
+
+// One record per column block c (grid.x = blocks): see k_subst_fused128.
+__global__ void __launch_bounds__(256) k_rprep128(const double *__restrict__ R, int64_t ldr, int n,
+                                                  unsigned char *__restrict__ rec, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const int Np = fu_npad(n, c), Nc = n - kFuBw * (c + 1);
+    unsigned char *r = rec + f2_rec_off(n, c);
+    int *cexp = reinterpret_cast<int *>(r + kFuDigits * Np * kFuBw * 2);
+    double *diag = reinterpret_cast<double *>(r + kFuDigits * Np * kFuBw * 2 + Np * 4);
+    double *dinv = diag + kFuBw * kFuBw;
+    for (int e = tid; e < kFuBw * kFuBw; e += blockDim.x) {
+        const int j = e / kFuBw, k = e % kFuBw;
+        const int gk = kFuBw * c + k, gj = kFuBw * c + j;
+        diag[e] = (k < j && gj < n) ? R[gk + (int64_t)gj * ldr] : 0.0;
+    }
+    for (int e = tid; e < kFuBw; e += blockDim.x) {
+        const int g = kFuBw * c + e;
+        dinv[e] = (g < n) ? 1.0 / R[g + (int64_t)g * ldr] : 0.0;
+    }
+    for (int l = tid; l < Np; l += blockDim.x) {
+        unsigned ex = 0;
+        if (l < Nc)
+            for (int k = 0; k < kFuBw; ++k)
+                ex = max(ex, ((unsigned)__double2hiint(R[(kFuBw * c + k) + (int64_t)(kFuBw * (c + 1) + l) * ldr]) >> 20) &
+                                 0x7FFu);
+        cexp[l] = (int)ex;
+        for (int k0 = 0; k0 < kFuBw; k0 += 8) {
+            unsigned long long U[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                U[k] = (l < Nc) ? digits_offset((unsigned long long)__double_as_longlong(
+                                                    R[(kFuBw * c + k0 + k) + (int64_t)(kFuBw * (c + 1) + l) * ldr]),
+                                                (int)ex)
+                                : 0x808080808080ull;  // the offset form of zero
+#pragma unroll
+            for (int q = 0; q < kFuDigits; ++q)
+                *reinterpret_cast<uint4 *>(r + q * Np * kFuBw * 2 + kmaj16_off(l, k0)) = pack_plane_f16(U, q);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_subst_fused128(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
+                     int use_tma, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
+                     const unsigned char *__restrict__ rec, int64_t tiles_total, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nb = fu_blocks(n);
+    const size_t tile_bytes = (size_t)kFuM * n * 8;
+    double *xs = reinterpret_cast<double *>(smem);
+    unsigned char *adig = smem + tile_bytes;                      // X_blk digits [7][128 x 16]
+    unsigned char *slots = adig + kFuDigits * kFuATile;           // two record slots
+    __shared__ __align__(8) uint64_t full_bar, mma_bar;
+    __shared__ __align__(8) uint64_t rbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int rowexp[kFuM];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        mbar_init(&full_bar, 1);
+        mbar_init(&mma_bar, 1);
+        mbar_init(&rbar[0], 1);
+        mbar_init(&rbar[1], 1);
+        fence_barrier_init();
+    }
+    for (int e = tid; e < kFuDigits * kFuATile / 16; e += blockDim.x)
+        reinterpret_cast<uint4 *>(adig)[e] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    fence_proxy_async_shared();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int64_t first = blockIdx.x;
+    // record sequence: rs = (tile iteration) * nb + c, slot rs & 1
+    auto issue_record = [&](int64_t rs) {
+        const int c = (int)(rs % nb);
+        const uint32_t bytes = (uint32_t)f2_rec_bytes(n, c);
+        mbar_arrive_expect_tx(&rbar[rs & 1], bytes);
+        bulk_load_1d(slots + (rs & 1) * kF2Slot, rec + f2_rec_off(n, c), bytes, &rbar[rs & 1]);
+    };
+    if (tid == 0 && first < tiles_total) {
+        issue_record(0);
+        if (use_tma) {
+            mbar_arrive_expect_tx(&full_bar, (uint32_t)tile_bytes);
+            tma_load_2d(xs, &tm_src, (int)(first * kFuM), 0, &full_bar);
+        }
+    }
+    // Waits are per thread and bounded; one that gives up records a timeout and
+    // the thread carries on (the loops are bounded), so no thread is left at a
+    // barrier; the status then flags the result.
+    uint32_t mphase = 0;
+    int64_t rs = 0;
+    int it = 0;
+    const int64_t ntiles = (first < tiles_total) ? (tiles_total - 1 - first) / gridDim.x + 1 : 0;
+    for (int64_t tile = first; tile < tiles_total; tile += gridDim.x, ++it) {
+        const int64_t r0 = tile * kFuM;
+        if (use_tma) {
+            mbar_wait_bounded(&full_bar, it & 1, st);
+        } else {
+            for (int e = tid; e < kFuM * n; e += blockDim.x) {
+                const int row = e & (kFuM - 1), col = e >> 7;
+                xs[e] = (r0 + row < m) ? src[r0 + row + (int64_t)col * lds] : 0.0;
+            }
+            __syncthreads();
+        }
+        for (int c = 0; c < nb; ++c, ++rs) {
+            const int c16 = kFuBw * c;
+            const int Nc = n - c16 - kFuBw, Np = fu_npad(n, c);
+            // the next record goes into the other slot (its last readers finished
+            // at the previous block's closing barrier)
+            if (tid == 0 && rs + 1 < ntiles * nb) issue_record(rs + 1);
+            mbar_wait_bounded(&rbar[rs & 1], (uint32_t)((rs >> 1) & 1), st);
+            const unsigned char *slot = slots + (rs & 1) * kF2Slot;
+            const int *cexp = reinterpret_cast<const int *>(slot + kFuDigits * Np * kFuBw * 2);
+            const double *rb = reinterpret_cast<const double *>(slot + kFuDigits * Np * kFuBw * 2 + Np * 4);
+            const double *dvb = rb + kFuBw * kFuBw;
+            if (tid < kFuM) {
+                const int row = tid;
+                double v[kFuBw];
+#pragma unroll
+                for (int j = 0; j < kFuBw; ++j) v[j] = (c16 + j < n) ? xs[(c16 + j) * kFuM + row] : 0.0;
+#pragma unroll
+                for (int k = 0; k < kFuBw; ++k) {
+                    v[k] *= dvb[k];
+#pragma unroll
+                    for (int j = k + 1; j < kFuBw; ++j) v[j] = fma(-v[k], rb[j * kFuBw + k], v[j]);
+                }
+                unsigned ex = 0;
+#pragma unroll
+                for (int j = 0; j < kFuBw; ++j) {
+                    if (c16 + j < n) xs[(c16 + j) * kFuM + row] = v[j];
+                    ex = max(ex, ((unsigned)__double2hiint(v[j]) >> 20) & 0x7FFu);
+                }
+                rowexp[row] = (int)ex;
+                if (Nc > 0) {
+#pragma unroll
+                    for (int j0 = 0; j0 < kFuBw; j0 += 8) {
+                        unsigned long long U[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            U[j] = digits_offset((unsigned long long)__double_as_longlong(v[j0 + j]), (int)ex);
+#pragma unroll
+                        for (int q = 0; q < kFuDigits; ++q)
+                            *reinterpret_cast<uint4 *>(adig + q * kFuATile + kmaj16_off(row, j0)) = pack_plane_f16(U, q);
+                    }
+                }
+            }
+            // trailing columns in rounds of at most 64
+            for (int n0 = 0; n0 < Np; n0 += 64) {
+                const int nw = min(64, Np - n0);
+                fence_proxy_async_shared();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint64_t da = smem_desc(smem_u32(adig), 128, 256);
+                    const uint64_t db = smem_desc(smem_u32(slot) + (uint32_t)(n0 * kFuBw * 2), 128, 256);
+                    const uint32_t idesc = idesc_f16(kFuM, nw);
+#pragma unroll
+                    for (int p = 0; p < kFuDigits; ++p)
+#pragma unroll
+                        for (int q = 0; p + q < kFuDigits; ++q)
+                            tc_mma(tmem + (uint32_t)((p + q) * 64), da + (uint64_t)((p * kFuATile) >> 4),
+                                   db + (uint64_t)((q * Np * kFuBw * 2) >> 4), idesc, p > 0 ? 1u : 0u);
+                    tc_commit(&mma_bar);
+                }
+                mbar_wait_bounded(&mma_bar, mphase, st);
+                mphase ^= 1u;
+                tc_fence_after();
+                {
+                    const int q4 = warp & 3, hf = warp >> 2;
+                    const int erow = 32 * q4 + lane;
+                    const int ei = rowexp[erow];
+#pragma unroll
+                    for (int sc = 0; sc < 2; ++sc) {
+                        const int h0 = 32 * hf + 16 * sc;
+                        if (h0 >= nw) continue;  // warp-uniform
+                        uint32_t gv[kFuDigits][16];
+#pragma unroll
+                        for (int d = 0; d < kFuDigits; ++d)
+                            tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + h0, gv[d]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            float hi = __uint_as_float(gv[0][t]), lo = 0.0f;
+#pragma unroll
+                            for (int d = 1; d < kFuDigits; ++d) {
+                                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+                                const float x = __fmul_rn(__uint_as_float(gv[d][t]), w8);
+                                const float sum = __fadd_rn(hi, x);
+                                const float bb = __fsub_rn(sum, hi);
+                                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                                hi = sum;
+                                lo = __fadd_rn(lo, err);
+                            }
+                            const int l = n0 + h0 + t;
+                            if (l < Nc) {
+                                const int el = cexp[l];
+                                if (ei > 0 && el > 0) {
+                                    const int be = ei + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
+                                    double *xp = xs + (c16 + kFuBw + l) * kFuM + erow;
+                                    *xp = (*xp - f2d_pow2(hi, be)) - f2d_pow2(lo, be);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+            }
+            __syncthreads();
+        }
+        // tile done: store it and fetch the next one into the same buffer once
+        // the store has read it out
+        if (use_tma) {
+            fence_proxy_async_shared();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store_2d(&tm_dst, (int)r0, 0, xs);
+                bulk_commit();
+                if (tile + gridDim.x < tiles_total) {
+                    bulk_wait_read_all();
+                    mbar_arrive_expect_tx(&full_bar, (uint32_t)tile_bytes);
+                    tma_load_2d(xs, &tm_src, (int)((tile + gridDim.x) * kFuM), 0, &full_bar);
+                }
+            }
+        } else {
+            for (int e = tid; e < kFuM * n; e += blockDim.x) {
+                const int row = e & (kFuM - 1), col = e >> 7;
+                if (r0 + row < m) dst[r0 + row + (int64_t)col * ldd] = xs[e];
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && use_tma) bulk_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -1946,16 +2220,27 @@ static size_t split_partial_bytes(int64_t m, int64_t n, int sms)
     return ((size_t)gx * n * n * sizeof(double) + 255) & ~(size_t)255;
 }
 
-// partial sums, then a column-exponent array (int[512]: the split sketch's
-// columns of A, later the n <= 64 Gram's columns of X)
+// records of R for the 64 < n <= 128 fused substitution
+static size_t split_rec_bytes(int64_t n)
+{
+    return (n > kFuMaxN && n <= kF2MaxN) ? ((size_t)f2_rec_off((int)n, fu_blocks((int)n)) + 255) & ~(size_t)255 : 0;
+}
+
+// partial sums, a column-exponent array (int[512]: the split sketch's columns
+// of A, later the n <= 64 Gram's columns of X), then the records of R
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
 {
-    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int);
+    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n);
 }
 
 int *split_colexp(const Plan &p)
 {
     return reinterpret_cast<int *>(p.split + split_partial_bytes(p.m, p.n, p.sms));
+}
+
+static unsigned char *split_records(const Plan &p)
+{
+    return reinterpret_cast<unsigned char *>(p.split + split_partial_bytes(p.m, p.n, p.sms) + RXR_MAX_N * sizeof(int));
 }
 
 // X <- X R^{-1} on the tensor cores through the explicit inverse (n <= 64);
@@ -2024,6 +2309,25 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
+// X = B R^{-1} for 64 < n <= 128 in one pass over B (k_rprep128 + k_subst_fused128).
+int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
+                           int64_t ldx, cudaStream_t st)
+{
+    if (p.n <= kFuMaxN || p.n > kF2MaxN) return RXR_ERR_UNSUPPORTED;
+    const int n = (int)p.n, nb = fu_blocks(n);
+    unsigned char *rec = split_records(p);
+    k_rprep128<<<nb, 256, 0, st>>>(R, ldr, n, rec, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    CUtensorMap ms, md;
+    const int use_tma =
+        (encode_tile_map(&ms, Bsrc, p.m, n, ldb, kFuM, n) && encode_tile_map(&md, X, p.m, n, ldx, kFuM, n)) ? 1 : 0;
+    const int64_t tiles = cdiv64(p.m, kFuM);
+    const int gx = (int)std::min<int64_t>(p.sms, tiles);
+    k_subst_fused128<<<gx, 256, f2_smem_bytes(n), st>>>(ms, md, use_tma, Bsrc, ldb, X, ldx, p.m, n, rec, tiles,
+                                                         p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
 int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, bool colexp_ready)
 {
     if (p.n > RXR_MAX_N) return RXR_ERR_UNSUPPORTED;
@@ -2080,6 +2384,9 @@ cudaError_t set_split_smem()
                                  (int)fu_smem_bytes(kFuMaxN));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gram_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kG6Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_subst_fused128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)f2_smem_bytes(kF2MaxN));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)aq_smem_bytes(64));
     return e;

@@ -160,3 +160,23 @@ def test_ozaki_gram_column_scales(h, m, n):
     bound = 8 * (m + 2) * U * (np.abs(X).T @ np.abs(X)) + 2.0**-52 * m * np.outer(cm, cm)
     assert np.all(np.abs(Gs - Go) <= bound), np.nanmax(np.abs(Gs - Go) / np.where(bound > 0, bound, 1))
     assert np.array_equal(Gs, Gs.T)
+
+
+@pytest.mark.parametrize("m,n,kappa", [(65, 65, 1e3), (3001, 80, 1e12), (128 * 152 + 5, 127, 1e14), (5000, 128, 1e15)])
+def test_fused128_substitution(h, m, n, kappa):
+    # the 64 < n <= 128 fused kernel (records of R streamed per column block):
+    # a narrow last block, a ragged last tile, more tiles than CTAs; backward
+    # error at FP64 rounding level, and TMA (even ld) and plain (odd ld) staging
+    # give the same bits
+    A = usv_matrix(m, n, kappa, seed=m + 7)
+    R = o.rxr_cholqr(A, o.VARIANT_QR, 2 * n, seed=2, passes=1).Rs
+    X, _ = h.precond_gram(to_dev(A), to_dev(R), prec="split")
+    Xg = to_host(X)
+    back = np.linalg.norm(Xg @ R - A) / (np.linalg.norm(Xg) * np.linalg.norm(R))
+    assert back <= 64 * n * U, back
+    Xodd, _ = h.precond_gram(to_dev(A, ld=m + 1), to_dev(R), X=rxr.empty_colmajor(m, n, ld=m + 1), prec="split")
+    assert np.array_equal(to_host(Xodd), Xg)
+    # against the oracle's substitution (for n > 64 the FP64 path splits each
+    # row's sums over two lanes, so bit equality is not expected)
+    Xo = o.trsm_right_upper(A, R)
+    assert np.linalg.norm(Xg - Xo) <= 64 * n * U * np.linalg.cond(R) * np.linalg.norm(Xo)
