@@ -1317,6 +1317,45 @@ __global__ void __launch_bounds__(256) k_rprep128(const double *__restrict__ R, 
     }
 }
 
+// Columns [lo, hi) (16-column chunks) of one update round of k_subst_fused128
+// applied to this thread's row of the tile: the seven tensor-memory groups
+// of each output combined in FP32 pairs and subtracted in FP64.  lane0 is the
+// thread's tensor-memory lane base (32 x its warp's lane quarter).
+__device__ __forceinline__ void f2_apply(uint32_t tmem, int q4, int lane, int ei, int lo, int hi, int n0,
+                                         const int *cexp, int cexp_base, double *xs, int col0, int Nc)
+{
+    const int erow = 32 * q4 + lane;
+    for (int h0 = lo; h0 < hi; h0 += 16) {
+        uint32_t gv[kFuDigits][16];
+#pragma unroll
+        for (int d = 0; d < kFuDigits; ++d) tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + h0, gv[d]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            float fhi = __uint_as_float(gv[0][t]), flo = 0.0f;
+#pragma unroll
+            for (int d = 1; d < kFuDigits; ++d) {
+                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
+                const float x = __fmul_rn(__uint_as_float(gv[d][t]), w8);
+                const float sum = __fadd_rn(fhi, x);
+                const float bb = __fsub_rn(sum, fhi);
+                const float err = __fadd_rn(__fsub_rn(fhi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
+                fhi = sum;
+                flo = __fadd_rn(flo, err);
+            }
+            const int l = n0 + h0 + t;  // trailing column of the block
+            if (l < Nc) {
+                const int el = cexp[l - cexp_base];
+                if (ei > 0 && el > 0) {
+                    const int be = ei + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
+                    double *xp = xs + (col0 + l) * kFuM + erow;
+                    *xp = (*xp - f2d_pow2(fhi, be)) - f2d_pow2(flo, be);
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256, 1)
     k_subst_fused128(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      int use_tma, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
@@ -1332,7 +1371,8 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ __align__(8) uint64_t full_bar, mma_bar;
     __shared__ __align__(8) uint64_t rbar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int rowexp[kFuM];
+    __shared__ int rowexp[2][kFuM];   // by block parity (the deferred epilogue reads the previous block's)
+    __shared__ int defexp[kF2MaxN];   // column exponents of the deferred columns
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -1371,6 +1411,13 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t mphase = 0;
     int64_t rs = 0;
     int it = 0;
+    // Lookahead: the last update round of block c holds block c + 1's columns
+    // first; all warps apply those, and warps 4-7 apply the round's other
+    // columns while warps 0-3 solve block c + 1 (disjoint columns of the tile),
+    // so that two warps per scheduler issue FP64.  Rounds further right go
+    // first and are applied by all warps.
+    bool has_def = false;
+    int def_nw = 0, def_col0 = 0, def_Nc = 0, def_par = 0;
     const int64_t ntiles = (first < tiles_total) ? (tiles_total - 1 - first) / gridDim.x + 1 : 0;
     for (int64_t tile = first; tile < tiles_total; tile += gridDim.x, ++it) {
         const int64_t r0 = tile * kFuM;
@@ -1394,6 +1441,14 @@ __global__ void __launch_bounds__(256, 1)
             const int *cexp = reinterpret_cast<const int *>(slot + kFuDigits * Np * kFuBw * 2);
             const double *rb = reinterpret_cast<const double *>(slot + kFuDigits * Np * kFuBw * 2 + Np * 4);
             const double *dvb = rb + kFuBw * kFuBw;
+            if (tid >= kFuM && has_def) {
+                // deferred columns [16, def_nw) of the previous block's first round
+                const int q4 = warp & 3;
+                f2_apply(tmem, q4, lane, rowexp[def_par][32 * q4 + lane], 16, def_nw, 0, defexp, 16, xs, def_col0,
+                         def_Nc);
+                tc_fence_before();
+            }
+            has_def = false;
             if (tid < kFuM) {
                 const int row = tid;
                 double v[kFuBw];
@@ -1411,7 +1466,7 @@ __global__ void __launch_bounds__(256, 1)
                     if (c16 + j < n) xs[(c16 + j) * kFuM + row] = v[j];
                     ex = max(ex, ((unsigned)__double2hiint(v[j]) >> 20) & 0x7FFu);
                 }
-                rowexp[row] = (int)ex;
+                rowexp[c & 1][row] = (int)ex;
                 if (Nc > 0) {
 #pragma unroll
                     for (int j0 = 0; j0 < kFuBw; j0 += 8) {
@@ -1425,9 +1480,10 @@ __global__ void __launch_bounds__(256, 1)
                     }
                 }
             }
-            // trailing columns in rounds of at most 64
-            for (int n0 = 0; n0 < Np; n0 += 64) {
-                const int nw = min(64, Np - n0);
+            // trailing columns in rounds of at most 64, the rightmost first
+            const int nrounds = (Np + 63) / 64;
+            for (int r = nrounds - 1; r >= 0; --r) {
+                const int n0 = 64 * r, nw = min(64, Np - n0);
                 fence_proxy_async_shared();
                 tc_fence_before();
                 __syncthreads();
@@ -1447,42 +1503,21 @@ __global__ void __launch_bounds__(256, 1)
                 mbar_wait_bounded(&mma_bar, mphase, st);
                 mphase ^= 1u;
                 tc_fence_after();
-                {
-                    const int q4 = warp & 3, hf = warp >> 2;
-                    const int erow = 32 * q4 + lane;
-                    const int ei = rowexp[erow];
-#pragma unroll
-                    for (int sc = 0; sc < 2; ++sc) {
-                        const int h0 = 32 * hf + 16 * sc;
-                        if (h0 >= nw) continue;  // warp-uniform
-                        uint32_t gv[kFuDigits][16];
-#pragma unroll
-                        for (int d = 0; d < kFuDigits; ++d)
-                            tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * 64 + h0, gv[d]);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            float hi = __uint_as_float(gv[0][t]), lo = 0.0f;
-#pragma unroll
-                            for (int d = 1; d < kFuDigits; ++d) {
-                                const float w8 = __uint_as_float((uint32_t)(127 - 8 * d) << 23);
-                                const float x = __fmul_rn(__uint_as_float(gv[d][t]), w8);
-                                const float sum = __fadd_rn(hi, x);
-                                const float bb = __fsub_rn(sum, hi);
-                                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(x, bb));
-                                hi = sum;
-                                lo = __fadd_rn(lo, err);
-                            }
-                            const int l = n0 + h0 + t;
-                            if (l < Nc) {
-                                const int el = cexp[l];
-                                if (ei > 0 && el > 0) {
-                                    const int be = ei + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
-                                    double *xp = xs + (c16 + kFuBw + l) * kFuM + erow;
-                                    *xp = (*xp - f2d_pow2(hi, be)) - f2d_pow2(lo, be);
-                                }
-                            }
-                        }
+                const int q4 = warp & 3, hf = warp >> 2;
+                const int ei = rowexp[c & 1][32 * q4 + lane];
+                if (r > 0) {
+                    // two warps per lane quarter, 32 columns each
+                    f2_apply(tmem, q4, lane, ei, 32 * hf, min(32 * hf + 32, nw), n0, cexp, 0, xs, c16 + kFuBw, Nc);
+                } else {
+                    // block c + 1's columns now; the rest of the round is deferred
+                    if (hf == 0) f2_apply(tmem, q4, lane, ei, 0, 16, 0, cexp, 0, xs, c16 + kFuBw, Nc);
+                    if (nw > 16) {
+                        for (int e = tid; e < nw - 16; e += blockDim.x) defexp[e] = cexp[16 + e];
+                        has_def = true;
+                        def_nw = nw;
+                        def_col0 = c16 + kFuBw;
+                        def_Nc = Nc;
+                        def_par = c & 1;
                     }
                 }
                 tc_fence_before();
