@@ -386,4 +386,8 @@ size_t split_workspace_bytes(int64_t m, int64_t n, int64_t s, int sms);
 size_t xr_smem_bytes(int64_t s, int64_t n);
 size_t factor_smem_bytes(int64_t n);
 cudaError_t set_small_smem();
+// blocked multi-CTA rQR of the sketch (small_kernels.cu)
+int blocked_qr_enqueue(const double *Y, int s, int n, int64_t ldy, double *W, double *Rs, int64_t ldrs,
+                       double *scratch, RxrStatus *status, cudaStream_t st);
+size_t blocked_qr_scratch_doubles(int64_t s, int64_t n);
 }  // namespace rxr

@@ -13,6 +13,8 @@
 //                   Section 4.2 with Dot2 compensated dot products (Ogita, Rump
 //                   & Oishi 2005);
 //   * k_fp64_peak : independent DFMA chains on every SM.
+#include <algorithm>
+
 #include "rxr_internal.cuh"
 
 namespace rxr {
@@ -511,6 +513,219 @@ __global__ void __launch_bounds__(256) k_fp64_peak(double *out, int iters, doubl
 #pragma unroll
     for (int c = 0; c < 8; ++c) s += acc[c];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Householder QR of the sketch (rQR, Algorithm 5 step 2) spread over
+// the GPU: for each panel of kQrB columns one CTA factors the panel with
+// reflectors H_k = I - tau_k v_k v_k^T (v_k(k) = 1, stored below the
+// diagonal; R on and above it) and forms the compact-WY factor T with
+// H_1 ... H_b = I - V T V^T; the trailing columns C then receive
+// C <- (I - V T^T V^T) C on many CTAs: partial V^T C over 128-row chunks, a
+// fixed-order sum of the chunks, W = T^T (V^T C), C -= V W.  Mathematically the
+// same Householder QR as the one-CTA form; the rounding order differs.
+// ---------------------------------------------------------------------------
+constexpr int kQrB = 32;       // panel width
+constexpr int kQrCols = 8;     // trailing columns per CTA of the update
+constexpr int kQrRows = 128;   // rows per chunk of the update
+
+__device__ __forceinline__ double qr_v(const double *W, int s, int kc, int i)  // V(i, column kc of W)
+{
+    return (i == kc) ? 1.0 : (i > kc ? W[i + (int64_t)kc * s] : 0.0);
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_qr_panel(double *__restrict__ W, int s, int n, int k0,
+                                                            double *__restrict__ T, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double red[33];
+    __shared__ double sh_tau[kQrB];
+    __shared__ double sh_S[kQrB * kQrB];   // V^T V, (q, k) at k * kQrB + q
+    __shared__ double sh_T[kQrB * kQrB];   // T, (q, k) at k * kQrB + q
+    __shared__ double sh_scale;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int bw = min(kQrB, n - k0);
+    for (int kk = 0; kk < bw; ++kk) {
+        const int k = k0 + kk;
+        double part = 0.0;
+        for (int i = k + 1 + tid; i < s; i += blockDim.x) part = fma(W[i + (int64_t)k * s], W[i + (int64_t)k * s], part);
+        const double xn2 = block_sum(part, red);
+        if (tid == 0) {
+            const double alpha = W[k + (int64_t)k * s];
+            double tau = 0.0, scale = 0.0, beta = alpha;
+            if (xn2 > 0.0) {
+                beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+                tau = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            W[k + (int64_t)k * s] = beta;
+            sh_tau[kk] = tau;
+            sh_scale = scale;
+        }
+        __syncthreads();
+        const double scale = sh_scale, tau = sh_tau[kk];
+        for (int i = k + 1 + tid; i < s; i += blockDim.x) W[i + (int64_t)k * s] *= scale;
+        __syncthreads();
+        // H_k on the panel's later columns, one warp per column
+        for (int j = k + 1 + warp; j < k0 + bw; j += nwarps) {
+            double w = 0.0;
+            for (int i = k + 1 + lane; i < s; i += 32) w = fma(W[i + (int64_t)k * s], W[i + (int64_t)j * s], w);
+            w = warp_sum(w) + W[k + (int64_t)j * s];
+            const double f = tau * w;
+            if (lane == 0) W[k + (int64_t)j * s] -= f;
+            for (int i = k + 1 + lane; i < s; i += 32) W[i + (int64_t)j * s] = fma(-f, W[i + (int64_t)k * s], W[i + (int64_t)j * s]);
+        }
+        __syncthreads();
+    }
+    // S = V^T V (q < k), one warp per pair
+    for (int pr = warp; pr < bw * bw; pr += nwarps) {
+        const int q = pr % bw, k = pr / bw;
+        if (q >= k) continue;
+        double d = 0.0;
+        for (int i = k0 + k + lane; i < s; i += 32) d = fma(qr_v(W, s, k0 + q, i), qr_v(W, s, k0 + k, i), d);
+        d = warp_sum(d);
+        if (lane == 0) sh_S[k * kQrB + q] = d;
+    }
+    __syncthreads();
+    // T(k, k) = tau_k, T(0:k, k) = -tau_k T(0:k, 0:k) S(0:k, k), column by column
+    for (int k = 0; k < bw; ++k) {
+        if (tid < k) {
+            double acc = 0.0;
+            for (int q = tid; q < k; ++q) acc = fma(sh_T[q * kQrB + tid], sh_S[k * kQrB + q], acc);
+            sh_T[k * kQrB + tid] = -sh_tau[k] * acc;
+        } else if (tid == k) {
+            sh_T[k * kQrB + k] = sh_tau[k];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kQrB * kQrB; e += blockDim.x) {
+        const int q = e % kQrB, k = e / kQrB;
+        T[e] = (q < bw && k < bw && q <= k) ? sh_T[e] : 0.0;
+    }
+}
+
+// P[(chunk * nc + c) * kQrB + k] = sum over the chunk's rows of V(i, k) C(i, c).
+__global__ void __launch_bounds__(256) k_qr_vtc(const double *__restrict__ W, int s, int n, int k0,
+                                                double *__restrict__ P, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double sv[kQrRows * kQrB];
+    __shared__ double sc[kQrRows * kQrCols];
+    const int bw = min(kQrB, n - k0), nc = n - k0 - bw;
+    const int c0 = blockIdx.x * kQrCols, i0 = k0 + blockIdx.y * kQrRows;
+    const int rows = min(kQrRows, s - i0);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kQrRows * kQrB; e += blockDim.x) {
+        const int r = e % kQrRows, k = e / kQrRows;
+        sv[e] = (r < rows && k < bw) ? qr_v(W, s, k0 + k, i0 + r) : 0.0;
+    }
+    for (int e = tid; e < kQrRows * kQrCols; e += blockDim.x) {
+        const int r = e % kQrRows, c = e / kQrRows;
+        sc[e] = (r < rows && c0 + c < nc) ? W[(i0 + r) + (int64_t)(k0 + bw + c0 + c) * s] : 0.0;
+    }
+    __syncthreads();
+    const int k = tid >> 3, c = tid & 7;
+    double acc = 0.0;
+    for (int r = 0; r < rows; ++r) acc = fma(sv[k * kQrRows + r], sc[c * kQrRows + r], acc);
+    if (k < bw && c0 + c < nc) P[((int64_t)blockIdx.y * nc + c0 + c) * kQrB + k] = acc;
+}
+
+// C -= V (T^T (sum_chunks P)) for the CTA's kQrCols columns and kQrRows rows.
+__global__ void __launch_bounds__(256) k_qr_apply(double *__restrict__ W, int s, int n, int k0,
+                                                  const double *__restrict__ P, int nchunks,
+                                                  const double *__restrict__ T, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double w1[kQrB * kQrCols], w2[kQrB * kQrCols];
+    const int bw = min(kQrB, n - k0), nc = n - k0 - bw;
+    const int c0 = blockIdx.x * kQrCols, i0 = k0 + blockIdx.y * kQrRows;
+    const int rows = min(kQrRows, s - i0);
+    const int tid = threadIdx.x;
+    {
+        const int k = tid >> 3, c = tid & 7;
+        double acc = 0.0;
+        if (k < bw && c0 + c < nc)
+            for (int ch = 0; ch < nchunks; ++ch) acc += P[((int64_t)ch * nc + c0 + c) * kQrB + k];
+        w1[c * kQrB + k] = acc;
+    }
+    __syncthreads();
+    {
+        const int k = tid >> 3, c = tid & 7;
+        double acc = 0.0;
+        for (int q = 0; q <= k && q < bw; ++q) acc = fma(T[k * kQrB + q], w1[c * kQrB + q], acc);
+        w2[c * kQrB + k] = (k < bw) ? acc : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < kQrRows * kQrCols; e += blockDim.x) {
+        const int r = e % kQrRows, c = e / kQrRows;
+        if (r >= rows || c0 + c >= nc) continue;
+        const int i = i0 + r;
+        double *cp = W + i + (int64_t)(k0 + bw + c0 + c) * s;
+        double acc = *cp;
+        for (int k = 0; k < bw; ++k) acc = fma(-qr_v(W, s, k0 + k, i), w2[c * kQrB + k], acc);
+        *cp = acc;
+    }
+}
+
+// Sign normalisation (rows of R scaled so diag > 0) and singularity test of
+// the factored W (R in its leading n x n upper triangle), R_s written out.
+__global__ void __launch_bounds__(kSmallThreads) k_xr_finish(const double *__restrict__ W, int s, int n,
+                                                             double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ int sh_bad;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        double mx = 0.0;
+        int bad = 0;
+        for (int k = 0; k < n; ++k) {
+            const double d = fabs(W[k + (int64_t)k * s]);
+            if (rxr_nonfinite(d)) bad = 1;
+            mx = fmax(mx, d);
+        }
+        const double tol = (double)n * 0x1p-53 * mx;
+        for (int k = 0; k < n; ++k)
+            if (!(fabs(W[k + (int64_t)k * s]) > tol)) bad = 1;
+        sh_bad = bad;
+    }
+    __syncthreads();
+    for (int64_t e = tid; e < (int64_t)n * n; e += blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        double v = 0.0;
+        if (i <= j) {
+            v = W[i + (int64_t)j * s];
+            if (W[i + (int64_t)i * s] < 0.0) v = -v;
+        }
+        Rs[i + j * ldrs] = v;
+    }
+    if (tid == 0 && sh_bad) rxr_fail(st, RXR_ERR_SKETCH_SINGULAR, 0, -1);
+}
+
+// The rQR factorisation of Y (s x n, ld ldy) into R_s: Y copied to W (ld s),
+// then the panels.  Scratch: T (kQrB^2 doubles) and P (ceil(s / kQrRows) x n
+// x kQrB doubles) from `scratch`.
+int blocked_qr_enqueue(const double *Y, int s, int n, int64_t ldy, double *W, double *Rs, int64_t ldrs,
+                       double *scratch, RxrStatus *status, cudaStream_t st)
+{
+    if (cudaMemcpy2DAsync(W, (size_t)s * 8, Y, (size_t)ldy * 8, (size_t)s * 8, n, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+        return RXR_ERR_CUDA;
+    double *T = scratch, *P = scratch + kQrB * kQrB;
+    for (int k0 = 0; k0 < n; k0 += kQrB) {
+        k_qr_panel<<<1, kSmallThreads, 0, st>>>(W, s, n, k0, T, status);
+        const int bw = std::min(kQrB, n - k0), nc = n - k0 - bw;
+        if (nc <= 0) continue;
+        const dim3 grid((unsigned)((nc + kQrCols - 1) / kQrCols), (unsigned)((s - k0 + kQrRows - 1) / kQrRows));
+        k_qr_vtc<<<grid, 256, 0, st>>>(W, s, n, k0, P, status);
+        k_qr_apply<<<grid, 256, 0, st>>>(W, s, n, k0, P, (int)grid.y, T, status);
+    }
+    k_xr_finish<<<1, kSmallThreads, 0, st>>>(W, s, n, Rs, ldrs, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+size_t blocked_qr_scratch_doubles(int64_t s, int64_t n)
+{
+    return (size_t)kQrB * kQrB + (size_t)((s + kQrRows - 1) / kQrRows) * n * kQrB;
 }
 
 cudaError_t set_small_smem()

@@ -101,10 +101,16 @@ def test_sketch_parity(h, m, n, s):
 
 # ------------------------------------------------------------------ XR factor of the sketch
 @pytest.mark.parametrize("variant", ["qr", "lu"])
-@pytest.mark.parametrize("s,n,kappa", [(32, 16, 1e4), (128, 64, 1e10), (17, 16, 1e2), (256, 128, 1e6), (3, 1, 1)])
+@pytest.mark.parametrize("s,n,kappa", [(32, 16, 1e4), (128, 64, 1e10), (17, 16, 1e2), (256, 128, 1e6), (3, 1, 1),
+                                         (1024, 512, 1e13), (300, 150, 1e12), (64, 33, 1e8)])
 def test_xr_factor_parity(h, variant, s, n, kappa):
-    A = usv_matrix(max(40 * n, 100), n, kappa, seed=3)
-    Y = o.sketch(A, s, seed=1)
+    if s * n <= 40000:
+        A = usv_matrix(max(40 * n, 100), n, kappa, seed=3)
+        Y = o.sketch(A, s, seed=1)
+    else:
+        # wide sketches (the blocked multi-CTA QR): a sketch-shaped matrix of the
+        # same conditioning, directly
+        Y = usv_matrix(s, n, kappa, seed=3)
     Rs, code = h.xr_factor(to_dev(Y), variant)
     assert code == 0
     Rg = to_host(Rs)
