@@ -326,6 +326,36 @@ def subst_fp64_flop_per_row(n, bw, sub_ops):
 
 
 def launches_per_step(prec, n):
+    """Kernels one CholeskyQR2 factorisation launches (P = 2, rQR, s = 2n)."""
+    npanel = (n + 31) // 32
+    xr = 1 if 2 * n * n <= 16384 else 3 * npanel - 1  # one-CTA XR, or blocked: panels, V^T C, updates, finish
+    if prec == "fp64":
+        # sketch, reduce, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
+        return (10 if n <= 128 else 12) + xr
+    if n <= 64:
+        # colexp, sketch, reduce, XR, 2 x (fused substitution, Gram, reduce, factor), inverse, apply, copy
+        return 14 + xr
+    if n <= 128:
+        # colexp, sketch, reduce, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
+        return 3 + xr + 3 * 2 + 2 * 2 + 2 + 1
+    blocked = 2 * ((n + 63) // 64) - 1  # diagonal solves + trailing updates
+    return 3 + xr + 3 * blocked + 2 * 2 + 2 + 1
+
+
+def subst_fp64_flop_per_row(n, bw, sub_ops):
+    """FP64 flop a blocked substitution issues per row: the diagonal-block
+    solves (bw (bw - 1) / 2 FMAs per block, 2 flop each), the n multiplications
+    by 1 / R_jj, and sub_ops FP64 operations per trailing output per block (the
+    subtraction of the tensor-core update)."""
+    flop, c0 = 0.0, 0
+    while c0 < n:
+        b = min(bw, n - c0)
+        flop += b * (b - 1) + sub_ops * (n - c0 - b)
+        c0 += b
+    return flop + n
+
+
+def launches_per_step(prec, n):
     """Kernels one CholeskyQR2 factorisation launches (P = 2)."""
     if prec == "fp64":
         # sketch, reduce, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
