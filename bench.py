@@ -342,35 +342,6 @@ def launches_per_step(prec, n):
     return 3 + xr + 3 * blocked + 2 * 2 + 2 + 1
 
 
-def subst_fp64_flop_per_row(n, bw, sub_ops):
-    """FP64 flop a blocked substitution issues per row: the diagonal-block
-    solves (bw (bw - 1) / 2 FMAs per block, 2 flop each), the n multiplications
-    by 1 / R_jj, and sub_ops FP64 operations per trailing output per block (the
-    subtraction of the tensor-core update)."""
-    flop, c0 = 0.0, 0
-    while c0 < n:
-        b = min(bw, n - c0)
-        flop += b * (b - 1) + sub_ops * (n - c0 - b)
-        c0 += b
-    return flop + n
-
-
-def launches_per_step(prec, n):
-    """Kernels one CholeskyQR2 factorisation launches (P = 2)."""
-    if prec == "fp64":
-        # sketch, reduce, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
-        return 11 if n <= 128 else 13
-    if n <= 64:
-        # colexp, sketch, reduce, XR, 2 x (fused substitution, Gram, reduce, factor), inverse, apply, copy
-        return 15
-    if n <= 128:
-        # colexp, sketch, reduce, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
-        return 4 + 3 * 2 + 2 * 2 + 2 + 1
-    bw = 64
-    blocked = 2 * ((n + bw - 1) // bw) - 1  # diagonal solves + trailing updates
-    return 4 + 3 * blocked + 2 * 2 + 2 + 1
-
-
 def roofline_entry(prec, stages, peak_fp64):
     """The dominant FP64 launch of the path against the measured DFMA peak,
     counting the FP64 flop that launch actually issues.
