@@ -517,8 +517,12 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     }
     // step 4: CholeskyQR passes on X
     for (int pass = 1; pass <= passes; ++pass) {
-        k_factor<<<1, 512, factor_smem_bytes(p.n), st>>>(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status);
-        if (launch_ok()) return RXR_ERR_CUDA;
+        if (p.n > 64) {
+            if (int e = blocked_factor_enqueue(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status, st)) return e;
+        } else {
+            k_factor<<<1, 512, factor_smem_bytes(p.n), st>>>(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        }
         const bool last = (pass == passes);
         // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
         // split path takes that Gram from the tensor cores at FP64 grade
@@ -1083,7 +1087,11 @@ int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *
     bind_plan(p, h->ws);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
-    k_factor<<<1, 512, factor_smem_bytes(n), st>>>(G, (int)n, ldg, p.Rp, p.Racc, p.C, 1, 0, p.status);
+    if (n > 64) {
+        if (int e = blocked_factor_enqueue(G, (int)n, ldg, p.Rp, p.Racc, p.C, 1, 0, p.status, st)) return e;
+    } else {
+        k_factor<<<1, 512, factor_smem_bytes(n), st>>>(G, (int)n, ldg, p.Rp, p.Racc, p.C, 1, 0, p.status);
+    }
     if (launch_ok()) return RXR_ERR_CUDA;
     if (cudaMemcpy2DAsync(R, ldr * 8, p.Rp, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;

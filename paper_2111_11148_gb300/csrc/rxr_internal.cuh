@@ -390,4 +390,7 @@ cudaError_t set_small_smem();
 int blocked_qr_enqueue(const double *Y, int s, int n, int64_t ldy, double *W, double *Rs, int64_t ldrs,
                        double *scratch, RxrStatus *status, cudaStream_t st);
 size_t blocked_qr_scratch_doubles(int64_t s, int64_t n);
+// blocked multi-CTA Cholesky R_p = chol(G) (+ R_acc <- R_p R_acc) for n > 64
+int blocked_factor_enqueue(const double *G, int n, int64_t ldg, double *Rp, double *Racc, double *C, int pass,
+                           int update_racc, RxrStatus *status, cudaStream_t st);
 }  // namespace rxr

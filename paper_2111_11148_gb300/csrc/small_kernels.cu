@@ -728,6 +728,177 @@ size_t blocked_qr_scratch_doubles(int64_t s, int64_t n)
     return (size_t)kQrB * kQrB + (size_t)((s + kQrRows - 1) / kQrRows) * n * kQrB;
 }
 
+// ---------------------------------------------------------------------------
+// Blocked Cholesky R_p = chol(G) (upper) and R_acc <- R_p R_acc for n > 64,
+// spread over the GPU: per panel of kChB columns one CTA factors the diagonal
+// block, a column-parallel kernel forms the panel's rows of R_p, and an
+// upper-triangle update of the trailing block runs over kChB x kChB tiles.
+// Every entry sees exactly the FMA sequence of the one-CTA form (updates in
+// ascending panel order, R_jl = C_jl * (1 / R_jj)), so the result is the same
+// to the bit.  C (n x n scratch, ld n) holds the working copy.
+// ---------------------------------------------------------------------------
+constexpr int kChB = 32;
+
+__global__ void __launch_bounds__(256) k_chol_init(const double *__restrict__ G, int n, int64_t ldg,
+                                                   double *__restrict__ C, double *__restrict__ Rp, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        C[e] = (i <= j) ? G[i + j * ldg] : 0.0;
+        Rp[e] = 0.0;
+    }
+}
+
+// Diagonal block [k0, k0 + b): unblocked Cholesky of the updated block; the
+// block's rows of R_p (its own columns) are written.
+__global__ void __launch_bounds__(256) k_chol_diag(double *__restrict__ C, double *__restrict__ Rp, int n, int k0,
+                                                   int pass, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double cs[kChB * kChB], rs[kChB * kChB];
+    __shared__ double sh_rjj;
+    __shared__ int sh_bad;
+    const int b = min(kChB, n - k0), tid = threadIdx.x;
+    for (int e = tid; e < kChB * kChB; e += blockDim.x) {
+        const int i = e % kChB, j = e / kChB;
+        cs[e] = (i < b && j < b) ? C[(k0 + i) + (int64_t)(k0 + j) * n] : 0.0;
+        rs[e] = 0.0;
+    }
+    if (tid == 0) sh_bad = -1;
+    __syncthreads();
+    for (int j = 0; j < b; ++j) {
+        if (tid == 0) {
+            const double d = cs[j + j * kChB];
+            if (!(d > 0.0) || rxr_nonfinite(d)) sh_bad = j;
+            else sh_rjj = sqrt(d);
+        }
+        __syncthreads();
+        if (sh_bad >= 0) break;
+        const double rjj = sh_rjj, inv = 1.0 / rjj;
+        for (int l = j + tid; l < b; l += blockDim.x) rs[j + l * kChB] = (l == j) ? rjj : cs[j + l * kChB] * inv;
+        __syncthreads();
+        const int w = b - j - 1;
+        for (int e = tid; e < w * w; e += blockDim.x) {
+            const int k = j + 1 + e % w, l = j + 1 + e / w;
+            if (k <= l) cs[k + l * kChB] = fma(-rs[j + k * kChB], rs[j + l * kChB], cs[k + l * kChB]);
+        }
+        __syncthreads();
+    }
+    if (sh_bad >= 0) {
+        if (tid == 0) rxr_fail(st, RXR_ERR_CHOL_BREAKDOWN, pass, k0 + sh_bad);
+        return;
+    }
+    for (int e = tid; e < kChB * kChB; e += blockDim.x) {
+        const int i = e % kChB, j = e / kChB;
+        if (i < b && j < b) Rp[(k0 + i) + (int64_t)(k0 + j) * n] = rs[e];
+    }
+}
+
+// Panel rows of R_p right of the diagonal block: column l (one thread each)
+// runs the one-CTA form's sequence for rows j of the block: C_jl receives the
+// block's earlier rows' updates, then R_jl = C_jl * (1 / R_jj).
+__global__ void __launch_bounds__(256) k_chol_panel(const double *__restrict__ C, double *__restrict__ Rp, int n,
+                                                    int k0, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double rk[kChB * kChB];
+    __shared__ double inv[kChB];
+    const int b = min(kChB, n - k0), tid = threadIdx.x;
+    for (int e = tid; e < kChB * kChB; e += blockDim.x) {
+        const int i = e % kChB, j = e / kChB;
+        rk[e] = (i < b && j < b) ? Rp[(k0 + i) + (int64_t)(k0 + j) * n] : 0.0;
+    }
+    __syncthreads();
+    if (tid < b) inv[tid] = 1.0 / rk[tid + tid * kChB];
+    __syncthreads();
+    const int l = k0 + b + blockIdx.x * blockDim.x + tid;
+    if (l >= n) return;
+    double x[kChB];
+#pragma unroll
+    for (int j = 0; j < kChB; ++j) x[j] = (j < b) ? C[(k0 + j) + (int64_t)l * n] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kChB; ++j) {
+        if (j < b) {
+            x[j] = x[j] * inv[j];
+#pragma unroll
+            for (int k = j + 1; k < kChB; ++k)
+                if (k < b) x[k] = fma(-rk[j + k * kChB], x[j], x[k]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kChB; ++j)
+        if (j < b) Rp[(k0 + j) + (int64_t)l * n] = x[j];
+}
+
+// Trailing update C_kl -= sum_{j in panel} R_jk R_jl for k0 + b <= k <= l < n,
+// one kChB x kChB tile (I <= J) per CTA.
+__global__ void __launch_bounds__(256) k_chol_syrk(double *__restrict__ C, const double *__restrict__ Rp, int n,
+                                                   int k0, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double ri[kChB * kChB], rj[kChB * kChB];  // panel rows x tile columns
+    const int b = min(kChB, n - k0), t0 = k0 + b;
+    const int nt = (n - t0 + kChB - 1) / kChB;
+    int I = 0, rem = blockIdx.x;
+    while (rem >= nt - I) {
+        rem -= nt - I;
+        ++I;
+    }
+    const int J = I + rem;
+    const int ci = t0 + I * kChB, cj = t0 + J * kChB, tid = threadIdx.x;
+    for (int e = tid; e < kChB * kChB; e += blockDim.x) {
+        const int q = e % kChB, c = e / kChB;
+        ri[e] = (q < b && ci + c < n) ? Rp[(k0 + q) + (int64_t)(ci + c) * n] : 0.0;
+        rj[e] = (q < b && cj + c < n) ? Rp[(k0 + q) + (int64_t)(cj + c) * n] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < kChB * kChB; e += blockDim.x) {
+        const int a = e % kChB, c = e / kChB;
+        const int k = ci + a, l = cj + c;
+        if (k >= n || l >= n || k > l) continue;
+        double acc = C[k + (int64_t)l * n];
+        for (int q = 0; q < b; ++q) acc = fma(-ri[q + a * kChB], rj[q + c * kChB], acc);
+        C[k + (int64_t)l * n] = acc;
+    }
+}
+
+// out_ij = sum_{k = i..j} Rp_ik Racc_kj (upper x upper), then copied to Racc.
+__global__ void __launch_bounds__(256) k_trmm_upper(const double *__restrict__ Rp, const double *__restrict__ Racc,
+                                                    double *__restrict__ out, int n, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        double acc = 0.0;
+        if (i <= j)
+            for (int k = i; k <= j; ++k) acc = fma(Rp[i + (int64_t)k * n], Racc[k + (int64_t)j * n], acc);
+        out[e] = acc;
+    }
+}
+
+int blocked_factor_enqueue(const double *G, int n, int64_t ldg, double *Rp, double *Racc, double *C, int pass,
+                           int update_racc, RxrStatus *status, cudaStream_t st)
+{
+    const int64_t nn = (int64_t)n * n;
+    const int g = (int)std::min<int64_t>(1024, (nn + 255) / 256);
+    k_chol_init<<<g, 256, 0, st>>>(G, n, ldg, C, Rp, status);
+    for (int k0 = 0; k0 < n; k0 += kChB) {
+        k_chol_diag<<<1, 256, 0, st>>>(C, Rp, n, k0, pass, status);
+        const int b = std::min(kChB, n - k0), rest = n - k0 - b;
+        if (rest <= 0) continue;
+        k_chol_panel<<<(rest + 255) / 256, 256, 0, st>>>(C, Rp, n, k0, status);
+        const int nt = (rest + kChB - 1) / kChB;
+        k_chol_syrk<<<nt * (nt + 1) / 2, 256, 0, st>>>(C, Rp, n, k0, status);
+    }
+    if (update_racc) {
+        k_trmm_upper<<<g, 256, 0, st>>>(Rp, Racc, C, n, status);
+        if (cudaMemcpyAsync(Racc, C, (size_t)nn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return RXR_ERR_CUDA;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
 cudaError_t set_small_smem()
 {
     cudaError_t e = cudaFuncSetAttribute(k_xr_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,

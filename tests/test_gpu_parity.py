@@ -166,7 +166,7 @@ def test_precond_gram_without_x(h):
 
 
 # ------------------------------------------------------------------ Cholesky
-@pytest.mark.parametrize("n", [1, 2, 16, 64, 128])
+@pytest.mark.parametrize("n", [1, 2, 16, 64, 65, 128, 200, 512])
 def test_cholesky_parity(h, n):
     X = np.random.default_rng(n).standard_normal((4 * n + 10, n))
     G = np.asfortranarray(X.T @ X)
@@ -183,6 +183,12 @@ def test_cholesky_breakdown_column(h):
     _, code = h.cholesky(to_dev(G), raise_on_error=False)
     assert code == rxr.CHOL_BREAKDOWN
     assert h.last_info()[1] == 2
+    # the blocked form (n > 64) reports the global column, here in the third panel
+    d = np.ones(150)
+    d[77] = -1.0
+    _, code = h.cholesky(to_dev(np.asfortranarray(np.diag(d))), raise_on_error=False)
+    assert code == rxr.CHOL_BREAKDOWN
+    assert h.last_info()[1] == 77
 
 
 # ------------------------------------------------------------------ end to end
