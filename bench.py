@@ -333,8 +333,10 @@ def launches_per_step(prec, n):
         # sketch, reduce, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
         return (10 if n <= 128 else 12) + xr
     if n <= 64:
-        # colexp, sketch, reduce, XR, 2 x (fused substitution, Gram, reduce, factor), inverse, apply, copy
-        return 14 + xr
+        # colexp, sketch, reduce, XR, fused substitution, Gram, reduce, factor, middle pass (inverse,
+        # condition estimate, apply, fused substitution: the one not selected returns at once), Gram,
+        # reduce, factor, inverse, apply, copy
+        return 17 + xr
     if n <= 128:
         # colexp, sketch, reduce, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
         return 3 + xr + 3 * 2 + 2 * 2 + 2 + 1

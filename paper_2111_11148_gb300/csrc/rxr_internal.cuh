@@ -373,7 +373,10 @@ int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaSt
 int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                           int64_t ldx, cudaStream_t st);
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                        int64_t ldx, int *colexp_out, cudaStream_t st);
+                        int64_t ldx, int *colexp_out, cudaStream_t st, const int *sel = nullptr);
+int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *colexp_out, int *sel,
+                        cudaStream_t st);
+int *split_select_flag(const Plan &p);
 int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                            int64_t ldx, cudaStream_t st);
 // 2-D tensor map of a column-major FP64 matrix (api.cu); false where TMA's

@@ -948,9 +948,11 @@ __device__ __forceinline__ bool group_or(int g, bool v)
 __global__ void __launch_bounds__(256, 1)
     k_subst_fused(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst, int use_tma,
                   const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
-                  const double *__restrict__ R, int64_t ldr, int64_t tiles_total, int *colexp_out, RxrStatus *st)
+                  const double *__restrict__ R, int64_t ldr, int64_t tiles_total, int *colexp_out,
+                  const int *__restrict__ sel, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
+    if (sel != nullptr && *sel != 0) return;  // the explicit-inverse product was chosen instead
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nb = fu_blocks(n);
     const size_t tile_bytes = (size_t)kFuM * n * 8;
@@ -1808,9 +1810,11 @@ __host__ __device__ inline size_t aq_smem_bytes(int n)
 
 __global__ void __launch_bounds__(256, 1)
     k_apply_oz64(const __grid_constant__ CUtensorMap tm_x, int use_tma, double *X, int64_t ldx, int64_t m, int n,
-                 const double *__restrict__ T, int64_t ldt, int64_t tiles_total, RxrStatus *st)
+                 const double *__restrict__ T, int64_t ldt, int64_t tiles_total, const int *__restrict__ sel,
+                 int *colexp_out, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
+    if (sel != nullptr && *sel != 1) return;  // substitution was chosen instead
     extern __shared__ __align__(1024) unsigned char smem[];
     const size_t tile_bytes = (size_t)kAqM * n * 8;
     double *xs = reinterpret_cast<double *>(smem);            // [n][128]
@@ -1821,11 +1825,13 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ uint32_t tmem_base;
     __shared__ int colexp_t[64];
     __shared__ int pexp[2][kAqM];
+    __shared__ int out_exp[64];  // largest exponent per column of Q (colexp_out)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & (kAqM - 1), h = tid >> 7;  // digit role: row of the tile, 8-column half of a K-step
 
     for (int e = tid; e < (int)((2 * kOzDigits * kAqPlane + kOzDigits * kAqTPlane) / 16); e += blockDim.x)
         reinterpret_cast<uint4 *>(adig)[e] = make_uint4(0, 0, 0, 0);
+    if (tid < 64) out_exp[tid] = 0;
     if (tid < 64) {
         unsigned ex = 0;
         if (tid < n)
@@ -1965,10 +1971,16 @@ __global__ void __launch_bounds__(256, 1)
                         lo = __fadd_rn(lo, err);
                     }
                     const int l = col0 + t;
+                    double qv = 0.0;
                     if (l < n && gr < m) {
                         const int el = colexp_t[l];
                         const int be = er + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
-                        X[gr + (int64_t)l * ldx] = (er > 0 && el > 0) ? f2d_pow2(hi, be) + f2d_pow2(lo, be) : 0.0;
+                        qv = (er > 0 && el > 0) ? f2d_pow2(hi, be) + f2d_pow2(lo, be) : 0.0;
+                        X[gr + (int64_t)l * ldx] = qv;
+                    }
+                    if (colexp_out != nullptr) {
+                        const unsigned e = __reduce_max_sync(0xFFFFFFFFu, ((unsigned)__double2hiint(qv) >> 20) & 0x7FFu);
+                        if (lane == 0 && e > 0 && l < n) atomicMax(&out_exp[l], (int)e);
                     }
                 }
             }
@@ -1980,6 +1992,7 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0 && use_tma && !ok) mbar_wait_bounded(&full_bar, loads & 1u, st);
     tc_fence_before();
     __syncthreads();
+    if (colexp_out != nullptr && tid < n && out_exp[tid] > 0) atomicMax(colexp_out + tid, out_exp[tid]);
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
@@ -2265,7 +2278,13 @@ static size_t split_rec_bytes(int64_t n)
 // of A, later the n <= 64 Gram's columns of X), then the records of R
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
 {
-    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n);
+    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n) + 256;
+}
+
+int *split_select_flag(const Plan &p)
+{
+    return reinterpret_cast<int *>(p.split + split_partial_bytes(p.m, p.n, p.sms) + RXR_MAX_N * sizeof(int) +
+                                   split_rec_bytes(p.n));
 }
 
 int *split_colexp(const Plan &p)
@@ -2280,6 +2299,79 @@ static unsigned char *split_records(const Plan &p)
 
 // X <- X R^{-1} on the tensor cores through the explicit inverse (n <= 64);
 // T is held in the XR scratch (s x n >= n x n).
+// Estimate of cond_2(R) = ||R||_2 ||R^{-1}||_2 (n <= 64, one CTA): twelve power
+// iterations on R^T R and on T^T T (T = R^{-1}) from the all-ones vector, in a
+// fixed order (deterministic).  *sel = 1 when the estimate is at most kExplicitCond,
+// else 0: the middle CholeskyQR pass then multiplies by T on the tensor cores
+// instead of substituting.
+constexpr double kExplicitCond = 16.0;
+
+__global__ void __launch_bounds__(64) k_cond_select(const double *__restrict__ R, const double *__restrict__ T, int n,
+                                                    int *sel, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double v[64], w[64];
+    const int i = threadIdx.x;
+    double est[2];
+    for (int which = 0; which < 2; ++which) {
+        const double *M = which == 0 ? R : T;  // upper triangular, ld n
+        double nrm = 0.0;
+        if (i < 64) v[i] = (i < n) ? 1.0 : 0.0;
+        __syncthreads();
+        for (int itn = 0; itn < 12; ++itn) {
+            // w = M v
+            double a = 0.0;
+            if (i < n)
+                for (int k = i; k < n; ++k) a = fma(M[i + (int64_t)k * n], v[k], a);
+            w[i] = a;
+            __syncthreads();
+            // v = M^T w, then normalise
+            double b = 0.0;
+            if (i < n)
+                for (int k = 0; k <= i; ++k) b = fma(M[k + (int64_t)i * n], w[k], b);
+            __syncthreads();
+            v[i] = b;
+            __syncthreads();
+            double ss = 0.0;
+            for (int k = 0; k < n; ++k) ss = fma(v[k], v[k], ss);  // every thread, same order
+            nrm = sqrt(sqrt(ss));  // ||M^T M v||^(1/2) with ||v|| = 1 before: an estimate of ||M||_2
+            const double inv = (ss > 0.0) ? 1.0 / sqrt(ss) : 0.0;
+            __syncthreads();
+            v[i] *= inv;
+            __syncthreads();
+        }
+        est[which] = nrm;
+    }
+    if (i == 0) {
+        const double c = est[0] * est[1];
+        *sel = (c > 0.0 && c <= kExplicitCond && !rxr_nonfinite(c)) ? 1 : 0;
+    }
+}
+
+// The middle CholeskyQR pass for n <= 64: X <- X R^{-1} by the tensor-core
+// product with T = R^{-1} when R is well conditioned (estimate <= 16), else by
+// the fused substitution; both kernels are launched and the one not selected
+// returns at once (no host synchronisation).  X's column exponents go to
+// colexp_out for the Gram that follows.
+int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *colexp_out, int *sel,
+                        cudaStream_t st)
+{
+    if (p.n > 64) return RXR_ERR_UNSUPPORTED;
+    double *T = p.W;
+    k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
+    k_cond_select<<<1, 64, 0, st>>>(R, T, (int)p.n, sel, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    const int n = (int)p.n;
+    CUtensorMap mx;
+    const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
+    const int64_t tiles = cdiv64(p.m, kAqM);
+    const int gx = (int)std::min<int64_t>(p.sms, tiles);
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, colexp_out,
+                                                    p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    return fused_subst_enqueue(p, X, ldx, R, p.n, X, ldx, colexp_out, st, sel);
+}
+
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
 {
     if (p.n > 64) return RXR_ERR_UNSUPPORTED;
@@ -2291,7 +2383,8 @@ int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaSt
     const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
     const int64_t tiles = cdiv64(p.m, kAqM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, p.status);
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, nullptr, nullptr,
+                                                    p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
@@ -2330,7 +2423,7 @@ int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double
 
 // X = B R^{-1} for n <= 64 in one pass over B (k_subst_fused); X may equal B.
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                        int64_t ldx, int *colexp_out, cudaStream_t st)
+                        int64_t ldx, int *colexp_out, cudaStream_t st, const int *sel)
 {
     if (p.n > kFuMaxN) return RXR_ERR_UNSUPPORTED;
     const int n = (int)p.n;
@@ -2340,7 +2433,7 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
     const int64_t tiles = cdiv64(p.m, kFuM);
     const int gx = (int)std::min<int64_t>(p.sms, cdiv64(tiles, 2));  // two tile streams per CTA
     k_subst_fused<<<gx, 256, fu_smem_bytes(n), st>>>(ms, md, use_tma, Bsrc, ldb, X, ldx, p.m, n, R, ldr, tiles,
-                                                      colexp_out, p.status);
+                                                      colexp_out, sel, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 

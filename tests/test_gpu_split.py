@@ -180,3 +180,19 @@ def test_fused128_substitution(h, m, n, kappa):
     # row's sums over two lanes, so bit equality is not expected)
     Xo = o.trsm_right_upper(A, R)
     assert np.linalg.norm(Xg - Xo) <= 64 * n * U * np.linalg.cond(R) * np.linalg.norm(Xo)
+
+
+@pytest.mark.parametrize("s_factor,kappa", [(2, 1e12), (1, 1e6), (1, 1e10)])
+def test_middle_pass_selection(h, s_factor, kappa):
+    # above 2^17 rows the middle CholeskyQR pass multiplies by the explicit
+    # inverse of R_1 on the tensor cores when its estimated condition number is
+    # at most 16, else substitutes; a square sketch (s = n) leaves X_1 worse
+    # conditioned than s = 2n.  Either way the factorisation meets the targets.
+    m, n = 1 << 17, 48
+    A = usv_matrix(m, n, kappa, seed=int(kappa) % 97 + s_factor)
+    Q, R, code = h.cholqr(to_dev(A), variant="qr", s=s_factor * n, seed=4, passes=2, prec="split")
+    assert code == 0
+    Qg, Rg = to_host(Q), to_host(R)
+    assert o.orth_error(Qg) <= 1e-13
+    assert o.resid_error(A, Qg, Rg) <= 1e-14
+    assert np.all(np.diag(Rg) > 0)
