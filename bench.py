@@ -335,8 +335,9 @@ def launches_per_step(prec, n):
     if n <= 64:
         # colexp, sketch, reduce, XR, fused substitution, Gram, reduce, factor, middle pass (inverse,
         # condition estimate, apply, fused substitution: the one not selected returns at once), Gram,
-        # reduce, factor, inverse, apply, copy
-        return 17 + xr
+        # reduce, factor, last pass (inverse, selection, FP32-correction apply, FP64-grade apply: the
+        # one not selected returns at once), copy
+        return 19 + xr
     if n <= 128:
         # colexp, sketch, reduce, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
         return 3 + xr + 3 * 2 + 2 * 2 + 2 + 1

@@ -198,6 +198,19 @@ RXR_API int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n
 RXR_API int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, double *G, int64_t ldg, int prec,
                      void *stream);
 
+/* X <- X R^{-1} in place (Algorithm 1 step 3, the Q of a CholeskyQR pass),
+ * R upper triangular n x n (leading dimension ldr >= n, read only), X m x n
+ * column-major (ldx >= m).  RXR_FP64: row-wise FP64 substitution.
+ * RXR_SPLIT_BF16, n <= 64: T = R^{-1} by FP64 back substitution; when every
+ * |T - I| <= 2^-38 (R within rounding of I, as after a repeated CholeskyQR
+ * pass) X + X (T - I) with the correction in FP32 (error below 2^-56 |X| per
+ * term), else X T on the tensor cores at FP64 grade (exact digit splitting).
+ * RXR_SPLIT_BF16, n > 64: the blocked substitution of rxr_precond_gram.
+ * R's diagonal must be nonzero and finite (not checked: X is then not
+ * finite).  Blocking; 0 or a negative argument error (-i: argument i). */
+RXR_API int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_t ldx, const double *R, int64_t ldr,
+                           int prec, void *stream);
+
 /* Upper Cholesky factor R (R^T R = G; reads the upper triangle of G).
  * Blocking; returns 0 or RXR_ERR_CHOL_BREAKDOWN (column in rxr_last_info). */
 RXR_API int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *R, int64_t ldr, void *stream);

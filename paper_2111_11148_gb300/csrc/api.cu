@@ -548,8 +548,9 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         }
         Timer t(th, last ? 3 : 2, st);
         if (p.prec == RXR_SPLIT_BF16 && last && pass > 1 && p.n <= 64) {
-            // the last pass's R_P is within rounding of I: apply its explicit
-            // inverse on the tensor cores at FP64 grade
+            // the last pass's R_P is within rounding of I: Q = X + X (R_P^{-1} - I)
+            // with the small correction in FP32, or (should R_P^{-1} - I exceed
+            // 2^-38) the explicit inverse on the tensor cores at FP64 grade
             if (int e = ozaki_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
         } else if (p.prec == RXR_SPLIT_BF16) {
             if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st)) return e;
@@ -1078,6 +1079,37 @@ int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, d
     }
     if (cudaMemcpy2DAsync(G, ldg * 8, p.G, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_t ldx, const double *R, int64_t ldr, int prec,
+                   void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (X == nullptr) return -2;
+    if (m < 1 || m < n) return -3;
+    if (n < 1) return -4;
+    if (ldx < m) return -5;
+    if (R == nullptr) return -6;
+    if (ldr < n) return -7;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -8;
+    if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, m, n, n, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    if (cudaMemcpy2DAsync(p.Rp, n * 8, R, ldr * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    if (prec == RXR_SPLIT_BF16 && n <= 64) {
+        if (int e = ozaki_apply_enqueue(p, X, ldx, p.Rp, st)) return e;
+    } else if (prec == RXR_SPLIT_BF16) {
+        if (int e = split_subst(p, X, ldx, p.Rp, X, ldx, st)) return e;
+    } else if (int e = enqueue_subst(p, X, ldx, p.Rp, 0, X, ldx, false, false, st)) {
+        return e;
+    }
     return finish_blocking(h, p.status, st);
 }
 

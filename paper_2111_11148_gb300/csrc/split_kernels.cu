@@ -1811,10 +1811,10 @@ __host__ __device__ inline size_t aq_smem_bytes(int n)
 __global__ void __launch_bounds__(256, 1)
     k_apply_oz64(const __grid_constant__ CUtensorMap tm_x, int use_tma, double *X, int64_t ldx, int64_t m, int n,
                  const double *__restrict__ T, int64_t ldt, int64_t tiles_total, const int *__restrict__ sel,
-                 int *colexp_out, RxrStatus *st)
+                 int want, int *colexp_out, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
-    if (sel != nullptr && *sel != 1) return;  // substitution was chosen instead
+    if (sel != nullptr && *sel != want) return;  // the other form was chosen
     extern __shared__ __align__(1024) unsigned char smem[];
     const size_t tile_bytes = (size_t)kAqM * n * 8;
     double *xs = reinterpret_cast<double *>(smem);            // [n][128]
@@ -2278,7 +2278,13 @@ static size_t split_rec_bytes(int64_t n)
 // of A, later the n <= 64 Gram's columns of X), then the records of R
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
 {
-    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n) + 256;
+    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n) + 256 + 64 * 64 * 4;
+}
+
+// E = R^{-1} - I of the last pass in FP32 (64 x 64), after the selection flags
+static float *split_delta(const Plan &p)
+{
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(split_select_flag(p)) + 256);
 }
 
 int *split_select_flag(const Plan &p)
@@ -2299,6 +2305,176 @@ static unsigned char *split_records(const Plan &p)
 
 // X <- X R^{-1} on the tensor cores through the explicit inverse (n <= 64);
 // T is held in the XR scratch (s x n >= n x n).
+// ---------------------------------------------------------------------------
+// The last pass's Q = X R_P^{-1} when R_P is within rounding of I: with
+// T = R_P^{-1} = I + E, Q = X + X E, and X E is a tiny correction (|E| <= 2^-38
+// checked on the device), so single precision is plenty for it: its error is
+// below n 2^-24 |E| |X| <= 2^-56 |X| for n <= 64.  k_delta_select forms E in FP32
+// and the flag; k_apply_delta computes the correction as an FP32 product over
+// 128-row tiles and adds it to X in FP64 (one addition per entry).
+// ---------------------------------------------------------------------------
+constexpr double kDeltaMax = 0x1p-38;
+
+// E = T - I (n <= 64) as FP32, row-major and zero padded to 64 x 64
+// (Ef[k * 64 + j] = E(k, j)), and the selection flag: 1 when every |E(k, j)| <=
+// 2^-38 and T is finite, else 0.
+__global__ void __launch_bounds__(256) k_delta_select(const double *__restrict__ T, int n, float *__restrict__ Ef,
+                                                      int *sel, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    __shared__ double red[8];
+    const int tid = threadIdx.x;
+    double mx = 0.0;
+    bool bad = false;
+    for (int e = tid; e < 64 * 64; e += blockDim.x) {
+        const int k = e >> 6, j = e & 63;
+        double d = 0.0;
+        if (k < n && j < n) {
+            d = T[k + (int64_t)j * n] - (k == j ? 1.0 : 0.0);
+            bad |= rxr_nonfinite(d);
+            mx = fmax(mx, fabs(d));
+        }
+        Ef[e] = (float)d;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    bad = __syncthreads_or(bad);
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v = fmax(v, red[w]);
+        *sel = (!bad && v <= kDeltaMax) ? 1 : 0;
+    }
+}
+
+// X <- X + X E over 128-row tiles (three CTAs per SM, grid-stride, so that
+// their loads, FP32 products and FP64 additions overlap).  Warp w
+// owns columns 8w .. 8w + 7, lane l rows l, l + 32, l + 64, l + 96 of a tile
+// (coalesced for any leading dimension).  The FP64 pipe (two operations per
+// clock per SM) does only the final addition: X enters FP32 scaled by its
+// row's largest power of two (x 2^(1023 - e_r), e_r the row's largest biased
+// exponent) by integer operations on its bits (mantissa truncated: relative
+// error 2^-23; entries below 2^-126 of the row's largest flush to zero), and
+// the FP32 correction leaves scaled back by f2d_pow2.  The tile's scaled X is
+// shared in FP32 (xf[k * 128 + r], conflict-free for the column stores and the
+// row reads; a register pair (x, x) makes it the packed FP32 FMA's row
+// operand) and E's row k as two broadcast 16-byte loads (its column pairs).
+// The FP64 entries are read again for the addition (an L2 hit: the tile was
+// read moments before), which keeps a thread within 80 registers.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// x 2^(1023 - er) in FP32 with the mantissa truncated; zero when x is zero,
+// subnormal or below 2^-126 of 2^(er - 1023)
+__device__ __forceinline__ float d2f_pow2(double x, int er)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int ed = (int)((hi >> 20) & 0x7FFu);
+    const int ef = ed - er + 127;
+    const uint32_t mant = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+    return (ed == 0 || ef <= 0) ? 0.0f : __uint_as_float((hi & 0x80000000u) | ((uint32_t)min(ef, 254) << 23) | mant);
+}
+
+__host__ __device__ constexpr size_t delta_smem_bytes(int n)
+{
+    return (size_t)n * 64 * 4 + (size_t)n * 128 * 4;
+}
+
+__global__ void __launch_bounds__(256, 3) k_apply_delta(double *X, int64_t ldx, int64_t m, int n,
+                                                        const float *__restrict__ Ef, int64_t tiles_total,
+                                                        const int *__restrict__ sel, RxrStatus *st)
+{
+    if (rxr_failed(st)) return;
+    if (*sel != 1) return;  // the FP64-grade product was chosen instead
+    extern __shared__ __align__(16) float dsm_delta[];
+    float *es = dsm_delta;                                                         // n x 64
+    float *xf = es + n * 64;  // n x 128
+    __shared__ int rowe[2][128];  // the rows' largest biased exponents (double buffered)
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int e = tid; e < n * 64; e += blockDim.x) es[e] = Ef[e];
+    rowe[tid >> 7][tid & 127] = 0;
+    __syncthreads();
+    const int j0 = 8 * w;
+    const int nb = max(0, min(8, n - j0));
+    for (int64_t tile = blockIdx.x, buf = 0; tile < tiles_total; tile += gridDim.x, buf ^= 1) {
+        const int64_t r0 = tile * 128;
+        double x[4][8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int64_t gr = r0 + lane + 32 * a;
+                x[a][b] = (b < nb && gr < m) ? X[gr + (int64_t)(j0 + b) * ldx] : 0.0;
+            }
+        if (nb > 0) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                int e = 0;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) e = max(e, (int)(((uint32_t)__double2hiint(x[a][b]) >> 20) & 0x7FFu));
+                atomicMax(&rowe[buf][lane + 32 * a], e);
+            }
+        }
+        __syncthreads();  // the row exponents are complete; the previous tile's reads of xf are done
+        if (nb > 0) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int er = rowe[buf][lane + 32 * a];
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    if (b < nb) {
+                        xf[(j0 + b) * 128 + lane + 32 * a] = d2f_pow2(x[a][b], er);
+                    }
+            }
+        }
+        if (tid < 128) rowe[buf ^ 1][tid] = 0;  // read last in the previous tile, before the barrier above
+        __syncthreads();
+        if (nb == 0) continue;
+        unsigned long long acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = 0ull;
+#pragma unroll 4
+        for (int k = 0; k < n; ++k) {
+            const ulonglong2 e01 = *reinterpret_cast<const ulonglong2 *>(es + k * 64 + j0);
+            const ulonglong2 e23 = *reinterpret_cast<const ulonglong2 *>(es + k * 64 + j0 + 4);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const uint32_t xv = __float_as_uint(xf[k * 128 + lane + 32 * a]);
+                const unsigned long long xa = ((unsigned long long)xv << 32) | xv;
+                acc[a][0] = ffma2(xa, e01.x, acc[a][0]);
+                acc[a][1] = ffma2(xa, e01.y, acc[a][1]);
+                acc[a][2] = ffma2(xa, e23.x, acc[a][2]);
+                acc[a][3] = ffma2(xa, e23.y, acc[a][3]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t gr = r0 + lane + 32 * a;
+            const int er = rowe[buf][lane + 32 * a];
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                if (b < nb && gr < m) {
+                    double *xp = X + gr + (int64_t)(j0 + b) * ldx;
+                    const uint32_t cb = (uint32_t)(acc[a][b >> 1] >> (32 * (b & 1)));
+                    __stcs(xp, __ldcs(xp) + f2d_pow2(__uint_as_float(cb), er));
+                }
+        }
+    }
+}
+
+static void delta_launch(int sms, double *X, int64_t ldx, int64_t m, int n, const float *Ef, int64_t tiles,
+                         const int *sel, const CUtensorMap &, int, RxrStatus *status, cudaStream_t st)
+{
+    k_apply_delta<<<(unsigned)std::min<int64_t>(3 * (int64_t)sms, tiles), 256, delta_smem_bytes(n), st>>>(
+        X, ldx, m, n, Ef, tiles, sel, status);
+}
+
 // Estimate of cond_2(R) = ||R||_2 ||R^{-1}||_2 (n <= 64, one CTA): twelve power
 // iterations on R^T R and on T^T T (T = R^{-1}) from the all-ones vector, in a
 // fixed order (deterministic).  *sel = 1 when the estimate is at most kExplicitCond,
@@ -2366,24 +2542,32 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
     const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
     const int64_t tiles = cdiv64(p.m, kAqM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, colexp_out,
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, 1, colexp_out,
                                                     p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     return fused_subst_enqueue(p, X, ldx, R, p.n, X, ldx, colexp_out, st, sel);
 }
 
+// X <- X R^{-1} for the last pass (n <= 64): T = R^{-1}; when |T - I| <= 2^-38
+// (R within rounding of I) the FP32 correction Q = X + X (T - I), else the
+// FP64-grade tensor-core product; both launched, the one not selected returns
+// at once.  T lives in the XR scratch W (s x n doubles >= n^2).
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
 {
     if (p.n > 64) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
+    float *Ef = split_delta(p);
+    int *sel = split_select_flag(p) + 1;
     k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
+    k_delta_select<<<1, 256, 0, st>>>(T, (int)p.n, Ef, sel, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int n = (int)p.n;
+    const int64_t tiles = cdiv64(p.m, kAqM);
     CUtensorMap mx;
     const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
-    const int64_t tiles = cdiv64(p.m, kAqM);
+    delta_launch(p.sms, X, ldx, p.m, n, Ef, tiles, sel, mx, use_tma, p.status, st);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, nullptr, nullptr,
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, 0, nullptr,
                                                     p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
@@ -2517,6 +2701,8 @@ cudaError_t set_split_smem()
                                  (int)f2_smem_bytes(kF2MaxN));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)aq_smem_bytes(64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_delta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)delta_smem_bytes(64));
     return e;
 }
 

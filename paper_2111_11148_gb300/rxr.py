@@ -64,6 +64,7 @@ def load() -> ctypes.CDLL:
         "rxr_xr_factor": ([vp, vp, i64, i64, i64, i, vp, i64, vp], i),
         "rxr_precond_gram": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, i, vp], i),
         "rxr_cholesky": ([vp, vp, i64, i64, vp, i64, vp], i),
+        "rxr_apply_rinv": ([vp, vp, i64, i64, i64, vp, i64, i, vp], i),
         "rxr_gram": ([vp, vp, i64, i64, i64, vp, i64, i, vp], i),
         "rxr_orth_error": ([vp, vp, i64, i64, i64, P(d), vp], i),
         "rxr_resid_error": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, P(d), vp], i),
@@ -84,7 +85,7 @@ def exported_symbols() -> list[str]:
     return [n for n in ("rxr_create", "rxr_destroy", "rxr_workspace_bytes", "rxr_set_workspace", "rxr_cholqr",
                         "rxr_cholqr_async", "rxr_cholqr_host", "rxr_cholqr_batched", "rxr_last_info",
                         "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_xr_factor", "rxr_precond_gram",
-                        "rxr_cholesky", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
+                        "rxr_cholesky", "rxr_apply_rinv", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
                         "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc")]
 
 
@@ -273,6 +274,13 @@ class Handle:
         if raise_on_error:
             _check(code, "rxr_cholesky")
         return R, code
+
+    def apply_rinv(self, X, R, prec="fp64", stream=None):
+        """X <- X R^{-1} in place (the Q of a CholeskyQR pass); returns X."""
+        m, n = X.shape
+        _check(load().rxr_apply_rinv(self._h, _ptr(X), m, n, _ld(X), _ptr(R), _ld(R), _PRECS[prec],
+                                     _stream(stream)), "rxr_apply_rinv")
+        return X
 
     def orth_error(self, Q, stream=None) -> float:
         m, n = Q.shape

@@ -196,3 +196,67 @@ def test_middle_pass_selection(h, s_factor, kappa):
     assert o.orth_error(Qg) <= 1e-13
     assert o.resid_error(A, Qg, Rg) <= 1e-14
     assert np.all(np.diag(Rg) > 0)
+
+
+def _upper(n, rng, eps):
+    """I + eps F with F upper triangular, standard normal entries."""
+    return np.asfortranarray(np.eye(n) + eps * np.triu(rng.standard_normal((n, n))))
+
+
+def _row_rel_err(Qg, Qo, T):
+    """max over rows of |Qg - Qo|_2 / (|x_row|_2 |T|_2), x_row = Qo_row R."""
+    den = np.linalg.norm(Qo, axis=1) * np.linalg.norm(T, 2) * max(1.0, np.linalg.cond(T))
+    return float(np.max(np.linalg.norm(Qg - Qo, axis=1) / np.maximum(den, 1e-300)))
+
+
+@pytest.mark.parametrize("m,n,eps", [(1, 1, 1e-14), (677, 7, 1e-14), (128 * 9 + 37, 33, 1e-15),
+                                     (4096 + 5, 64, 1e-13), (900, 64, 1e-12), (900, 64, 1e-11),
+                                     (900, 48, 0.3), (3000, 64, 0.05), (250, 1, 0.5)])
+def test_apply_rinv_split(h, m, n, eps):
+    # X <- X R^{-1}, n <= 64: with R - I at most about 2^-38 the correction
+    # X (R^{-1} - I) is formed in FP32 (error below 2^-56 |X| per term); a
+    # larger R - I (eps = 1e-11 lies above 2^-38 after inversion, 0.05 .. 0.5
+    # far above) takes the FP64-grade tensor-core product.  Both must match the
+    # oracle's substitution to FP64 accuracy, far below what an FP32 product of
+    # X and R^{-1} reaches (about 1e-7).
+    rng = np.random.default_rng(m + n)
+    X = usv_matrix(m, n, 10.0, seed=n)
+    R = _upper(n, rng, eps)
+    Qo = o.trsm_right_upper(X, R)
+    Xd = to_dev(X)
+    h.apply_rinv(Xd, to_dev(R), prec="split")
+    Qg = to_host(Xd)
+    T = np.linalg.inv(R)
+    err = _row_rel_err(Qg, Qo, T)
+    assert err <= 64 * U, err
+
+
+def test_apply_rinv_split_odd_ld_and_large(h):
+    # a leading dimension that is not a multiple of the tile, and 2^20 + 77 rows
+    # (sampled rows against the oracle): the FP32-correction form
+    m, n = (1 << 20) + 77, 64
+    rng = np.random.default_rng(5)
+    R = _upper(n, rng, 2e-15)
+    X = np.asfortranarray(rng.standard_normal((m + 3, n)))
+    Xfull = to_dev(X)
+    Xd = Xfull[:m]
+    assert Xd.stride() == (1, m + 3)
+    h.apply_rinv(Xd, to_dev(R), prec="split")
+    Qg = to_host(Xd)
+    rows = np.concatenate([np.arange(0, 300), rng.integers(0, m, 2000), np.arange(m - 300, m)])
+    Qo = o.trsm_right_upper(np.asfortranarray(X[rows]), R)
+    assert _row_rel_err(Qg[rows], Qo, np.linalg.inv(R)) <= 64 * U
+    # the padding rows are not touched
+    assert np.array_equal(to_host(Xfull)[m:], X[m:])
+
+
+@pytest.mark.parametrize("prec,m,n", [("fp64", 700, 20), ("fp64", 3000, 100), ("split", 2100, 100),
+                                      ("split", 999, 128)])
+def test_apply_rinv_other_forms(h, prec, m, n):
+    rng = np.random.default_rng(n)
+    X = usv_matrix(m, n, 10.0, seed=n + 1)
+    R = _upper(n, rng, 0.1)
+    Qo = o.trsm_right_upper(X, R)
+    Xd = to_dev(X)
+    h.apply_rinv(Xd, to_dev(R), prec=prec)
+    assert _row_rel_err(to_host(Xd), Qo, np.linalg.inv(R)) <= 64 * U
