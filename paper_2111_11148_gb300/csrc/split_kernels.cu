@@ -404,6 +404,19 @@ __device__ __forceinline__ uint4 pack_plane_f16(const unsigned long long U[8], i
     return w;
 }
 
+// Four small integers t[i] + 128 in [0, 256] (i = 0..3) as FP16 t[i].
+__device__ __forceinline__ uint2 pack_int4x_f16(const uint32_t t[4])
+{
+    uint32_t w[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const uint32_t v = t[2 * i] | (t[2 * i + 1] << 16) | 0x64006400u;
+        const __half2 r = __hsub2(*reinterpret_cast<const __half2 *>(&v), __half2half2(__ushort_as_half((unsigned short)0x6480u)));
+        w[i] = *reinterpret_cast<const uint32_t *>(&r);
+    }
+    return make_uint2(w[0], w[1]);
+}
+
 // Eight small integers t[i] + 128 in [0, 256] (i = 0..7) as FP16 t[i].
 __device__ __forceinline__ uint4 pack_int8x_f16(const uint32_t t[8])
 {
@@ -927,6 +940,13 @@ __device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t r[16])
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t r[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -2034,20 +2054,20 @@ __global__ void __launch_bounds__(32) k_tri_inverse64(const double *__restrict__
 }
 
 // One exact window of the split sketch folded into this thread's FP64
-// accumulators (tensor-memory lane 32 q4 + lane, columns 32 half .. + 31):
+// accumulators (tensor-memory lane 32 q4 + lane, columns col0 .. + 15):
 // weights 2^-8d combined in FP32 pairs, added in FP64 without the column
 // scale.
-__device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int half, double acc[32])
+__device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int col0, double acc[16])
 {
 #pragma unroll
-    for (int c16 = 0; c16 < 2; ++c16) {
-        uint32_t g[kSpDigits][16];
+    for (int c8 = 0; c8 < 2; ++c8) {
+        uint32_t g[kSpDigits][8];
 #pragma unroll
         for (int d = 0; d < kSpDigits; ++d)
-            tmem_ld16_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * kSpN + 32 * half + 16 * c16, g[d]);
+            tmem_ld8_issue(tmem + ((uint32_t)(32 * q4) << 16) + d * kSpN + col0 + 8 * c8, g[d]);
         tmem_wait_ld();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
+        for (int t = 0; t < 8; ++t) {
             float hi = __uint_as_float(g[0][t]), lo = 0.0f;
 #pragma unroll
             for (int d = 1; d < kSpDigits; ++d) {
@@ -2059,7 +2079,7 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int half, do
                 hi = sum;
                 lo = __fadd_rn(lo, err);
             }
-            acc[16 * c16 + t] += rxr_f2d_exact(hi) + rxr_f2d_exact(lo);
+            acc[8 * c8 + t] += rxr_f2d_exact(hi) + rxr_f2d_exact(lo);
         }
     }
 }
@@ -2071,7 +2091,10 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int half, do
 // all rows (from k_colexp), so the scale of every product is fixed.  Operand
 // tiles of 64 rows alternate between two buffers: the Omega' pieces and A
 // digits of one are written while the tensor core reads the other (A's next
-// rows are already in registers).  Every 512 rows the seven tensor-memory
+// rows are already in registers).  Sixteen warps (at most 128 registers a
+// thread) share the Gaussian generation, the digits and the drains, so that
+// four warps per scheduler hide the latency of the generator's dependent
+// chains.  Every 512 rows the seven tensor-memory
 // groups (each an exact integer below 2^24: at most two pairs of products
 // below 2^14 per row) are combined in FP32 pairs and added in FP64; the fixed
 // scale 2^(e_j - 1033) is applied once at the end.
@@ -2079,7 +2102,7 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int half, do
 constexpr int kSpBuf = kSpDigits * kSpB + kSpZ * kSpA;  // 88 KB per buffer
 constexpr size_t kSpSmem2 = 2 * (size_t)kSpBuf;
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(512, 1)
     k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed,
                    const int *__restrict__ colexp_g, int64_t subs_total, int64_t subs_per_cta,
                    double *__restrict__ Ypart, RxrStatus *st)
@@ -2114,25 +2137,25 @@ __global__ void __launch_bounds__(256, 1)
     constexpr uint32_t idesc = idesc_f16(kSpM, kSpN);
     const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
 
-    // roles: A digits -> column j, rows 16 rq .. + 15 of each 64-row tile;
-    // Omega' -> sketch rows 4 kq .. + 3, data rows 8 warp .. + 7
-    const int j = tid >> 2, rq = tid & 3;
+    // roles: A digits -> column j, rows 8 rq .. + 7 of each 64-row tile;
+    // Omega' -> sketch rows 4 kq .. + 3, data rows 4 warp .. + 3
+    const int j = tid >> 3, rq = tid & 7;
     const int kq = lane;
     const bool has_col = j < nw;
     const int ej = cex[j];
     const double *acol = A + (int64_t)(c0 + j) * lda;
-    // epilogue: tensor-memory lane quarter (sketch rows), column half
-    const int q4 = warp & 3, half = warp >> 2;
-    double acc[32];
+    // epilogue: tensor-memory lane quarter (sketch rows), 16-column quarter
+    const int q4 = warp & 3, cq = warp >> 2;
+    double acc[16];
 #pragma unroll
-    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+    for (int t = 0; t < 16; ++t) acc[t] = 0.0;
 
     const int64_t b_begin = blockIdx.x * subs_per_cta;
     const int64_t b_end = min(subs_total, b_begin + subs_per_cta);
-    double vn[16];
+    double vn[8];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int64_t r = b_begin * kSpSub + 16 * rq + i;
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = b_begin * kSpSub + 8 * rq + i;
         vn[i] = (has_col && b_begin < b_end && r < m) ? acol[r] : 0.0;
     }
     // Waits are per thread and bounded; one that gives up records a timeout
@@ -2145,13 +2168,13 @@ __global__ void __launch_bounds__(256, 1)
         unsigned char *bop = smem + buf * kSpBuf;  // A digits: kSpDigits planes, N x K
         unsigned char *aop = bop + kSpDigits * kSpB;  // Omega' pieces: kSpZ planes, M x K
         const int64_t r0 = b * kSpSub;
-        double v[16];
+        double v[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = vn[i];
+        for (int i = 0; i < 8; ++i) v[i] = vn[i];
         if (b + 1 < b_end) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int64_t r = (b + 1) * kSpSub + 16 * rq + i;
+            for (int i = 0; i < 8; ++i) {
+                const int64_t r = (b + 1) * kSpSub + 8 * rq + i;
                 vn[i] = (has_col && r < m) ? acol[r] : 0.0;
             }
         }
@@ -2159,15 +2182,15 @@ __global__ void __launch_bounds__(256, 1)
         // Omega' on the 2^-12 grid: 4096 z' = 256 zeta0 + zeta1 (round to nearest
         // even by the 1.5 * 2^23 addition, as rint), both pieces exact in FP16
         if (4 * kq < sw) {
-            float z[8][4];
+            float z[4][4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                rxr_normal4(seed, (uint64_t)(r0 + 8 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
+            for (int i = 0; i < 4; ++i)
+                rxr_normal4(seed, (uint64_t)(r0 + 4 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
 #pragma unroll
             for (int t4 = 0; t4 < 4; ++t4) {
-                uint32_t p0[8], p1[8];  // zeta + 128, in [0, 256]
+                uint32_t p0[4], p1[4];  // zeta + 128, in [0, 256]
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < 4; ++i) {
                     const int q = (int)(__float_as_uint(__fadd_rn(__fmul_rn(z[i][t4], 4096.0f), 12582912.0f)) & 0x7FFFFFu) -
                                   0x400000;
                     const int z0 = (q + 128) >> 8;
@@ -2177,30 +2200,27 @@ __global__ void __launch_bounds__(256, 1)
                 }
                 const int r = 4 * kq + t4;
                 if (r < sw) {
-                    *reinterpret_cast<uint4 *>(aop + kmaj_off(r, 8 * warp)) = pack_int8x_f16(p0);
-                    *reinterpret_cast<uint4 *>(aop + kSpA + kmaj_off(r, 8 * warp)) = pack_int8x_f16(p1);
+                    *reinterpret_cast<uint2 *>(aop + kmaj_off(r, 4 * warp)) = pack_int4x_f16(p0);
+                    *reinterpret_cast<uint2 *>(aop + kSpA + kmaj_off(r, 4 * warp)) = pack_int4x_f16(p1);
                 }
             }
         }
         // digits of A: element (row k, column j) -> B tile (j, k)
         if (has_col) {
+            unsigned long long U[8];
 #pragma unroll
-            for (int g8 = 0; g8 < 2; ++g8) {
-                unsigned long long U[8];
+            for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[r]), ej);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[8 * g8 + r]), ej);
-#pragma unroll
-                for (int q = 0; q < kSpDigits; ++q) {
-                    const uint4 w = pack_plane_f16(U, q);
-                    *reinterpret_cast<uint4 *>(bop + q * kSpB + kmaj_off(j, 16 * rq + 8 * g8)) = w;
-                }
+            for (int q = 0; q < kSpDigits; ++q) {
+                const uint4 w = pack_plane_f16(U, q);
+                *reinterpret_cast<uint4 *>(bop + q * kSpB + kmaj_off(j, 8 * rq)) = w;
             }
         }
         const bool first_of_window = (it % kWinSubs) == 0;
         if (first_of_window && it > 0) {
             ok &= mbar_wait_bounded(&mma_bar[buf ^ 1], ((it - 1) >> 1) & 1, st);
             tc_fence_after();
-            sketch_drain(tmem, q4, half, acc);
+            sketch_drain(tmem, q4, 16 * cq, acc);
         }
         fence_proxy_async_shared();
         tc_fence_before();
@@ -2225,7 +2245,7 @@ __global__ void __launch_bounds__(256, 1)
     if (it > 0) {
         ok &= mbar_wait_bounded(&mma_bar[(it - 1) & 1], ((it - 1) >> 1) & 1, st);
         tc_fence_after();
-        sketch_drain(tmem, q4, half, acc);
+        sketch_drain(tmem, q4, 16 * cq, acc);
     }
     ok = __syncthreads_and(ok) != 0;
     if (ok) {
@@ -2233,8 +2253,8 @@ __global__ void __launch_bounds__(256, 1)
         const int my_row = 32 * q4 + lane;
         const int r = s0 + my_row;
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const int cl = half * 32 + t;
+        for (int t = 0; t < 16; ++t) {
+            const int cl = 16 * cq + t;
             if (my_row < sw && cl < nw) {
                 const int ce = cex[cl];
                 out[r + (int64_t)(c0 + cl) * s] = (ce > 0) ? ldexp(acc[t], ce - 1033) : 0.0;
@@ -2482,43 +2502,54 @@ static void delta_launch(int sms, double *X, int64_t ldx, int64_t m, int n, cons
 // instead of substituting.
 constexpr double kExplicitCond = 16.0;
 
-__global__ void __launch_bounds__(64) k_cond_select(const double *__restrict__ R, const double *__restrict__ T, int n,
-                                                    int *sel, RxrStatus *st)
+__global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ R, const double *__restrict__ T, int n,
+                                                     int *sel, RxrStatus *st)
 {
     if (rxr_failed(st)) return;
-    __shared__ double v[64], w[64];
-    const int i = threadIdx.x;
+    __shared__ double Ms[64 * 65];  // the matrix, column-major with a padded stride (zero below the diagonal)
+    __shared__ double v[64], w[64], red[8];
+    const int tid = threadIdx.x, row = tid >> 2, q = tid & 3, lane = tid & 31, warp = tid >> 5;
     double est[2];
     for (int which = 0; which < 2; ++which) {
         const double *M = which == 0 ? R : T;  // upper triangular, ld n
-        double nrm = 0.0;
-        if (i < 64) v[i] = (i < n) ? 1.0 : 0.0;
+        for (int e = tid; e < 64 * 64; e += blockDim.x) {
+            const int i = e & 63, k = e >> 6;
+            Ms[i + k * 65] = (i <= k && k < n) ? M[i + (int64_t)k * n] : 0.0;
+        }
+        if (q == 0) v[row] = (row < n) ? 1.0 : 0.0;
         __syncthreads();
+        double nrm = 0.0;
         for (int itn = 0; itn < 12; ++itn) {
-            // w = M v
+            // w = M v: four threads per row, terms k = q, q + 4, ...
             double a = 0.0;
-            if (i < n)
-                for (int k = i; k < n; ++k) a = fma(M[i + (int64_t)k * n], v[k], a);
-            w[i] = a;
+#pragma unroll
+            for (int k = q; k < 64; k += 4) a = fma(Ms[row + k * 65], v[k], a);
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, 1);
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, 2);
+            if (q == 0) w[row] = a;
             __syncthreads();
-            // v = M^T w, then normalise
+            // v = M^T w
             double b = 0.0;
-            if (i < n)
-                for (int k = 0; k <= i; ++k) b = fma(M[k + (int64_t)i * n], w[k], b);
-            __syncthreads();
-            v[i] = b;
+#pragma unroll
+            for (int k = q; k < 64; k += 4) b = fma(Ms[k + row * 65], w[k], b);
+            b += __shfl_xor_sync(0xFFFFFFFFu, b, 1);
+            b += __shfl_xor_sync(0xFFFFFFFFu, b, 2);
+            double t = (q == 0) ? b * b : 0.0;
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+            if (lane == 0) red[warp] = t;
             __syncthreads();
             double ss = 0.0;
-            for (int k = 0; k < n; ++k) ss = fma(v[k], v[k], ss);  // every thread, same order
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ss += red[k];  // every thread, same order
             nrm = sqrt(sqrt(ss));  // ||M^T M v||^(1/2) with ||v|| = 1 before: an estimate of ||M||_2
             const double inv = (ss > 0.0) ? 1.0 / sqrt(ss) : 0.0;
-            __syncthreads();
-            v[i] *= inv;
+            if (q == 0) v[row] = b * inv;
             __syncthreads();
         }
         est[which] = nrm;
     }
-    if (i == 0) {
+    if (tid == 0) {
         const double c = est[0] * est[1];
         *sel = (c > 0.0 && c <= kExplicitCond && !rxr_nonfinite(c)) ? 1 : 0;
     }
@@ -2535,7 +2566,7 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
     if (p.n > 64) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
     k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
-    k_cond_select<<<1, 64, 0, st>>>(R, T, (int)p.n, sel, p.status);
+    k_cond_select<<<1, 256, 0, st>>>(R, T, (int)p.n, sel, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int n = (int)p.n;
     CUtensorMap mx;
@@ -2720,7 +2751,7 @@ int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, c
     const int64_t spc = cdiv64(subs_total, gx);
     gx = cdiv64(subs_total, spc);
     if (gx > p.sk_gx) return RXR_ERR_NOMEM;  // partial buffer sized by the FP64 plan
-    k_sketch_split<<<dim3((unsigned)gx, (unsigned)gy), 256, kSpSmem2, st>>>(A, lda, p.m, (int)p.n, (int)p.s, seed, cx,
+    k_sketch_split<<<dim3((unsigned)gx, (unsigned)gy), 512, kSpSmem2, st>>>(A, lda, p.m, (int)p.n, (int)p.s, seed, cx,
                                                                           subs_total, spc, p.Ypart, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t sn = p.s * p.n;
