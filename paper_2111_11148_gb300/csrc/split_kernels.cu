@@ -2090,11 +2090,10 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int col0, do
 // cut into seven digits relative to 2^(e_j + 1), e_j its largest exponent over
 // all rows (from k_colexp), so the scale of every product is fixed.  Operand
 // tiles of 64 rows alternate between two buffers: the Omega' pieces and A
-// digits of one are written while the tensor core reads the other (A's next
-// rows are already in registers).  Sixteen warps (at most 128 registers a
-// thread) share the Gaussian generation, the digits and the drains, so that
-// four warps per scheduler hide the latency of the generator's dependent
-// chains.  Every 512 rows the seven tensor-memory
+// digits of one are written while the tensor core reads the other.  Sixteen warps (at most 128 registers a
+// thread) in two roles that run side by side: warps 0-7 generate and quantise
+// Omega' (the generator's long dependent chains), warps 8-15 cut A into
+// digits and issue the MMAs; all sixteen drain the window sums.  Every 512 rows the seven tensor-memory
 // groups (each an exact integer below 2^24: at most two pairs of products
 // below 2^14 per row) are combined in FP32 pairs and added in FP64; the fixed
 // scale 2^(e_j - 1033) is applied once at the end.
@@ -2137,11 +2136,13 @@ __global__ void __launch_bounds__(512, 1)
     constexpr uint32_t idesc = idesc_f16(kSpM, kSpN);
     const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 1024);
 
-    // roles: A digits -> column j, rows 8 rq .. + 7 of each 64-row tile;
-    // Omega' -> sketch rows 4 kq .. + 3, data rows 4 warp .. + 3
-    const int j = tid >> 3, rq = tid & 7;
+    // roles: warps 0-7 Omega' -> sketch rows 4 kq .. + 3, data rows 8 warp .. + 7;
+    // warps 8-15 A digits -> column j, rows 16 rq .. + 15 of each 64-row tile
+    const bool gauss = warp < 8;
+    const int dt = tid - 256;
+    const int j = gauss ? 0 : dt >> 2, rq = dt & 3;
     const int kq = lane;
-    const bool has_col = j < nw;
+    const bool has_col = !gauss && j < nw;
     const int ej = cex[j];
     const double *acol = A + (int64_t)(c0 + j) * lda;
     // epilogue: tensor-memory lane quarter (sketch rows), 16-column quarter
@@ -2152,12 +2153,6 @@ __global__ void __launch_bounds__(512, 1)
 
     const int64_t b_begin = blockIdx.x * subs_per_cta;
     const int64_t b_end = min(subs_total, b_begin + subs_per_cta);
-    double vn[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t r = b_begin * kSpSub + 8 * rq + i;
-        vn[i] = (has_col && b_begin < b_end && r < m) ? acol[r] : 0.0;
-    }
     // Waits are per thread and bounded; one that gives up records a timeout
     // and the loop runs to its end without publishing the sums.
     bool ok = true;
@@ -2168,29 +2163,27 @@ __global__ void __launch_bounds__(512, 1)
         unsigned char *bop = smem + buf * kSpBuf;  // A digits: kSpDigits planes, N x K
         unsigned char *aop = bop + kSpDigits * kSpB;  // Omega' pieces: kSpZ planes, M x K
         const int64_t r0 = b * kSpSub;
-        double v[8];
+        // A's rows for the digit warps (their phase is shorter than the
+        // generator's, so the load latency stays off the critical path)
+        double v[16];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = vn[i];
-        if (b + 1 < b_end) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t r = (b + 1) * kSpSub + 8 * rq + i;
-                vn[i] = (has_col && r < m) ? acol[r] : 0.0;
-            }
+        for (int i = 0; i < 16; ++i) {
+            const int64_t r = r0 + 16 * rq + i;
+            v[i] = (has_col && r < m) ? acol[r] : 0.0;
         }
         if (it >= 2) ok &= mbar_wait_bounded(&mma_bar[buf], ((it - 2) >> 1) & 1, st);
         // Omega' on the 2^-12 grid: 4096 z' = 256 zeta0 + zeta1 (round to nearest
         // even by the 1.5 * 2^23 addition, as rint), both pieces exact in FP16
-        if (4 * kq < sw) {
-            float z[4][4];
+        if (gauss && 4 * kq < sw) {
+            float z[8][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                rxr_normal4(seed, (uint64_t)(r0 + 4 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
+            for (int i = 0; i < 8; ++i)
+                rxr_normal4(seed, (uint64_t)(r0 + 8 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
 #pragma unroll
             for (int t4 = 0; t4 < 4; ++t4) {
-                uint32_t p0[4], p1[4];  // zeta + 128, in [0, 256]
+                uint32_t p0[8], p1[8];  // zeta + 128, in [0, 256]
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 8; ++i) {
                     const int q = (int)(__float_as_uint(__fadd_rn(__fmul_rn(z[i][t4], 4096.0f), 12582912.0f)) & 0x7FFFFFu) -
                                   0x400000;
                     const int z0 = (q + 128) >> 8;
@@ -2200,20 +2193,24 @@ __global__ void __launch_bounds__(512, 1)
                 }
                 const int r = 4 * kq + t4;
                 if (r < sw) {
-                    *reinterpret_cast<uint2 *>(aop + kmaj_off(r, 4 * warp)) = pack_int4x_f16(p0);
-                    *reinterpret_cast<uint2 *>(aop + kSpA + kmaj_off(r, 4 * warp)) = pack_int4x_f16(p1);
+                    *reinterpret_cast<uint4 *>(aop + kmaj_off(r, 8 * warp)) = pack_int8x_f16(p0);
+                    *reinterpret_cast<uint4 *>(aop + kSpA + kmaj_off(r, 8 * warp)) = pack_int8x_f16(p1);
                 }
             }
         }
         // digits of A: element (row k, column j) -> B tile (j, k)
         if (has_col) {
-            unsigned long long U[8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[r]), ej);
+            for (int g8 = 0; g8 < 2; ++g8) {
+                unsigned long long U[8];
 #pragma unroll
-            for (int q = 0; q < kSpDigits; ++q) {
-                const uint4 w = pack_plane_f16(U, q);
-                *reinterpret_cast<uint4 *>(bop + q * kSpB + kmaj_off(j, 8 * rq)) = w;
+                for (int r = 0; r < 8; ++r)
+                    U[r] = digits_offset((unsigned long long)__double_as_longlong(v[8 * g8 + r]), ej);
+#pragma unroll
+                for (int q = 0; q < kSpDigits; ++q) {
+                    const uint4 w = pack_plane_f16(U, q);
+                    *reinterpret_cast<uint4 *>(bop + q * kSpB + kmaj_off(j, 16 * rq + 8 * g8)) = w;
+                }
             }
         }
         const bool first_of_window = (it % kWinSubs) == 0;
@@ -2225,7 +2222,7 @@ __global__ void __launch_bounds__(512, 1)
         fence_proxy_async_shared();
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 256) {
             tc_fence_after();
             const uint64_t db = desc0 + (uint64_t)((buf * kSpBuf) >> 4);
             const uint64_t da = db + (uint64_t)((kSpDigits * kSpB) >> 4);
