@@ -58,6 +58,9 @@ using namespace rxr;
 // passes (+ fused Gram), 3 last apply, 4 tensor-core first Gram, 5 tensor-core
 // later Gram, 6 XR factorisation of the sketch
 constexpr int kTimers = 7;
+// row chunks of the _host entry point's copies (overlapped with the sketch
+// and with the last apply)
+constexpr int kIoChunks = kSketchChunks;
 
 struct rxr_ctx {
     int device = 0;
@@ -78,6 +81,9 @@ struct rxr_ctx {
     size_t eval_bytes = 0;
     void *h_stage = nullptr;  // pinned host staging of batched job tables
     size_t h_stage_bytes = 0;
+    // the _host entry point's copy stream and its chunk events
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t io_ev[2 * kIoChunks + 2] = {};
 };
 
 namespace {
@@ -206,6 +212,12 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     int64_t gx = balanced_chunks(p.sk_gy, 2 * (int64_t)sms, std::min(p.sk_panels, std::max<int64_t>(1, max_chunks)));
     p.sk_ppc = cdiv(p.sk_panels, gx);
     p.sk_gx = (int)cdiv(p.sk_panels, p.sk_ppc);
+    p.yslots = p.sk_gx;
+    if (prec == RXR_SPLIT_BF16) {
+        int64_t sgx, spc;
+        split_sketch_grid(p, &sgx, &spc);
+        p.yslots = std::max<int64_t>(p.yslots, sgx);
+    }
 
     p.wide = n > kNarrowN;
     if (p.wide) {
@@ -246,7 +258,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
         return o;
     };
     const size_t o_status = take(sizeof(RxrStatus));
-    const size_t o_ypart = take((size_t)p.sk_gx * s * n * 8);
+    const size_t o_ypart = take((size_t)p.yslots * s * n * 8);
     const size_t o_y = take((size_t)s * n * 8);
     const size_t o_w = take((size_t)s * n * 8);
     const size_t o_gpart = take((size_t)std::max(p.sg_gx, p.gt_gx) * n * n * 8);
@@ -414,7 +426,8 @@ int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, c
                                                                      p.status);
     if (launch_ok()) return RXR_ERR_CUDA;
     const int64_t sn = p.s * p.n;
-    k_reduce_parts<<<(int)cdiv(sn, 256), 256, 0, st>>>(p.Ypart, p.sk_gx, sn, (int)p.s, (int)p.n,
+    const int64_t threads = (p.sk_gx >= kReduceWarpParts) ? 32 * sn : sn;
+    k_reduce_parts<<<(int)cdiv(threads, 256), 256, 0, st>>>(p.Ypart, p.sk_gx, sn, (int)p.s, (int)p.n,
                                                        1.0 / sqrt((double)p.s), 0, p.Y, p.s, p.status);
     return launch_ok();
 }
@@ -467,18 +480,63 @@ struct Timer {
 };
 
 // The whole factorisation, stream-ordered, no host synchronisation.
+// Host buffers of the _host entry point: A arrives in row chunks on the copy
+// stream while the split sketch works on the chunks already in, and Q leaves
+// in row chunks as the split path's last apply finishes them.  Other paths
+// copy whole matrices before and after.
+struct HostIO {
+    const double *hA;
+    int64_t lda;
+    double *hQ;
+    int64_t ldq;
+    cudaStream_t cs;
+    cudaEvent_t *ev;  // 2 kIoChunks + 2
+};
+
 int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, int variant, uint64_t seed, int passes,
-                   double *Q, int64_t ldq, double *R, int64_t ldr, cudaStream_t st, bool timed)
+                   double *Q, int64_t ldq, double *R, int64_t ldr, cudaStream_t st, bool timed,
+                   const HostIO *io = nullptr)
 {
     rxr_handle th = timed ? h : nullptr;
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
     const int n = (int)p.n;
+    const bool chunk_in = io && p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE;
+    const bool chunk_out = io && p.prec == RXR_SPLIT_BF16 && passes > 1 && p.n <= 64;
+    if (io) {
+        // the copy stream starts after this stream's earlier work
+        if (cudaEventRecord(io->ev[2 * kIoChunks], st) != cudaSuccess ||
+            cudaStreamWaitEvent(io->cs, io->ev[2 * kIoChunks], 0) != cudaSuccess)
+            return RXR_ERR_CUDA;
+        if (!chunk_in && cudaMemcpy2DAsync(const_cast<double *>(A), lda * 8, io->hA, io->lda * 8, p.m * 8, p.n,
+                                           cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return RXR_ERR_CUDA;
+    }
     // steps 1-2: sketch and its R factor (R_s = I without preconditioner)
     if (variant == RXR_NONE) {
         k_identity<<<(int)cdiv(p.n * p.n, 256), 256, 0, st>>>(p.Rs, n);
         if (launch_ok()) return RXR_ERR_CUDA;
     } else {
-        {
+        if (chunk_in) {
+            // chunk c of A's rows lands on the copy stream, then its CTAs of
+            // the sketch run (the same partition and partial sums as one launch)
+            Timer t(th, 0, st);
+            Plan &pm = const_cast<Plan &>(p);
+            int64_t gx, spc;
+            split_sketch_grid(p, &gx, &spc);
+            const int K = (int)std::min<int64_t>(kIoChunks, gx);
+            for (int c = 0; c < K; ++c) {
+                const int64_t cb = gx * c / K, ce = gx * (c + 1) / K;
+                const int64_t rb = std::min<int64_t>(p.m, cb * spc * 64), re = std::min<int64_t>(p.m, ce * spc * 64);
+                if (re > rb && cudaMemcpy2DAsync(const_cast<double *>(A) + rb, lda * 8, io->hA + rb, io->lda * 8,
+                                                 (re - rb) * 8, p.n, cudaMemcpyHostToDevice, io->cs) != cudaSuccess)
+                    return RXR_ERR_CUDA;
+                if (cudaEventRecord(io->ev[c], io->cs) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, io->ev[c], 0) != cudaSuccess)
+                    return RXR_ERR_CUDA;
+                if (int e = split_sketch_part_enqueue(pm, A, lda, seed, cb, ce, st)) return e;
+            }
+            if (int e = split_sketch_reduce_enqueue(pm, st)) return e;
+        } else {
             Timer t(th, 0, st);
             if (int e = enqueue_sketch(p, A, lda, seed, st)) return e;
         }
@@ -551,7 +609,25 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             // the last pass's R_P is within rounding of I: Q = X + X (R_P^{-1} - I)
             // with the small correction in FP32, or (should R_P^{-1} - I exceed
             // 2^-38) the explicit inverse on the tensor cores at FP64 grade
-            if (int e = ozaki_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
+            Plan &pm = const_cast<Plan &>(p);
+            if (int e = ozaki_apply_prepare(pm, p.Rp, st)) return e;
+            if (chunk_out) {
+                // chunk c of Q leaves on the copy stream as soon as it is final
+                const int64_t tiles = cdiv(p.m, 128);
+                for (int c = 0; c < kIoChunks; ++c) {
+                    const int64_t rb = std::min<int64_t>(p.m, tiles * c / kIoChunks * 128);
+                    const int64_t re = std::min<int64_t>(p.m, tiles * (c + 1) / kIoChunks * 128);
+                    if (re <= rb) continue;
+                    if (int e = ozaki_apply_rows(pm, Q, ldq, rb, re - rb, st)) return e;
+                    if (cudaEventRecord(io->ev[kIoChunks + c], st) != cudaSuccess ||
+                        cudaStreamWaitEvent(io->cs, io->ev[kIoChunks + c], 0) != cudaSuccess ||
+                        cudaMemcpy2DAsync(io->hQ + rb, io->ldq * 8, Q + rb, ldq * 8, (re - rb) * 8, p.n,
+                                          cudaMemcpyDeviceToHost, io->cs) != cudaSuccess)
+                        return RXR_ERR_CUDA;
+                }
+            } else if (int e = ozaki_apply_rows(pm, Q, ldq, 0, p.m, st)) {
+                return e;
+            }
         } else if (p.prec == RXR_SPLIT_BF16) {
             if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st)) return e;
         } else if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) {
@@ -561,6 +637,15 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     if (R) {
         k_copy_upper<<<(int)cdiv(p.n * p.n, 256), 256, 0, st>>>(p.Racc, n, R, ldr, p.status);
         if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    if (io) {
+        if (!chunk_out && cudaMemcpy2DAsync(io->hQ, io->ldq * 8, Q, ldq * 8, p.m * 8, p.n, cudaMemcpyDeviceToHost,
+                                            st) != cudaSuccess)
+            return RXR_ERR_CUDA;
+        // this stream waits for every copy of the copy stream
+        if (cudaEventRecord(io->ev[2 * kIoChunks + 1], io->cs) != cudaSuccess ||
+            cudaStreamWaitEvent(st, io->ev[2 * kIoChunks + 1], 0) != cudaSuccess)
+            return RXR_ERR_CUDA;
     }
     return 0;
 }
@@ -664,6 +749,9 @@ int rxr_destroy(rxr_handle h)
     for (int k = 0; k < kTimers; ++k)
         for (int j = 0; j < 2; ++j)
             if (h->ev[k][j]) cudaEventDestroy(h->ev[k][j]);
+    for (cudaEvent_t e : h->io_ev)
+        if (e) cudaEventDestroy(e);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
     return 0;
 }
@@ -752,20 +840,33 @@ int rxr_cholqr_host(rxr_handle h, const double *hA, int64_t m, int64_t n, int64_
     if (grow((void **)&h->dA, &h->dA_bytes, mat) || grow((void **)&h->dQ, &h->dQ_bytes, mat) ||
         grow((void **)&h->dR, &h->dR_bytes, (size_t)n * n * 8))
         return RXR_ERR_NOMEM;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpy2DAsync(h->dA, ldd * 8, hA, lda * 8, m * 8, n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return RXR_ERR_CUDA;
+    if (h->copy_stream == nullptr) {  // first call: the copy stream and its events
+        for (cudaEvent_t &e : h->io_ev)
+            if (e == nullptr && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                (void)cudaGetLastError();
+                e = nullptr;
+                return RXR_ERR_CUDA;
+            }
+        if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            h->copy_stream = nullptr;
+            return RXR_ERR_CUDA;
+        }
     }
+    cudaStream_t st = (cudaStream_t)stream;
     Plan p;
     make_plan(p, m, n, s, prec, h->sms);
     if (int e = ensure_ws(h, p.bytes)) return e;
     bind_plan(p, h->ws);
+    const HostIO io{hA, lda, hQ, ldq, h->copy_stream, h->io_ev};
     int e = enqueue_cholqr(h, p, h->dA, ldd, variant, seed, passes, h->dQ, ldd, hR ? h->dR : nullptr, n, st,
-                           h->timing);
-    if (e) return e;
-    if (cudaMemcpy2DAsync(hQ, ldq * 8, h->dQ, ldd * 8, m * 8, n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        (hR && cudaMemcpy2DAsync(hR, ldr * 8, h->dR, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st) != cudaSuccess)) {
+                           h->timing, &io);
+    if (e) {
+        (void)cudaGetLastError();
+        cudaStreamSynchronize(h->copy_stream);
+        return e;
+    }
+    if (hR && cudaMemcpy2DAsync(hR, ldr * 8, h->dR, n * 8, n * 8, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         (void)cudaGetLastError();
         return RXR_ERR_CUDA;
     }

@@ -35,6 +35,15 @@ __device__ __forceinline__ bool rxr_failed(const RxrStatus *st)
     return *((volatile const int *)&st->code) != 0;
 }
 
+// The same check taken once for the whole CTA (every thread must call it):
+// another CTA may set the status word at any moment, and threads that read it
+// at different times and decided differently would leave the others waiting
+// at the CTA's next barrier.
+__device__ __forceinline__ bool rxr_failed_block(const RxrStatus *st)
+{
+    return __syncthreads_or(threadIdx.x == 0 && rxr_failed(st)) != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of
 //   (c0,c1,c2,c3) -> (hi(Mb*c2)^c1^k0, lo(Mb*c2), hi(Ma*c0)^c3^k1, lo(Ma*c0))
@@ -342,6 +351,7 @@ struct Plan {
     // sketch
     int sk_gx, sk_gy;
     int64_t sk_panels, sk_ppc;
+    int64_t yslots;  // partial sums the sketch buffer holds (>= sk_gx; the split sketch may use more)
     // substitution + Gram
     int sg_gx;
     int64_t sg_panels, sg_ppc;
@@ -361,15 +371,28 @@ struct Plan {
 }  // namespace rxr
 
 namespace rxr {
+// Row chunks of the split sketch's CTA partition: the sketch of a matrix that
+// arrives from the host in this many row chunks starts on each chunk as it
+// lands, with the partition (and so the result) of a single launch.
+constexpr int kSketchChunks = 8;
+// From this many partial sums on, k_reduce_parts gives each output a warp
+// (launch it with 32 threads per output).
+constexpr int kReduceWarpParts = 256;
 int64_t balanced_chunks(int64_t gy, int64_t slots, int64_t max_gx);
 // split-precision contractions (split_kernels.cu)
 int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st);
+void split_sketch_grid(const Plan &p, int64_t *gx, int64_t *spc);
+int split_sketch_part_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, int64_t cta_begin, int64_t cta_end,
+                              cudaStream_t st);
+int split_sketch_reduce_enqueue(Plan &p, cudaStream_t st);
 int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st);
 // colexp_ready: the column exponents of X (n <= 64) are already in
 // split_colexp(p), written by the substitution that produced X
 int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, bool colexp_ready = false);
 int *split_colexp(const Plan &p);
 int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);
+int ozaki_apply_prepare(Plan &p, const double *R, cudaStream_t st);
+int ozaki_apply_rows(Plan &p, double *X, int64_t ldx, int64_t r0, int64_t rows, cudaStream_t st);
 int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
                           int64_t ldx, cudaStream_t st);
 int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,

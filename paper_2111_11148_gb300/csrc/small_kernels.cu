@@ -46,7 +46,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 __device__ __forceinline__ void xr_body(const double *__restrict__ Y, int s, int n, int64_t ldy, int variant,
                                         double *__restrict__ W, double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double red[33];
     __shared__ double sh_beta, sh_v0, sh_piv;
     __shared__ int sh_idx[32];
@@ -204,7 +204,7 @@ __device__ __forceinline__ void factor_body(const double *__restrict__ G, int n,
                                             double *__restrict__ Racc, double *__restrict__ C, int pass,
                                             int update_racc, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ int sh_bad;
     __shared__ double sh_rjj;
     const int tid = threadIdx.x;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kSmallThreads)
         factor_body(G, n, ldg, Rp, Racc, C, pass, update_racc, st);
         return;
     }
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ double fac_smem[];
     const int nn = n * n;
     double *Cs = fac_smem, *Rps = fac_smem + nn, *Ras = fac_smem + 2 * nn;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kSmallThreads)
     __syncthreads();
     factor_body(G, n, ldg, Rps, Ras, Cs, pass, update_racc, st);
     __syncthreads();
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         Rp[e] = Rps[e];
         if (update_racc) Racc[e] = Ras[e];
@@ -334,7 +334,7 @@ __global__ void k_finish_batched(const FinishJob *__restrict__ jobs)
 __global__ void k_copy_upper(const double *__restrict__ R, int n, double *__restrict__ out, int64_t ldo,
                              const RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % n), j = (int)(e / n);
@@ -537,7 +537,7 @@ __device__ __forceinline__ double qr_v(const double *W, int s, int kc, int i)  /
 __global__ void __launch_bounds__(kSmallThreads) k_qr_panel(double *__restrict__ W, int s, int n, int k0,
                                                             double *__restrict__ T, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double red[33];
     __shared__ double sh_tau[kQrB];
     __shared__ double sh_S[kQrB * kQrB];   // V^T V, (q, k) at k * kQrB + q
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_qr_panel(double *__restrict__
 __global__ void __launch_bounds__(256) k_qr_vtc(const double *__restrict__ W, int s, int n, int k0,
                                                 double *__restrict__ P, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double sv[kQrRows * kQrB];
     __shared__ double sc[kQrRows * kQrCols];
     const int bw = min(kQrB, n - k0), nc = n - k0 - bw;
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(256) k_qr_apply(double *__restrict__ W, int s,
                                                   const double *__restrict__ P, int nchunks,
                                                   const double *__restrict__ T, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double w1[kQrB * kQrCols], w2[kQrB * kQrCols];
     const int bw = min(kQrB, n - k0), nc = n - k0 - bw;
     const int c0 = blockIdx.x * kQrCols, i0 = k0 + blockIdx.y * kQrRows;
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(256) k_qr_apply(double *__restrict__ W, int s,
 __global__ void __launch_bounds__(kSmallThreads) k_xr_finish(const double *__restrict__ W, int s, int n,
                                                              double *__restrict__ Rs, int64_t ldrs, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ int sh_bad;
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -742,7 +742,7 @@ constexpr int kChB = 32;
 __global__ void __launch_bounds__(256) k_chol_init(const double *__restrict__ G, int n, int64_t ldg,
                                                    double *__restrict__ C, double *__restrict__ Rp, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % n), j = (int)(e / n);
         C[e] = (i <= j) ? G[i + j * ldg] : 0.0;
@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(256) k_chol_init(const double *__restrict__ G,
 __global__ void __launch_bounds__(256) k_chol_diag(double *__restrict__ C, double *__restrict__ Rp, int n, int k0,
                                                    int pass, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double cs[kChB * kChB], rs[kChB * kChB];
     __shared__ double sh_rjj;
     __shared__ int sh_bad;
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(double *__restrict__ C, doubl
 __global__ void __launch_bounds__(256) k_chol_panel(const double *__restrict__ C, double *__restrict__ Rp, int n,
                                                     int k0, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double rk[kChB * kChB];
     __shared__ double inv[kChB];
     const int b = min(kChB, n - k0), tid = threadIdx.x;
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(const double *__restrict__ C
 __global__ void __launch_bounds__(256) k_chol_syrk(double *__restrict__ C, const double *__restrict__ Rp, int n,
                                                    int k0, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double ri[kChB * kChB], rj[kChB * kChB];  // panel rows x tile columns
     const int b = min(kChB, n - k0), t0 = k0 + b;
     const int nt = (n - t0 + kChB - 1) / kChB;
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(256) k_chol_syrk(double *__restrict__ C, const
 __global__ void __launch_bounds__(256) k_trmm_upper(const double *__restrict__ Rp, const double *__restrict__ Racc,
                                                     double *__restrict__ out, int n, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % n), j = (int)(e / n);
         double acc = 0.0;

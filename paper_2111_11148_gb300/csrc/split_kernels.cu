@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256, 1)
     k_gram_split(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t win_total, int64_t win_per_cta,
                  double *__restrict__ Gpart, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mma_bar;
     __shared__ uint32_t tmem_base;
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(256, 1)
     k_gram_ozaki(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t win_total, int64_t win_per_cta,
                  double *__restrict__ Gpart, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *aop = smem;
     unsigned char *bsep = smem + kOzDigits * kOzTile;
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(256, 1)
                    int N, const double *B, int64_t ldb, double *C, int64_t ldc, int64_t m, int64_t tiles_total,
                    int64_t tiles_per_cta, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *aop = smem;
     unsigned char *bop = smem + kApDigits * kApATile;
@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(256)
     k_solve_block(const double *B, int64_t ldb, double *X, int64_t ldx, const double *__restrict__ R, int64_t ldr,
                   int c0, int b, int64_t m, int64_t tiles_total, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *xs = reinterpret_cast<double *>(smem_raw);  // [b][kSbRows]
     double *rb = xs + (int64_t)b * kSbRows;              // packed upper block of R
@@ -971,7 +971,7 @@ __global__ void __launch_bounds__(256, 1)
                   const double *__restrict__ R, int64_t ldr, int64_t tiles_total, int *colexp_out,
                   const int *__restrict__ sel, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     if (sel != nullptr && *sel != 0) return;  // the explicit-inverse product was chosen instead
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nb = fu_blocks(n);
@@ -1301,7 +1301,7 @@ __host__ __device__ inline size_t f2_smem_bytes(int n)
 __global__ void __launch_bounds__(256) k_rprep128(const double *__restrict__ R, int64_t ldr, int n,
                                                   unsigned char *__restrict__ rec, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     const int c = blockIdx.x, tid = threadIdx.x;
     const int Np = fu_npad(n, c), Nc = n - kFuBw * (c + 1);
     unsigned char *r = rec + f2_rec_off(n, c);
@@ -1383,7 +1383,7 @@ __global__ void __launch_bounds__(256, 1)
                      int use_tma, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
                      const unsigned char *__restrict__ rec, int64_t tiles_total, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nb = fu_blocks(n);
     const size_t tile_bytes = (size_t)kFuM * n * 8;
@@ -1604,7 +1604,7 @@ constexpr size_t kG6Smem = 2 * (size_t)kG6Buf + 2 * (size_t)kG6Stage;  // 192 KB
 // colexp[0 .. n) (zeroed by the caller).  grid.y = column.
 __global__ void k_colexp(const double *__restrict__ X, int64_t ldx, int64_t m, int *colexp, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     const int col = blockIdx.y;
     unsigned e = 0;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
@@ -1624,7 +1624,7 @@ __global__ void __launch_bounds__(kG6Producers, 1)
                 int64_t m, int n, const int *__restrict__ colexp_g, int64_t bufs_total, int64_t bufs_per_cta,
                 double *__restrict__ Gpart, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t ready[2];  // producers -> MMA thread: digits of a buffer written (256 arrivals)
     __shared__ __align__(8) uint64_t done[2];   // MMA thread -> producers: a buffer's MMAs completed (commit)
@@ -1833,7 +1833,7 @@ __global__ void __launch_bounds__(256, 1)
                  const double *__restrict__ T, int64_t ldt, int64_t tiles_total, const int *__restrict__ sel,
                  int want, int *colexp_out, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     if (sel != nullptr && *sel != want) return;  // the other form was chosen
     extern __shared__ __align__(1024) unsigned char smem[];
     const size_t tile_bytes = (size_t)kAqM * n * 8;
@@ -2027,7 +2027,7 @@ __global__ void __launch_bounds__(256, 1)
 __global__ void __launch_bounds__(32) k_tri_inverse64(const double *__restrict__ R, int n, int64_t ldr,
                                                        double *__restrict__ T, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double rs[64 * 64];  // R[i][k] at k * 64 + i
     const int c = blockIdx.x, lane = threadIdx.x;
     for (int k = 0; k <= c; ++k) {
@@ -2086,9 +2086,12 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int col0, do
 
 // ---------------------------------------------------------------------------
 // Split sketch Y' = Omega' A (see the file header).  grid.y = (s-tile,
-// n-tile) output tiles of 128 x 64; grid.x = row chunks.  Column j of A is
+// n-tile) output tiles of 128 x 64; grid.x = row chunks (CTA cta0 + blockIdx.x
+// of the whole sketch: a caller may launch the chunks of a matrix that is
+// still arriving one group at a time, with the same result).  Column j of A is
 // cut into seven digits relative to 2^(e_j + 1), e_j its largest exponent over
-// all rows (from k_colexp), so the scale of every product is fixed.  Operand
+// the CTA's rows (found in a first pass over them), so the scale of every
+// product in the CTA is fixed.  Operand
 // tiles of 64 rows alternate between two buffers: the Omega' pieces and A
 // digits of one are written while the tensor core reads the other.  Sixteen warps (at most 128 registers a
 // thread) in two roles that run side by side: warps 0-7 generate and quantise
@@ -2102,11 +2105,10 @@ constexpr int kSpBuf = kSpDigits * kSpB + kSpZ * kSpA;  // 88 KB per buffer
 constexpr size_t kSpSmem2 = 2 * (size_t)kSpBuf;
 
 __global__ void __launch_bounds__(512, 1)
-    k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed,
-                   const int *__restrict__ colexp_g, int64_t subs_total, int64_t subs_per_cta,
-                   double *__restrict__ Ypart, RxrStatus *st)
+    k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed, int64_t cta0,
+                   int64_t subs_total, int64_t subs_per_cta, double *__restrict__ Ypart, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mma_bar[2];
     __shared__ uint32_t tmem_base;
@@ -2118,10 +2120,32 @@ __global__ void __launch_bounds__(512, 1)
     const int s0 = si * kSpM, c0 = ni * kSpN;
     const int sw = min(kSpM, s - s0), nw = min(kSpN, n - c0);
 
+    const int64_t cta = cta0 + blockIdx.x;
+    const int64_t b_begin = cta * subs_per_cta;
+    const int64_t b_end = min(subs_total, b_begin + subs_per_cta);
     for (int e = tid; e < (int)(kSpSmem2 / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
-    if (tid < kSpN) {
-        cex[tid] = (tid < nw) ? colexp_g[c0 + tid] : 0;
-        if (tid < nw && cex[tid] == 0x7FF) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+    // largest exponent of each column over this CTA's rows: warp w scans
+    // columns w, w + 16, ... (four at a time, coalesced down the rows)
+    {
+        const int64_t ra = b_begin * kSpSub, rb = min(m, b_end * kSpSub);
+        for (int cl = warp; cl < kSpN; cl += 16) {
+            unsigned ex = 0;
+            if (cl < nw) {
+                const double *col = A + (int64_t)(c0 + cl) * lda;
+                int64_t r = ra + lane;
+                for (; r + 96 < rb; r += 128) {
+                    const double a0 = col[r], a1 = col[r + 32], a2 = col[r + 64], a3 = col[r + 96];
+                    ex = max(ex, max(max(((unsigned)__double2hiint(a0) >> 20) & 0x7FFu, ((unsigned)__double2hiint(a1) >> 20) & 0x7FFu),
+                                     max(((unsigned)__double2hiint(a2) >> 20) & 0x7FFu, ((unsigned)__double2hiint(a3) >> 20) & 0x7FFu)));
+                }
+                for (; r < rb; r += 32) ex = max(ex, ((unsigned)__double2hiint(col[r]) >> 20) & 0x7FFu);
+            }
+            ex = __reduce_max_sync(0xFFFFFFFFu, ex);
+            if (lane == 0) {
+                cex[cl] = (int)ex;
+                if (ex == 0x7FFu) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+            }
+        }
     }
     if (tid == 0) {
         mbar_init(&mma_bar[0], 1);
@@ -2151,8 +2175,6 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
     for (int t = 0; t < 16; ++t) acc[t] = 0.0;
 
-    const int64_t b_begin = blockIdx.x * subs_per_cta;
-    const int64_t b_end = min(subs_total, b_begin + subs_per_cta);
     // Waits are per thread and bounded; one that gives up records a timeout
     // and the loop runs to its end without publishing the sums.
     bool ok = true;
@@ -2246,7 +2268,7 @@ __global__ void __launch_bounds__(512, 1)
     }
     ok = __syncthreads_and(ok) != 0;
     if (ok) {
-        double *out = Ypart + (int64_t)blockIdx.x * s * n;
+        double *out = Ypart + cta * s * n;
         const int my_row = 32 * q4 + lane;
         const int r = s0 + my_row;
 #pragma unroll
@@ -2338,7 +2360,7 @@ constexpr double kDeltaMax = 0x1p-38;
 __global__ void __launch_bounds__(256) k_delta_select(const double *__restrict__ T, int n, float *__restrict__ Ef,
                                                       int *sel, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double red[8];
     const int tid = threadIdx.x;
     double mx = 0.0;
@@ -2405,7 +2427,7 @@ __global__ void __launch_bounds__(256, 3) k_apply_delta(double *X, int64_t ldx, 
                                                         const float *__restrict__ Ef, int64_t tiles_total,
                                                         const int *__restrict__ sel, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     if (*sel != 1) return;  // the FP64-grade product was chosen instead
     extern __shared__ __align__(16) float dsm_delta[];
     float *es = dsm_delta;                                                         // n x 64
@@ -2502,7 +2524,7 @@ constexpr double kExplicitCond = 16.0;
 __global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ R, const double *__restrict__ T, int n,
                                                      int *sel, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     __shared__ double Ms[64 * 65];  // the matrix, column-major with a padded stride (zero below the diagonal)
     __shared__ double v[64], w[64], red[8];
     const int tid = threadIdx.x, row = tid >> 2, q = tid & 3, lane = tid & 31, warp = tid >> 5;
@@ -2580,24 +2602,36 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
 // (R within rounding of I) the FP32 correction Q = X + X (T - I), else the
 // FP64-grade tensor-core product; both launched, the one not selected returns
 // at once.  T lives in the XR scratch W (s x n doubles >= n^2).
-int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
+int ozaki_apply_prepare(Plan &p, const double *R, cudaStream_t st)
 {
     if (p.n > 64) return RXR_ERR_UNSUPPORTED;
-    double *T = p.W;
-    float *Ef = split_delta(p);
-    int *sel = split_select_flag(p) + 1;
-    k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
-    k_delta_select<<<1, 256, 0, st>>>(T, (int)p.n, Ef, sel, p.status);
-    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, p.W, p.status);
+    k_delta_select<<<1, 256, 0, st>>>(p.W, (int)p.n, split_delta(p), split_select_flag(p) + 1, p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+// Rows [r0, r0 + rows) of X (r0 a multiple of 128): both product forms, the
+// one not selected returns at once.
+int ozaki_apply_rows(Plan &p, double *X, int64_t ldx, int64_t r0, int64_t rows, cudaStream_t st)
+{
+    if (rows <= 0) return 0;
     const int n = (int)p.n;
-    const int64_t tiles = cdiv64(p.m, kAqM);
+    double *Xr = X + r0;
+    const int *sel = split_select_flag(p) + 1;
+    const int64_t tiles = cdiv64(rows, kAqM);
     CUtensorMap mx;
-    const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
-    delta_launch(p.sms, X, ldx, p.m, n, Ef, tiles, sel, mx, use_tma, p.status, st);
+    const int use_tma = encode_tile_map(&mx, Xr, rows, n, ldx, kAqM, n) ? 1 : 0;
+    delta_launch(p.sms, Xr, ldx, rows, n, split_delta(p), tiles, sel, mx, use_tma, p.status, st);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, 0, nullptr,
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, Xr, ldx, rows, n, p.W, p.n, tiles, sel, 0, nullptr,
                                                     p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+int ozaki_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
+{
+    if (int e = ozaki_apply_prepare(p, R, st)) return e;
+    return ozaki_apply_rows(p, X, ldx, 0, p.m, st);
 }
 
 // X = B R^{-1} by right-looking column blocks of width bw: FP64 substitution of
@@ -2734,27 +2768,55 @@ cudaError_t set_split_smem()
     return e;
 }
 
-int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st)
+// Row partition of the split sketch: gx CTAs of spc 64-row sub-tiles each.
+// Where every CTA still gets a 512-row window, kSketchChunks times the
+// balanced CTA count, so that each of kSketchChunks row chunks spreads over
+// the whole GPU.
+void split_sketch_grid(const Plan &p, int64_t *gx_out, int64_t *spc_out)
 {
-    // column exponents of A over all rows (the digit scale of each column)
-    int *cx = split_colexp(p);
-    if (cudaMemsetAsync(cx, 0, (size_t)p.n * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
-    const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
-    k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(A, lda, p.m, cx, p.status);
-    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t gy = cdiv64(p.s, kSpM) * cdiv64(p.n, kSpN);
     const int64_t subs_total = cdiv64(p.m, kSpSub);
     int64_t gx = balanced_chunks(gy, p.sms, cdiv64(p.m, kSpWin));
+    if (subs_total >= (int64_t)kSketchChunks * gx * (kSpWin / kSpSub)) gx *= kSketchChunks;
     const int64_t spc = cdiv64(subs_total, gx);
-    gx = cdiv64(subs_total, spc);
-    if (gx > p.sk_gx) return RXR_ERR_NOMEM;  // partial buffer sized by the FP64 plan
-    k_sketch_split<<<dim3((unsigned)gx, (unsigned)gy), 512, kSpSmem2, st>>>(A, lda, p.m, (int)p.n, (int)p.s, seed, cx,
-                                                                          subs_total, spc, p.Ypart, p.status);
-    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    *gx_out = cdiv64(subs_total, spc);
+    *spc_out = spc;
+}
+
+// CTAs [cta_begin, cta_end) of the split sketch (rows [cta_begin * spc * 64,
+// cta_end * spc * 64) of A): their partial sums only.
+int split_sketch_part_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, int64_t cta_begin, int64_t cta_end,
+                              cudaStream_t st)
+{
+    int64_t gx, spc;
+    split_sketch_grid(p, &gx, &spc);
+    if (gx > p.yslots) return RXR_ERR_NOMEM;  // partial buffer of the plan
+    cta_end = std::min(cta_end, gx);
+    if (cta_end <= cta_begin) return 0;
+    const int64_t gy = cdiv64(p.s, kSpM) * cdiv64(p.n, kSpN);
+    k_sketch_split<<<dim3((unsigned)(cta_end - cta_begin), (unsigned)gy), 512, kSpSmem2, st>>>(
+        A, lda, p.m, (int)p.n, (int)p.s, seed, cta_begin, cdiv64(p.m, kSpSub), spc, p.Ypart, p.status);
+    return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+// Y = Omega' A / sqrt(s) from the partial sums of all CTAs.
+int split_sketch_reduce_enqueue(Plan &p, cudaStream_t st)
+{
+    int64_t gx, spc;
+    split_sketch_grid(p, &gx, &spc);
     const int64_t sn = p.s * p.n;
-    k_reduce_parts<<<(int)cdiv64(sn, 256), 256, 0, st>>>(p.Ypart, (int)gx, sn, (int)p.s, (int)p.n,
+    const int64_t threads = (gx >= kReduceWarpParts) ? 32 * sn : sn;
+    k_reduce_parts<<<(int)cdiv64(threads, 256), 256, 0, st>>>(p.Ypart, (int)gx, sn, (int)p.s, (int)p.n,
                                                          1.0 / sqrt((double)p.s), 0, p.Y, p.s, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+int split_sketch_enqueue(Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st)
+{
+    int64_t gx, spc;
+    split_sketch_grid(p, &gx, &spc);
+    if (int e = split_sketch_part_enqueue(p, A, lda, seed, 0, gx, st)) return e;
+    return split_sketch_reduce_enqueue(p, st);
 }
 
 int split_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st)

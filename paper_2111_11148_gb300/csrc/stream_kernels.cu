@@ -106,7 +106,7 @@ __device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tm
                                             int64_t panels_per_cta, int box_cols, double *__restrict__ Ypart,
                                             RxrStatus *st, int bx, int by)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *ap = reinterpret_cast<double *>(smem_raw);  // [kSkNTile][kSkP]
     double *zp = ap + kSkNTile * kSkP;                   // [kSkP][kSkSTile]
@@ -235,8 +235,28 @@ __device__ __forceinline__ void reduce_body(const double *__restrict__ parts, in
                                             int cols, double scale, int symmetric, double *__restrict__ out,
                                             int64_t ldo, RxrStatus *st, int bx, int nbx)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     const int64_t total = (int64_t)rows * cols;
+    if (nparts >= kReduceWarpParts) {
+        // many partial sums: one warp per output, lane l adding partials l,
+        // l + 32, ..., then a fixed shuffle tree (lane 0's order is fixed)
+        const int lane = threadIdx.x & 31;
+        const int64_t w0 = (bx * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)nbx * blockDim.x) >> 5;
+        for (int64_t e = w0; e < total; e += nw) {
+            const int r = (int)(e % rows), c = (int)(e / rows);
+            if (symmetric && r > c) continue;
+            double v = 0.0;
+            for (int x = lane; x < nparts; x += 32) v += parts[x * stride + e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            if (lane == 0) {
+                v *= scale;
+                out[r + c * ldo] = v;
+                if (symmetric && r != c) out[c + r * ldo] = v;
+            }
+        }
+        return;
+    }
     for (int64_t e = bx * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)nbx * blockDim.x) {
         const int r = (int)(e % rows), c = (int)(e / rows);
         if (symmetric && r > c) continue;
@@ -273,7 +293,7 @@ __device__ __forceinline__ void subst_gram_body(const CUtensorMap *tmapB, int us
                                                 double *__restrict__ Gpart, int64_t panels_total,
                                                 int64_t panels_per_cta, int check_finite, RxrStatus *st, int bx)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int n4 = (n + 3) & ~3;
     double *xp = reinterpret_cast<double *>(smem_raw);  // [n4][kSgP]
@@ -534,7 +554,7 @@ __global__ void __launch_bounds__(RXR_THREADS, 1)
     k_subst_wide(const double *__restrict__ src, int64_t lds, int64_t m, int n, const double *__restrict__ R,
                  int64_t ldr, double *dst, int64_t ldd, int64_t panels_total, int64_t panels_per_cta, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *ut = reinterpret_cast<double *>(smem_raw);  // [kWB][kWP] block being solved
     double *xi = ut + kWB * kWP;                          // [kWB][kWP] an earlier block of X
@@ -607,7 +627,7 @@ __global__ void __launch_bounds__(RXR_THREADS)
     k_gram_tiles(const double *__restrict__ X, int64_t ldx, int64_t m, int n, int64_t panels_total,
                  int64_t panels_per_cta, double *__restrict__ Gpart, RxrStatus *st)
 {
-    if (rxr_failed(st)) return;
+    if (rxr_failed_block(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double *xa = reinterpret_cast<double *>(smem_raw);  // [kWB][kWP]
     double *xb = xa + kWB * kWP;

@@ -409,3 +409,15 @@ def test_wide_panel_precond_gram_parity(h):
     bound = 4 * n * U * (np.abs(Xo) @ np.abs(R) @ np.abs(np.linalg.inv(R))) + 1e-300
     assert np.all(np.abs(Xg - Xo) <= bound), np.max(np.abs(Xg - Xo) / bound)
     assert np.all(np.abs(Gg - o.gram(Xg)) <= 4 * (m + 2) * U * (np.abs(Xg).T @ np.abs(Xg)))
+
+
+@pytest.mark.parametrize("m,n", [((1 << 18) + 77, 40), (300000, 64), (5000, 100)])
+def test_host_entry_point_split_matches_device(h, m, n):
+    # the split path brings A in row chunks (the sketch's CTAs of a chunk start
+    # once it has landed) and sends Q out in row chunks after the last apply:
+    # the same partition and arithmetic as the device-buffer call, bit for bit
+    A = usv_matrix(m, n, 1e9, seed=n)
+    Qh, Rh = h.cholqr_host(A, variant="qr", seed=3, prec="split")
+    Q, R, code = h.cholqr(to_dev(A), variant="qr", seed=3, prec="split")
+    assert code == 0
+    assert np.array_equal(Qh, to_host(Q)) and np.array_equal(Rh, to_host(R))
