@@ -2091,15 +2091,15 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int col0, do
 // still arriving one group at a time, with the same result).  Column j of A is
 // cut into seven digits relative to 2^(e_j + 1), e_j its largest exponent over
 // the CTA's rows (found in a first pass over them), so the scale of every
-// product in the CTA is fixed.  Operand
-// tiles of 64 rows alternate between two buffers: the Omega' pieces and A
-// digits of one are written while the tensor core reads the other.  Sixteen warps (at most 128 registers a
-// thread) in two roles that run side by side: warps 0-7 generate and quantise
-// Omega' (the generator's long dependent chains), warps 8-15 cut A into
-// digits and issue the MMAs; all sixteen drain the window sums.  Every 512 rows the seven tensor-memory
-// groups (each an exact integer below 2^24: at most two pairs of products
-// below 2^14 per row) are combined in FP32 pairs and added in FP64; the fixed
-// scale 2^(e_j - 1033) is applied once at the end.
+// product in the CTA is fixed.  Operand tiles of 64 rows alternate between two
+// buffers: the Omega' pieces and A digits of one are written while the tensor
+// core reads the other.  Sixteen warps (at most 128 registers a thread) in two
+// roles that run side by side: warps 0-7 generate and quantise Omega' (the
+// generator's long dependent chains), warps 8-15 cut A into digits and issue
+// the MMAs; all sixteen drain the window sums.  Every 512 rows the seven
+// tensor-memory groups (each an exact integer below 2^24: at most two pairs of
+// products below 2^14 per row) are combined in FP32 pairs and added in FP64;
+// the fixed scale 2^(e_j - 1033) is applied once at the end.
 // ---------------------------------------------------------------------------
 constexpr int kSpBuf = kSpDigits * kSpB + kSpZ * kSpA;  // 88 KB per buffer
 constexpr size_t kSpSmem2 = 2 * (size_t)kSpBuf;
