@@ -26,6 +26,7 @@ _lib = None
 
 OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE = 0, 1, 2, 3
 VARIANT_LU, VARIANT_QR, VARIANT_NONE = 0, 1, 2
+SKETCH_ROWS = 16  # flag OR-ed into VARIANT_LU / VARIANT_QR: row extraction (Section 2.3)
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +57,8 @@ def _load():
             lib.rxo_omega_z.argtypes = [u64, i64, i64, i64, vp]
             lib.rxo_sketch.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
             lib.rxo_sketch_quantised.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
+            lib.rxo_row_indices.argtypes = [u64, i64, i64, vp]
+            lib.rxo_sketch_rows.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
             lib.rxo_geqr_r.argtypes = [vp, i64, i64, i64, vp, i64]
             lib.rxo_getrf_u.argtypes = [vp, i64, i64, i64, vp, i64, vp]
             lib.rxo_sign_normalise.argtypes = [vp, i64, i64]
@@ -148,6 +151,23 @@ def sketch_quantised(A: np.ndarray, s: int, seed: int) -> np.ndarray:
     m, n = A.shape
     Y = np.zeros((s, n), order="F")
     _load().rxo_sketch_quantised(_p(A), m, n, _ld(A), s, seed, _p(Y), s)
+    return Y
+
+
+def row_indices(seed: int, l: int, m: int) -> np.ndarray:
+    """Row extraction (Section 2.3, Theorem 3.2): l rows of m drawn independently
+    with probability 1/m each (with replacement), in draw order."""
+    idx = np.zeros(l, np.int64)
+    _load().rxo_row_indices(seed, l, m, _p(idx))
+    return idx
+
+
+def sketch_rows(A: np.ndarray, l: int, seed: int) -> np.ndarray:
+    """A_1 = PA: row k is row row_indices(seed, l, m)[k] of A."""
+    A = _f64(A)
+    m, n = A.shape
+    Y = np.zeros((l, n), order="F")
+    _load().rxo_sketch_rows(_p(A), m, n, _ld(A), l, seed, _p(Y), l)
     return Y
 
 

@@ -29,6 +29,7 @@
 #define RXO_VARIANT_LU 0
 #define RXO_VARIANT_QR 1
 #define RXO_VARIANT_NONE 2 /* no preconditioner: plain CholeskyQR repeated (Alg. 1/2) */
+#define RXO_SKETCH_ROWS 16 /* flag: row extraction (Section 2.3) instead of the Gaussian sketch */
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror & Shaw,        */
@@ -285,6 +286,37 @@ static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int6
 }
 
 /* ------------------------------------------------------------------------- */
+/* Row extraction (Section 2.3; Theorem 3.2's equal-probability case): the   */
+/* submatrix A_1 = PA takes l rows of A chosen independently, each row i     */
+/* with probability 1/m (with replacement), in draw order.  Draw k uses one  */
+/* Philox4x32-10 call, counter (k_lo, k_hi, 0, 3), key (seed_lo, seed_hi):   */
+/* u = out0 + 2^32 out1 is uniform on [0, 2^64), and the row is              */
+/* floor(u m / 2^64) (exact in 128-bit integers).                            */
+/* ------------------------------------------------------------------------- */
+void rxo_row_indices(uint64_t seed, int64_t l, int64_t m, int64_t *idx)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t k = 0; k < l; ++k) {
+        const uint32_t ctr[4] = {(uint32_t)k, (uint32_t)((uint64_t)k >> 32), 0u, 3u};
+        uint32_t out[4];
+        rxo_philox4x32_10(ctr, key, out);
+        const uint64_t u = (uint64_t)out[0] | ((uint64_t)out[1] << 32);
+        idx[k] = (int64_t)(((unsigned __int128)u * (unsigned __int128)(uint64_t)m) >> 64);
+    }
+}
+
+/* Y (l x n, leading dimension ldy): row k of Y is row idx[k] of A. */
+void rxo_sketch_rows(const double *A, int64_t m, int64_t n, int64_t lda, int64_t l, uint64_t seed, double *Y,
+                     int64_t ldy)
+{
+    int64_t *idx = (int64_t *)malloc((size_t)l * sizeof(int64_t));
+    rxo_row_indices(seed, l, m, idx);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t k = 0; k < l; ++k) Y[k + j * ldy] = A[idx[k] + j * lda];
+    free(idx);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Householder Q-less QR of an l x n matrix (l >= n): the R factor of the    */
 /* sketch, Algorithm 5 step 2.  Column k: x = W(k:l, k), alpha = ||x||,      */
 /* v = x + sign(x_0) alpha e_1 (sign(0) = +1), beta = 2 / v^T v,            */
@@ -486,7 +518,8 @@ static int all_finite(const double *A, int64_t m, int64_t n, int64_t lda)
 /*   3  X = A R_s^{-1}                                                        */
 /*   4  for p = 1..passes: G = X^T X, R_p = chol(G), X = X R_p^{-1}           */
 /*   5  Q = X, R = R_passes ... R_1 R_s                                       */
-/* Variant NONE takes R_s = I (plain CholeskyQR / CholeskyQR2).               */
+/* Variant NONE takes R_s = I (plain CholeskyQR / CholeskyQR2).  LU or QR    */
+/* with RXO_SKETCH_ROWS takes the sketch by row extraction.                  */
 /* Optional outputs (NULL to skip): Y (s x n, ld s), Rs (n x n), G1, R1      */
 /* (n x n, the first pass), G2, R2 (the second pass), info = breakdown pass  */
 /* and column.                                                                */
@@ -508,11 +541,16 @@ int rxo_rxr_cholqr(const double *A, int64_t m, int64_t n, int64_t lda, int varia
     double *Rp = (double *)calloc(nn, sizeof(double));
     int status = RXO_OK;
 
+    const int rows = (variant & RXO_SKETCH_ROWS) != 0;
+    variant &= ~RXO_SKETCH_ROWS;
     if (variant == RXO_VARIANT_NONE) {
         for (int64_t k = 0; k < n; ++k) Rs[k + k * n] = 1.0;
     } else {
         double *Y = (double *)malloc((size_t)(s * n) * sizeof(double));
-        rxo_sketch(A, m, n, lda, s, seed, Y, s);
+        if (rows)
+            rxo_sketch_rows(A, m, n, lda, s, seed, Y, s);
+        else
+            rxo_sketch(A, m, n, lda, s, seed, Y, s);
         if (Y_out) memcpy(Y_out, Y, (size_t)(s * n) * sizeof(double));
         if (variant == RXO_VARIANT_QR)
             rxo_geqr_r(Y, s, n, s, Rs, n);
