@@ -118,7 +118,9 @@ def oracle_rows(target_s: float = 15.0) -> int:
 def run_oracle_sample(A_sample: np.ndarray, variant: str):
     import oracle
 
-    ov = oracle.VARIANT_QR if variant == "qr" else oracle.VARIANT_LU
+    ov = oracle.VARIANT_QR if variant.startswith("qr") else oracle.VARIANT_LU
+    if variant.endswith("-rows"):
+        ov |= oracle.SKETCH_ROWS
     t0 = time.perf_counter()
     r = oracle.rxr_cholqr(A_sample, ov, S, seed=SEED, passes=PASSES)
     dt = time.perf_counter() - t0
@@ -325,24 +327,25 @@ def subst_fp64_flop_per_row(n, bw, sub_ops):
     return flop + n
 
 
-def launches_per_step(prec, n):
+def launches_per_step(prec, n, m, rows=False):
     """Kernels one CholeskyQR2 factorisation launches (P = 2, rQR, s = 2n)."""
     npanel = (n + 31) // 32
     xr = 1 if 2 * n * n <= 16384 else 3 * npanel - 1  # one-CTA XR, or blocked: panels, V^T C, updates, finish
+    sk = 1 if rows else 2  # row gather, or the Gaussian sketch and its reduction
     if prec == "fp64":
-        # sketch, reduce, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
-        return (10 if n <= 128 else 12) + xr
+        # sketch, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
+        return sk + (8 if n <= 128 else 10) + xr
     if n <= 64:
-        # colexp, sketch, reduce, XR, fused substitution, Gram, reduce, factor, middle pass (inverse,
-        # condition estimate, apply, fused substitution: the one not selected returns at once), Gram,
-        # reduce, factor, last pass (inverse, selection, FP32-correction apply, FP64-grade apply: the
-        # one not selected returns at once), copy
-        return 19 + xr
+        # sketch, XR, fused substitution, Gram, reduce, factor, middle pass (above 2^17 rows: inverse,
+        # condition estimate, apply, fused substitution, the one not selected returning at once; else the
+        # fused substitution), Gram, reduce, factor, last pass (inverse, selection, FP32-correction apply,
+        # FP64-grade apply: the one not selected returns at once), copy
+        return sk + xr + 4 + (4 if m >= 1 << 17 else 1) + 3 + 4 + 1
     if n <= 128:
-        # colexp, sketch, reduce, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
-        return 3 + xr + 3 * 2 + 2 * 2 + 2 + 1
+        # sketch, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
+        return sk + xr + 3 * 2 + 2 * 2 + 2 + 1 + (1 if rows else 0)
     blocked = 2 * ((n + 63) // 64) - 1  # diagonal solves + trailing updates
-    return 3 + xr + 3 * blocked + 2 * 2 + 2 + 1
+    return sk + xr + 3 * blocked + 2 * 2 + 2 + 1 + (1 if rows else 0)
 
 
 def roofline_entry(prec, stages, peak_fp64):
@@ -399,7 +402,7 @@ def e2e_leg(h, A_np, args, world):
 
 
 def _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu):
-    launches = launches_per_step(args.prec, N) if PASSES == 2 else None
+    launches = launches_per_step(args.prec, N, M, args.variant.endswith("-rows")) if PASSES == 2 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -435,6 +438,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--variant", default="qr", choices=["qr", "lu"])
+    ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "rows"],
+                    help="Gaussian sketch (the workload's) or row extraction (Section 2.3)")
     ap.add_argument("--prec", default="split", choices=["fp64", "split"],
                     help="the reported path; the other precision is timed alongside unless --no-compare")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision")
@@ -455,6 +460,9 @@ def main():
         KAPPA = float(args.kappa)
     WORKLOAD = (f"{'rQR' if args.variant == 'qr' else 'rLU'}-CholeskyQR2 m={'2^22' if M == 2**22 else M} n={N} "
                 f"s={S} kappa={KAPPA:g} {'FP64' if args.prec == 'fp64' else 'split BF16 sketch+Gram1, FP64 rest'}")
+    if args.sketch == "rows":
+        WORKLOAD += ", row-extraction sketch"
+        args.variant += "-rows"
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -48,8 +48,16 @@ extern "C" {
 
 /* XR factorisation of the sketch (Section 2.2).  RXR_NONE skips the sketch and
  * takes R_s = I, i.e. plain CholeskyQR repeated `passes` times (Algorithms 1
- * and 2), the paper's unpreconditioned comparator. */
+ * and 2), the paper's unpreconditioned comparator.  RXR_SKETCH_ROWS, OR-ed into
+ * RXR_LU or RXR_QR, takes the sketch by row extraction (Section 2.3, the
+ * paper's experimental choice; Theorem 3.2) instead of the Gaussian product:
+ * s rows of A drawn independently with probability 1/m each (with
+ * replacement), draw k from Philox4x32-10 at counter (k_lo, k_hi, 0, 3) and key
+ * (seed_lo, seed_hi), u = out0 + 2^32 out1, row floor(u m / 2^64).  Coherent A
+ * (large m max_i ||Q(i,:)||^2, e.g. A = [I; 0]) can leave that sketch
+ * rank-deficient: RXR_ERR_SKETCH_SINGULAR. */
 typedef enum { RXR_LU = 0, RXR_QR = 1, RXR_NONE = 2 } rxr_variant;
+#define RXR_SKETCH_ROWS 16
 
 /* Arithmetic of the two contractions that only shape the preconditioner (the
  * sketch Y = Omega A and the first pass's Gram X^T X).
@@ -145,7 +153,9 @@ RXR_API int rxr_cholqr_host(rxr_handle h, const double *hA, int64_t m, int64_t n
  * arrays of length `count`; the matrix pointers in them are device pointers.
  * variant, passes and prec are common; s_k, seed_k per problem.  Per-problem
  * status {code, pass, column, 0} goes to d_status[4k..4k+3] (device, caller
- * owned).  Blocking; returns the first non-zero problem status (or 0). */
+ * owned).  Blocking; returns the first non-zero problem status (or 0), or
+ * RXR_ERR_UNSUPPORTED without factorising any problem for RXR_SKETCH_ROWS
+ * (the batched stages take the Gaussian sketch only). */
 RXR_API int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
                        const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
                        double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
@@ -175,6 +185,13 @@ RXR_API int rxr_omega(uint64_t seed, int64_t s, int64_t row0, int64_t rows, floa
  * prec selects FP64 or the split BF16 tensor-core contraction. */
 RXR_API int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                double *Y, int64_t ldy, int prec, void *stream);
+
+/* Row-extraction sketch Y = P A (Section 2.3): row k of Y (s x n, ldy >= s)
+ * is row idx_k of A, the draws of RXR_SKETCH_ROWS.  A is a read-only device
+ * buffer (lda >= m).  Blocking; 0, RXR_ERR_NONFINITE (a drawn row holds NaN or
+ * Inf) or a negative argument error. */
+RXR_API int rxr_sketch_rows(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                            double *Y, int64_t ldy, void *stream);
 
 /* R_s (n x n upper, diag > 0, zeros below) = R factor of Y (s x n) by LU with
  * partial pivoting (RXR_LU) or Householder QR (RXR_QR), step 2.  Y is read

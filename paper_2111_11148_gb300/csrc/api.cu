@@ -28,6 +28,8 @@ cudaError_t set_wide_smem();
 __global__ void k_subst_wide(const double *, int64_t, int64_t, int, const double *, int64_t, double *, int64_t, int64_t,
                              int64_t, RxrStatus *);
 __global__ void k_gram_tiles(const double *, int64_t, int64_t, int, int64_t, int64_t, double *, RxrStatus *);
+__global__ void k_sketch_rows(const double *, int64_t, int64_t, int, int64_t, uint64_t, double *, int64_t, RxrStatus *);
+__global__ void k_check_finite(const double *, int64_t, int64_t, int, RxrStatus *);
 __global__ void k_sketch_fp64_batched(const SketchJob *, const int *, int);
 __global__ void k_reduce_parts_batched(const ReduceJob *, const int *, int);
 __global__ void k_subst_gram_batched(const SubstJob *, const int *, int, int);
@@ -500,7 +502,9 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     rxr_handle th = timed ? h : nullptr;
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
     const int n = (int)p.n;
-    const bool chunk_in = io && p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE;
+    const bool rows = (variant & RXR_SKETCH_ROWS) != 0;  // row extraction instead of the Gaussian sketch
+    variant &= ~RXR_SKETCH_ROWS;
+    const bool chunk_in = io && p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE && !rows;
     const bool chunk_out = io && p.prec == RXR_SPLIT_BF16 && passes > 1 && p.n <= 64;
     if (io) {
         // the copy stream starts after this stream's earlier work
@@ -516,7 +520,11 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         k_identity<<<(int)cdiv(p.n * p.n, 256), 256, 0, st>>>(p.Rs, n);
         if (launch_ok()) return RXR_ERR_CUDA;
     } else {
-        if (chunk_in) {
+        if (rows) {
+            Timer t(th, 0, st);
+            k_sketch_rows<<<(int)cdiv(p.s, 8), 256, 0, st>>>(A, lda, p.m, n, p.s, seed, p.Y, p.s, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        } else if (chunk_in) {
             // chunk c of A's rows lands on the copy stream, then its CTAs of
             // the sketch run (the same partition and partial sums as one launch)
             Timer t(th, 0, st);
@@ -558,6 +566,12 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
             {
                 Timer t(th, 1, st);
+                // a row sketch reads only the drawn rows: NaN or Inf elsewhere in A is
+                // found by the Gram from X's column exponents (n <= 64) or here
+                if (rows && !cx) {
+                    k_check_finite<<<4 * p.sms, 256, 0, st>>>(A, lda, p.m, n, p.status);
+                    if (launch_ok()) return RXR_ERR_CUDA;
+                }
                 if (int e = split_subst(p, A, lda, p.Rs, Q, ldq, st, cx)) return e;
             }
             Timer t(th, 4, st);
@@ -569,7 +583,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         } else {
             Timer t(th, 1, st);
             if (int e = enqueue_subst(p, A, lda, p.Rs, variant == RXR_NONE ? 1 : 0, Q, ldq, true,
-                                      variant == RXR_NONE, st))
+                                      variant == RXR_NONE || rows, st))
                 return e;
         }
     }
@@ -657,8 +671,10 @@ int check_args(const double *A, int64_t m, int64_t n, int64_t lda, int variant, 
     if (m < 1 || m < n) return -2;
     if (n < 1) return -3;
     if (lda < m) return -4;
-    if (variant != RXR_LU && variant != RXR_QR && variant != RXR_NONE) return -5;
-    if (variant != RXR_NONE && (s < n || s > RXR_MAX_S)) return -6;
+    const int base = variant & ~RXR_SKETCH_ROWS;
+    if (base != RXR_LU && base != RXR_QR && base != RXR_NONE) return -5;
+    if (base == RXR_NONE && variant != base) return -5;  // no sketch to take by rows
+    if (base != RXR_NONE && (s < n || s > RXR_MAX_S)) return -6;
     if (passes < 1 || passes > 3) return -8;
     if (Q == nullptr) return -9;
     if (ldq < m) return -10;
@@ -890,6 +906,7 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     std::vector<int64_t> sk(count);
     int64_t total_rows = 0;
     for (int k = 0; k < count; ++k) {
+        if (variant & RXR_SKETCH_ROWS) return RXR_ERR_UNSUPPORTED;
         sk[k] = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
         if (int e = check_args(A[k], m[k], n[k], lda[k], variant, sk[k], passes, Q[k], ldq[k], R[k], ldr[k], prec))
             return e;
@@ -1088,6 +1105,29 @@ int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda,
     if (int e = enqueue_sketch(p, A, lda, seed, st)) return e;
     if (cudaMemcpy2DAsync(Y, ldy * 8, p.Y, s * 8, s * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_sketch_rows(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                    double *Y, int64_t ldy, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (m < 1) return -3;
+    if (n < 1) return -4;
+    if (lda < m) return -5;
+    if (s < 1 || s > RXR_MAX_S) return -6;
+    if (Y == nullptr) return -8;
+    if (ldy < s) return -9;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, s, n, s, RXR_FP64, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    k_sketch_rows<<<(int)cdiv(s, 8), 256, 0, st>>>(A, lda, m, (int)n, s, seed, Y, ldy, p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
     return finish_blocking(h, p.status, st);
 }
 

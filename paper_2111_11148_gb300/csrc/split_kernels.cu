@@ -1637,7 +1637,10 @@ __global__ void __launch_bounds__(kG6Producers, 1)
     const bool mma_thread = (warp == kG6MmaWarp && lane == 0);
 
     for (int e = tid; e < (int)(kG6Smem / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
-    if (tid < 64) cex[tid] = (tid < n) ? colexp_g[tid] : 0;
+    if (tid < 64) {
+        cex[tid] = (tid < n) ? colexp_g[tid] : 0;
+        if (cex[tid] == 0x7FF) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);  // NaN or Inf in X
+    }
     if (tid == 0) {
         mbar_init(&ready[0], kG6Producers);
         mbar_init(&ready[1], kG6Producers);

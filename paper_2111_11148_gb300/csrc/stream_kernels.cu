@@ -268,6 +268,44 @@ __device__ __forceinline__ void reduce_body(const double *__restrict__ parts, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row extraction (Section 2.3; Theorem 3.2's equal-probability case): row k
+// of Y is row idx_k of A, idx_k = floor(u_k m / 2^64) with u_k = out0 +
+// 2^32 out1 of Philox4x32-10 at counter (k_lo, k_hi, 0, 3), key (seed_lo,
+// seed_hi) -- independent draws, each row with probability 1/m.  One warp per
+// drawn row, lanes across the columns.
+// ---------------------------------------------------------------------------
+__global__ void k_sketch_rows(const double *__restrict__ A, int64_t lda, int64_t m, int n, int64_t l, uint64_t seed,
+                              double *__restrict__ Y, int64_t ldy, RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= l) return;
+    uint32_t c0 = (uint32_t)k, c1 = (uint32_t)((uint64_t)k >> 32), c2 = 0u, c3 = 3u;
+    philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t u = (uint64_t)c0 | ((uint64_t)c1 << 32);
+    const int64_t i = (int64_t)__umul64hi(u, (uint64_t)m);
+    bool bad = false;
+    for (int j = lane; j < n; j += 32) {
+        const double v = A[i + (int64_t)j * lda];
+        bad |= rxr_nonfinite(v);
+        Y[k + (int64_t)j * ldy] = v;
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+}
+
+// NaN or Inf anywhere in A (m x n, lda) -> RXR_ERR_NONFINITE (grid-stride).
+__global__ void k_check_finite(const double *__restrict__ A, int64_t lda, int64_t m, int n, RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    bool bad = false;
+    const int64_t total = m * (int64_t)n, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride)
+        bad |= rxr_nonfinite(A[e % m + (e / m) * lda]);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+}
+
 __global__ void k_reduce_parts(const double *__restrict__ parts, int nparts, int64_t stride, int rows, int cols,
                                double scale, int symmetric, double *__restrict__ out, int64_t ldo, RxrStatus *st)
 {

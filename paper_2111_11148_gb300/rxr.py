@@ -20,11 +20,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librxr.so")
 
 LU, QR, NONE = 0, 1, 2
+SKETCH_ROWS = 16  # OR-ed into LU / QR: the sketch by row extraction
 FP64, SPLIT_BF16 = 0, 1
 OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED = range(8)
 KERNEL_SKETCH, KERNEL_PRECOND_GRAM, KERNEL_PASS_GRAM, KERNEL_APPLY = range(4)
 
-_VARIANTS = {"lu": LU, "qr": QR, "none": NONE, LU: LU, QR: QR, NONE: NONE}
+_VARIANTS = {"lu": LU, "qr": QR, "none": NONE, "lu-rows": LU | SKETCH_ROWS, "qr-rows": QR | SKETCH_ROWS,
+             LU: LU, QR: QR, NONE: NONE, LU | SKETCH_ROWS: LU | SKETCH_ROWS, QR | SKETCH_ROWS: QR | SKETCH_ROWS}
 _PRECS = {"fp64": FP64, "split": SPLIT_BF16, "split_bf16": SPLIT_BF16, FP64: FP64, SPLIT_BF16: SPLIT_BF16}
 
 
@@ -61,6 +63,7 @@ def load() -> ctypes.CDLL:
         "rxr_status_string": ([i], ctypes.c_char_p),
         "rxr_omega": ([u64, i64, i64, i64, vp, vp], i),
         "rxr_sketch": ([vp, vp, i64, i64, i64, i64, u64, vp, i64, i, vp], i),
+        "rxr_sketch_rows": ([vp, vp, i64, i64, i64, i64, u64, vp, i64, vp], i),
         "rxr_xr_factor": ([vp, vp, i64, i64, i64, i, vp, i64, vp], i),
         "rxr_precond_gram": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, i, vp], i),
         "rxr_cholesky": ([vp, vp, i64, i64, vp, i64, vp], i),
@@ -84,7 +87,8 @@ def load() -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return [n for n in ("rxr_create", "rxr_destroy", "rxr_workspace_bytes", "rxr_set_workspace", "rxr_cholqr",
                         "rxr_cholqr_async", "rxr_cholqr_host", "rxr_cholqr_batched", "rxr_last_info",
-                        "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_xr_factor", "rxr_precond_gram",
+                        "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_sketch_rows", "rxr_xr_factor",
+                        "rxr_precond_gram",
                         "rxr_cholesky", "rxr_apply_rinv", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
                         "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc")]
 
@@ -229,7 +233,7 @@ class Handle:
             arr(vp, [q.data_ptr() for q in Qs]), arr(ctypes.c_int64, [_ld(q) for q in Qs]),
             arr(vp, [r.data_ptr() for r in Rs]), arr(ctypes.c_int64, [_ld(r) for r in Rs]), _PRECS[prec],
             _stream(stream), _ptr(st))
-        if code < 0:
+        if code < 0 or code == UNSUPPORTED:  # nothing was factorised
             raise RxrError(code, "rxr_cholqr_batched")
         return Qs, Rs, st.view(cnt, 4).cpu().numpy()
 
@@ -239,6 +243,14 @@ class Handle:
         Y = empty_colmajor(s, n, device=A.device)
         _check(load().rxr_sketch(self._h, _ptr(A), m, n, _ld(A), s, seed, _ptr(Y), _ld(Y), _PRECS[prec],
                                  _stream(stream)), "rxr_sketch")
+        return Y
+
+    def sketch_rows(self, A, s: int, seed: int = 0, stream=None):
+        """Row-extraction sketch: s rows of A drawn uniformly with replacement."""
+        m, n = A.shape
+        Y = empty_colmajor(s, n, device=A.device)
+        _check(load().rxr_sketch_rows(self._h, _ptr(A), m, n, _ld(A), s, seed, _ptr(Y), _ld(Y), _stream(stream)),
+               "rxr_sketch_rows")
         return Y
 
     def xr_factor(self, Y, variant="qr", stream=None, raise_on_error=True):
