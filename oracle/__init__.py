@@ -73,6 +73,8 @@ def _load():
                                            vp, vp, vp, vp, vp, vp, vp]
             lib.rxo_rxr_cholqr.restype = i
             lib.rxo_householder_qr.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
+            lib.rxo_scholqr.argtypes = [vp, i64, i64, i64, d, i, vp, i64, vp, i64, vp]
+            lib.rxo_scholqr.restype = i
             lib.rxo_orth_error.argtypes = [vp, i64, i64, i64]
             lib.rxo_orth_error.restype = d
             lib.rxo_resid_error.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
@@ -263,6 +265,18 @@ def rxr_cholqr(A: np.ndarray, variant: int = VARIANT_QR, s: int | None = None, s
                                 _p(Y), *[_p(x) for x in mats], _p(info))
     return Result(status=int(st), Q=Q, R=R, Y=Y, Rs=mats[0], G1=mats[1], R1=mats[2], G2=mats[3], R2=mats[4],
                   info=(int(info[0]), int(info[1])))
+
+
+def scholqr(A: np.ndarray, shift: float, passes: int = 3) -> Result:
+    """Shifted CholeskyQR3 (Section 2.1): R_1 = chol(A^T A + shift I), Q_1 = A R_1^{-1},
+    then passes - 1 CholeskyQR steps; the shift is absolute."""
+    A = _f64(A)
+    m, n = A.shape
+    Q = np.zeros((m, n), order="F")
+    R = np.zeros((n, n), order="F")
+    info = np.zeros(2, np.int32)
+    st = _load().rxo_scholqr(_p(A), m, n, _ld(A), float(shift), int(passes), _p(Q), max(1, m), _p(R), n, _p(info))
+    return Result(status=int(st), Q=Q, R=R, info=(int(info[0]), int(info[1])))
 
 
 def householder_qr(A: np.ndarray):

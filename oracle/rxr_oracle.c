@@ -596,6 +596,56 @@ int rxo_rxr_cholqr(const double *A, int64_t m, int64_t n, int64_t lda, int varia
 }
 
 /* ------------------------------------------------------------------------- */
+/* Shifted CholeskyQR3 (the comparator of Section 2.1's algorithm            */
+/* sCholeskyQR3): G = A^T A, R_1 = chol(G + shift I), Q_1 = A R_1^{-1}, then */
+/* passes - 1 plain CholeskyQR steps (two for sCholeskyQR3), R = R_p ... R_1. */
+/* The shift is an input (absolute).  info = breakdown pass and column.      */
+/* ------------------------------------------------------------------------- */
+int rxo_scholqr(const double *A, int64_t m, int64_t n, int64_t lda, double shift, int passes, double *Q,
+                int64_t ldq, double *R, int64_t ldr, int *info)
+{
+    if (info) {
+        info[0] = 0;
+        info[1] = 0;
+    }
+    if (!all_finite(A, m, n, lda)) return RXO_NONFINITE;
+    size_t nn = (size_t)(n * n);
+    double *Racc = (double *)calloc(nn, sizeof(double));
+    double *tmp = (double *)calloc(nn, sizeof(double));
+    double *G = (double *)calloc(nn, sizeof(double));
+    double *Rp = (double *)calloc(nn, sizeof(double));
+    int status = RXO_OK;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) Q[i + j * ldq] = A[i + j * lda];
+    for (int64_t k = 0; k < n; ++k) Racc[k + k * n] = 1.0;
+    for (int p = 1; p <= passes; ++p) {
+        rxo_gram(Q, m, n, ldq, G, n);
+        if (p == 1)
+            for (int64_t k = 0; k < n; ++k) G[k + k * n] += shift;
+        int bad = rxo_potrf_u(G, n, n, Rp, n);
+        if (bad) {
+            status = RXO_CHOL_BREAKDOWN;
+            if (info) {
+                info[0] = p;
+                info[1] = bad - 1;
+            }
+            break;
+        }
+        rxo_trsm_right_upper(Q, m, n, ldq, Rp, n, Q, ldq);
+        rxo_trmm_upper(Rp, n, Racc, n, n, tmp, n);
+        memcpy(Racc, tmp, nn * sizeof(double));
+    }
+    if (status == RXO_OK && R)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < n; ++i) R[i + j * ldr] = Racc[i + j * n];
+    free(Racc);
+    free(tmp);
+    free(G);
+    free(Rp);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
 /* The plain definition of the result: the thin QR factorisation A = QR with */
 /* diag(R) > 0, which is unique for full-rank A (footnote to Algorithm 1).   */
 /* Householder QR of A (copied), then Q = H_1 ... H_n [I; 0] accumulated     */
