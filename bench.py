@@ -118,11 +118,14 @@ def oracle_rows(target_s: float = 15.0) -> int:
 def run_oracle_sample(A_sample: np.ndarray, variant: str):
     import oracle
 
-    ov = oracle.VARIANT_QR if variant.startswith("qr") else oracle.VARIANT_LU
-    if variant.endswith("-rows"):
-        ov |= oracle.SKETCH_ROWS
     t0 = time.perf_counter()
-    r = oracle.rxr_cholqr(A_sample, ov, S, seed=SEED, passes=PASSES)
+    if variant == "shifted":
+        r = oracle.scholqr(A_sample, 1e-15 * np.linalg.norm(A_sample, 2) ** 2, passes=PASSES)
+    else:
+        ov = {"qr": oracle.VARIANT_QR, "lu": oracle.VARIANT_LU, "none": oracle.VARIANT_NONE}[variant.split("-")[0]]
+        if variant.endswith("-rows"):
+            ov |= oracle.SKETCH_ROWS
+        r = oracle.rxr_cholqr(A_sample, ov, S, seed=SEED, passes=PASSES)
     dt = time.perf_counter() - t0
     if r.status != 0:
         raise RuntimeError(f"oracle status {r.status}")
@@ -402,7 +405,8 @@ def e2e_leg(h, A_np, args, world):
 
 
 def _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu):
-    launches = launches_per_step(args.prec, N, M, args.variant.endswith("-rows")) if PASSES == 2 else None
+    launches = (launches_per_step(args.prec, N, M, args.variant.endswith("-rows"))
+                if PASSES == 2 and args.variant.split("-")[0] in ("qr", "lu") else None)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -437,7 +441,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--variant", default="qr", choices=["qr", "lu"])
+    ap.add_argument("--variant", default="qr", choices=["qr", "lu", "none", "shifted"],
+                    help="rQR / rLU preconditioning, or the comparators CholeskyQR2 (none) and sCholeskyQR3")
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "rows"],
                     help="Gaussian sketch (the workload's) or row extraction (Section 2.3)")
     ap.add_argument("--prec", default="split", choices=["fp64", "split"],
@@ -451,14 +456,18 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batched"])
     ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
     args = ap.parse_args()
-    global M, N, S, KAPPA, WORKLOAD
+    global M, N, S, KAPPA, WORKLOAD, PASSES
+    if args.variant == "shifted":
+        PASSES = 3
     if args.m:
         M = int(args.m)
     if args.n:
         N, S = int(args.n), 2 * int(args.n)
     if args.kappa:
         KAPPA = float(args.kappa)
-    WORKLOAD = (f"{'rQR' if args.variant == 'qr' else 'rLU'}-CholeskyQR2 m={'2^22' if M == 2**22 else M} n={N} "
+    method = {"qr": "rQR-CholeskyQR2", "lu": "rLU-CholeskyQR2", "none": "CholeskyQR2",
+              "shifted": "sCholeskyQR3"}[args.variant]
+    WORKLOAD = (f"{method} m={'2^22' if M == 2**22 else M} n={N} "
                 f"s={S} kappa={KAPPA:g} {'FP64' if args.prec == 'fp64' else 'split BF16 sketch+Gram1, FP64 rest'}")
     if args.sketch == "rows":
         WORKLOAD += ", row-extraction sketch"

@@ -55,8 +55,13 @@ extern "C" {
  * replacement), draw k from Philox4x32-10 at counter (k_lo, k_hi, 0, 3) and key
  * (seed_lo, seed_hi), u = out0 + 2^32 out1, row floor(u m / 2^64).  Coherent A
  * (large m max_i ||Q(i,:)||^2, e.g. A = [I; 0]) can leave that sketch
- * rank-deficient: RXR_ERR_SKETCH_SINGULAR. */
-typedef enum { RXR_LU = 0, RXR_QR = 1, RXR_NONE = 2 } rxr_variant;
+ * rank-deficient: RXR_ERR_SKETCH_SINGULAR.  RXR_SHIFTED is the shifted
+ * CholeskyQR comparator of Section 2.1 (sCholeskyQR3 with passes = 3): no
+ * sketch, R_1 = chol(A^T A + eps I) with eps = 1e-15 ||A||_2^2 (the shift of the
+ * paper's experiments; ||A||_2^2 by 40 power iterations on A^T A), then
+ * passes - 1 plain CholeskyQR steps.  RXR_NONE and RXR_SHIFTED ignore s and take
+ * n <= 128; the batched form takes neither RXR_SHIFTED nor RXR_SKETCH_ROWS. */
+typedef enum { RXR_LU = 0, RXR_QR = 1, RXR_NONE = 2, RXR_SHIFTED = 3 } rxr_variant;
 #define RXR_SKETCH_ROWS 16
 
 /* Arithmetic of the two contractions that only shape the preconditioner (the

@@ -42,6 +42,7 @@ __global__ void k_xr_factor(const double *, int, int, int64_t, int, double *, do
 __global__ void k_factor(const double *, int, int64_t, double *, double *, double *, int, int, RxrStatus *);
 __global__ void k_copy_upper(const double *, int, double *, int64_t, const RxrStatus *);
 __global__ void k_identity(double *, int);
+__global__ void k_shift_gram(double *, int, int64_t, double, RxrStatus *);
 __global__ void k_status_out(const RxrStatus *, int *);
 __global__ void k_orth_partial(const double *, int64_t, int, int64_t, int64_t, int, double *);
 __global__ void k_orth_final(const double *, int, int, double *);
@@ -63,6 +64,8 @@ constexpr int kTimers = 7;
 // row chunks of the _host entry point's copies (overlapped with the sketch
 // and with the last apply)
 constexpr int kIoChunks = kSketchChunks;
+// shifted CholeskyQR3's shift, relative to ||A||_2^2 (the paper's experiments, Section 4.1)
+constexpr double kShiftCoef = 1e-15;
 
 struct rxr_ctx {
     int device = 0;
@@ -504,6 +507,8 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     const int n = (int)p.n;
     const bool rows = (variant & RXR_SKETCH_ROWS) != 0;  // row extraction instead of the Gaussian sketch
     variant &= ~RXR_SKETCH_ROWS;
+    const bool shifted = variant == RXR_SHIFTED;  // sCholeskyQR3: no sketch, the first Gram shifted
+    if (shifted) variant = RXR_NONE;
     const bool chunk_in = io && p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE && !rows;
     const bool chunk_out = io && p.prec == RXR_SPLIT_BF16 && passes > 1 && p.n <= 64;
     if (io) {
@@ -580,6 +585,21 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             } else if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) {
                 return e;
             }
+        } else if (p.prec == RXR_SPLIT_BF16) {
+            // no preconditioner (CholeskyQR2, shifted CholeskyQR3): X_0 = A, and the
+            // first Gram on the tensor cores at FP64 grade (it decides breakdown)
+            {
+                Timer t(th, 1, st);
+                if (Q != A && cudaMemcpy2DAsync(Q, ldq * 8, A, lda * 8, p.m * 8, p.n, cudaMemcpyDeviceToDevice, st) !=
+                                  cudaSuccess)
+                    return RXR_ERR_CUDA;
+                if (p.n > 64) {  // n <= 64: the Gram reports NaN or Inf from the column exponents
+                    k_check_finite<<<4 * p.sms, 256, 0, st>>>(A, lda, p.m, n, p.status);
+                    if (launch_ok()) return RXR_ERR_CUDA;
+                }
+            }
+            Timer t(th, 4, st);
+            if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st, false)) return e;
         } else {
             Timer t(th, 1, st);
             if (int e = enqueue_subst(p, A, lda, p.Rs, variant == RXR_NONE ? 1 : 0, Q, ldq, true,
@@ -589,6 +609,10 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
     }
     // step 4: CholeskyQR passes on X
     for (int pass = 1; pass <= passes; ++pass) {
+        if (shifted && pass == 1) {
+            k_shift_gram<<<1, 256, 0, st>>>(p.G, n, p.n, kShiftCoef, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        }
         if (p.n > 64) {
             if (int e = blocked_factor_enqueue(p.G, n, p.n, p.Rp, p.Racc, p.C, pass, 1, p.status, st)) return e;
         } else {
@@ -672,16 +696,17 @@ int check_args(const double *A, int64_t m, int64_t n, int64_t lda, int variant, 
     if (n < 1) return -3;
     if (lda < m) return -4;
     const int base = variant & ~RXR_SKETCH_ROWS;
-    if (base != RXR_LU && base != RXR_QR && base != RXR_NONE) return -5;
-    if (base == RXR_NONE && variant != base) return -5;  // no sketch to take by rows
-    if (base != RXR_NONE && (s < n || s > RXR_MAX_S)) return -6;
+    const bool sketchless = base == RXR_NONE || base == RXR_SHIFTED;
+    if (base != RXR_LU && base != RXR_QR && !sketchless) return -5;
+    if (sketchless && variant != base) return -5;  // no sketch to take by rows
+    if (!sketchless && (s < n || s > RXR_MAX_S)) return -6;
     if (passes < 1 || passes > 3) return -8;
     if (Q == nullptr) return -9;
     if (ldq < m) return -10;
     if (R != nullptr && ldr < n) return -12;
     if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -13;
     if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
-    if (n > kNarrowN && variant == RXR_NONE) return RXR_ERR_UNSUPPORTED;
+    if (n > kNarrowN && sketchless) return RXR_ERR_UNSUPPORTED;
     if (m > ((int64_t)1 << 31)) return RXR_ERR_UNSUPPORTED;
     (void)Q;
     return 0;
@@ -809,7 +834,7 @@ static int cholqr_common(rxr_handle h, const double *A, int64_t m, int64_t n, in
                          void *stream, int *d_status, bool blocking)
 {
     if (h == nullptr) return RXR_ERR_CUDA;
-    if (variant == RXR_NONE && s < n) s = n;
+    if ((variant == RXR_NONE || variant == RXR_SHIFTED) && s < n) s = n;
     if (int e = check_args(A, m, n, lda, variant, s, passes, Q, ldq, R, ldr, prec)) return e;
     DeviceGuard g(h->device);
     if (!g.ok) return RXR_ERR_CUDA;
@@ -847,7 +872,7 @@ int rxr_cholqr_host(rxr_handle h, const double *hA, int64_t m, int64_t n, int64_
                     void *stream)
 {
     if (h == nullptr) return RXR_ERR_CUDA;
-    if (variant == RXR_NONE && s < n) s = n;
+    if ((variant == RXR_NONE || variant == RXR_SHIFTED) && s < n) s = n;
     if (int e = check_args(hA, m, n, lda, variant, s, passes, hQ, ldq, hR, ldr, prec)) return e;
     DeviceGuard g(h->device);
     if (!g.ok) return RXR_ERR_CUDA;
@@ -906,7 +931,7 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     std::vector<int64_t> sk(count);
     int64_t total_rows = 0;
     for (int k = 0; k < count; ++k) {
-        if (variant & RXR_SKETCH_ROWS) return RXR_ERR_UNSUPPORTED;
+        if ((variant & RXR_SKETCH_ROWS) || variant == RXR_SHIFTED) return RXR_ERR_UNSUPPORTED;
         sk[k] = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
         if (int e = check_args(A[k], m[k], n[k], lda[k], variant, sk[k], passes, Q[k], ldq[k], R[k], ldr[k], prec))
             return e;

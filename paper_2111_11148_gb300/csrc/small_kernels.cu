@@ -343,6 +343,54 @@ __global__ void k_copy_upper(const double *__restrict__ R, int n, double *__rest
 }
 
 // Identity into an n x n (ld n) matrix.
+// Shifted CholeskyQR's first Gram (Section 2.1, sCholeskyQR3): G += eps I with
+// eps = coef lambda_max(G), lambda_max(G) = ||A||_2^2 estimated by 40 power
+// iterations from the all-ones vector in a fixed order (G is symmetric
+// positive semidefinite, so ||G v|| / ||v|| rises towards lambda_max).  One
+// CTA of 256 threads, n <= 512, G column-major with leading dimension ldg.
+__global__ void __launch_bounds__(256) k_shift_gram(double *__restrict__ G, int n, int64_t ldg, double coef,
+                                                    RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    __shared__ double v[512], w[512], red[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < n; i += blockDim.x) v[i] = 1.0;
+    __syncthreads();
+    double lam = 0.0;
+    for (int it = 0; it < 40; ++it) {
+        double t = 0.0;
+        for (int i = tid; i < n; i += blockDim.x) {
+            double a = 0.0;
+            for (int k = 0; k < n; ++k) a = fma(G[i + (int64_t)k * ldg], v[k], a);
+            w[i] = a;
+            t = fma(a, a, t);
+        }
+        double u = 0.0;  // ||v||^2
+        for (int i = tid; i < n; i += blockDim.x) u = fma(v[i], v[i], u);
+        for (int o = 16; o > 0; o >>= 1) {
+            t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+            u += __shfl_xor_sync(0xFFFFFFFFu, u, o);
+        }
+        __syncthreads();  // every thread's reads of v are done
+        if (lane == 0) red[warp] = t;
+        __syncthreads();
+        double ss = 0.0;
+        for (int k = 0; k < 8; ++k) ss += red[k];  // ||G v||^2, same order in every thread
+        __syncthreads();
+        if (lane == 0) red[warp] = u;
+        __syncthreads();
+        double vv = 0.0;
+        for (int k = 0; k < 8; ++k) vv += red[k];
+        if (!(ss > 0.0) || !(vv > 0.0)) break;  // G = 0 (or not finite): no shift
+        lam = sqrt(ss / vv);
+        const double inv = 1.0 / sqrt(ss);
+        for (int i = tid; i < n; i += blockDim.x) v[i] = w[i] * inv;
+        __syncthreads();
+    }
+    if (!rxr_nonfinite(lam))
+        for (int i = tid; i < n; i += blockDim.x) G[i + (int64_t)i * ldg] += coef * lam;
+}
+
 __global__ void k_identity(double *__restrict__ R, int n)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;

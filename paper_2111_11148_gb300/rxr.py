@@ -19,14 +19,15 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librxr.so")
 
-LU, QR, NONE = 0, 1, 2
+LU, QR, NONE, SHIFTED = 0, 1, 2, 3
 SKETCH_ROWS = 16  # OR-ed into LU / QR: the sketch by row extraction
 FP64, SPLIT_BF16 = 0, 1
 OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED = range(8)
 KERNEL_SKETCH, KERNEL_PRECOND_GRAM, KERNEL_PASS_GRAM, KERNEL_APPLY = range(4)
 
-_VARIANTS = {"lu": LU, "qr": QR, "none": NONE, "lu-rows": LU | SKETCH_ROWS, "qr-rows": QR | SKETCH_ROWS,
-             LU: LU, QR: QR, NONE: NONE, LU | SKETCH_ROWS: LU | SKETCH_ROWS, QR | SKETCH_ROWS: QR | SKETCH_ROWS}
+_VARIANTS = {"lu": LU, "qr": QR, "none": NONE, "shifted": SHIFTED, "lu-rows": LU | SKETCH_ROWS,
+             "qr-rows": QR | SKETCH_ROWS, LU: LU, QR: QR, NONE: NONE, SHIFTED: SHIFTED,
+             LU | SKETCH_ROWS: LU | SKETCH_ROWS, QR | SKETCH_ROWS: QR | SKETCH_ROWS}
 _PRECS = {"fp64": FP64, "split": SPLIT_BF16, "split_bf16": SPLIT_BF16, FP64: FP64, SPLIT_BF16: SPLIT_BF16}
 
 
