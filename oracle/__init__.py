@@ -75,6 +75,8 @@ def _load():
             lib.rxo_householder_qr.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
             lib.rxo_scholqr.argtypes = [vp, i64, i64, i64, d, i, vp, i64, vp, i64, vp]
             lib.rxo_scholqr.restype = i
+            lib.rxo_lstsq.argtypes = [vp, i64, i64, i64, vp, i64, i64, i, i64, u64, vp, i64]
+            lib.rxo_lstsq.restype = i
             lib.rxo_orth_error.argtypes = [vp, i64, i64, i64]
             lib.rxo_orth_error.restype = d
             lib.rxo_resid_error.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64]
@@ -277,6 +279,19 @@ def scholqr(A: np.ndarray, shift: float, passes: int = 3) -> Result:
     info = np.zeros(2, np.int32)
     st = _load().rxo_scholqr(_p(A), m, n, _ld(A), float(shift), int(passes), _p(Q), max(1, m), _p(R), n, _p(info))
     return Result(status=int(st), Q=Q, R=R, info=(int(info[0]), int(info[1])))
+
+
+def lstsq(A: np.ndarray, b: np.ndarray, variant: int = VARIANT_QR, s: int | None = None, seed: int = 0):
+    """min ||A x - b|| by Section 5.2's solver preconditioned by the sketch's R
+    factor; b is m or m x k.  Returns (x, status)."""
+    A = _f64(A)
+    m, n = A.shape
+    s = 2 * n if s is None else int(s)
+    b2 = _f64(b.reshape(m, -1))
+    k = b2.shape[1]
+    x = np.zeros((n, k), order="F")
+    st = _load().rxo_lstsq(_p(A), m, n, _ld(A), _p(b2), k, max(1, m), variant, s, seed, _p(x), n)
+    return (x[:, 0] if b.ndim == 1 else x), int(st)
 
 
 def householder_qr(A: np.ndarray):

@@ -596,6 +596,77 @@ int rxo_rxr_cholqr(const double *A, int64_t m, int64_t n, int64_t lda, int varia
 }
 
 /* ------------------------------------------------------------------------- */
+/* Least squares preconditioned by the sketch's R factor (Section 5.2):      */
+/*   1  B = A R_s^{-1}  (R_s from the sketch: rQR / rLU, Gaussian or rows)    */
+/*   2  y = (B^T B)^{-1} B^T b  by the normal equations: G = B^T B,           */
+/*      R_G = chol(G), c = B^T b, R_G^T z = c, R_G y = z                      */
+/*   3  x = R_s^{-1} y                                                        */
+/* b is m x k (ldb), x is n x k (ldx).  Returns the status of the sketch's   */
+/* factor, of the Cholesky step, or NONFINITE for A or b.                    */
+/* ------------------------------------------------------------------------- */
+int rxo_lstsq(const double *A, int64_t m, int64_t n, int64_t lda, const double *b, int64_t k, int64_t ldb, int variant,
+              int64_t s, uint64_t seed, double *x, int64_t ldx)
+{
+    if (!all_finite(A, m, n, lda) || !all_finite(b, m, k, ldb)) return RXO_NONFINITE;
+    const int rows = (variant & RXO_SKETCH_ROWS) != 0;
+    variant &= ~RXO_SKETCH_ROWS;
+    size_t nn = (size_t)(n * n);
+    double *Y = (double *)malloc((size_t)(s * n) * sizeof(double));
+    double *Rs = (double *)calloc(nn, sizeof(double));
+    double *G = (double *)calloc(nn, sizeof(double));
+    double *RG = (double *)calloc(nn, sizeof(double));
+    double *B = (double *)malloc((size_t)(m * n) * sizeof(double));
+    double *c = (double *)malloc((size_t)n * sizeof(double));
+    int status = RXO_OK;
+    if (rows)
+        rxo_sketch_rows(A, m, n, lda, s, seed, Y, s);
+    else
+        rxo_sketch(A, m, n, lda, s, seed, Y, s);
+    if (variant == RXO_VARIANT_QR)
+        rxo_geqr_r(Y, s, n, s, Rs, n);
+    else
+        rxo_getrf_u(Y, s, n, s, Rs, n, NULL);
+    rxo_sign_normalise(Rs, n, n);
+    status = rxo_check_factor(Rs, n, n);
+    if (status == RXO_OK) {
+        rxo_trsm_right_upper(A, m, n, lda, Rs, n, B, m);
+        rxo_gram(B, m, n, m, G, n);
+        if (rxo_potrf_u(G, n, n, RG, n)) status = RXO_CHOL_BREAKDOWN;
+    }
+    for (int64_t r = 0; status == RXO_OK && r < k; ++r) {
+        const double *br = b + r * ldb;
+        double *xr = x + r * ldx;
+        for (int64_t j = 0; j < n; ++j) { /* c = B^T b */
+            double acc = 0.0;
+            for (int64_t i = 0; i < m; ++i) acc += B[i + j * m] * br[i];
+            c[j] = acc;
+        }
+        for (int64_t j = 0; j < n; ++j) { /* R_G^T z = c (forward) */
+            double acc = c[j];
+            for (int64_t l = 0; l < j; ++l) acc -= RG[l + j * n] * c[l];
+            c[j] = acc / RG[j + j * n];
+        }
+        for (int64_t j = n - 1; j >= 0; --j) { /* R_G y = z (backward) */
+            double acc = c[j];
+            for (int64_t l = j + 1; l < n; ++l) acc -= RG[j + l * n] * c[l];
+            c[j] = acc / RG[j + j * n];
+        }
+        for (int64_t j = n - 1; j >= 0; --j) { /* R_s x = y (backward) */
+            double acc = c[j];
+            for (int64_t l = j + 1; l < n; ++l) acc -= Rs[j + l * n] * xr[l];
+            xr[j] = acc / Rs[j + j * n];
+        }
+    }
+    free(Y);
+    free(Rs);
+    free(G);
+    free(RG);
+    free(B);
+    free(c);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Shifted CholeskyQR3 (the comparator of Section 2.1's algorithm            */
 /* sCholeskyQR3): G = A^T A, R_1 = chol(G + shift I), Q_1 = A R_1^{-1}, then */
 /* passes - 1 plain CholeskyQR steps (two for sCholeskyQR3), R = R_p ... R_1. */
