@@ -229,6 +229,47 @@ def batched_arm(args, rank: int, world: int, local_rank: int):
 STAGES = ["sketch", "precond_subst", "pass_subst", "last_apply", "gram1_tensor", "gram2_tensor", "xr_factor"]
 
 
+def lstsq_arm(args, rank: int, world: int, local_rank: int):
+    """Least squares (Section 5.2) on the workload's A with one right-hand side
+    b = A x_true: one rxr_lstsq per step, B_alg = 8 m n (sketch read, B = A R_s^-1
+    read) + 8 m n (B written) + 8 m n (B read for B^T b)."""
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    A_np = make_input()
+    xt = np.random.default_rng(1).standard_normal(N)
+    A = rxr.colmajor(torch.from_numpy(A_np).to(dev))
+    b = torch.from_numpy(A_np @ xt).to(dev)
+    h = rxr.Handle(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    step = lambda: h.lstsq(A, b, variant=args.variant, s=S, seed=SEED, prec=args.prec)
+    for _ in range(max(3, args.warmup)):
+        x, code = step()
+    assert code == 0
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x, code = step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    err = float(np.linalg.norm(x.cpu().numpy() - xt) / np.linalg.norm(xt))
+    balg = 8.0 * M * N * 4
+    if rank == 0:
+        print(json.dumps({"metric": "least-squares solve effective GB/s (B_alg = 32mn)", "value": balg / ms / 1e6,
+                          "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64+bf16" if args.prec == "split" else "f64", "data": "synthetic",
+                          "config": {"workload": f"least squares (Section 5.2) {WORKLOAD}", "m": M, "n": N, "s": S,
+                                     "kappa": KAPPA, "rhs": 1},
+                          "accuracy": {"x_rel_err": err}}), flush=True)
+    h.close()
+
+
 def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=False):
     """Time `steps` factorisations (after `warmup`) with CUDA events on the
     launching stream; then per-stage event times and the accuracy."""
@@ -453,7 +494,7 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (s = 2n)")
     ap.add_argument("--kappa", type=float, default=None, help="condition number of A")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "lstsq"])
     ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
     args = ap.parse_args()
     global M, N, S, KAPPA, WORKLOAD, PASSES
@@ -480,6 +521,9 @@ def main():
         return
     if args.workload == "batched":
         batched_arm(args, rank, world, local_rank)
+        return
+    if args.workload == "lstsq":
+        lstsq_arm(args, rank, world, local_rank)
         return
     gpu_arm(args, rank, world, local_rank)
 

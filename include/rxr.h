@@ -233,6 +233,20 @@ RXR_API int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_
 RXR_API int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_t ldx, const double *R, int64_t ldr,
                            int prec, void *stream);
 
+/* Least squares min ||A x - b||_2 by the solver of Section 5.2, preconditioned
+ * by the sketch's R factor: B = A R_s^{-1} (the fused precondition step, its
+ * Gram G = B^T B at FP64 grade on either path), c = B^T b, R_G = chol(G),
+ * y = R_G^{-1} R_G^{-T} c, x = R_s^{-1} y.  A (m x n, lda >= m, m >= n) and b
+ * (m x k, ldb >= m, 1 <= k <= 64) read-only device buffers; x (n x k,
+ * ldx >= n) device output; variant RXR_LU or RXR_QR, optionally
+ * | RXR_SKETCH_ROWS; s, seed and prec as for rxr_cholqr.  The handle holds B
+ * (m x n) as scratch.  Blocking; 0, RXR_ERR_SKETCH_SINGULAR,
+ * RXR_ERR_CHOL_BREAKDOWN, RXR_ERR_NONFINITE (A or b) or a negative argument
+ * error (-i: argument i). */
+RXR_API int rxr_lstsq(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *b, int64_t k,
+                      int64_t ldb, int variant, int64_t s, uint64_t seed, double *x, int64_t ldx, int prec,
+                      void *stream);
+
 /* Upper Cholesky factor R (R^T R = G; reads the upper triangle of G).
  * Blocking; returns 0 or RXR_ERR_CHOL_BREAKDOWN (column in rxr_last_info). */
 RXR_API int rxr_cholesky(rxr_handle h, const double *G, int64_t n, int64_t ldg, double *R, int64_t ldr, void *stream);

@@ -43,6 +43,9 @@ __global__ void k_factor(const double *, int, int64_t, double *, double *, doubl
 __global__ void k_copy_upper(const double *, int, double *, int64_t, const RxrStatus *);
 __global__ void k_identity(double *, int);
 __global__ void k_shift_gram(double *, int, int64_t, double, RxrStatus *);
+__global__ void k_ls_btb(const double *, int64_t, int64_t, int, const double *, int64_t, int, int64_t, double *,
+                         RxrStatus *);
+__global__ void k_ls_solve(const double *, const double *, int, int, const double *, double *, int64_t, RxrStatus *);
 __global__ void k_status_out(const RxrStatus *, int *);
 __global__ void k_orth_partial(const double *, int64_t, int, int64_t, int64_t, int, double *);
 __global__ void k_orth_final(const double *, int, int, double *);
@@ -84,6 +87,8 @@ struct rxr_ctx {
     size_t dA_bytes = 0, dQ_bytes = 0, dR_bytes = 0;
     double *eval_buf = nullptr;
     size_t eval_bytes = 0;
+    double *ls_buf = nullptr;  // least squares: B^T b partial sums and c
+    size_t ls_bytes = 0;
     void *h_stage = nullptr;  // pinned host staging of batched job tables
     size_t h_stage_bytes = 0;
     // the _host entry point's copy stream and its chunk events
@@ -786,6 +791,7 @@ int rxr_destroy(rxr_handle h)
     if (h->dQ) cudaFree(h->dQ);
     if (h->dR) cudaFree(h->dR);
     if (h->eval_buf) cudaFree(h->eval_buf);
+    if (h->ls_buf) cudaFree(h->ls_buf);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     for (int k = 0; k < kTimers; ++k)
         for (int j = 0; j < 2; ++j)
@@ -1245,6 +1251,79 @@ int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, d
     }
     if (cudaMemcpy2DAsync(G, ldg * 8, p.G, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_lstsq(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *b, int64_t k,
+              int64_t ldb, int variant, int64_t s, uint64_t seed, double *x, int64_t ldx, int prec, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (m < 1 || m < n) return -3;
+    if (n < 1) return -4;
+    if (lda < m) return -5;
+    if (b == nullptr) return -6;
+    if (k < 1 || k > 64) return -7;
+    if (ldb < m) return -8;
+    const int base = variant & ~RXR_SKETCH_ROWS;
+    if (base != RXR_LU && base != RXR_QR) return -9;
+    if (s < n || s > RXR_MAX_S) return -10;
+    if (x == nullptr) return -12;
+    if (ldx < n) return -13;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -14;
+    if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    const bool rows = (variant & RXR_SKETCH_ROWS) != 0;
+    Plan p;
+    make_plan(p, m, n, s, prec, h->sms);
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    const int64_t ldB = (m + 1) & ~(int64_t)1;  // even: TMA-compatible rows
+    const int64_t rpc = std::max<int64_t>(256, cdiv(m, 4 * (int64_t)h->sms));  // rows of B^T b per CTA
+    const int64_t gx = cdiv(m, rpc);
+    if (grow((void **)&h->dQ, &h->dQ_bytes, (size_t)ldB * n * 8) ||
+        grow((void **)&h->ls_buf, &h->ls_bytes, (size_t)(gx + 1) * n * k * 8))
+        return RXR_ERR_NOMEM;
+    double *B = h->dQ, *parts = h->ls_buf, *c = h->ls_buf + gx * n * k;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    // the sketch's R factor
+    if (rows) {
+        k_sketch_rows<<<(int)cdiv(s, 8), 256, 0, st>>>(A, lda, m, (int)n, s, seed, p.Y, s, p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    } else if (int e = enqueue_sketch(p, A, lda, seed, st)) {
+        return e;
+    }
+    if (int e = enqueue_xr(p, p.Y, s, base, p.Rs, n, st)) return e;
+    // B = A R_s^{-1} with G = B^T B at FP64 grade (it sets the solution's accuracy)
+    if (prec == RXR_SPLIT_BF16) {
+        int *cx = (n <= 64) ? split_colexp(p) : nullptr;
+        if (rows && !cx) {
+            k_check_finite<<<4 * p.sms, 256, 0, st>>>(A, lda, m, (int)n, p.status);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        }
+        if (int e = split_subst(p, A, lda, p.Rs, B, ldB, st, cx)) return e;
+        if (int e = ozaki_gram_enqueue(p, B, ldB, st, cx != nullptr)) return e;
+    } else if (int e = enqueue_subst(p, A, lda, p.Rs, 0, B, ldB, true, rows, st)) {
+        return e;
+    }
+    // c = B^T b, R_G = chol(G), then the three small solves
+    k_ls_btb<<<(int)gx, 256, 0, st>>>(B, ldB, m, (int)n, b, ldb, (int)k, rpc, parts, p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    const int64_t nk = n * k;
+    const int64_t threads = (gx >= kReduceWarpParts) ? 32 * nk : nk;
+    k_reduce_parts<<<(int)cdiv(threads, 256), 256, 0, st>>>(parts, (int)gx, nk, (int)n, (int)k, 1.0, 0, c, n,
+                                                           p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    if (n > 64) {
+        if (int e = blocked_factor_enqueue(p.G, (int)n, n, p.Rp, p.Racc, p.C, 1, 0, p.status, st)) return e;
+    } else {
+        k_factor<<<1, 512, factor_smem_bytes(n), st>>>(p.G, (int)n, n, p.Rp, p.Racc, p.C, 1, 0, p.status);
+        if (launch_ok()) return RXR_ERR_CUDA;
+    }
+    k_ls_solve<<<1, 512, 0, st>>>(p.Rp, p.Rs, (int)n, (int)k, c, x, ldx, p.status);
+    if (launch_ok()) return RXR_ERR_CUDA;
     return finish_blocking(h, p.status, st);
 }
 

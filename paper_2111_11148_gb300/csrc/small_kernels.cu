@@ -391,6 +391,72 @@ __global__ void __launch_bounds__(256) k_shift_gram(double *__restrict__ G, int 
         for (int i = tid; i < n; i += blockDim.x) G[i + (int64_t)i * ldg] += coef * lam;
 }
 
+// Least squares (Section 5.2), c = B^T b over one CTA's rows: warp w takes the
+// (column j, right-hand side r) pairs w, w + 8, ..., its lanes the rows (a
+// fixed order, then a shuffle tree); partial sums to parts[cta][j + n r].
+// A NaN or Inf in b is reported.
+__global__ void __launch_bounds__(256) k_ls_btb(const double *__restrict__ B, int64_t ldb, int64_t m, int n,
+                                                const double *__restrict__ b, int64_t ldbb, int k, int64_t rows_per_cta,
+                                                double *__restrict__ parts, RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = blockIdx.x * rows_per_cta, r1 = min(m, r0 + rows_per_cta);
+    bool bad = false;
+    for (int q = warp; q < n * k; q += 8) {
+        const int j = q % n, r = q / n;
+        const double *bc = B + (int64_t)j * ldb, *rc = b + (int64_t)r * ldbb;
+        double a = 0.0;
+        for (int64_t i = r0 + lane; i < r1; i += 32) {
+            const double bv = rc[i];
+            bad |= (j == 0) && rxr_nonfinite(bv);
+            a = fma(bc[i], bv, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        if (lane == 0) parts[(int64_t)blockIdx.x * n * k + q] = a;
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);
+}
+
+// Least squares (Section 5.2), the small solves: R_G^T z = c, R_G y = z,
+// R_s x = y for the k right-hand sides (c: n x k packed, R_G and R_s upper n x
+// n packed), in place in x (n x k, ldx).  Column-oriented substitution: step
+// j fixes entry j of every right-hand side, then all threads update the
+// remaining entries (one CTA, one barrier per step; global writes are visible
+// to the CTA after the barrier).
+__global__ void __launch_bounds__(512) k_ls_solve(const double *__restrict__ RG, const double *__restrict__ Rs, int n,
+                                                  int k, const double *__restrict__ c, double *x, int64_t ldx,
+                                                  RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * k; e += nt) x[e % n + (int64_t)(e / n) * ldx] = c[e];
+    __syncthreads();
+    // forward: R_G^T z = c  (z_j = v_j / R_jj, then v_l -= R_jl z_j for l > j)
+    for (int j = 0; j < n; ++j) {
+        for (int r = tid; r < k; r += nt) x[j + r * ldx] /= RG[j + (int64_t)j * n];
+        __syncthreads();
+        for (int e = tid; e < (n - j - 1) * k; e += nt) {
+            const int l = j + 1 + e % (n - j - 1), r = e / (n - j - 1);
+            x[l + r * ldx] = fma(-RG[j + (int64_t)l * n], x[j + r * ldx], x[l + r * ldx]);
+        }
+        __syncthreads();
+    }
+    // backward twice: R_G y = z, then R_s x = y  (y_j = v_j / R_jj, v_l -= R_lj y_j for l < j)
+    for (int pass = 0; pass < 2; ++pass) {
+        const double *R = pass == 0 ? RG : Rs;
+        for (int j = n - 1; j >= 0; --j) {
+            for (int r = tid; r < k; r += nt) x[j + r * ldx] /= R[j + (int64_t)j * n];
+            __syncthreads();
+            for (int e = tid; e < j * k; e += nt) {
+                const int l = e % j, r = e / j;
+                x[l + r * ldx] = fma(-R[l + (int64_t)j * n], x[j + r * ldx], x[l + r * ldx]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void k_identity(double *__restrict__ R, int n)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;

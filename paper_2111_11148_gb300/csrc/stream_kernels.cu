@@ -191,13 +191,15 @@ __device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tm
     // combine the row groups in a fixed order (group 0 first)
     double *out = Ypart + (int64_t)bx * s * n;
     if (ngroups == 1) {
+        // threads past the one group (tg < 256) hold no sums: only the group writes
+        if (active)
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+            for (int a = 0; a < 8; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int r = s0 + sb * 8 + a, c = c0 + nb * 4 + b;
-                if (r < s && c < n) out[r + (int64_t)c * s] = acc[a][b];
-            }
+                for (int b = 0; b < 4; ++b) {
+                    const int r = s0 + sb * 8 + a, c = c0 + nb * 4 + b;
+                    if (r < s && c < n) out[r + (int64_t)c * s] = acc[a][b];
+                }
         return;
     }
     double *red = reinterpret_cast<double *>(smem_raw);  // [ngroups][tg][32]

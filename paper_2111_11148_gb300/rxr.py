@@ -69,6 +69,7 @@ def load() -> ctypes.CDLL:
         "rxr_precond_gram": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, i, vp], i),
         "rxr_cholesky": ([vp, vp, i64, i64, vp, i64, vp], i),
         "rxr_apply_rinv": ([vp, vp, i64, i64, i64, vp, i64, i, vp], i),
+        "rxr_lstsq": ([vp, vp, i64, i64, i64, vp, i64, i64, i, i64, u64, vp, i64, i, vp], i),
         "rxr_gram": ([vp, vp, i64, i64, i64, vp, i64, i, vp], i),
         "rxr_orth_error": ([vp, vp, i64, i64, i64, P(d), vp], i),
         "rxr_resid_error": ([vp, vp, i64, i64, i64, vp, i64, vp, i64, P(d), vp], i),
@@ -90,7 +91,7 @@ def exported_symbols() -> list[str]:
                         "rxr_cholqr_async", "rxr_cholqr_host", "rxr_cholqr_batched", "rxr_last_info",
                         "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_sketch_rows", "rxr_xr_factor",
                         "rxr_precond_gram",
-                        "rxr_cholesky", "rxr_apply_rinv", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
+                        "rxr_cholesky", "rxr_apply_rinv", "rxr_lstsq", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
                         "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc")]
 
 
@@ -287,6 +288,20 @@ class Handle:
         if raise_on_error:
             _check(code, "rxr_cholesky")
         return R, code
+
+    def lstsq(self, A, b, variant="qr", s=None, seed=0, prec="fp64", stream=None, raise_on_error=True):
+        """x = argmin ||A x - b|| (Section 5.2's preconditioned normal equations);
+        b is m or m x k (column-major CUDA tensors).  Returns (x, status)."""
+        m, n = A.shape
+        s = 2 * n if s is None else int(s)
+        b2 = b.reshape(m, 1) if b.dim() == 1 else b
+        k = b2.shape[1]
+        x = empty_colmajor(n, k, device=A.device)
+        code = load().rxr_lstsq(self._h, _ptr(A), m, n, _ld(A), _ptr(b2), k, _ld(b2) if k > 1 or b.dim() == 2 else m,
+                                _VARIANTS[variant], s, seed, _ptr(x), _ld(x), _PRECS[prec], _stream(stream))
+        if raise_on_error:
+            _check(code, "rxr_lstsq")
+        return (x[:, 0] if b.dim() == 1 else x), code
 
     def apply_rinv(self, X, R, prec="fp64", stream=None):
         """X <- X R^{-1} in place (the Q of a CholeskyQR pass); returns X."""

@@ -89,7 +89,8 @@ def test_philox_matches_curand():
 
 # ------------------------------------------------------------------ sketch
 @pytest.mark.parametrize("m,n,s", [(1, 1, 1), (63, 3, 7), (64, 16, 32), (1000, 16, 33), (4097, 64, 128),
-                                   (3000, 70, 140), (2500, 128, 256), (700, 5, 300)])
+                                   (3000, 70, 140), (2500, 128, 256), (700, 5, 300), (2100, 100, 200),
+                                   (1000, 40, 128), (900, 52, 104), (1500, 100, 256)])
 def test_sketch_parity(h, m, n, s):
     A = usv_matrix(m, n, 1e3, seed=m + n)
     Y = to_host(h.sketch(to_dev(A), s, seed=7))
