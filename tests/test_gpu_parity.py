@@ -422,3 +422,18 @@ def test_host_entry_point_split_matches_device(h, m, n):
     Q, R, code = h.cholqr(to_dev(A), variant="qr", seed=3, prec="split")
     assert code == 0
     assert np.array_equal(Qh, to_host(Q)) and np.array_equal(Rh, to_host(R))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+@pytest.mark.parametrize("m,n", [(2100, 100), (1000, 40), (3000, 70), (900, 52), (5000, 64), (4000, 128),
+                                 (3000, 33), (700, 1)])
+def test_preconditioner_quality(h, prec, m, n):
+    # Theorem 3.4: with a Gaussian sketch of s = 2n rows, X = A R_s^{-1} is well
+    # conditioned whatever cond(A) is.  The final QR is unique, so a weak
+    # preconditioner would not show in the factorisation tests; this does.
+    A = usv_matrix(m, n, 1e8, seed=n + 7)
+    Y = h.sketch(to_dev(A), 2 * n, seed=3, prec=prec)
+    Rs, code = h.xr_factor(Y, "qr")
+    assert code == 0
+    X = np.linalg.solve(to_host(Rs).T, A.T).T
+    assert np.linalg.cond(X) <= 30
