@@ -436,11 +436,13 @@ def e2e_leg(h, A_np, args, world):
     hR = torch.empty((N, N), dtype=torch.float64).pin_memory().numpy().T
     for _ in range(2):
         h.cholqr_host(hA, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=hQ, R=hR)
-    e_steps = max(2, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
+    e_steps = max(3, min(args.steps, 7))
+    times = []
+    for _ in range(e_steps):  # each call is blocking; the median of the calls' wall-clock times
+        t0 = time.perf_counter()
         h.cholqr_host(hA, variant=args.variant, s=S, seed=SEED, passes=PASSES, prec=args.prec, Q=hQ, R=hR)
-    e2e_s = (time.perf_counter() - t0) / e_steps
+        times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(times)
     return {"value": world * b_alg(M, N, PASSES) / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * M * N,
             "d2h_bytes_per_step": 8 * M * N + 8 * N * N}
 
