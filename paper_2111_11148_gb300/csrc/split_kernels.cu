@@ -2511,7 +2511,7 @@ __global__ void __launch_bounds__(256, 3) k_apply_delta(double *X, int64_t ldx, 
 }
 
 static void delta_launch(int sms, double *X, int64_t ldx, int64_t m, int n, const float *Ef, int64_t tiles,
-                         const int *sel, const CUtensorMap &, int, RxrStatus *status, cudaStream_t st)
+                         const int *sel, RxrStatus *status, cudaStream_t st)
 {
     k_apply_delta<<<(unsigned)std::min<int64_t>(3 * (int64_t)sms, tiles), 256, delta_smem_bytes(n), st>>>(
         X, ldx, m, n, Ef, tiles, sel, status);
@@ -2624,7 +2624,7 @@ int ozaki_apply_rows(Plan &p, double *X, int64_t ldx, int64_t r0, int64_t rows, 
     const int64_t tiles = cdiv64(rows, kAqM);
     CUtensorMap mx;
     const int use_tma = encode_tile_map(&mx, Xr, rows, n, ldx, kAqM, n) ? 1 : 0;
-    delta_launch(p.sms, Xr, ldx, rows, n, split_delta(p), tiles, sel, mx, use_tma, p.status, st);
+    delta_launch(p.sms, Xr, ldx, rows, n, split_delta(p), tiles, sel, p.status, st);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
     k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, Xr, ldx, rows, n, p.W, p.n, tiles, sel, 0, nullptr,
                                                     p.status);
