@@ -304,6 +304,23 @@ def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=
     return {"ms": ms, "stages_ms": stages, "orth": h.orth_error(Q), "resid": h.resid_error(A, Q, R), "clocks": clk}
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The whole job's step time: the slowest rank's (each rank factorises its
+    own replica of the workload; no data-path collective)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms: float, world: int) -> float:
+    """Whole-job throughput: every rank's algorithmic bytes over the slowest time."""
+    return world * b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9
+
+
 def gpu_arm(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -332,12 +349,8 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
         dist.barrier()
     main = time_path(h, A, Q, R, args.prec, args, dev, stream, args.steps, warm, sample_clocks=True)
     ref = None if args.no_compare else time_path(h, A, Q, R, other, args, dev, stream, max(2, args.steps // 2), warm)
-    ms = main["ms"]
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(main["ms"], dist, dev)
+    value = job_value(ms, world)
 
     e2e = None if args.no_e2e else e2e_leg(h, A_np, args, world)
     cpu = None
