@@ -323,19 +323,19 @@ constexpr size_t kOzSmem = (size_t)kOzDigits * (kOzTile + kOzBTile);
 // 256^(6-q) with balanced digits alpha_1..6 in [-128, 127], byte k of U is
 // alpha_(6-k) + 128 (k = 0..5) and U >> 48 (arithmetic) is alpha_0: the
 // carries of the offset do the balancing.
+// Without branches: with x = 4 m53 (< 2^55) and sh = emax - ea >= 0, T = x / 2^sh
+// rounded to nearest (halves away from zero, on the magnitude) is
+// (x + 2^(sh-1)) >> sh, which is exact for sh <= 2 and zero from sh = 56 on.
 __device__ __forceinline__ unsigned long long digits_offset(unsigned long long bits, int emax)
 {
-    long long T = 0;
     const int ea = (int)((bits >> 52) & 0x7FF);
-    if (ea > 0 && ea < 0x7FF) {
-        const long long m53 = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-        const int sh = emax - ea;
-        if (sh <= 2)
-            T = m53 << (2 - sh);
-        else if (sh < 56)
-            T = (m53 + (1ll << (sh - 3))) >> (sh - 2);
-        if (bits >> 63) T = -T;
-    }
+    const int sh = emax - ea;
+    const unsigned long long x = ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2;
+    const int s = min(max(sh, 0), 63);
+    unsigned long long t = (x + ((1ull << s) >> 1)) >> s;
+    if (sh < 0) t = x << min(-sh, 8);  // only if emax is not the largest exponent
+    long long T = (bits >> 63) ? -(long long)t : (long long)t;
+    T = (ea > 0 && ea < 0x7FF) ? T : 0;
     return (unsigned long long)(T + 0x808080808080ll);
 }
 
