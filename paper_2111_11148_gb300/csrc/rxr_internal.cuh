@@ -163,10 +163,9 @@ __device__ __forceinline__ double rxr_f2d_exact(float f)
     const uint32_t b = __float_as_uint(f);
     const uint32_t sign = b & 0x80000000u;
     const uint32_t mag = b & 0x7FFFFFFFu;
-    if (mag == 0u) return __hiloint2double((int)sign, 0);
     const uint32_t e = (mag >> 23) + (1023u - 127u);
     const uint32_t mant = mag & 0x007FFFFFu;
-    const uint32_t hi = sign | (e << 20) | (mant >> 3);
+    const uint32_t hi = (mag == 0u) ? sign : (sign | (e << 20) | (mant >> 3));  // a select, not a branch
     const uint32_t lo = mant << 29;
     return __hiloint2double((int)hi, (int)lo);
 }

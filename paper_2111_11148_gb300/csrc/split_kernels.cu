@@ -365,10 +365,11 @@ __device__ __forceinline__ double f2d_pow2(float f, int be)
     const uint32_t u = __float_as_uint(f);
     const int e8 = (int)((u >> 23) & 0xFFu);
     const int e = e8 - 127 + be;
-    if (e8 == 0 || e <= 0) return 0.0;
     const uint32_t sign = u & 0x80000000u;
-    if (e >= 2047) return __hiloint2double((int)(sign | 0x7FF00000u), 0);
-    return __hiloint2double((int)(sign | ((uint32_t)e << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+    const bool zero = (e8 == 0) | (e <= 0), inf = e >= 2047;  // selects, not branches
+    const uint32_t hi = zero ? 0u : inf ? (sign | 0x7FF00000u) : (sign | ((uint32_t)e << 20) | ((u & 0x7FFFFFu) >> 3));
+    const uint32_t lo = (zero | inf) ? 0u : (u << 29);
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // Digit q of two offset forms as one packed FP16 pair (value a in the low
