@@ -127,12 +127,10 @@ __device__ __forceinline__ void rxr_sincos2pi(uint32_t n, float &s_out, float &c
     cp = __fmaf_rn(cp, f2, c4);
     cp = __fmaf_rn(cp, f2, c2);
     const float cs = __fmaf_rn(cp, f2, c0);
-    switch (q & 3) {
-    case 0: s_out = sn; c_out = cs; break;
-    case 1: s_out = cs; c_out = -sn; break;
-    case 2: s_out = -sn; c_out = -cs; break;
-    default: s_out = -cs; c_out = sn; break;
-    }
+    // quadrant q: (sin, cos) = (sn, cs), (cs, -sn), (-sn, -cs), (-cs, sn), by selects
+    const float a = (q & 1) ? cs : sn, b = (q & 1) ? sn : cs;
+    s_out = (q & 2) ? -a : a;
+    c_out = ((q + 1) & 2) ? -b : b;
 }
 
 // Four N(0,1) values for sketch rows 4k..4k+3 of column i (row i of A):
