@@ -78,12 +78,10 @@ __device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32
 __device__ __forceinline__ float rxr_logf(float u)
 {
     const uint32_t b = __float_as_uint(u);
-    int e = (int)((b >> 23) & 0xFFu) - 127;
-    float x = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
-    if (__float_as_uint(x) > 0x3FB504F3u) {  // above sqrt(2): halve (exact)
-        x = __fmul_rn(x, 0.5f);
-        e += 1;
-    }
+    const uint32_t xb = (b & 0x007FFFFFu) | 0x3F800000u;
+    const bool big = xb > 0x3FB504F3u;  // above sqrt(2): halve (exact; the exponent field drops by one)
+    const int e = (int)((b >> 23) & 0xFFu) - 127 + (big ? 1 : 0);
+    const float x = __uint_as_float(big ? xb - 0x00800000u : xb);
     const float t = __fdiv_rn(__fsub_rn(x, 1.0f), __fadd_rn(x, 1.0f));
     const float t2 = __fmul_rn(t, t);
     float p = (float)(2.0 / 13.0);
