@@ -39,8 +39,8 @@ WORKLOAD = "rQR-CholeskyQR2 m=2^22 n=64 s=128 kappa=1e10 FP64"
 # ncu capture at m = 2^19 scaled by 8 rows-for-rows (profiles/k_subst_gram_precond_m524288_n64.md)
 TRAFFIC_PG = (268.552704e6 + 225.660672e6) * 8
 # DRAM bytes (read + write) of one k_subst_fused launch at m = 2^22, n = 64: the ncu capture at
-# m = 2^19 (268.66 MB read + 217.17 MB written) scaled by the 8x rows (traffic grows with the rows)
-TRAFFIC_SUBST = (268.662016e6 + 217.168640e6) * 8
+# m = 2^19 (268.58 MB read + 216.93 MB written) scaled by the 8x rows (traffic grows with the rows)
+TRAFFIC_SUBST = (268.584960e6 + 216.926208e6) * 8
 HBM_GBS = 6795.5  # measured copy bandwidth of this GPU pool (STREAM-style copy)
 
 
