@@ -297,6 +297,33 @@ def test_invalid_arguments(h):
     assert lib.rxr_cholqr(h._h, p(A), 100, 4, 100, 1, 8, 0, 2, None, 100, None, 4, 0, None) == -9
 
 
+def test_invalid_arguments_of_the_later_entry_points(h):
+    lib = rxr.load()
+    A = to_dev(usv_matrix(100, 4, 10, seed=0))
+    b = to_dev(np.ones((100, 2)))
+    Q = rxr.empty_colmajor(100, 4)
+    x = rxr.empty_colmajor(4, 2)
+    Y = rxr.empty_colmajor(8, 4)
+    R = to_dev(np.eye(4))
+    p = lambda t: t.data_ptr()
+    # row extraction only with a sketch: not with RXR_NONE or RXR_SHIFTED
+    assert lib.rxr_cholqr(h._h, p(A), 100, 4, 100, 2 | 16, 8, 0, 2, p(Q), 100, None, 4, 0, None) == -5
+    assert lib.rxr_cholqr(h._h, p(A), 100, 4, 100, 3 | 16, 8, 0, 3, p(Q), 100, None, 4, 0, None) == -5
+    # least squares: k in [1, 64], ldb >= m, LU or QR, x non-null
+    ls = lambda k, ldb, v, xp: lib.rxr_lstsq(h._h, p(A), 100, 4, 100, p(b), k, ldb, v, 8, 0, xp, 4, 0, None)
+    assert ls(0, 100, 1, p(x)) == -7
+    assert ls(65, 100, 1, p(x)) == -7
+    assert ls(2, 99, 1, p(x)) == -8
+    assert ls(2, 100, 2, p(x)) == -9
+    assert ls(2, 100, 1, None) == -12
+    # row sketch: s >= 1, ldy >= s
+    assert lib.rxr_sketch_rows(h._h, p(A), 100, 4, 100, 0, 0, p(Y), 8, None) == -6
+    assert lib.rxr_sketch_rows(h._h, p(A), 100, 4, 100, 8, 0, p(Y), 7, None) == -9
+    # X R^{-1}: ldx >= m, ldr >= n
+    assert lib.rxr_apply_rinv(h._h, p(Q), 100, 4, 99, p(R), 4, 0, None) == -5
+    assert lib.rxr_apply_rinv(h._h, p(Q), 100, 4, 100, p(R), 3, 0, None) == -7
+
+
 # ------------------------------------------------------------------ async / graph / host / batched
 def test_async_status_and_graph_capture(h):
     A = to_dev(usv_matrix(4000, 32, 1e10, seed=3))
