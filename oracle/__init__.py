@@ -6,7 +6,9 @@ path; the product never falls back to it.
 
 The arithmetic lives in ``rxr_oracle.c`` (plain C, compiled with
 -ffp-contract=off); this module compiles it on demand with gcc and wraps it
-with ctypes.  All matrices are float64 and column-major (Fortran order).
+with ctypes.  All matrices are float64 and column-major (Fortran order).  The
+randomized SVD of Section 5.1 (``rsvd``) is composed here from the C
+factorisation and library steps (sparse/dense products, LAPACK's SVD).
 """
 from __future__ import annotations
 
@@ -318,3 +320,45 @@ def dot2(x, y) -> float:
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     return float(_load().rxo_dot2(_p(x), _p(y), x.size))
+
+
+def rsvd(A, X: np.ndarray, K: int, variant: int = VARIANT_QR, s: int | None = None, seed: int = 0,
+         passes: int = 2, orth: str = "rxr") -> Result:
+    """Randomized SVD with power iteration (Algorithm 7, Section 5.1) of an
+    m x n matrix A (a scipy.sparse matrix or an ndarray) from the n x k
+    starting block X:
+
+        Y = orth(A X); K times: Y = orth(A^T Y), Y = orth(A Y);
+        B = Y^T A (k x n) = U_B diag(S) V^T by LAPACK's SVD; U = Y U_B.
+
+    orth="rxr": the j-th orthonormalisation (j = 0, 1, ...) is the Q factor of
+    rxr_cholqr(., variant, s (default 2k), seed + j, passes), the replacement
+    Section 5.1 makes; orth="householder": the Householder QR's Q.  A failed
+    factorisation stops the iteration and its status is returned."""
+    X = _f64(X)
+    k = X.shape[1]
+    s = 2 * k if s is None else int(s)
+    calls = 0
+
+    def orth_(Y):
+        nonlocal calls
+        Y = _f64(Y)
+        if orth == "householder":
+            return householder_qr(Y)[0], 0
+        r = rxr_cholqr(Y, variant, s, seed + calls, passes)
+        calls += 1
+        return r.Q, r.status
+
+    Y, st = orth_(A @ X)
+    for _ in range(int(K)):
+        if st:
+            break
+        Y, st = orth_(A.T @ Y)
+        if st:
+            break
+        Y, st = orth_(A @ Y)
+    if st:
+        return Result(status=st, U=None, S=None, V=None, Q=None, calls=calls)
+    B = np.asarray(A.T @ Y).T  # Y^T A
+    Ub, S, Vt = np.linalg.svd(B, full_matrices=False)
+    return Result(status=0, U=np.asfortranarray(Y @ Ub), S=S, V=np.asfortranarray(Vt.T), Q=Y, calls=calls)

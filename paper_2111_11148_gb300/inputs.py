@@ -14,7 +14,17 @@ moved into Q), which gives the same distribution of singular subspaces.
 
 Random bits come from numpy's Philox counter-based generator, keyed by
 (seed, stream): stream 1 feeds U and stream 2 feeds V.  Stream 0 is reserved
-for the sketch matrix Omega, which the method draws itself.
+for the sketch matrix Omega, which the method draws itself.  Stream 3 feeds
+the batch shapes, stream 4 the randomized SVD's starting block and streams 5-6
+the sparse operators.
+
+Sparse operators for the randomized SVD of Section 5.1 (the paper's test
+matrices come from the SuiteSparse collection, which is not available here):
+``sparse_operator`` draws square matrices with the row-length statistics of
+that table (a nonzero diagonal plus Poisson-distributed off-diagonal entries
+at uniform random columns, N(0,1) values), and ``planted_operator`` builds a
+sparse matrix with a prescribed spectrum (randomly permuted b x b blocks
+U_j diag(sigma_j) V_j^T, Haar U_j and V_j), whose singular values are known.
 """
 from __future__ import annotations
 
@@ -22,7 +32,8 @@ import math
 
 import numpy as np
 
-__all__ = ["sigma_profile", "usv_matrix", "batch_specs", "BatchSpec"]
+__all__ = ["sigma_profile", "usv_matrix", "batch_specs", "BatchSpec", "Csr", "sparse_operator",
+           "planted_operator", "start_block"]
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:
@@ -112,3 +123,94 @@ def batch_specs(count: int = 512, seed: int = 0, *, log2m=(12, 18), ns=(8, 16, 3
         kappa = 10.0 ** rng.uniform(*log10k)
         out.append(BatchSpec(m, n, kappa, i))
     return out
+
+
+class Csr:
+    """A sparse m x n matrix in compressed sparse row form (indptr int64[m+1],
+    indices int32[nnz] sorted within each row, data float64[nnz]), together
+    with the same form of its transpose: the randomized SVD multiplies by both
+    A and A^T."""
+
+    __slots__ = ("m", "n", "indptr", "indices", "data", "t_indptr", "t_indices", "t_data")
+
+    def __init__(self, m, n, indptr, indices, data):
+        self.m, self.n = int(m), int(n)
+        self.indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+        self.indices = np.ascontiguousarray(indices, dtype=np.int32)
+        self.data = np.ascontiguousarray(data, dtype=np.float64)
+        # transpose by a stable counting sort on the column index
+        order = np.argsort(self.indices, kind="stable")
+        rows = np.repeat(np.arange(self.m, dtype=np.int64), np.diff(self.indptr))
+        counts = np.bincount(self.indices, minlength=self.n)
+        self.t_indptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        self.t_indices = rows[order].astype(np.int32)
+        self.t_data = self.data[order]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indptr[-1])
+
+    def scipy(self):
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((self.data, self.indices, self.indptr), shape=(self.m, self.n))
+
+    def dense(self) -> np.ndarray:
+        a = np.zeros((self.m, self.n), order="F")
+        rows = np.repeat(np.arange(self.m), np.diff(self.indptr))
+        a[rows, self.indices] = self.data
+        return a
+
+
+def _csr_from_coo(m, n, rows, cols, vals) -> Csr:
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    keep = np.ones(rows.size, dtype=bool)
+    keep[1:] = (rows[1:] != rows[:-1]) | (cols[1:] != cols[:-1])  # first of each duplicate
+    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    indptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))])
+    return Csr(m, n, indptr, cols, vals)
+
+
+def sparse_operator(m: int, nnz_per_row: float, seed: int = 0) -> Csr:
+    """Square m x m sparse matrix: a diagonal entry in every row plus
+    Poisson(nnz_per_row - 1) off-diagonal entries at uniform random columns
+    (duplicates merged), all values N(0,1)."""
+    if m < 1 or nnz_per_row < 1:
+        raise ValueError("need m >= 1 and nnz_per_row >= 1")
+    rng = _rng(seed, 5)
+    extra = rng.poisson(nnz_per_row - 1.0, m)
+    rows = np.concatenate([np.arange(m, dtype=np.int64), np.repeat(np.arange(m, dtype=np.int64), extra)])
+    cols = np.concatenate([np.arange(m, dtype=np.int64), rng.integers(0, m, int(extra.sum()))])
+    vals = rng.standard_normal(rows.size)
+    return _csr_from_coo(m, m, rows, cols, vals)
+
+
+def planted_operator(sigma, block: int = 4, seed: int = 0) -> Csr:
+    """Square sparse matrix with singular values ``sigma`` (length a multiple
+    of ``block``): the values are shuffled into blocks of ``block``, block j is
+    U_j diag(sigma_j) V_j^T with Haar U_j, V_j, and the rows and columns of
+    the block-diagonal matrix are then permuted at random."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    n = sigma.size
+    if n % block:
+        raise ValueError("len(sigma) must be a multiple of block")
+    rng = _rng(seed, 6)
+    vals = sigma[rng.permutation(n)].reshape(-1, block)
+    nb = n // block
+    g = rng.standard_normal((2, nb, block, block))
+    qu, ru = np.linalg.qr(g[0])
+    qv, rv = np.linalg.qr(g[1])
+    qu = qu * np.sign(np.diagonal(ru, axis1=1, axis2=2))[:, None, :]
+    qv = qv * np.sign(np.diagonal(rv, axis1=1, axis2=2))[:, None, :]
+    blocks = np.einsum("jab,jb,jcb->jac", qu, vals, qv)  # U_j diag(s_j) V_j^T
+    pr, pc = rng.permutation(n), rng.permutation(n)
+    j, a, c = np.meshgrid(np.arange(nb), np.arange(block), np.arange(block), indexing="ij")
+    rows = pr[j * block + a].ravel()
+    cols = pc[j * block + c].ravel()
+    return _csr_from_coo(n, n, rows, cols, blocks.ravel())
+
+
+def start_block(n: int, k: int, seed: int = 0) -> np.ndarray:
+    """The randomized SVD's starting block X (n x k, column-major, N(0,1))."""
+    return np.asfortranarray(_rng(seed, 4).standard_normal((n, k)))
