@@ -270,6 +270,144 @@ def lstsq_arm(args, rank: int, world: int, local_rank: int):
     h.close()
 
 
+# the randomized SVD's stand-in for the sparsest matrix of Section 5.1's table
+# (1,447,360 rows and columns, 3.81 nonzeros per row)
+RSVD_M, RSVD_D, RSVD_K, RSVD_ITERS = 1447360, 3.81, 20, 4
+
+
+def rsvd_bytes_per_iter(m, nnz, k, passes):
+    """Algorithmic bytes of one power iteration (A^T Y, orth, A Y, orth): per
+    sparse product the CSR arrays (12 bytes a nonzero, 8 a row), one read of
+    the k-column block and one write of the product; per transpose a read and a
+    write of the block; per orthonormalisation 8 m k (P + 3)."""
+    spmm = 12.0 * nnz + 8.0 * (m + 1) + 2 * 8.0 * m * k
+    return 2 * spmm + 2 * 16.0 * m * k + 2 * b_alg(m, k, passes)
+
+
+def rsvd_launches(prec, k, iters):
+    """Kernels one rxr_rsvd call launches: per orthonormalisation the
+    factorisation's kernels (no R copy but for the last), the status merge, a
+    transpose and a sparse product; then the Jacobi SVD and two products."""
+    c = launches_per_step(prec, k, RSVD_M)
+    return (2 * iters + 2) * (c + 2) + 4
+
+
+def rsvd_oracle_ms_per_iter(k: int, rows: int = 2**18) -> tuple[float, int]:
+    """The oracle's time for one power iteration on a 2^18-row operator of the
+    same density, scaled to the workload's rows (the work grows with the rows)."""
+    import oracle
+    from paper_2111_11148_gb300.inputs import sparse_operator, start_block
+
+    P = sparse_operator(rows, RSVD_D, seed=SEED)
+    A = P.scipy()
+    X = start_block(rows, k, SEED)
+    t0 = time.perf_counter()
+    oracle.rsvd(A, X, 0, seed=SEED)
+    t1 = time.perf_counter()
+    oracle.rsvd(A, X, 1, seed=SEED)
+    t2 = time.perf_counter()
+    return ((t2 - t1) - (t1 - t0)) * 1e3 * RSVD_M / rows, rows
+
+
+def rsvd_arm(args, rank: int, world: int, local_rank: int):
+    """Randomized SVD with power iteration (Algorithm 7, Section 5.1) of the
+    sparse stand-in, each orthonormalisation by rQR-CholeskyQR2: the metric is
+    the time of one power iteration, (t(K) - t(0)) / K from calls with K and
+    with no iterations, as Section 5.1's table reports it."""
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+    from paper_2111_11148_gb300.inputs import sparse_operator, start_block
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    k = args.k or RSVD_K
+    t0 = time.perf_counter()
+    P = sparse_operator(RSVD_M, RSVD_D, seed=SEED)
+    X_np = start_block(RSVD_M, k, SEED)
+    gen_s = time.perf_counter() - t0
+    A = rxr.DeviceCsr.from_host(P, device=dev)
+    X = rxr.colmajor(torch.from_numpy(X_np).to(dev))
+    h = rxr.Handle(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    U = rxr.empty_colmajor(RSVD_M, k, device=dev)
+    V = rxr.empty_colmajor(RSVD_M, k, device=dev)
+    S = torch.empty(k, dtype=torch.float64, device=dev)
+    call = lambda iters: h.rsvd(A, X, iters, variant=args.variant, seed=SEED, prec=args.prec, U=U, S=S, V=V)
+    for _ in range(max(3, args.warmup)):
+        call(RSVD_ITERS)
+        call(0)
+    torch.cuda.synchronize(dev)
+
+    def timed(iters, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            call(iters)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_k = timed(RSVD_ITERS, args.steps)
+    t_0 = timed(0, args.steps)
+    clk = clocks.stop()
+    ms_iter = max_over_ranks((t_k - t_0) / RSVD_ITERS, None, dev)
+    # accuracy of the result: orthonormal factors and A^T U = V diag(S) on sampled rows
+    call(RSVD_ITERS)
+    Uh, Sh, Vh = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    rows = np.random.default_rng(0).integers(0, RSVD_M, 2000)
+    AtU = np.stack([P.t_data[P.t_indptr[i]:P.t_indptr[i + 1]] @ Uh[P.t_indices[P.t_indptr[i]:P.t_indptr[i + 1]]]
+                    for i in rows])
+    ident = float(np.max(np.abs(AtU - Vh[rows] * Sh)) / Sh[0])
+    # end to end: the operator and X from host memory, U, S, V back to host memory
+    def e2e_call():
+        Ad = rxr.DeviceCsr.from_host(P, device=dev)
+        Xd = rxr.colmajor(torch.from_numpy(X_np).to(dev))
+        Ue, Se, Ve, _ = h.rsvd(Ad, Xd, RSVD_ITERS, variant=args.variant, seed=SEED, prec=args.prec)
+        return Ue.cpu(), Se.cpu(), Ve.cpu()
+
+    e2e_call()
+    torch.cuda.synchronize(dev)
+    w0 = time.perf_counter()
+    for _ in range(3):
+        e2e_call()
+    e2e_ms = (time.perf_counter() - w0) * 1e3 / 3
+    h2d = P.indptr.nbytes + P.indices.nbytes + P.data.nbytes + P.t_indptr.nbytes + P.t_indices.nbytes
+    h2d += P.t_data.nbytes + X_np.nbytes
+    d2h = 8 * (2 * RSVD_M * k + k)
+    balg = rsvd_bytes_per_iter(RSVD_M, P.nnz, k, PASSES)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        cms, crow = rsvd_oracle_ms_per_iter(k)
+        cpu = {"value": cms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"one power iteration of the oracle on a {crow}-row operator of the same density, "
+                         f"scaled by rows to {RSVD_M}"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "randomized SVD (Algorithm 7) time per power iteration", "value": ms_iter, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_iter,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+bf16" if args.prec == "split" else "f64", "data": "synthetic",
+            "config": {"workload": f"RSVD power iteration, sparse {RSVD_M}x{RSVD_M} with {RSVD_D} nonzeros/row "
+                                   f"(stand-in for Section 5.1's sparsest matrix), k={k}, orth = "
+                                   f"{'rLU' if args.variant == 'lu' else 'rQR'}-CholeskyQR2",
+                       "m": RSVD_M, "nnz": P.nnz, "k": k, "iters_timed": RSVD_ITERS, "generation_s": gen_s,
+                       "l2": "working set (CSR + 5 blocks of m x k) larger than L2"},
+            "roofline": {"bound": "hbm", "kernel": "whole power iteration", "achieved": balg / (ms_iter * 1e-3) / 1e9,
+                         "peak": HBM_GBS, "unit": "GB/s", "frac": balg / (ms_iter * 1e-3) / 1e9 / HBM_GBS,
+                         "traffic": None},
+            "e2e": {"value": e2e_ms, "unit": f"ms per call with {RSVD_ITERS} iterations", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "ms_call_iters": {str(RSVD_ITERS): t_k, "0": t_0},
+            "accuracy": {"orth_U": h.orth_error(U), "orth_V": h.orth_error(V), "AtU_minus_VS_sampled": ident},
+            "gpu_launches": args.steps * (rsvd_launches(args.prec, k, RSVD_ITERS) + rsvd_launches(args.prec, k, 0)),
+            "cpu_baseline": cpu, "clocks": clk,
+        }), flush=True)
+    h.close()
+
+
 def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=False):
     """Time `steps` factorisations (after `warmup`) with CUDA events on the
     launching stream; then per-stage event times and the accuracy."""
@@ -509,7 +647,8 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (s = 2n)")
     ap.add_argument("--kappa", type=float, default=None, help="condition number of A")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "lstsq"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "lstsq", "rsvd"])
+    ap.add_argument("--k", type=int, default=None, help="block width of the rsvd workload (default 20)")
     ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
     args = ap.parse_args()
     global M, N, S, KAPPA, WORKLOAD, PASSES
@@ -539,6 +678,9 @@ def main():
         return
     if args.workload == "lstsq":
         lstsq_arm(args, rank, world, local_rank)
+        return
+    if args.workload == "rsvd":
+        rsvd_arm(args, rank, world, local_rank)
         return
     gpu_arm(args, rank, world, local_rank)
 

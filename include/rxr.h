@@ -85,7 +85,8 @@ enum {
     RXR_ERR_CUDA = 4,            /* a CUDA runtime call failed (no GPU, bad pointer, ...) */
     RXR_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
     RXR_ERR_NOMEM = 6,           /* the library could not allocate its workspace */
-    RXR_ERR_UNSUPPORTED = 7      /* valid arguments outside what this build supports */
+    RXR_ERR_UNSUPPORTED = 7,     /* valid arguments outside what this build supports */
+    RXR_ERR_BAD_SPARSE = 8       /* rxr_rsvd: a CSR row pointer or column index out of range */
 };
 
 /* Limits of this build. */
@@ -246,6 +247,35 @@ RXR_API int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_
 RXR_API int rxr_lstsq(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *b, int64_t k,
                       int64_t ldb, int variant, int64_t s, uint64_t seed, double *x, int64_t ldx, int prec,
                       void *stream);
+
+/* Randomized SVD with power iteration (Algorithm 7, Section 5.1) of a sparse
+ * m x n matrix A, every orthonormalisation done by this library's CholeskyQR
+ * (the replacement for Householder QR that Section 5.1 makes):
+ *   Y = orth(A X); `iters` times: Y = orth(A^T Y), Y = orth(A Y);
+ *   then B = Y^T A through Z = A^T Y = Q_z R_z (one more orth), R_z = U_r S V_r^T
+ *   by one-sided Jacobi, and U = Y V_r, V = Q_z U_r, so that
+ *   Y Y^T A = U diag(S) V^T, A^T U = V diag(S), S descending.
+ * Orthonormalisation j (j = 0 .. 2 iters + 1) is rxr_cholqr(., variant, s,
+ * seed + j, passes, prec) of an m x k or n x k block.
+ * A in compressed sparse row form, DEVICE arrays: a_ptr int64[m+1] (a_ptr[0]
+ * = 0, nondecreasing, a_ptr[m] = nnz), a_idx int32[nnz] column indices in
+ * [0, n), a_val double[nnz]; the same form of A^T in t_ptr int64[n+1],
+ * t_idx int32[nnz] (row indices of A) and t_val double[nnz] (the caller
+ * builds A^T: the iteration multiplies by both).  An index or row pointer out
+ * of range is reported as RXR_ERR_BAD_SPARSE (the arrays themselves must have
+ * the stated lengths).  X: the n x k starting block (ldx >= n), read-only;
+ * 1 <= k <= min(m, n), k <= 128; 0 <= iters <= 1000; variant, s (>= k),
+ * passes and prec as for rxr_cholqr.  Outputs (device): U (m x k, ldu >= m),
+ * S (k), V (n x k, ldv >= n).  The handle keeps 2 (m + n) k + max(m, n) k
+ * doubles of scratch.  A rank of A below k makes a factorisation fail.
+ * Blocking; 0, the first failure of the factorisations (RXR_ERR_*; for a
+ * breakdown rxr_last_info gives its pass and column), RXR_ERR_BAD_SPARSE, or a
+ * negative argument error (-i: argument i). */
+RXR_API int rxr_rsvd(rxr_handle h, int64_t m, int64_t n, const int64_t *a_ptr, const int32_t *a_idx,
+                     const double *a_val, const int64_t *t_ptr, const int32_t *t_idx, const double *t_val,
+                     int64_t nnz, const double *X, int64_t ldx, int64_t k, int iters, int variant, int64_t s,
+                     uint64_t seed, int passes, int prec, double *U, int64_t ldu, double *S, double *V, int64_t ldv,
+                     void *stream);
 
 /* Upper Cholesky factor R (R^T R = G; reads the upper triangle of G).
  * Blocking; returns 0 or RXR_ERR_CHOL_BREAKDOWN (column in rxr_last_info). */

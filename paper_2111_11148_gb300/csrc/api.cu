@@ -89,6 +89,8 @@ struct rxr_ctx {
     size_t eval_bytes = 0;
     double *ls_buf = nullptr;  // least squares: B^T b partial sums and c
     size_t ls_bytes = 0;
+    double *sv_buf = nullptr;  // randomized SVD: the blocks, the row-major copy and the k x k factors
+    size_t sv_bytes = 0;
     void *h_stage = nullptr;  // pinned host staging of batched job tables
     size_t h_stage_bytes = 0;
     // the _host entry point's copy stream and its chunk events
@@ -370,6 +372,7 @@ int set_kernel_attrs()
         set_batched_smem(big),
         set_wide_smem(),
         set_small_smem(),
+        set_rsvd_smem(),
     };
     for (cudaError_t e : es)
         if (e != cudaSuccess) {
@@ -792,6 +795,7 @@ int rxr_destroy(rxr_handle h)
     if (h->dR) cudaFree(h->dR);
     if (h->eval_buf) cudaFree(h->eval_buf);
     if (h->ls_buf) cudaFree(h->ls_buf);
+    if (h->sv_buf) cudaFree(h->sv_buf);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     for (int k = 0; k < kTimers; ++k)
         for (int j = 0; j < 2; ++j)
@@ -1096,6 +1100,7 @@ const char *rxr_status_string(int code)
     case RXR_ERR_TIMEOUT: return "bounded device wait timed out";
     case RXR_ERR_NOMEM: return "workspace allocation failed or too small";
     case RXR_ERR_UNSUPPORTED: return "arguments outside what this build supports";
+    case RXR_ERR_BAD_SPARSE: return "sparse matrix row pointer or column index out of range";
     default: return code < 0 ? "invalid argument" : "unknown status";
     }
 }
@@ -1325,6 +1330,97 @@ int rxr_lstsq(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, 
     k_ls_solve<<<1, 512, 0, st>>>(p.Rp, p.Rs, (int)n, (int)k, c, x, ldx, p.status);
     if (launch_ok()) return RXR_ERR_CUDA;
     return finish_blocking(h, p.status, st);
+}
+
+int rxr_rsvd(rxr_handle h, int64_t m, int64_t n, const int64_t *a_ptr, const int32_t *a_idx, const double *a_val,
+             const int64_t *t_ptr, const int32_t *t_idx, const double *t_val, int64_t nnz, const double *X,
+             int64_t ldx, int64_t k, int iters, int variant, int64_t s, uint64_t seed, int passes, int prec,
+             double *U, int64_t ldu, double *S, double *V, int64_t ldv, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (m < 1) return -2;
+    if (n < 1) return -3;
+    if (a_ptr == nullptr) return -4;
+    if (nnz > 0 && a_idx == nullptr) return -5;
+    if (nnz > 0 && a_val == nullptr) return -6;
+    if (t_ptr == nullptr) return -7;
+    if (nnz > 0 && t_idx == nullptr) return -8;
+    if (nnz > 0 && t_val == nullptr) return -9;
+    if (nnz < 0) return -10;
+    if (X == nullptr) return -11;
+    if (ldx < n) return -12;
+    if (k < 1 || k > m || k > n) return -13;
+    if (iters < 0 || iters > 1000) return -14;
+    const int base = variant & ~RXR_SKETCH_ROWS;
+    if ((base == RXR_NONE || base == RXR_SHIFTED) && s < k) s = k;
+    // the factorisations' own checks, for the m x k and the n x k blocks
+    for (int64_t rows : {m, n}) {
+        const int e = check_args(X, rows, k, rows, variant, s, passes, X, rows, nullptr, k, prec);
+        if (e == -5) return -15;
+        if (e == -6) return -16;
+        if (e == -8) return -18;
+        if (e == -13) return -19;
+        if (e) return e;
+    }
+    if (U == nullptr) return -20;
+    if (ldu < m) return -21;
+    if (S == nullptr) return -22;
+    if (V == nullptr) return -23;
+    if (ldv < n) return -24;
+    if (k > kNarrowN || n > INT32_MAX) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    Plan pm, pn;
+    make_plan(pm, m, k, s, prec, h->sms);
+    make_plan(pn, n, k, s, prec, h->sms);
+    if (int e = ensure_ws(h, std::max(pm.bytes, pn.bytes))) return e;
+    bind_plan(pm, h->ws);
+    bind_plan(pn, h->ws);
+    // scratch: status | Y (m x k) | Q (m x k) | Z (n x k) | Q_z (n x k) | row-major
+    // copy (max(m, n) x k) | R_z | U_r | V_r | V_r's Jacobi scratch (k x k each)
+    const int64_t ldm = (m + 1) & ~(int64_t)1, ldn = (n + 1) & ~(int64_t)1;  // even: TMA-compatible rows
+    auto al = [](int64_t d) { return (d + 31) & ~(int64_t)31; };
+    const int64_t o_ym = 32, o_qm = o_ym + al(ldm * k), o_zn = o_qm + al(ldm * k), o_qn = o_zn + al(ldn * k);
+    const int64_t o_xr = o_qn + al(ldn * k), o_rz = o_xr + al(std::max(m, n) * k), o_ur = o_rz + al(k * k);
+    const int64_t o_vr = o_ur + al(k * k), o_vg = o_vr + al(k * k), total = o_vg + al(k * k);
+    if (grow((void **)&h->sv_buf, &h->sv_bytes, (size_t)total * 8)) return RXR_ERR_NOMEM;
+    double *b = h->sv_buf;
+    RxrStatus *acc = (RxrStatus *)b;
+    double *Ym = b + o_ym, *Qm = b + o_qm, *Zn = b + o_zn, *Qn = b + o_qn, *Xr = b + o_xr;
+    double *Rz = b + o_rz, *Ur = b + o_ur, *Vr = b + o_vr, *Vg = b + o_vg;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(acc, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    const int kk = (int)k;
+    int call = 0;
+    // orthonormalisation `call`: Q_b = the Q factor of Y_b by CholeskyQR, seed + call
+    auto orth = [&](const Plan &p, double *Yb, int64_t ld, double *Qb, double *R) -> int {
+        if (int e = enqueue_cholqr(h, p, Yb, ld, variant, seed + (uint64_t)call, passes, Qb, ld, R, kk, st, false))
+            return e;
+        return rsvd_status_keep_enqueue(p.status, acc, call++, st);
+    };
+    auto a_mul = [&](const double *B, int64_t ldb) -> int {  // Y = A B, B n x k
+        if (int e = rsvd_transpose_enqueue(B, ldb, n, kk, Xr, st)) return e;
+        return rsvd_spmm_enqueue(a_ptr, a_idx, a_val, nnz, m, n, Xr, kk, Ym, ldm, acc, st);
+    };
+    auto at_mul = [&](const double *B, int64_t ldb) -> int {  // Z = A^T B, B m x k
+        if (int e = rsvd_transpose_enqueue(B, ldb, m, kk, Xr, st)) return e;
+        return rsvd_spmm_enqueue(t_ptr, t_idx, t_val, nnz, n, m, Xr, kk, Zn, ldn, acc, st);
+    };
+    if (int e = a_mul(X, ldx)) return e;
+    if (int e = orth(pm, Ym, ldm, Qm, nullptr)) return e;
+    for (int it = 0; it < iters; ++it) {
+        if (int e = at_mul(Qm, ldm)) return e;
+        if (int e = orth(pn, Zn, ldn, Qn, nullptr)) return e;
+        if (int e = a_mul(Qn, ldn)) return e;
+        if (int e = orth(pm, Ym, ldm, Qm, nullptr)) return e;
+    }
+    // B^T = A^T Y = Q_z R_z, R_z = U_r S V_r^T: Y^T A = V_r S (Q_z U_r)^T
+    if (int e = at_mul(Qm, ldm)) return e;
+    if (int e = orth(pn, Zn, ldn, Qn, Rz)) return e;
+    if (int e = rsvd_jacobi_enqueue(Rz, k, kk, Ur, Vr, S, Vg, acc, st)) return e;
+    if (int e = rsvd_right_mult_enqueue(Qm, ldm, m, kk, Vr, U, ldu, acc, st)) return e;
+    if (int e = rsvd_right_mult_enqueue(Qn, ldn, n, kk, Ur, V, ldv, acc, st)) return e;
+    return finish_blocking(h, acc, st);
 }
 
 int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_t ldx, const double *R, int64_t ldr, int prec,

@@ -414,4 +414,15 @@ size_t blocked_qr_scratch_doubles(int64_t s, int64_t n);
 // blocked multi-CTA Cholesky R_p = chol(G) (+ R_acc <- R_p R_acc) for n > 64
 int blocked_factor_enqueue(const double *G, int n, int64_t ldg, double *Rp, double *Racc, double *C, int pass,
                            int update_racc, RxrStatus *status, cudaStream_t st);
+// randomized SVD (rsvd_kernels.cu): sparse products, the k x k SVD and the
+// finishing products; every launcher returns 0 or RXR_ERR_CUDA
+int rsvd_transpose_enqueue(const double *X, int64_t ldx, int64_t rows, int k, double *Xr, cudaStream_t st);
+int rsvd_spmm_enqueue(const int64_t *ptr, const int32_t *idx, const double *val, int64_t nnz, int64_t rows,
+                      int64_t cols, const double *Xr, int k, double *Y, int64_t ldy, RxrStatus *acc, cudaStream_t st);
+int rsvd_jacobi_enqueue(const double *R, int64_t ldr, int k, double *Ur, double *Vr, double *S, double *Vg,
+                        const RxrStatus *acc, cudaStream_t st);
+int rsvd_right_mult_enqueue(const double *X, int64_t ldx, int64_t rows, int k, const double *T, double *Y,
+                            int64_t ldy, const RxrStatus *acc, cudaStream_t st);
+int rsvd_status_keep_enqueue(const RxrStatus *cur, RxrStatus *acc, int call, cudaStream_t st);
+cudaError_t set_rsvd_smem();
 }  // namespace rxr

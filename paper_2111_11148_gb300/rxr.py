@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "librxr.so")
 LU, QR, NONE, SHIFTED = 0, 1, 2, 3
 SKETCH_ROWS = 16  # OR-ed into LU / QR: the sketch by row extraction
 FP64, SPLIT_BF16 = 0, 1
-OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED = range(8)
+OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED, BAD_SPARSE = range(9)
 KERNEL_SKETCH, KERNEL_PRECOND_GRAM, KERNEL_PASS_GRAM, KERNEL_APPLY = range(4)
 
 _VARIANTS = {"lu": LU, "qr": QR, "none": NONE, "shifted": SHIFTED, "lu-rows": LU | SKETCH_ROWS,
@@ -77,6 +77,8 @@ def load() -> ctypes.CDLL:
         "rxr_last_kernel_ms": ([vp, i, P(ctypes.c_float)], i),
         "rxr_set_kernel_timing": ([vp, i], i),
         "rxr_sketch_noalloc": ([vp, i64, i64, i64, i64, u64, vp, i64, vp], i),
+        "rxr_rsvd": ([vp, i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, i64, i64, i, i, i64, u64, i, i, vp, i64, vp, vp,
+                      i64, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -92,7 +94,7 @@ def exported_symbols() -> list[str]:
                         "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_sketch_rows", "rxr_xr_factor",
                         "rxr_precond_gram",
                         "rxr_cholesky", "rxr_apply_rinv", "rxr_lstsq", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
-                        "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc")]
+                        "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc", "rxr_rsvd")]
 
 
 def status_string(code: int) -> str:
@@ -303,6 +305,29 @@ class Handle:
             _check(code, "rxr_lstsq")
         return (x[:, 0] if b.dim() == 1 else x), code
 
+    def rsvd(self, A: "DeviceCsr", X, iters: int, variant="qr", s: Optional[int] = None, seed: int = 0,
+             passes: int = 2, prec="fp64", U=None, S=None, V=None, stream=None, raise_on_error: bool = True):
+        """Randomized SVD with power iteration (Algorithm 7) of the sparse A from
+        the n x k starting block X (column-major CUDA tensor), each
+        orthonormalisation by CholeskyQR.  Returns (U, S, V, status) with
+        Y Y^T A = U diag(S) V^T."""
+        import torch
+
+        n, k = X.shape
+        if n != A.n:
+            raise ValueError("X must have A.n rows")
+        s = 2 * k if s is None else int(s)
+        U = empty_colmajor(A.m, k, device=X.device) if U is None else U
+        V = empty_colmajor(A.n, k, device=X.device) if V is None else V
+        S = torch.empty(k, dtype=torch.float64, device=X.device) if S is None else S
+        code = load().rxr_rsvd(self._h, A.m, A.n, _ptr(A.indptr), _ptr(A.indices), _ptr(A.data), _ptr(A.t_indptr),
+                               _ptr(A.t_indices), _ptr(A.t_data), A.nnz, _ptr(X), _ld(X), k, int(iters),
+                               _VARIANTS[variant], s, seed & (2**64 - 1), int(passes), _PRECS[prec], _ptr(U), _ld(U),
+                               _ptr(S), _ptr(V), _ld(V), _stream(stream))
+        if raise_on_error and code != 0:
+            raise RxrError(code, "rxr_rsvd")
+        return U, S, V, code
+
     def apply_rinv(self, X, R, prec="fp64", stream=None):
         """X <- X R^{-1} in place (the Q of a CholeskyQR pass); returns X."""
         m, n = X.shape
@@ -336,6 +361,33 @@ class Handle:
         v = ctypes.c_float()
         load().rxr_last_kernel_ms(self._h, int(kernel), ctypes.byref(v))
         return v.value
+
+
+class DeviceCsr:
+    """A sparse m x n matrix and its transpose in compressed sparse row form on
+    a CUDA device: the arrays rxr_rsvd reads (int64 row pointers, int32
+    indices, float64 values)."""
+
+    def __init__(self, m, n, indptr, indices, data, t_indptr, t_indices, t_data, device="cuda"):
+        import torch
+
+        def dev(a, dt):
+            return torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+
+        self.m, self.n = int(m), int(n)
+        self.indptr, self.t_indptr = dev(indptr, torch.int64), dev(t_indptr, torch.int64)
+        self.indices, self.t_indices = dev(indices, torch.int32), dev(t_indices, torch.int32)
+        self.data, self.t_data = dev(data, torch.float64), dev(t_data, torch.float64)
+
+    @classmethod
+    def from_host(cls, A, device="cuda") -> "DeviceCsr":
+        """Copy an object with fields m, n, indptr, indices, data, t_indptr,
+        t_indices, t_data (numpy arrays) to the device."""
+        return cls(A.m, A.n, A.indptr, A.indices, A.data, A.t_indptr, A.t_indices, A.t_data, device)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indices.numel())
 
 
 def omega(seed: int, s: int, row0: int, rows: int, device="cuda", stream=None):

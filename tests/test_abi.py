@@ -42,8 +42,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for code in range(0, 8):
-        assert rxr.status_string(code)
+    for code in range(0, 9):
+        assert rxr.status_string(code) != "unknown status"
     assert "invalid" in rxr.status_string(-3)
 
 
