@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(256) k_csr_spmm(const int64_t *__restrict__ pt
 
 // R (k x k, ldr) = U_r diag(S) V_r^T: one-sided Jacobi on W = R (columns
 // rotated in pairs until every pair's cosine is below sqrt(k) eps, LAPACK's
-// threshold when singular vectors are wanted), V_r the product of the rotations, S the column norms of W and
+// threshold when singular vectors are wanted; sweeps end once none rotates a
+// pair by more than 2^-27), V_r the product of the rotations, S the column norms of W and
 // U_r = W diag(S)^{-1}; columns sorted by decreasing S.  Outputs k x k
 // column-major with leading dimension k.  Vg: k x k global scratch used for
 // V_r when k > 112.  One CTA of 512 threads; bounded sweeps.
@@ -148,7 +149,10 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__r
     const int kk = k + (k & 1);  // an odd k adds a dummy column that sits out one pair per round
     const double tol = sqrt((double)k) * 0x1p-52;
     for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-        bool rotated = false;
+        // convergence is quadratic: once no rotation of a sweep had a cosine above
+        // 2^-27, the cosines it leaves are at rounding level and the next sweep
+        // would rotate noise only
+        bool large = false;
         for (int round = 0; round < kk - 1; ++round) {
             // circle method: position kk-1 fixed, the others turn one step per round
             for (int pr = warp; pr < kk / 2; pr += nwarps) {
@@ -172,7 +176,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__r
                 al = warp_sum(al);
                 be = warp_sum(be);
                 ga = warp_sum(ga);
-                if (!(fabs(ga) > tol * sqrt(al) * sqrt(be))) continue;  // also for NaN
+                const double nrm = sqrt(al) * sqrt(be);
+                if (!(fabs(ga) > tol * nrm)) continue;  // also for NaN
                 // rotation that makes columns p, q orthogonal: t the smaller root of
                 // t^2 + 2 zeta t - 1 = 0, zeta = (be - al) / (2 ga)
                 const double zeta = (be - al) / (2.0 * ga);
@@ -190,11 +195,11 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__r
                     vp[r] = c * x - s * y;
                     vq[r] = s * x + c * y;
                 }
-                rotated = true;
+                large |= fabs(ga) > 0x1p-27 * nrm;
             }
             __syncthreads();
         }
-        if (!__syncthreads_or(rotated)) break;
+        if (!__syncthreads_or(large)) break;
     }
     for (int j = tid; j < k; j += blockDim.x) {
         double s2 = 0.0;
