@@ -223,7 +223,10 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__r
 }
 
 // Y (rows x k, ldy) = X (rows x k, ldx) T (k x k, column-major, ld k); Y and X
-// must not overlap.  A CTA takes 64 rows; thread (r, g) sums columns g, g+4, ...
+// must not overlap.  A CTA takes 64 rows; thread (r, g) sums columns g, g+4,
+// ..., g + 4(NC-1) below k, NC >= k/4 (a multiple of 2 or 8, so that the
+// warp-uniform column guards skip at most 3/8 of the FP64 issue).
+template <int NC>
 __global__ void __launch_bounds__(256) k_right_mult(const double *__restrict__ X, int64_t ldx, int64_t rows, int k,
                                                     const double *__restrict__ T, double *__restrict__ Y, int64_t ldy,
                                                     const RxrStatus *acc)
@@ -235,20 +238,20 @@ __global__ void __launch_bounds__(256) k_right_mult(const double *__restrict__ X
     const int r = threadIdx.x & (kRmRows - 1), g = threadIdx.x / kRmRows;
     const int64_t row = (int64_t)blockIdx.x * kRmRows + r;
     if (row >= rows) return;
-    double a[kSvdMaxK / 4];
+    double a[NC];
 #pragma unroll
-    for (int i = 0; i < kSvdMaxK / 4; ++i) a[i] = 0.0;
+    for (int i = 0; i < NC; ++i) a[i] = 0.0;
     for (int l = 0; l < k; ++l) {
         const double x = X[row + (int64_t)l * ldx];
         const double *tl = Ts + l;
 #pragma unroll
-        for (int i = 0; i < kSvdMaxK / 4; ++i) {
+        for (int i = 0; i < NC; ++i) {
             const int c = g + 4 * i;
             if (c < k) a[i] = fma(x, tl[c * k], a[i]);
         }
     }
 #pragma unroll
-    for (int i = 0; i < kSvdMaxK / 4; ++i) {
+    for (int i = 0; i < NC; ++i) {
         const int c = g + 4 * i;
         if (c < k) Y[row + (int64_t)c * ldy] = a[i];
     }
@@ -304,8 +307,20 @@ int rsvd_right_mult_enqueue(const double *X, int64_t ldx, int64_t rows, int k, c
                             int64_t ldy, const RxrStatus *acc, cudaStream_t st)
 {
     if (rows < 1) return 0;
-    k_right_mult<<<(unsigned)cdiv(rows, kRmRows), 256, (size_t)k * k * sizeof(double), st>>>(X, ldx, rows, k, T, Y,
-                                                                                            ldy, acc);
+    const unsigned grid = (unsigned)cdiv(rows, kRmRows);
+    const size_t smem = (size_t)k * k * sizeof(double);
+    if (k <= 8)
+        k_right_mult<2><<<grid, 256, smem, st>>>(X, ldx, rows, k, T, Y, ldy, acc);
+    else if (k <= 16)
+        k_right_mult<4><<<grid, 256, smem, st>>>(X, ldx, rows, k, T, Y, ldy, acc);
+    else if (k <= 32)
+        k_right_mult<8><<<grid, 256, smem, st>>>(X, ldx, rows, k, T, Y, ldy, acc);
+    else if (k <= 64)
+        k_right_mult<16><<<grid, 256, smem, st>>>(X, ldx, rows, k, T, Y, ldy, acc);
+    else if (k <= 96)
+        k_right_mult<24><<<grid, 256, smem, st>>>(X, ldx, rows, k, T, Y, ldy, acc);
+    else
+        k_right_mult<32><<<grid, 256, smem, st>>>(X, ldx, rows, k, T, Y, ldy, acc);
     return rsvd_launch_ok();
 }
 
@@ -319,9 +334,13 @@ cudaError_t set_rsvd_smem()
 {
     cudaError_t e = cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max(rsvd_jacobi_smem(kJacobiVSmemK), rsvd_jacobi_smem(kSvdMaxK)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_right_mult, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSvdMaxK * kSvdMaxK * sizeof(double)));
+    const int rm = (int)(kSvdMaxK * kSvdMaxK * sizeof(double));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_right_mult<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_right_mult<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, rm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_right_mult<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, rm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_right_mult<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, rm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_right_mult<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, rm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_right_mult<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, rm);
     return e;
 }
 

@@ -97,7 +97,7 @@ def test_subspaces_match_oracle_across_a_gap(h, prec):
     assert np.max(np.abs(S[:8] - sig[:8]) / sig[:8]) <= 1e-6
 
 
-@pytest.mark.parametrize("k", [1, 7, 113, 128])
+@pytest.mark.parametrize("k", [1, 7, 80, 113, 128])
 def test_block_widths(h, k):
     P = sparse_operator(1500, 6.0, seed=k)
     U, S, V, code = _gpu(h, P, k, 1, xseed=3)
