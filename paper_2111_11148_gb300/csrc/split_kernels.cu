@@ -121,7 +121,7 @@ __device__ __forceinline__ void st_bf16(unsigned char *base, int off, float v)
 }
 
 // Wait for the tensor-core work committed to `bar` (phase `phase`), bounded;
-// the verdict is made block-uniform.
+// the decision is made block-uniform.
 __device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t phase, RxrStatus *st)
 {
     const bool ok = mbar_wait_bounded(bar, phase, st);

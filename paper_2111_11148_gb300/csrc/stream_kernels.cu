@@ -54,7 +54,7 @@ __device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, 
         }
         const bool ok = mbar_wait_bounded(bar, phase, st);
         phase ^= 1u;
-        // every thread leaves with the same verdict (no thread left at a barrier)
+        // every thread leaves with the same decision (no thread left at a barrier)
         return __syncthreads_or(ok ? 0 : 1) == 0;
     }
     const int total = P * nc;
