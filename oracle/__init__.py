@@ -1,4 +1,4 @@
-"""CPU oracle for randomized XR-preconditioned CholeskyQR (FP64, single thread).
+"""CPU oracle for randomized XR-preconditioned CholeskyQR (FP64).
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
 CPU-baseline leg may import this package.  It shares no code with the CUDA
@@ -6,7 +6,10 @@ path; the product never falls back to it.
 
 The arithmetic lives in ``rxr_oracle.c`` (plain C, compiled with
 -ffp-contract=off); this module compiles it on demand with gcc and wraps it
-with ctypes.  All matrices are float64 and column-major (Fortran order).  The
+with ctypes; a second build with -fopenmp runs the independent row blocks and
+rows on all host cores with the same bits (the benchmark's multi-core CPU
+baseline; ``rxr_cholqr(..., parallel=True)``).  All matrices are float64 and
+column-major (Fortran order).  The
 randomized SVD of Section 5.1 (``rsvd``) is composed here from the C
 factorisation and library steps (sparse/dense products, LAPACK's SVD).
 """
@@ -23,31 +26,41 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rxr_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "librxr_oracle.so")
+# the same source built with -fopenmp: the multi-core CPU baseline (identical bits)
+_LIB_OMP = os.path.join(_LIB_DIR, "librxr_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE = 0, 1, 2, 3
 VARIANT_LU, VARIANT_QR, VARIANT_NONE = 0, 1, 2
 SKETCH_ROWS = 16  # flag OR-ed into VARIANT_LU / VARIANT_QR: row extraction (Section 2.3)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build/librxr_oracle.so (gcc, -O2)."""
-    os.makedirs(_LIB_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+def _compile(out: str, extra: list[str], force: bool) -> str:
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", *extra,
                _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/librxr_oracle.so (gcc, -O2,
+    single-threaded) and librxr_oracle_omp.so (the same source with -fopenmp)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    _compile(_LIB_OMP, ["-fopenmp"], force)
+    return _compile(_LIB, [], force)
+
+
+def _load(parallel: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if (_lib_omp if parallel else _lib) is None:
+            build()
+            lib = ctypes.CDLL(_LIB_OMP if parallel else _LIB)
             P = ctypes.POINTER
             d, i64, u64, u32, i = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
             vp = ctypes.c_void_p
@@ -85,8 +98,18 @@ def _load():
             lib.rxo_resid_error.restype = d
             lib.rxo_dot2.argtypes = [vp, vp, i64]
             lib.rxo_dot2.restype = d
-            _lib = lib
-    return _lib
+            lib.rxo_threads.restype = i
+            if parallel:
+                _lib_omp = lib
+            else:
+                _lib = lib
+    return _lib_omp if parallel else _lib
+
+
+def threads(parallel: bool = True) -> int:
+    """Host threads the oracle's loops use: the OpenMP build's count
+    (OMP_NUM_THREADS, else every core) or 1 for the serial build."""
+    return int(_load(parallel).rxo_threads())
 
 
 def _p(a: np.ndarray):
@@ -255,8 +278,9 @@ class Result:
 
 
 def rxr_cholqr(A: np.ndarray, variant: int = VARIANT_QR, s: int | None = None, seed: int = 0,
-               passes: int = 2) -> Result:
-    """rLU-/rQR-CholeskyQR (Algorithms 4/5) with `passes` CholeskyQR passes."""
+               passes: int = 2, parallel: bool = False) -> Result:
+    """rLU-/rQR-CholeskyQR (Algorithms 4/5) with `passes` CholeskyQR passes.
+    parallel: run the OpenMP build of the same code (the same bits)."""
     A = _f64(A)
     m, n = A.shape
     s = 2 * n if s is None else int(s)
@@ -265,7 +289,7 @@ def rxr_cholqr(A: np.ndarray, variant: int = VARIANT_QR, s: int | None = None, s
     Y = np.zeros((s, n), order="F")
     mats = [np.zeros((n, n), order="F") for _ in range(5)]
     info = np.zeros(2, np.int32)
-    st = _load().rxo_rxr_cholqr(_p(A), m, n, _ld(A), variant, s, seed, passes, _p(Q), max(1, m), _p(R), n,
+    st = _load(parallel).rxo_rxr_cholqr(_p(A), m, n, _ld(A), variant, s, seed, passes, _p(Q), max(1, m), _p(R), n,
                                 _p(Y), *[_p(x) for x in mats], _p(info))
     return Result(status=int(st), Q=Q, R=R, Y=Y, Rs=mats[0], G1=mats[1], R1=mats[2], G2=mats[3], R2=mats[4],
                   info=(int(info[0]), int(info[1])))

@@ -14,11 +14,31 @@
  *
  * Compile with -ffp-contract=off: the FP32 normal generator must round exactly
  * as written (no fused multiply-adds other than the explicit fmaf calls).
+ *
+ * Built with -fopenmp (the multi-core CPU baseline), the loops over
+ * independent 256-row blocks and over independent rows run on all host cores.
+ * Each block's partial sum and each row's result is computed exactly as in the
+ * serial build, and the partial sums are combined in the same order, so both
+ * builds return the same bits.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads the parallel loops use: 1 in the serial build. */
+int rxo_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* Status codes (same meaning as the library's, defined here independently). */
 #define RXO_OK 0
@@ -254,35 +274,54 @@ void rxo_sketch_quantised(const double *A, int64_t m, int64_t n, int64_t lda, in
     sketch_impl(A, m, n, lda, s, seed, Y, ldy, 1);
 }
 
+/* The partial sum of one 256-row block of Omega A (block rows b0 .. b0 + rows). */
+static void sketch_block(const double *A, int64_t lda, int64_t n, int64_t s, uint64_t seed, int quantise, double c,
+                         int64_t b0, int64_t rows, float *z, double *blk)
+{
+    rxo_omega_z(seed, s, b0, rows, z);
+    memset(blk, 0, (size_t)(s * n) * sizeof(double));
+    for (int64_t i = 0; i < rows; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double a = A[(b0 + i) + j * lda];
+            for (int64_t r = 0; r < s; ++r) {
+                double zr = (double)z[i * s + r];
+                if (quantise) zr = nearbyint(zr * 4096.0) / 4096.0;
+                double om = c * zr;
+                blk[r + j * s] += om * a;
+            }
+        }
+}
+
+/* Blocks whose partial sums are formed side by side (then combined in order). */
+#define RXO_BATCH 64
+
 static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                         double *Y, int64_t ldy, int quantise)
 {
     const double c = 1.0 / sqrt((double)s);
-    double *blk = (double *)malloc((size_t)(s * n) * sizeof(double));
-    float *z = (float *)malloc((size_t)(s * RXO_BLOCK) * sizeof(float));
+    double *blk = (double *)malloc((size_t)(RXO_BATCH * s * n) * sizeof(double));
     pairwise_t pw;
     pw_init(&pw, s * n);
-    for (int64_t b0 = 0; b0 < m; b0 += RXO_BLOCK) {
-        int64_t rows = (m - b0 < RXO_BLOCK) ? m - b0 : RXO_BLOCK;
-        rxo_omega_z(seed, s, b0, rows, z);
-        memset(blk, 0, (size_t)(s * n) * sizeof(double));
-        for (int64_t i = 0; i < rows; ++i)
-            for (int64_t j = 0; j < n; ++j) {
-                double a = A[(b0 + i) + j * lda];
-                for (int64_t r = 0; r < s; ++r) {
-                    double zr = (double)z[i * s + r];
-                    if (quantise) zr = nearbyint(zr * 4096.0) / 4096.0;
-                    double om = c * zr;
-                    blk[r + j * s] += om * a;
-                }
+    const int64_t nblocks = (m + RXO_BLOCK - 1) / RXO_BLOCK;
+    for (int64_t g0 = 0; g0 < nblocks; g0 += RXO_BATCH) {
+        const int64_t nb = (nblocks - g0 < RXO_BATCH) ? nblocks - g0 : RXO_BATCH;
+#pragma omp parallel
+        {
+            float *z = (float *)malloc((size_t)(s * RXO_BLOCK) * sizeof(float));
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t q = 0; q < nb; ++q) {
+                const int64_t b0 = (g0 + q) * RXO_BLOCK;
+                const int64_t rows = (m - b0 < RXO_BLOCK) ? m - b0 : RXO_BLOCK;
+                sketch_block(A, lda, n, s, seed, quantise, c, b0, rows, z, blk + q * s * n);
             }
-        pw_push(&pw, blk);
+            free(z);
+        }
+        for (int64_t q = 0; q < nb; ++q) pw_push(&pw, blk + q * s * n);
     }
     pw_finish(&pw, blk);
     for (int64_t j = 0; j < n; ++j)
         for (int64_t r = 0; r < s; ++r) Y[r + j * ldy] = blk[r + j * s];
     free(blk);
-    free(z);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -423,35 +462,46 @@ int rxo_check_factor(const double *R, int64_t n, int64_t ldr)
 void rxo_trsm_right_upper(const double *A, int64_t m, int64_t n, int64_t lda, const double *R, int64_t ldr,
                           double *X, int64_t ldx)
 {
-    double *x = (double *)malloc((size_t)n * sizeof(double));
-    for (int64_t i = 0; i < m; ++i) {
-        for (int64_t j = 0; j < n; ++j) {
-            double acc = A[i + j * lda];
-            for (int64_t k = 0; k < j; ++k) acc -= x[k] * R[k + j * ldr];
-            x[j] = acc / R[j + j * ldr];
+#pragma omp parallel
+    {
+        double *x = (double *)malloc((size_t)n * sizeof(double));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; ++i) {
+            for (int64_t j = 0; j < n; ++j) {
+                double acc = A[i + j * lda];
+                for (int64_t k = 0; k < j; ++k) acc -= x[k] * R[k + j * ldr];
+                x[j] = acc / R[j + j * ldr];
+            }
+            for (int64_t j = 0; j < n; ++j) X[i + j * ldx] = x[j];
         }
-        for (int64_t j = 0; j < n; ++j) X[i + j * ldx] = x[j];
+        free(x);
     }
-    free(x);
 }
 
 /* G = X^T X (n x n, full symmetric), Algorithm 1 step 1; 256-row blocks     */
 /* combined pairwise as in the sketch.                                        */
 void rxo_gram(const double *X, int64_t m, int64_t n, int64_t ldx, double *G, int64_t ldg)
 {
-    double *blk = (double *)malloc((size_t)(n * n) * sizeof(double));
+    double *blk = (double *)malloc((size_t)(RXO_BATCH * n * n) * sizeof(double));
     pairwise_t pw;
     pw_init(&pw, n * n);
-    for (int64_t b0 = 0; b0 < m; b0 += RXO_BLOCK) {
-        int64_t rows = (m - b0 < RXO_BLOCK) ? m - b0 : RXO_BLOCK;
-        memset(blk, 0, (size_t)(n * n) * sizeof(double));
-        for (int64_t j = 0; j < n; ++j)
-            for (int64_t l = 0; l <= j; ++l) {
-                double acc = 0.0;
-                for (int64_t i = b0; i < b0 + rows; ++i) acc += X[i + l * ldx] * X[i + j * ldx];
-                blk[l + j * n] = acc;
-            }
-        pw_push(&pw, blk);
+    const int64_t nblocks = (m + RXO_BLOCK - 1) / RXO_BLOCK;
+    for (int64_t g0 = 0; g0 < nblocks; g0 += RXO_BATCH) {
+        const int64_t nb = (nblocks - g0 < RXO_BATCH) ? nblocks - g0 : RXO_BATCH;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < nb; ++q) {
+            const int64_t b0 = (g0 + q) * RXO_BLOCK;
+            const int64_t rows = (m - b0 < RXO_BLOCK) ? m - b0 : RXO_BLOCK;
+            double *bq = blk + q * n * n;
+            memset(bq, 0, (size_t)(n * n) * sizeof(double));
+            for (int64_t j = 0; j < n; ++j)
+                for (int64_t l = 0; l <= j; ++l) {
+                    double acc = 0.0;
+                    for (int64_t i = b0; i < b0 + rows; ++i) acc += X[i + l * ldx] * X[i + j * ldx];
+                    bq[l + j * n] = acc;
+                }
+        }
+        for (int64_t q = 0; q < nb; ++q) pw_push(&pw, blk + q * n * n);
     }
     pw_finish(&pw, blk);
     for (int64_t j = 0; j < n; ++j)

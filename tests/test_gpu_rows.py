@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle as o
-from gpu_util import U, to_dev, to_host
+from gpu_util import R_TOL, U, r_rel, to_dev, to_host
 from paper_2111_11148_gb300.inputs import usv_matrix
 
 pytestmark = pytest.mark.gpu
@@ -48,7 +48,7 @@ def _check(A, Qg, Rg, ref, kappa):
     assert o.resid_error(A, Qg, Rg) <= 1e-14
     assert np.all(np.diag(Rg) > 0) and np.all(np.tril(Rg, -1) == 0)
     rel = np.linalg.norm(Rg - ref.R) / np.linalg.norm(ref.R)
-    assert rel <= max(100 * kappa * U, 1e-13), rel
+    assert rel <= R_TOL, rel
 
 
 @pytest.mark.parametrize("prec", ["fp64", "split"])

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as o
-from gpu_util import U, to_dev, to_host
+from gpu_util import R_TOL, U, r_rel, to_dev, to_host
 from paper_2111_11148_gb300.inputs import usv_matrix
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +39,7 @@ def test_scholqr3_matches_oracle(h, prec, m, n, kappa):
     assert o.resid_error(A, Qg, Rg) <= 1e-14
     assert np.all(np.diag(Rg) > 0) and np.all(np.tril(Rg, -1) == 0)
     rel = np.linalg.norm(Rg - ref.R) / np.linalg.norm(ref.R)
-    assert rel <= max(100 * kappa * U, 1e-13), rel
+    assert rel <= R_TOL, rel
 
 
 @pytest.mark.parametrize("prec", ["fp64", "split"])
@@ -70,7 +70,7 @@ def test_choleskyqr_split_matches_oracle(h, m, n, kappa, passes):
     assert o.orth_error(Qg) <= 1e-13
     assert o.resid_error(A, Qg, Rg) <= 1e-14
     rel = np.linalg.norm(Rg - ref.R) / np.linalg.norm(ref.R)
-    assert rel <= max(100 * kappa * U, 1e-13), rel
+    assert rel <= R_TOL, rel
 
 
 @pytest.mark.parametrize("variant,n", [("none", 16), ("none", 100), ("shifted", 32)])
