@@ -64,15 +64,37 @@ extern "C" {
 typedef enum { RXR_LU = 0, RXR_QR = 1, RXR_NONE = 2, RXR_SHIFTED = 3 } rxr_variant;
 #define RXR_SKETCH_ROWS 16
 
-/* Arithmetic of the two contractions that only shape the preconditioner (the
- * sketch Y = Omega A and the first pass's Gram X^T X).
- *   RXR_FP64       : FP64 throughout.
- *   RXR_SPLIT_BF16 : those two contractions on tcgen05 tensor cores with BF16
- *                    operand slices and FP32 accumulation in tensor memory,
- *                    combined in FP64; everything else stays FP64.  Rounding in
- *                    them changes only the preconditioner, not what A = QR the
- *                    FP64 passes converge to (Appendix A). */
-typedef enum { RXR_FP64 = 0, RXR_SPLIT_BF16 = 1 } rxr_precision;
+/* Arithmetic of the passes over A (the m-row contractions).
+ *   RXR_FP64          : FP64 FMAs throughout.
+ *   RXR_SPLIT_BF16    : every contraction over the m rows runs on the tcgen05
+ *                       tensor cores: the sketch, both Grams, the trailing
+ *                       updates of the substitutions (their 16-column diagonal
+ *                       blocks are FP64 solves), and, for n <= 64 and m >= 2^17,
+ *                       the middle pass's and the last pass's applies through
+ *                       the explicit inverse (each chosen on the device; the
+ *                       substitution otherwise).  Operands are exact balanced
+ *                       8-bit digit slices of FP64 values (FP16 operands for
+ *                       n <= 128, BF16 above) with FP32 accumulation kept exact
+ *                       and combined in FP64, so these contractions are
+ *                       FP64-grade (error about 2^-53 of the largest entries per
+ *                       column), except the first Gram for 64 < n <= 128
+ *                       (BF16x3: three 8-bit significand chunks, about 2^-19)
+ *                       and the last apply's correction X (R_P^{-1} - I) for
+ *                       n <= 64, formed in FP32 when |R_P^{-1} - I| <= 2^-38.
+ *                       The sketch takes Omega on the 2^-12 grid (the same
+ *                       Philox draws, rint(4096 z) / 4096).  The n x n
+ *                       factorisations, inverses and all combining stay FP64.
+ *   RXR_SPLIT_PRECOND : only the two contractions that shape the
+ *                       preconditioner leave FP64: the sketch (as above) and
+ *                       the first pass's Gram (BF16x3 for n <= 128, FP64-grade
+ *                       digit slices above).  X = A R_s^{-1}, the later Grams
+ *                       and every apply are FP64 FMAs; the repeated FP64 pass
+ *                       wins the accuracy back (Appendix A's perturbation
+ *                       argument).  Without a sketch (RXR_NONE, RXR_SHIFTED)
+ *                       it is RXR_FP64.  Taken by rxr_cholqr, rxr_cholqr_async,
+ *                       rxr_cholqr_host, rxr_rsvd and rxr_sketch (the split
+ *                       sketch); the other entry points take the first two. */
+typedef enum { RXR_FP64 = 0, RXR_SPLIT_BF16 = 1, RXR_SPLIT_PRECOND = 3 } rxr_precision;
 
 /* Positive status codes. */
 enum {
@@ -86,7 +108,9 @@ enum {
     RXR_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
     RXR_ERR_NOMEM = 6,           /* the library could not allocate its workspace */
     RXR_ERR_UNSUPPORTED = 7,     /* valid arguments outside what this build supports */
-    RXR_ERR_BAD_SPARSE = 8       /* rxr_rsvd: a CSR row pointer or column index out of range */
+    RXR_ERR_BAD_SPARSE = 8,      /* rxr_rsvd: a CSR row pointer or column index out of range */
+    RXR_ERR_NO_CONVERGENCE = 9   /* rxr_rsvd: the k x k Jacobi SVD still rotated a pair by more
+                                    than 2^-27 in its last allowed sweep (40, or the test hook's) */
 };
 
 /* Limits of this build. */
@@ -167,6 +191,27 @@ RXR_API int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, 
                        double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
                        void *stream, int *d_status);
 
+/* Test hooks: they make error paths that correct inputs never reach run on
+ * request, without faulting or hanging the GPU.  They are meant for tests.
+ *   RXR_HOOK_STALL, value != 0: the following factorisations on this handle
+ *     (rxr_cholqr and the calls built on it) make one bounded device-side wait
+ *     run out.  The FP64 path's sketch kernel (its first CTA) and the
+ *     split path's fused substitution (n <= 64, the first CTA's first row
+ *     group) skip their first TMA copy and wait on an mbarrier that nothing
+ *     arrives at.  No copy is in flight.  After about a second per wait the
+ *     kernel records RXR_ERR_TIMEOUT, frees its tensor memory and returns.
+ *     Every later kernel of the call returns at once, and the call returns
+ *     RXR_ERR_TIMEOUT.  Only a TMA-eligible A (16-byte aligned, even lda)
+ *     takes these waits.  value 0 restores normal operation; the handle stays
+ *     usable.
+ *   RXR_HOOK_JACOBI_SWEEPS, value in 0..40: caps the sweeps of rxr_rsvd's
+ *     Jacobi SVD (0 = the default bound, 40); a cap it reaches before
+ *     convergence makes rxr_rsvd return RXR_ERR_NO_CONVERGENCE.
+ * Returns 0, -1 (h NULL), -2 (unknown hook) or -3 (value out of range). */
+#define RXR_HOOK_STALL 1
+#define RXR_HOOK_JACOBI_SWEEPS 2
+RXR_API int rxr_set_test_hook(rxr_handle h, int hook, int value);
+
 /* Pass and column (0-based) of the last Cholesky breakdown seen by a blocking
  * call on this handle; both -1 if none. */
 RXR_API int rxr_last_info(rxr_handle h, int *pass, int *column);
@@ -215,9 +260,12 @@ RXR_API int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n
                      int64_t ldr, double *X, int64_t ldx, double *G, int64_t ldg, int prec, void *stream);
 
 /* G = X^T X (full symmetric n x n, ldg >= n) of a tall-skinny X (Algorithm 1
- * step 1).  RXR_FP64: FP64 FMAs.  RXR_SPLIT_BF16: the tensor-core Gram with
- * exact 7-digit splitting (FP64-grade: error about 2^-53 of |X|^T |X|
- * column-normwise), n <= 128.  Blocking. */
+ * step 1).  RXR_FP64: FP64 FMAs, n <= 128.  RXR_SPLIT_BF16: the tensor-core
+ * Gram with exact 7-digit splitting (FP64-grade: error about 2^-53 of
+ * |X|^T |X| column-normwise), n <= 512.  RXR_SPLIT_PRECOND: the first-pass Gram
+ * of that mode, BF16x3 on the tensor cores (three 8-bit significand chunks,
+ * FP32 accumulation drained to FP64 every 64 rows; error about 2^-19 of
+ * |X|^T |X|), n <= 128.  Blocking. */
 RXR_API int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, double *G, int64_t ldg, int prec,
                      void *stream);
 
@@ -269,8 +317,9 @@ RXR_API int rxr_lstsq(rxr_handle h, const double *A, int64_t m, int64_t n, int64
  * S (k), V (n x k, ldv >= n).  The handle keeps 2 (m + n) k + max(m, n) k
  * doubles of scratch.  A rank of A below k makes a factorisation fail.
  * Blocking; 0, the first failure of the factorisations (RXR_ERR_*; for a
- * breakdown rxr_last_info gives its pass and column), RXR_ERR_BAD_SPARSE, or a
- * negative argument error (-i: argument i). */
+ * breakdown rxr_last_info gives its pass and column), RXR_ERR_BAD_SPARSE,
+ * RXR_ERR_NO_CONVERGENCE (S holds the unconverged column norms, U and V are
+ * not written), or a negative argument error (-i: argument i). */
 RXR_API int rxr_rsvd(rxr_handle h, int64_t m, int64_t n, const int64_t *a_ptr, const int32_t *a_idx,
                      const double *a_val, const int64_t *t_ptr, const int32_t *t_idx, const double *t_val,
                      int64_t nnz, const double *X, int64_t ldx, int64_t k, int iters, int variant, int64_t s,
@@ -308,29 +357,35 @@ RXR_API int rxr_last_kernel_ms(rxr_handle h, int kernel, float *ms);
 RXR_API int rxr_set_kernel_timing(rxr_handle h, int enable);
 
 /* ---- Allocation-free sketch.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate device memory -- code that runs
- * while a stream is captured in global mode (cudaMalloc is not allowed there),
- * processes whose device memory is reserved in full by another allocator, or
- * loops that forbid allocation after start-up -- and so cannot create a handle
- * or hand over a workspace.
+ * point exists for callers that cannot allocate device memory, and so cannot
+ * create a handle or hand one a workspace: processes whose device memory is
+ * reserved in full by another allocator (a framework's caching pool that owns
+ * the whole GPU), and loops that forbid allocation after start-up because
+ * cudaMalloc may synchronise the device or take an unbounded time.
  *
  * Y = Omega A exactly as rxr_sketch with RXR_FP64 (same kernels, same Omega),
  * but its scratch (the per-chunk partial sums and the status word) lives in a
  * fixed array of RXR_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
  * that loads the library holds until the process exits.  The number of row
- * chunks is capped so that the partial sums fit, so the result may differ
- * from rxr_sketch's in rounding (not in the tolerance).
+ * chunks is capped so that the partial sums fit (at s = 2048, n = 128 at most
+ * 7 chunks), so the result may differ from rxr_sketch's in rounding (not in
+ * the tolerance).
  *   A, m, n, lda (1-4)  device, column-major, m >= n >= 1, n <= 128, lda >= m.
  *   s (5), seed (6)     sketch rows (1..RXR_MAX_S) and the Philox key.
  *   Y, ldy (7-8)        device output, s x n, ldy >= s.
- *   stream (9)          cudaStream_t; the call is blocking (synchronises it).
- * Returns 0, -i for an invalid argument i, RXR_ERR_NOMEM when s * n exceeds
- * what the scratch array holds, RXR_ERR_NONFINITE, or RXR_ERR_CUDA.
+ *   stream (9)          cudaStream_t; the call is blocking (it copies the
+ *                       status word to the host and synchronises the stream).
+ * Returns 0, -i for an invalid argument i (s above RXR_MAX_S: -5),
+ * RXR_ERR_UNSUPPORTED for n > 128 or m > 2^31, RXR_ERR_NONFINITE, or
+ * RXR_ERR_CUDA.  Every admissible s x n fits the array (checked when the
+ * library is compiled).
  * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine.  Its first call on a device (the current device) looks up the
  * array's device address and sets the kernel's shared-memory limit; make that
- * first call before any stream capture.  Every call uses the same array, so
- * calls whose work overlaps on the GPU (other threads, other streams) race:
+ * first call before any stream capture.  Every call uses the same array and
+ * the array keeps the last call's contents (the status word is cleared at the
+ * start of each call; the partial sums are overwritten in full), so calls
+ * whose work overlaps on the GPU (other threads, other streams) race:
  * serialise them. */
 #define RXR_NOALLOC_SCRATCH_BYTES (16u << 20)
 RXR_API int rxr_sketch_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,

@@ -96,6 +96,9 @@ struct rxr_ctx {
     // the _host entry point's copy stream and its chunk events
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t io_ev[2 * kIoChunks + 2] = {};
+    // test hooks (rxr_set_test_hook)
+    int test_stall = 0;
+    int jacobi_sweeps = 0;  // 0: the default bound
 };
 
 namespace {
@@ -225,7 +228,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     p.sk_ppc = cdiv(p.sk_panels, gx);
     p.sk_gx = (int)cdiv(p.sk_panels, p.sk_ppc);
     p.yslots = p.sk_gx;
-    if (prec == RXR_SPLIT_BF16) {
+    if (prec != RXR_FP64) {  // the sketch on the tensor cores
         int64_t sgx, spc;
         split_sketch_grid(p, &sgx, &spc);
         p.yslots = std::max<int64_t>(p.yslots, sgx);
@@ -280,7 +283,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     const size_t o_racc = take((size_t)n * n * 8);
     const size_t o_c = take((size_t)n * n * 8);
     size_t o_split = off;
-    if (prec == RXR_SPLIT_BF16) o_split = take(split_workspace_bytes(m, n, s, sms));
+    if (prec != RXR_FP64) o_split = take(split_workspace_bytes(m, n, s, sms));
     p.bytes = off;
     p.base = nullptr;
     p.status = nullptr;
@@ -429,7 +432,7 @@ int enqueue_subst(const Plan &p, const double *src, int64_t lds, const double *R
 
 int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, cudaStream_t st)
 {
-    if (p.prec == RXR_SPLIT_BF16) return split_sketch_enqueue(const_cast<Plan &>(p), A, lda, seed, st);
+    if (p.prec != RXR_FP64) return split_sketch_enqueue(const_cast<Plan &>(p), A, lda, seed, st);
     CUtensorMap map;
     const int box_cols = (int)std::min<int64_t>(p.n, kSkNTile);
     const int use_tma = encode_2d(&map, A, p.m, p.n, lda, kSkP, box_cols) ? 1 : 0;
@@ -512,12 +515,17 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
 {
     rxr_handle th = timed ? h : nullptr;
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    if (h && h->test_stall && cudaMemsetAsync(&p.status->flags, kFlagStall, 1, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
     const int n = (int)p.n;
     const bool rows = (variant & RXR_SKETCH_ROWS) != 0;  // row extraction instead of the Gaussian sketch
     variant &= ~RXR_SKETCH_ROWS;
     const bool shifted = variant == RXR_SHIFTED;  // sCholeskyQR3: no sketch, the first Gram shifted
     if (shifted) variant = RXR_NONE;
-    const bool chunk_in = io && p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE && !rows;
+    // RXR_SPLIT_PRECOND without a sketch (CholeskyQR2, shifted CholeskyQR3) has
+    // nothing to take off FP64: its first Gram decides breakdown on A itself
+    const bool precond_only = p.prec == RXR_SPLIT_PRECOND && variant != RXR_NONE;
+    const bool chunk_in = io && p.prec != RXR_FP64 && variant != RXR_NONE && !rows;
     const bool chunk_out = io && p.prec == RXR_SPLIT_BF16 && passes > 1 && p.n <= 64;
     if (io) {
         // the copy stream starts after this stream's earlier work
@@ -593,6 +601,17 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             } else if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) {
                 return e;
             }
+        } else if (precond_only) {
+            // the preconditioning placement: X = A R_s^{-1} by FP64 substitution,
+            // its Gram on the tensor cores (BF16x3 up to n = 128, digit slices above)
+            {
+                Timer t(th, 1, st);
+                if (int e = enqueue_subst(p, A, lda, p.Rs, 0, Q, ldq, false, rows, st)) return e;
+            }
+            Timer t(th, 4, st);
+            if (int e = p.wide ? ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st, false)
+                               : split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st))
+                return e;
         } else if (p.prec == RXR_SPLIT_BF16) {
             // no preconditioner (CholeskyQR2, shifted CholeskyQR3): X_0 = A, and the
             // first Gram on the tensor cores at FP64 grade (it decides breakdown)
@@ -712,7 +731,7 @@ int check_args(const double *A, int64_t m, int64_t n, int64_t lda, int variant, 
     if (Q == nullptr) return -9;
     if (ldq < m) return -10;
     if (R != nullptr && ldr < n) return -12;
-    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -13;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16 && prec != RXR_SPLIT_PRECOND) return -13;
     if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
     if (n > kNarrowN && sketchless) return RXR_ERR_UNSUPPORTED;
     if (m > ((int64_t)1 << 31)) return RXR_ERR_UNSUPPORTED;
@@ -1081,6 +1100,19 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     return code;
 }
 
+int rxr_set_test_hook(rxr_handle h, int hook, int value)
+{
+    if (h == nullptr) return -1;
+    switch (hook) {
+    case RXR_HOOK_STALL: h->test_stall = value != 0; return 0;
+    case RXR_HOOK_JACOBI_SWEEPS:
+        if (value < 0 || value > 40) return -3;
+        h->jacobi_sweeps = value;
+        return 0;
+    default: return -2;
+    }
+}
+
 int rxr_last_info(rxr_handle h, int *pass, int *column)
 {
     if (h == nullptr) return -1;
@@ -1101,6 +1133,7 @@ const char *rxr_status_string(int code)
     case RXR_ERR_NOMEM: return "workspace allocation failed or too small";
     case RXR_ERR_UNSUPPORTED: return "arguments outside what this build supports";
     case RXR_ERR_BAD_SPARSE: return "sparse matrix row pointer or column index out of range";
+    case RXR_ERR_NO_CONVERGENCE: return "Jacobi SVD did not converge within its sweep limit";
     default: return code < 0 ? "invalid argument" : "unknown status";
     }
 }
@@ -1129,7 +1162,7 @@ int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda,
     if (s < 1 || s > RXR_MAX_S) return -6;
     if (Y == nullptr) return -8;
     if (ldy < s) return -9;
-    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -10;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16 && prec != RXR_SPLIT_PRECOND) return -10;
     if (n > kMaxStreamN) return RXR_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     Plan p;
@@ -1240,8 +1273,8 @@ int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, d
     if (ldx < m) return -5;
     if (G == nullptr) return -6;
     if (ldg < n) return -7;
-    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16) return -8;
-    if (n > RXR_MAX_N || (n > kNarrowN && prec == RXR_FP64)) return RXR_ERR_UNSUPPORTED;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16 && prec != RXR_SPLIT_PRECOND) return -8;
+    if (n > RXR_MAX_N || (n > kNarrowN && prec != RXR_SPLIT_BF16)) return RXR_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     Plan p;
     make_plan(p, m, n, n, prec, h->sms);
@@ -1251,6 +1284,8 @@ int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_t ldx, d
     if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
     if (prec == RXR_SPLIT_BF16) {
         if (int e = ozaki_gram_enqueue(p, X, ldx, st)) return e;
+    } else if (prec == RXR_SPLIT_PRECOND) {
+        if (int e = split_gram_enqueue(p, X, ldx, st)) return e;
     } else if (int e = enqueue_subst(p, X, ldx, nullptr, 1, nullptr, m, true, false, st)) {
         return e;
     }
@@ -1417,7 +1452,7 @@ int rxr_rsvd(rxr_handle h, int64_t m, int64_t n, const int64_t *a_ptr, const int
     // B^T = A^T Y = Q_z R_z, R_z = U_r S V_r^T: Y^T A = V_r S (Q_z U_r)^T
     if (int e = at_mul(Qm, ldm)) return e;
     if (int e = orth(pn, Zn, ldn, Qn, Rz)) return e;
-    if (int e = rsvd_jacobi_enqueue(Rz, k, kk, Ur, Vr, S, Vg, acc, st)) return e;
+    if (int e = rsvd_jacobi_enqueue(Rz, k, kk, Ur, Vr, S, Vg, acc, h->jacobi_sweeps, st)) return e;
     if (int e = rsvd_right_mult_enqueue(Qm, ldm, m, kk, Vr, U, ldu, acc, st)) return e;
     if (int e = rsvd_right_mult_enqueue(Qn, ldn, n, kk, Ur, V, ldv, acc, st)) return e;
     return finish_blocking(h, acc, st);

@@ -3,12 +3,13 @@
 //
 // The ordinary entry points keep their scratch (per-chunk partial sums of the
 // sketch and the status word) in a workspace that the handle allocates with
-// cudaMalloc or that the caller hands over.  Some callers can do neither: code
-// that runs while a stream is being captured in global mode (where cudaMalloc
-// is not allowed), processes whose device memory is entirely reserved by
-// another allocator, or loops that forbid any allocation after start-up.  This
-// entry point serves them: its scratch is the file-scope array below, which
-// every GPU that loads the library holds until the process exits.
+// cudaMalloc or that the caller hands over.  Some callers can do neither:
+// processes whose device memory is entirely reserved by another allocator
+// (a framework's caching pool that owns the whole GPU), or loops that forbid
+// any allocation after start-up because cudaMalloc may synchronise the device
+// or take an unbounded time.  This entry point serves them: its scratch is the
+// file-scope array below, which every GPU that loads the library holds until
+// the process exits.
 #include <math.h>
 #include <string.h>
 
@@ -29,6 +30,10 @@ namespace {
 
 // 256 bytes for the status word, then the partial sums: 2^21 doubles (16 MiB).
 constexpr int64_t kNoallocPartials = (int64_t)RXR_NOALLOC_SCRATCH_BYTES / 8 - 32;
+// every admissible request (s <= RXR_MAX_S, n <= 128) has room for at least one
+// row chunk's s x n partial sum, so no size that passes the argument checks is
+// refused for lack of scratch
+static_assert((int64_t)RXR_MAX_S * 128 <= kNoallocPartials, "scratch array below one chunk's partial sum");
 static __device__ __align__(256) double g_noalloc_scratch[RXR_NOALLOC_SCRATCH_BYTES / 8];
 
 constexpr int kMaxDevices = 64;
@@ -83,8 +88,6 @@ extern "C" RXR_API int rxr_sketch_noalloc(const double *A, int64_t m, int64_t n,
     if (Y == nullptr) return -7;
     if (ldy < s) return -8;
     if (n > 128 || m > ((int64_t)1 << 31)) return RXR_ERR_UNSUPPORTED;
-    // at least one row chunk's s x n partial sum must fit in the scratch array
-    if (s * n > kNoallocPartials) return RXR_ERR_NOMEM;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {

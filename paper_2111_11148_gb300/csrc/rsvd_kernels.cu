@@ -127,11 +127,13 @@ __global__ void __launch_bounds__(256) k_csr_spmm(const int64_t *__restrict__ pt
 // pair by more than 2^-27), V_r the product of the rotations, S the column norms of W and
 // U_r = W diag(S)^{-1}; columns sorted by decreasing S.  Outputs k x k
 // column-major with leading dimension k.  Vg: k x k global scratch used for
-// V_r when k > 112.  One CTA of 512 threads; bounded sweeps.
+// V_r when k > 112.  One CTA of 512 threads; at most max_sweeps sweeps, and
+// RXR_ERR_NO_CONVERGENCE in acc when the last one still rotated a pair by more
+// than 2^-27.
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__restrict__ R, int64_t ldr, int k,
                                                               double *__restrict__ Ur, double *__restrict__ Vr,
                                                               double *__restrict__ S, double *__restrict__ Vg,
-                                                              const RxrStatus *acc)
+                                                              RxrStatus *acc, int max_sweeps)
 {
     extern __shared__ double sm[];
     __shared__ double sig[kSvdMaxK];
@@ -148,7 +150,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__r
     __syncthreads();
     const int kk = k + (k & 1);  // an odd k adds a dummy column that sits out one pair per round
     const double tol = sqrt((double)k) * 0x1p-52;
-    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+    bool converged = false;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         // convergence is quadratic: once no rotation of a sweep had a cosine above
         // 2^-27, the cosines it leaves are at rounding level and the next sweep
         // would rotate noise only
@@ -199,8 +202,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_svd(const double *__r
             }
             __syncthreads();
         }
-        if (!__syncthreads_or(large)) break;
+        if (!__syncthreads_or(large)) {
+            converged = true;
+            break;
+        }
     }
+    // the sweep limit reached with a rotation above 2^-27 in the last sweep:
+    // the columns may not be orthogonal yet, reported (column = the limit)
+    if (!converged && tid == 0) rxr_fail(acc, RXR_ERR_NO_CONVERGENCE, -1, max_sweeps);
     for (int j = tid; j < k; j += blockDim.x) {
         double s2 = 0.0;
         for (int r = 0; r < k; ++r) s2 = fma(W[j * k + r], W[j * k + r], s2);
@@ -297,9 +306,10 @@ size_t rsvd_jacobi_smem(int k)
 }
 
 int rsvd_jacobi_enqueue(const double *R, int64_t ldr, int k, double *Ur, double *Vr, double *S, double *Vg,
-                        const RxrStatus *acc, cudaStream_t st)
+                        RxrStatus *acc, int max_sweeps, cudaStream_t st)
 {
-    k_jacobi_svd<<<1, kJacobiThreads, rsvd_jacobi_smem(k), st>>>(R, ldr, k, Ur, Vr, S, Vg, acc);
+    if (max_sweeps < 1 || max_sweeps > kJacobiSweeps) max_sweeps = kJacobiSweeps;
+    k_jacobi_svd<<<1, kJacobiThreads, rsvd_jacobi_smem(k), st>>>(R, ldr, k, Ur, Vr, S, Vg, acc, max_sweeps);
     return rsvd_launch_ok();
 }
 

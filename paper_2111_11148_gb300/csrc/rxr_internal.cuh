@@ -44,6 +44,17 @@ __device__ __forceinline__ bool rxr_failed_block(const RxrStatus *st)
     return __syncthreads_or(threadIdx.x == 0 && rxr_failed(st)) != 0;
 }
 
+// Test hook (rxr_set_test_hook, RXR_HOOK_STALL): when the host sets this bit in
+// the status word's flags, the kernels that stream A by TMA skip the first copy
+// of their first CTA, so that CTA's bounded wait runs out on an mbarrier that
+// nothing arrives at (no copy is in flight) and the call reports
+// RXR_ERR_TIMEOUT through the ordinary error path.
+constexpr int kFlagStall = 1;
+__device__ __forceinline__ bool rxr_stall_requested(const RxrStatus *st)
+{
+    return (*((volatile const int *)&st->flags) & kFlagStall) != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of
 //   (c0,c1,c2,c3) -> (hi(Mb*c2)^c1^k0, lo(Mb*c2), hi(Ma*c0)^c3^k1, lo(Ma*c0))
@@ -174,9 +185,12 @@ __device__ __forceinline__ bool rxr_nonfinite(double v)
 
 // ---------------------------------------------------------------------------
 // mbarrier + TMA (cp.async.bulk.tensor) helpers.  Every wait is bounded: after
-// kSpinLimit polls the waiter records RXR_ERR_TIMEOUT and gives up.
+// kSpinLimit polls the waiter records RXR_ERR_TIMEOUT and gives up.  Each poll
+// may suspend the thread for at most kWaitHintNs (the phase completing wakes it
+// earlier), so a wait that never completes gives up after about a second.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr uint32_t kWaitHintNs = 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -214,10 +228,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
@@ -419,8 +433,9 @@ int blocked_factor_enqueue(const double *G, int n, int64_t ldg, double *Rp, doub
 int rsvd_transpose_enqueue(const double *X, int64_t ldx, int64_t rows, int k, double *Xr, cudaStream_t st);
 int rsvd_spmm_enqueue(const int64_t *ptr, const int32_t *idx, const double *val, int64_t nnz, int64_t rows,
                       int64_t cols, const double *Xr, int k, double *Y, int64_t ldy, RxrStatus *acc, cudaStream_t st);
+// max_sweeps outside 1..40 takes the default bound of 40 sweeps
 int rsvd_jacobi_enqueue(const double *R, int64_t ldr, int k, double *Ur, double *Vr, double *S, double *Vg,
-                        const RxrStatus *acc, cudaStream_t st);
+                        RxrStatus *acc, int max_sweeps, cudaStream_t st);
 int rsvd_right_mult_enqueue(const double *X, int64_t ldx, int64_t rows, int k, const double *T, double *Y,
                             int64_t ldy, const RxrStatus *acc, cudaStream_t st);
 int rsvd_status_keep_enqueue(const RxrStatus *cur, RxrStatus *acc, int call, cudaStream_t st);

@@ -1055,15 +1055,21 @@ __global__ void __launch_bounds__(256, 1)
     uint32_t loads = 0, mphase = 0;  // TMA loads consumed; tensor-core commits consumed
     unsigned cmax_lo = 0, cmax_hi = 0;  // largest exponent of columns lane and lane + 32 (colexp_out)
     bool ok = true, load_pending = false, mma_pending = false;
+    // the stall test hook: group 0 of the first CTA skips its first copy, so its
+    // wait runs out with nothing in flight and the drain below runs
+    bool stall = use_tma && blockIdx.x == 0 && g == 0 && rxr_stall_requested(st);
     const int64_t stride = 2 * (int64_t)gridDim.x;
     for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < tiles_total && ok; tile += stride) {
         const int64_t r0 = tile * kFuM;
         if (use_tma) {
             if (leader) {
                 bulk_wait_read_all();  // the previous tile's store has left shared memory
-                mbar_arrive_expect_tx(&full_bar[g], (uint32_t)tile_bytes);
-                tma_load_2d(xs, &tm_src, (int)r0, 0, &full_bar[g]);
+                if (!stall) {
+                    mbar_arrive_expect_tx(&full_bar[g], (uint32_t)tile_bytes);
+                    tma_load_2d(xs, &tm_src, (int)r0, 0, &full_bar[g]);
+                }
             }
+            stall = false;
             load_pending = true;
             const bool got = mbar_wait_bounded(&full_bar[g], loads & 1u, st);
             ok = !group_or(g, !got);

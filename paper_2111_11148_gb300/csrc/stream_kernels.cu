@@ -45,10 +45,12 @@ __global__ void k_omega(uint64_t seed, int64_t s, int64_t row0, int64_t rows, fl
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, bool use_tma, uint64_t *bar,
                                            uint32_t &phase, const double *__restrict__ src, int64_t ld, int64_t m,
-                                           int64_t r0, int c0, int P, int nc, int ncols_total, RxrStatus *st)
+                                           int64_t r0, int c0, int P, int nc, int ncols_total, RxrStatus *st,
+                                           bool skip_copy = false)
 {
     if (use_tma) {
-        if (threadIdx.x == 0) {
+        // skip_copy (the stall test hook): nothing arrives, the wait runs out
+        if (threadIdx.x == 0 && !skip_copy) {
             mbar_arrive_expect_tx(bar, (uint32_t)(P * nc * 8));
             tma_load_2d(dst, map, (int)r0, c0, bar);
         }
@@ -145,9 +147,12 @@ __device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tm
 
     const int64_t p_begin = bx * panels_per_cta;
     const int64_t p_end = min(panels_total, p_begin + panels_per_cta);
+    const bool stall = use_tma && bx == 0 && by == 0 && rxr_stall_requested(st);
     for (int64_t p = p_begin; p < p_end; ++p) {
         const int64_t r0 = p * kSkP;
-        if (!load_panel(ap, tmapA, use_tma, &bar, phase, A, lda, m, r0, c0, kSkP, box_cols, n, st)) return;
+        if (!load_panel(ap, tmapA, use_tma, &bar, phase, A, lda, m, r0, c0, kSkP, box_cols, n, st,
+                        stall && p == p_begin))
+            return;
         // Omega columns for the panel's rows: zp[row][r - s0]
         for (int c = threadIdx.x; c < kSkP * kcount; c += blockDim.x) {
             const int row = c / kcount, kk = c % kcount;

@@ -32,7 +32,7 @@ import math
 
 import numpy as np
 
-__all__ = ["sigma_profile", "usv_matrix", "batch_specs", "BatchSpec", "Csr", "sparse_operator",
+__all__ = ["sigma_profile", "usv_factors", "usv_matrix", "batch_specs", "BatchSpec", "Csr", "sparse_operator",
            "planted_operator", "start_block"]
 
 
@@ -71,6 +71,12 @@ def _haar(n: int, rng: np.random.Generator) -> np.ndarray:
     d = np.sign(np.diag(r))
     d[d == 0] = 1.0
     return q * d
+
+
+def usv_factors(n: int, kappa: float, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """(sigma, V) of ``usv_matrix(m, n, kappa, seed)``: the singular values and
+    the n x n orthogonal factor, the same for every m."""
+    return sigma_profile(n, kappa), _haar(n, _rng(seed, 2))
 
 
 def usv_matrix(m: int, n: int, kappa: float, seed: int = 0, *, order: str = "F",

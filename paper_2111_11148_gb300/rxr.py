@@ -21,14 +21,17 @@ LIB_PATH = os.path.join(_HERE, "librxr.so")
 
 LU, QR, NONE, SHIFTED = 0, 1, 2, 3
 SKETCH_ROWS = 16  # OR-ed into LU / QR: the sketch by row extraction
-FP64, SPLIT_BF16 = 0, 1
-OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED, BAD_SPARSE = range(9)
+FP64, SPLIT_BF16, SPLIT_PRECOND = 0, 1, 3
+(OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED, BAD_SPARSE,
+ NO_CONVERGENCE) = range(10)
+HOOK_STALL, HOOK_JACOBI_SWEEPS = 1, 2  # rxr_set_test_hook
 KERNEL_SKETCH, KERNEL_PRECOND_GRAM, KERNEL_PASS_GRAM, KERNEL_APPLY = range(4)
 
 _VARIANTS = {"lu": LU, "qr": QR, "none": NONE, "shifted": SHIFTED, "lu-rows": LU | SKETCH_ROWS,
              "qr-rows": QR | SKETCH_ROWS, LU: LU, QR: QR, NONE: NONE, SHIFTED: SHIFTED,
              LU | SKETCH_ROWS: LU | SKETCH_ROWS, QR | SKETCH_ROWS: QR | SKETCH_ROWS}
-_PRECS = {"fp64": FP64, "split": SPLIT_BF16, "split_bf16": SPLIT_BF16, FP64: FP64, SPLIT_BF16: SPLIT_BF16}
+_PRECS = {"fp64": FP64, "split": SPLIT_BF16, "split_bf16": SPLIT_BF16, "split_precond": SPLIT_PRECOND,
+          FP64: FP64, SPLIT_BF16: SPLIT_BF16, SPLIT_PRECOND: SPLIT_PRECOND}
 
 
 class RxrError(RuntimeError):
@@ -77,6 +80,7 @@ def load() -> ctypes.CDLL:
         "rxr_last_kernel_ms": ([vp, i, P(ctypes.c_float)], i),
         "rxr_set_kernel_timing": ([vp, i], i),
         "rxr_sketch_noalloc": ([vp, i64, i64, i64, i64, u64, vp, i64, vp], i),
+        "rxr_set_test_hook": ([vp, i, i], i),
         "rxr_rsvd": ([vp, i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, i64, i64, i, i, i64, u64, i, i, vp, i64, vp, vp,
                       i64, vp], i),
     }
@@ -94,7 +98,8 @@ def exported_symbols() -> list[str]:
                         "rxr_status_string", "rxr_omega", "rxr_sketch", "rxr_sketch_rows", "rxr_xr_factor",
                         "rxr_precond_gram",
                         "rxr_cholesky", "rxr_apply_rinv", "rxr_lstsq", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
-                        "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc", "rxr_rsvd")]
+                        "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc", "rxr_rsvd",
+                        "rxr_set_test_hook")]
 
 
 def status_string(code: int) -> str:
@@ -171,6 +176,11 @@ class Handle:
 
     def __enter__(self):
         return self
+
+    def set_test_hook(self, hook: int, value: int):
+        """rxr_set_test_hook: HOOK_STALL (a bounded device wait runs out) or
+        HOOK_JACOBI_SWEEPS (cap on the randomized SVD's Jacobi sweeps)."""
+        _check(load().rxr_set_test_hook(self._h, int(hook), int(value)), "rxr_set_test_hook")
 
     def __exit__(self, *a):
         self.close()

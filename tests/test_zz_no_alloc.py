@@ -38,7 +38,11 @@ def _bound(A_np, s, seed):
 
 
 def test_noalloc_sketch_matches_workspace_sketch_on_consecutive_calls():
-    cases = [(20000, 64, 128, 0, 1e4), (5000, 16, 33, 7, 1e10), (20000, 64, 128, 0, 1e4)]
+    # the third case is the largest admissible sketch (s = 2048, n = 128): there
+    # the scratch array holds 7 row chunks' partial sums, fewer than the launch
+    # geometry asks for (10), so the chunk cap binds
+    cases = [(20000, 64, 128, 0, 1e4), (5000, 16, 33, 7, 1e10), (20000, 128, 2048, 3, 1e6),
+             (20000, 64, 128, 0, 1e4)]
     with rxr.Handle(0) as h:
         first = None
         for m, n, s, seed, kappa in cases:
@@ -51,8 +55,8 @@ def test_noalloc_sketch_matches_workspace_sketch_on_consecutive_calls():
             assert np.all(np.abs(Yn - Yref) <= 2 * _bound(A_np, s, seed))
             if first is None:
                 first = Yn
-        # the array keeps the previous call's contents; the third call repeats the
-        # first and must not depend on what the second left behind
+        # the array keeps the previous call's contents; the last call repeats the
+        # first and must not depend on what the calls between left behind
         assert np.array_equal(first, Yn)
 
 
