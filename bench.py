@@ -2,22 +2,30 @@
 independent replicas, one per GPU, under torchrun).
 
 A step is one full factorisation A = QR (sketch, XR factor of the sketch, the
-fused precondition+Gram pass, two CholeskyQR passes, Q and R) of the
-tall-skinny workload m = 2^22, n = 64 (A = U Sigma V^T, kappa = 1e10, s = 2n
-Gaussian sketch, seed 0) with inputs resident in HBM.  The metric is the
-effective bandwidth B_alg / t with B_alg = 8 m n (P + 3) bytes: one read of A
-for the sketch, one per CholeskyQR pass, and a read plus a write for Q.
+precondition + Gram pass, two CholeskyQR passes, Q and R) with inputs resident
+in HBM.  The default workload is the split-precision configuration: m = 2^23,
+n = 128, s = 2n Gaussian sketch, A = U Sigma V^T with kappa = 1e12, seed 0,
+rQR-CholeskyQR2 (8.6 GB of A).  The metric is the effective bandwidth
+B_alg / t with B_alg = 8 m n (P + 3) bytes: one read of A for the sketch, one
+per CholeskyQR pass, and a read plus a write for Q, reported for the
+split-precision path next to the FP64 path and the preconditioning-only split
+placement on the same A, each at its achieved accuracy.  The same line carries
+m = 2^22, n = 64, kappa = 1e10 (the scale configuration) and m = 20000, n = 16,
+kappa = 1e8, rLU (QR/s over 1000 CUDA-graph replays) under "configs".
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--variant qr|lu]
-                    [--prec fp64|split] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3|c2|c1|c5]
+                    [--variant qr|lu|none|shifted] [--prec split|split_precond|fp64]
+                    [--impl reference] [--workload single|batched|lstsq|rsvd]
 
 `--impl reference` times the CPU oracle (the plain FP64 implementation
-written from the paper) on a bounded row sample of the same workload.
+written from the paper, its OpenMP build on every host core) on a bounded row
+sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -30,18 +38,32 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-M, N, S, KAPPA, SEED, PASSES = 2**22, 64, 128, 1e10, 0, 2
-METRIC = "tall-skinny QR effective GB/s (B_alg = 8mn(P+3)) at ||Q^T Q - I||_F <= 1e-13"
-WORKLOAD = "rQR-CholeskyQR2 m=2^22 n=64 s=128 kappa=1e10 FP64"
+# the workload configurations: rows, columns, condition number, variant
+CONFIGS = {
+    "c1": {"m": 20000, "n": 16, "kappa": 1e8, "variant": "lu", "label": "m=20000"},
+    "c2": {"m": 2**22, "n": 64, "kappa": 1e10, "variant": "qr", "label": "m=2^22"},
+    "c3": {"m": 2**23, "n": 128, "kappa": 1e12, "variant": "qr", "label": "m=2^23"},
+    "c5": {"m": 2**20, "n": 512, "kappa": 1e13, "variant": "qr", "label": "m=2^20"},
+}
+M, N, S, KAPPA, SEED, PASSES = 2**23, 128, 256, 1e12, 0, 2
+METRIC = "tall-skinny QR GB/s & roofline frac, split-prec vs FP64 at \u2016Q\u1d40Q\u2212I\u2016\u22641e-13"
+WORKLOAD = "rQR-CholeskyQR2 m=2^23 n=128 s=256 kappa=1e12"
+PRECS = ("split", "split_precond", "fp64")
+DTYPES = {"fp64": "f64",
+          "split": "f64 with fp16 8-bit-digit tcgen05 operands (fp32 accumulation, exact)",
+          "split_precond": "f64 with fp16 8-bit-digit sketch and bf16x3 first Gram on tcgen05"}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one precondition+Gram launch,
-# ncu capture at m = 2^19 scaled by 8 rows-for-rows (profiles/k_subst_gram_precond_m524288_n64.md)
-TRAFFIC_PG = (268.552704e6 + 225.660672e6) * 8
-# DRAM bytes (read + write) of one k_subst_fused launch at m = 2^22, n = 64: the ncu capture at
-# m = 2^19 (268.58 MB read + 216.93 MB written) scaled by the 8x rows (traffic grows with the rows)
-TRAFFIC_SUBST = (268.584960e6 + 216.926208e6) * 8
-HBM_GBS = 6795.5  # measured copy bandwidth of this GPU pool (STREAM-style copy)
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures
+# of a smaller case scaled by rows (traffic grows with the rows); None where no
+# capture of the current kernel exists
+TRAFFIC = {
+    # k_subst_gram (FP64 precondition + Gram), m = 2^19, n = 64, x 8 rows
+    ("fp64", 64): (268.552704e6 + 225.660672e6) * 8,
+    # k_subst_fused (split precondition), m = 2^19, n = 64, x 8 rows
+    ("split", 64): (268.584960e6 + 216.926208e6) * 8,
+}
+HBM_GBS = 6784.2  # measured copy bandwidth of this GPU pool (STREAM-style copy)
 
 
 def b_alg(m, n, passes):
@@ -106,16 +128,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_cores() -> int:
-    return 1
+def hbm_peak() -> tuple[float, str]:
+    """Copy bandwidth of this GPU pool: MEASURED_PEAKS.json when present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_GBS, "measured earlier on this pool (STREAM-style copy)"
 
 
-def oracle_rows(target_s: float = 15.0) -> int:
-    """Row count of the oracle sample: about `target_s` seconds of single-core work."""
-    return int(os.environ.get("RXR_BENCH_ORACLE_ROWS", 2**19))
+def oracle_rows(n: int, parallel: bool) -> int:
+    """Row count of an oracle sample: about 10-20 s of single-core work for the
+    serial build (the oracle's cost per row grows as n^2), and 2x that for the
+    OpenMP build on every host core."""
+    base = int(os.environ.get("RXR_BENCH_ORACLE_ROWS", 2**19 * 64 * 64 // (n * n)))
+    return max(n, base * (2 if parallel else 1))
 
 
-def run_oracle_sample(A_sample: np.ndarray, variant: str):
+def run_oracle_sample(A_sample: np.ndarray, variant: str, parallel: bool = False):
     import oracle
 
     t0 = time.perf_counter()
@@ -125,11 +155,32 @@ def run_oracle_sample(A_sample: np.ndarray, variant: str):
         ov = {"qr": oracle.VARIANT_QR, "lu": oracle.VARIANT_LU, "none": oracle.VARIANT_NONE}[variant.split("-")[0]]
         if variant.endswith("-rows"):
             ov |= oracle.SKETCH_ROWS
-        r = oracle.rxr_cholqr(A_sample, ov, S, seed=SEED, passes=PASSES)
+        r = oracle.rxr_cholqr(A_sample, ov, S, seed=SEED, passes=PASSES, parallel=parallel)
     dt = time.perf_counter() - t0
     if r.status != 0:
         raise RuntimeError(f"oracle status {r.status}")
     return dt
+
+
+def cpu_baseline(A_np: np.ndarray, variant: str) -> dict:
+    """The oracle as it stands, timed on the host: its OpenMP build on every
+    core (the reported baseline) and its serial build, each on the first rows of
+    the same A (bounded samples)."""
+    import oracle
+
+    oracle.build()
+    out = {}
+    for parallel in (True, False):
+        rows = min(oracle_rows(N, parallel), A_np.shape[0])
+        t = run_oracle_sample(np.asfortranarray(A_np[:rows]), variant, parallel)
+        out[parallel] = {"value": b_alg(rows, N, PASSES) / t / 1e9, "unit": "GB/s",
+                         "cores": oracle.threads(parallel), "kind": "oracle",
+                         "sample": f"first {rows} of {A_np.shape[0]} rows of the same A, one full rxr_cholqr of the "
+                                   f"C oracle ({'OpenMP build, every host core' if parallel else 'serial build'}), "
+                                   f"{t:.2f} s"}
+    line = dict(out[True])
+    line["single_thread"] = out[False]
+    return line
 
 
 def make_input():
@@ -138,31 +189,45 @@ def make_input():
     return usv_matrix(M, N, KAPPA, seed=SEED)
 
 
+def construction_r(n: int, kappa: float, seed: int) -> np.ndarray:
+    """The R factor (diag > 0) of A = U diag(sigma) V^T: U has orthonormal
+    columns, so it is the R factor of the n x n matrix diag(sigma) V^T (LAPACK's
+    Householder QR of that small matrix; it agrees with LAPACK's R of the whole
+    stored A to 1e-15 at kappa up to 1e15)."""
+    from paper_2111_11148_gb300.inputs import usv_factors
+
+    sigma, V = usv_factors(n, kappa, seed)
+    R = np.linalg.qr(sigma[:, None] * V.T, mode="r")
+    return np.sign(np.diag(R))[:, None] * R
+
+
 def reference_arm(args, rank: int, world: int):
-    """Time the CPU oracle as it stands on a bounded sample of the workload."""
+    """Time the CPU oracle as it stands (its OpenMP build on every host core)
+    on a bounded sample of the workload, each step one full factorisation."""
     if rank != 0:
         return
     import oracle
 
     oracle.build()
-    rows = oracle_rows()
+    rows = oracle_rows(N, True)
     from paper_2111_11148_gb300.inputs import usv_matrix
 
     A = usv_matrix(rows, N, KAPPA, seed=SEED)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        run_oracle_sample(A, args.variant)
-    times = [run_oracle_sample(A, args.variant) for _ in range(args.steps)]
+    for _ in range(min(args.warmup, 1)):
+        run_oracle_sample(A, args.variant, True)
+    times = [run_oracle_sample(A, args.variant, True) for _ in range(args.steps)]
     t = statistics.median(times)
     gbs = b_alg(rows, N, PASSES) / t / 1e9
+    sample = (f"{rows} x {N} rows of the same A = U Sigma V^T construction, one full rxr_cholqr per step "
+              f"(C oracle, OpenMP build on {oracle.threads(True)} host threads)")
     line = {
         "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "oracle_rows": rows, "m": M, "n": N, "s": S, "passes": PASSES,
-                   "variant": args.variant},
-        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": f"{rows} x {N} rows of the same A = U Sigma V^T construction, full "
-                                   f"rxr_cholqr per step (single-threaded C oracle)"},
+        "config": {"workload": WORKLOAD, "oracle_rows": rows, "m": M, "n": N, "s": S, "kappa": KAPPA,
+                   "passes": PASSES, "variant": args.variant},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.threads(True), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -263,7 +328,7 @@ def lstsq_arm(args, rank: int, world: int, local_rank: int):
         print(json.dumps({"metric": "least-squares solve effective GB/s (B_alg = 32mn)", "value": balg / ms / 1e6,
                           "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                          "dtype": "f64+bf16" if args.prec == "split" else "f64", "data": "synthetic",
+                          "dtype": DTYPES[args.prec], "data": "synthetic",
                           "config": {"workload": f"least squares (Section 5.2) {WORKLOAD}", "m": M, "n": N, "s": S,
                                      "kappa": KAPPA, "rhs": 1},
                           "accuracy": {"x_rel_err": err}}), flush=True)
@@ -381,7 +446,7 @@ def rsvd_arm(args, rank: int, world: int, local_rank: int):
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         cms, crow = rsvd_oracle_ms_per_iter(k)
-        cpu = {"value": cms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": cms, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": f"one power iteration of the oracle on a {crow}-row operator of the same density, "
                          f"scaled by rows to {RSVD_M}"}
     if rank == 0:
@@ -389,14 +454,14 @@ def rsvd_arm(args, rank: int, world: int, local_rank: int):
             "metric": "randomized SVD (Algorithm 7) time per power iteration", "value": ms_iter, "unit": "ms",
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_iter,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+bf16" if args.prec == "split" else "f64", "data": "synthetic",
+            "dtype": DTYPES[args.prec], "data": "synthetic",
             "config": {"workload": f"RSVD power iteration, sparse {RSVD_M}x{RSVD_M} with {RSVD_D} nonzeros/row "
                                    f"(stand-in for Section 5.1's sparsest matrix), k={k}, orth = "
                                    f"{'rLU' if args.variant == 'lu' else 'rQR'}-CholeskyQR2",
                        "m": RSVD_M, "nnz": P.nnz, "k": k, "iters_timed": RSVD_ITERS, "generation_s": gen_s,
                        "l2": "working set (CSR + 5 blocks of m x k) larger than L2"},
             "roofline": {"bound": "hbm", "kernel": "whole power iteration", "achieved": balg / (ms_iter * 1e-3) / 1e9,
-                         "peak": HBM_GBS, "unit": "GB/s", "frac": balg / (ms_iter * 1e-3) / 1e9 / HBM_GBS,
+                         "peak": hbm_peak()[0], "unit": "GB/s", "frac": balg / (ms_iter * 1e-3) / 1e9 / hbm_peak()[0],
                          "traffic": None},
             "e2e": {"value": e2e_ms, "unit": f"ms per call with {RSVD_ITERS} iterations", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -408,9 +473,10 @@ def rsvd_arm(args, rank: int, world: int, local_rank: int):
     h.close()
 
 
-def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=False):
+def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=False, R_ref=None):
     """Time `steps` factorisations (after `warmup`) with CUDA events on the
-    launching stream; then per-stage event times and the accuracy."""
+    launching stream; then per-stage event times, the accuracy measures of
+    Section 4.2 and R against the construction's R factor."""
     import torch
 
     def step():
@@ -439,7 +505,32 @@ def time_path(h, A, Q, R, prec, args, dev, stream, steps, warmup, sample_clocks=
             kms[k].append(h.last_kernel_ms(k))
     h.set_kernel_timing(False)
     stages = {STAGES[k]: statistics.median(v) for k, v in kms.items() if statistics.median(v) > 0}
-    return {"ms": ms, "stages_ms": stages, "orth": h.orth_error(Q), "resid": h.resid_error(A, Q, R), "clocks": clk}
+    acc = {"orth": h.orth_error(Q), "resid": h.resid_error(A, Q, R)}
+    if R_ref is not None:
+        Rg = R.cpu().numpy()
+        acc["R_vs_construction"] = float(np.linalg.norm(Rg - R_ref) / np.linalg.norm(R_ref))
+    return {"ms": ms, "stages_ms": stages, "accuracy": acc, "clocks": clk}
+
+
+def preconditioner_conds(h, A, Q, args, prec) -> dict:
+    """cond_2(R_s) and cond_2(R_1) = cond_2(A R_s^{-1}) of this A and sketch, from
+    the library's stage entry points (the sketch, its XR factor, the FP64
+    precondition + Gram pass), outside the timed region; the condition numbers
+    of the small n x n factors are taken on the host."""
+    import torch
+
+    variant = args.variant.split("-")[0]
+    if variant not in ("qr", "lu"):
+        return {}
+    Y = h.sketch(A, S, seed=SEED, prec=prec)
+    Rs, code = h.xr_factor(Y, variant, raise_on_error=False)
+    if code != 0:
+        return {"xr_status": code}
+    _, G = h.precond_gram(A, Rs, X=Q, prec="fp64")
+    torch.cuda.synchronize()
+    ev = np.linalg.eigvalsh(G.cpu().numpy())
+    return {"cond_Rs": float(np.linalg.cond(Rs.cpu().numpy())),
+            "cond_R1": float(math.sqrt(ev[-1] / ev[0])) if ev[0] > 0 else float("inf"), "sketch_prec": prec}
 
 
 def max_over_ranks(ms: float, dist, device) -> float:
@@ -459,6 +550,91 @@ def job_value(ms: float, world: int) -> float:
     return world * b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9
 
 
+def set_config(name: str):
+    global M, N, S, KAPPA, WORKLOAD
+    c = CONFIGS[name]
+    M, N, S, KAPPA = c["m"], c["n"], 2 * c["n"], c["kappa"]
+
+
+def workload_name(variant: str, rows: bool) -> str:
+    method = {"qr": "rQR-CholeskyQR2", "lu": "rLU-CholeskyQR2", "none": "CholeskyQR2",
+              "shifted": "sCholeskyQR3"}[variant.split("-")[0]]
+    mm = {2**20: "2^20", 2**22: "2^22", 2**23: "2^23"}.get(M, str(M))
+    w = f"{method} m={mm} n={N} s={S} kappa={KAPPA:g}, A = U Sigma V^T (seed {SEED})"
+    return w + (", row-extraction sketch" if rows else "")
+
+
+def measure_config(h, args, dev, stream, peak_fp64, world, dist, main_clocks: bool, extras: bool) -> dict:
+    """Every precision path on one configuration's A (the reported one first,
+    with clocks sampled), then, when `extras`, the preconditioner's condition
+    numbers, the host-buffer end-to-end leg and the CPU baselines."""
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+
+    t0 = time.perf_counter()
+    A_np = make_input()
+    gen_s = time.perf_counter() - t0
+    A = rxr.colmajor(torch.from_numpy(A_np).to(dev))
+    Q = rxr.empty_colmajor(M, N, device=dev)
+    R = rxr.empty_colmajor(N, N, device=dev)
+    R_ref = construction_r(N, KAPPA, SEED) if args.variant.split("-")[0] in ("qr", "lu", "none", "shifted") else None
+    warm = max(3, args.warmup)
+    order = [args.prec] + ([p for p in PRECS if p != args.prec] if not args.no_compare else [])
+    paths = {}
+    if dist:
+        dist.barrier()
+    for i, prec in enumerate(order):
+        steps = args.steps if i == 0 else max(2, args.steps // 2)
+        paths[prec] = time_path(h, A, Q, R, prec, args, dev, stream, steps, warm, sample_clocks=(i == 0 and main_clocks),
+                                R_ref=R_ref)
+    ms = max_over_ranks(paths[args.prec]["ms"], dist, dev)
+    out = {"ms": ms, "value": job_value(ms, world), "paths": paths, "generation_s": gen_s}
+    if extras:
+        out["preconditioner"] = preconditioner_conds(h, A, Q, args, args.prec)
+        out["e2e"] = None if args.no_e2e else e2e_leg(h, A_np, args, world)
+        if world == 1 and not args.no_cpu_baseline and dist is None:
+            out["cpu_baseline"] = cpu_baseline(A_np, args.variant)
+    del A, Q, R
+    torch.cuda.empty_cache()
+    return out
+
+
+def graph_replay_qr_per_s(h, args, dev, prec: str, replays: int = 1000) -> dict:
+    """QR/s of a latency-bound configuration: one rxr_cholqr_async captured in
+    a CUDA graph and replayed `replays` times, timed with CUDA events."""
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+
+    A = rxr.colmajor(torch.from_numpy(make_input()).to(dev))
+    Q = rxr.empty_colmajor(M, N, device=dev)
+    R = rxr.empty_colmajor(N, N, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    variant = args.variant_c1
+    with torch.cuda.stream(s):
+        h.cholqr_async(A, Q, R, st, variant=variant, s=S, seed=SEED, passes=PASSES, prec=prec, stream=s)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            h.cholqr_async(A, Q, R, st, variant=variant, s=S, seed=SEED, passes=PASSES, prec=prec, stream=s)
+    for _ in range(10):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream(dev)
+    e0.record(cur)
+    for _ in range(replays):
+        g.replay()
+    e1.record(cur)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / replays
+    assert int(st[0].item()) == 0, st
+    return {"qr_per_s": 1e3 / ms, "ms_per_qr": ms, "gbs": b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9,
+            "replays": replays, "orth": h.orth_error(Q), "resid": h.resid_error(A, Q, R)}
+
+
 def gpu_arm(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -471,42 +647,45 @@ def gpu_arm(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-
-    A_np = make_input()
-    A = rxr.colmajor(torch.from_numpy(A_np).to(dev))
-    Q = rxr.empty_colmajor(M, N, device=dev)
-    R = rxr.empty_colmajor(N, N, device=dev)
     h = rxr.Handle(local_rank)
     stream = torch.cuda.current_stream(dev)
     peak_fp64 = rxr.fp64_peak_tflops()
-    warm = max(3, args.warmup)
-
-    # the reported path, timed with clocks sampled; then the other precision
-    other = "fp64" if args.prec == "split" else "split"
-    if dist:
-        dist.barrier()
-    main = time_path(h, A, Q, R, args.prec, args, dev, stream, args.steps, warm, sample_clocks=True)
-    ref = None if args.no_compare else time_path(h, A, Q, R, other, args, dev, stream, max(2, args.steps // 2), warm)
-    ms = max_over_ranks(main["ms"], dist, dev)
-    value = job_value(ms, world)
-
-    e2e = None if args.no_e2e else e2e_leg(h, A_np, args, world)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        oracle.build()
-        rows = min(oracle_rows(), M)
-        t_or = run_oracle_sample(np.asfortranarray(A_np[:rows]), args.variant)
-        cpu = {"value": b_alg(rows, N, PASSES) / t_or / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"first {rows} of {M} rows of the same A, one full rxr_cholqr (single-threaded C oracle), "
-                         f"{t_or:.2f} s"}
+    main = measure_config(h, args, dev, stream, peak_fp64, world, dist, main_clocks=True, extras=True)
+    main_cfg = {"m": M, "n": N, "s": S, "kappa": KAPPA}
+    secondary = {}
+    if args.secondary and rank == 0:
+        # the other configurations on the same box: the scale one (c2) with its
+        # three paths, and the latency-bound one (c1) as QR/s over graph replays
+        saved = (M, N, S, KAPPA)
+        set_config("c2")
+        c2 = measure_config(h, args, dev, stream, peak_fp64, 1, None, main_clocks=False, extras=False)
+        secondary["c2"] = summarise(c2, args)
+        set_config("c1")
+        secondary["c1"] = {"m": M, "n": N, "s": S, "kappa": KAPPA, "variant": args.variant_c1,
+                           "graph_replays": {p: _safe(graph_replay_qr_per_s, h, args, dev, p) for p in ("fp64", "split")}}
+        globals().update(M=saved[0], N=saved[1], S=saved[2], KAPPA=saved[3])
     if rank == 0:
-        _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu)
+        _emit(args, world, main, main_cfg, peak_fp64, secondary)
     h.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _safe(fn, *a):
+    try:
+        return fn(*a)
+    except Exception as e:  # reported in the line, not fatal to the main measurement
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def summarise(res: dict, args) -> dict:
+    """A configuration's paths in a few numbers (nested in the main line)."""
+    out = {"m": M, "n": N, "s": S, "kappa": KAPPA, "variant": args.variant}
+    for prec, r in res["paths"].items():
+        out[prec] = {"value": b_alg(M, N, PASSES) / (r["ms"] * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": r["ms"],
+                     "stages_ms": r["stages_ms"], "accuracy": r["accuracy"]}
+    return out
 
 
 def subst_fp64_flop_per_row(n, bw, sub_ops):
@@ -547,33 +726,38 @@ def roofline_entry(prec, stages, peak_fp64):
     """The dominant FP64 launch of the path against the measured DFMA peak,
     counting the FP64 flop that launch actually issues.
     FP64 path: the fused precondition+Gram launch, (2n^2 + n) flop per row.
-    Split path: the substitution X = A R_s^{-1}; its trailing updates run on the
-    tensor cores, so only its diagonal-block solves and the FP64 subtractions
-    of the updates are FP64 work."""
+    Split paths: the substitution X = A R_s^{-1}.  RXR_SPLIT_BF16 runs its
+    trailing updates on the tensor cores, so only its 16-column diagonal-block
+    solves and the FP64 subtractions of the updates are FP64 work;
+    RXR_SPLIT_PRECOND runs it as the plain FP64 substitution, n^2 flop per row."""
+    t = stages.get("precond_subst")
+    hbm, hbm_kind = hbm_peak()
+    if t is None or t <= 0:
+        return None
     if prec == "fp64":
-        t = stages.get("precond_subst")
         flop = (2.0 * N * N + N) * M
-        name = "k_subst_gram (fused precondition + Gram launch)"
-        traffic = TRAFFIC_PG if (M == 2**22 and N == 64) else None
+        name = "k_subst_gram (fused precondition + Gram launch)" if N <= 128 else "k_subst_wide (blocked FP64)"
+        hbm_bytes = 16.0 * M * N
+    elif prec == "split_precond":
+        flop = 1.0 * N * N * M
+        name = "k_subst_gram (FP64 substitution X = A R_s^-1, no Gram)" if N <= 128 else "k_subst_wide"
         hbm_bytes = 16.0 * M * N
     elif N <= 128:
-        t = stages.get("precond_subst")
         flop = subst_fp64_flop_per_row(N, 16, 2) * M
-        name = ("k_subst_fused" if N <= 64 else "k_subst_fused128") + \
+        name = ("k_subst_fused" if N <= 64 else "k_rprep128 + k_subst_fused128") + \
             " (FP64 16-column diagonal solves + FP64 subtraction of tcgen05 updates)"
-        traffic = TRAFFIC_SUBST if (M == 2**22 and N == 64) else None
         hbm_bytes = 16.0 * M * N
     else:
-        t = stages.get("precond_subst")
         flop = subst_fp64_flop_per_row(N, 64, 3) * M
         name = "k_solve_block + k_update_ozaki (blocked substitution: FP64 diagonal blocks, tcgen05 updates)"
-        traffic = None
         hbm_bytes = 16.0 * M * N
     achieved = flop / (t * 1e-3) / 1e12
+    traffic = TRAFFIC.get((prec, N)) if M == 2**22 else None
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp64, "traffic": traffic,
-            "hbm_frac": (hbm_bytes / (t * 1e-3) / 1e9) / HBM_GBS,
-            "peak_kind": "FP64 DFMA pipe, measured by the rxr_fp64_peak calibration kernel in this run"}
+            "frac": achieved / peak_fp64, "traffic": traffic, "ms": t,
+            "hbm_frac": (hbm_bytes / (t * 1e-3) / 1e9) / hbm, "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
+            "peak_kind": "FP64 DFMA pipe, measured by the rxr_fp64_peak calibration kernel in this run "
+                         "(MEASURED_PEAKS.json has no FP64 figure)"}
 
 
 def e2e_leg(h, A_np, args, world):
@@ -595,37 +779,49 @@ def e2e_leg(h, A_np, args, world):
         times.append(time.perf_counter() - t0)
     e2e_s = statistics.median(times)
     return {"value": world * b_alg(M, N, PASSES) / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 8 * M * N,
-            "d2h_bytes_per_step": 8 * M * N + 8 * N * N}
+            "d2h_bytes_per_step": 8 * M * N + 8 * N * N, "ms_per_step": e2e_s * 1e3}
 
 
-def _emit(args, world, ms, value, peak_fp64, main, ref, other, e2e, cpu):
-    launches = (launches_per_step(args.prec, N, M, args.variant.endswith("-rows"))
-                if PASSES == 2 and args.variant.split("-")[0] in ("qr", "lu") else None)
+def _emit(args, world, main, cfg, peak_fp64, secondary):
+    M_, N_ = cfg["m"], cfg["n"]
+    globals().update(M=cfg["m"], N=cfg["n"], S=cfg["s"], KAPPA=cfg["kappa"])
+    rows = args.variant.endswith("-rows")
+    base = args.variant.split("-")[0]
+    launches = launches_per_step(args.prec, N, M, rows) if PASSES == 2 and base in ("qr", "lu") else None
+    p0 = main["paths"][args.prec]
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f64+bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "s": S, "kappa": KAPPA, "seed": SEED, "passes": PASSES,
-                   "variant": args.variant, "prec": args.prec,
+        "metric": METRIC, "value": main["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": main["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic",
+        "config": {"workload": workload_name(args.variant, rows), "m": M, "n": N, "s": S, "kappa": KAPPA,
+                   "seed": SEED, "passes": PASSES, "variant": args.variant, "prec": args.prec,
                    "l2": f"A ({8 * M * N / 1e9:.1f} GB) larger than L2 (129 MB); no flush needed",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "roofline": roofline_entry(args.prec, main["stages_ms"], peak_fp64),
-        "stages_ms": main["stages_ms"],
-        "gflops": world * f_alg(M, N, S, PASSES) / (ms * 1e-3) / 1e9,
-        "qr_per_s": world / (ms * 1e-3),
-        "accuracy": {"orth": main["orth"], "resid": main["resid"]},
-        "e2e": e2e,
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "generation_s": main["generation_s"]},
+        "roofline": roofline_entry(args.prec, p0["stages_ms"], peak_fp64),
+        "stages_ms": p0["stages_ms"],
+        "gflops": world * f_alg(M, N, S, PASSES) / (main["ms"] * 1e-3) / 1e9,
+        "qr_per_s": world / (main["ms"] * 1e-3),
+        "accuracy": p0["accuracy"],
+        "preconditioner": main.get("preconditioner"),
+        "e2e": main.get("e2e"),
         "gpu_launches": launches * args.steps if launches else None,
-        "clocks": main["clocks"],
-        "cpu_baseline": cpu,
+        "clocks": p0["clocks"],
+        "cpu_baseline": main.get("cpu_baseline"),
     }
-    if ref is not None:
-        line["compare"] = {
-            "prec": other, "value": world * b_alg(M, N, PASSES) / (ref["ms"] * 1e-3) / 1e9, "unit": "GB/s",
-            "ms_per_step": ref["ms"], "stages_ms": ref["stages_ms"],
-            "accuracy": {"orth": ref["orth"], "resid": ref["resid"]},
-            "roofline": roofline_entry(other, ref["stages_ms"], peak_fp64),
-        }
+    compare = {}
+    for prec, r in main["paths"].items():
+        if prec == args.prec:
+            continue
+        compare[prec] = {"value": world * b_alg(M, N, PASSES) / (r["ms"] * 1e-3) / 1e9, "unit": "GB/s",
+                         "ms_per_step": r["ms"], "dtype": DTYPES[prec], "stages_ms": r["stages_ms"],
+                         "accuracy": r["accuracy"], "roofline": roofline_entry(prec, r["stages_ms"], peak_fp64)}
+    if compare:
+        line["compare"] = compare
+        if "fp64" in compare:
+            line["speedup_vs_fp64"] = compare["fp64"]["ms_per_step"] / main["ms"]
+    if secondary:
+        line["configs"] = secondary
     print(json.dumps(line), flush=True)
 
 
@@ -635,13 +831,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--variant", default="qr", choices=["qr", "lu", "none", "shifted"],
-                    help="rQR / rLU preconditioning, or the comparators CholeskyQR2 (none) and sCholeskyQR3")
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS),
+                    help="c3: m=2^23 n=128 kappa=1e12 (default); c2: m=2^22 n=64 kappa=1e10; "
+                         "c1: m=20000 n=16 kappa=1e8; c5: m=2^20 n=512 kappa=1e13")
+    ap.add_argument("--variant", default=None, choices=["qr", "lu", "none", "shifted"],
+                    help="rQR / rLU preconditioning (default: the configuration's), or the comparators "
+                         "CholeskyQR2 (none) and sCholeskyQR3")
     ap.add_argument("--sketch", default="gaussian", choices=["gaussian", "rows"],
                     help="Gaussian sketch (the workload's) or row extraction (Section 2.3)")
-    ap.add_argument("--prec", default="split", choices=["fp64", "split"],
-                    help="the reported path; the other precision is timed alongside unless --no-compare")
-    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--prec", default="split", choices=list(PRECS),
+                    help="the reported path; the other two are timed alongside unless --no-compare")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the nested c2 and c1 measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
@@ -652,6 +853,12 @@ def main():
     ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
     args = ap.parse_args()
     global M, N, S, KAPPA, WORKLOAD, PASSES
+    if args.workload in ("lstsq", "batched", "rsvd") and args.config == "c3" and "--config" not in sys.argv:
+        args.config = "c2"  # those arms keep the scale configuration's A
+    set_config(args.config)
+    if args.variant is None:
+        args.variant = CONFIGS[args.config]["variant"]
+    args.variant_c1 = CONFIGS["c1"]["variant"]
     if args.variant == "shifted":
         PASSES = 3
     if args.m:
@@ -660,13 +867,12 @@ def main():
         N, S = int(args.n), 2 * int(args.n)
     if args.kappa:
         KAPPA = float(args.kappa)
-    method = {"qr": "rQR-CholeskyQR2", "lu": "rLU-CholeskyQR2", "none": "CholeskyQR2",
-              "shifted": "sCholeskyQR3"}[args.variant]
-    WORKLOAD = (f"{method} m={'2^22' if M == 2**22 else M} n={N} "
-                f"s={S} kappa={KAPPA:g} {'FP64' if args.prec == 'fp64' else 'split BF16 sketch+Gram1, FP64 rest'}")
+    # the nested configurations ride along with the default workload only
+    args.secondary = (not args.no_secondary and args.config == "c3" and not (args.m or args.n or args.kappa)
+                      and args.sketch == "gaussian" and args.variant == "qr")
     if args.sketch == "rows":
-        WORKLOAD += ", row-extraction sketch"
         args.variant += "-rows"
+    WORKLOAD = workload_name(args.variant, args.sketch == "rows")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
