@@ -1,5 +1,6 @@
-"""Benchmark of randomized XR-preconditioned CholeskyQR on one GB300 (or N
-independent replicas, one per GPU, under torchrun).
+"""Benchmark of randomized XR-preconditioned CholeskyQR on one GB300 (under
+torchrun with N GPUs: the row-sharded factorisation of N x m rows, or with
+--replicas N independent factorisations).
 
 A step is one full factorisation A = QR (sketch, XR factor of the sketch, the
 precondition + Gram pass, two CholeskyQR passes, Q and R) with inputs resident
@@ -635,6 +636,79 @@ def graph_replay_qr_per_s(h, args, dev, prec: str, replays: int = 1000) -> dict:
             "replays": replays, "orth": h.orth_error(Q), "resid": h.resid_error(A, Q, R)}
 
 
+def sharded_arm(args, rank: int, world: int, local_rank: int):
+    """N GPUs factorise one matrix of N x m rows, split by contiguous row
+    blocks (Section 2.4's parallel scheme): rank r holds rows r m .. (r + 1) m - 1
+    (its block an independent A = U Sigma V^T of the configuration, seed + r),
+    and the ranks exchange the sketch and Gram partials with one NCCL allgather
+    per stage (paper_2111_11148_gb300.sharded).  Weak scaling: m rows per GPU;
+    value = all ranks' algorithmic bytes over the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2111_11148_gb300 import rxr
+    from paper_2111_11148_gb300.inputs import usv_matrix
+    from paper_2111_11148_gb300.sharded import LibraryOps, cholqr_sharded, torch_allgather
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if "MASTER_ADDR" not in os.environ:  # one process without torchrun: a group of one
+        import socket
+
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK="0", WORLD_SIZE="1")
+    dist.init_process_group("nccl", device_id=dev)
+    A = rxr.colmajor(torch.from_numpy(usv_matrix(M, N, KAPPA, seed=SEED + rank)).to(dev))
+    h = rxr.Handle(local_rank)
+    ops = LibraryOps(h)
+    gather = torch_allgather()
+    variant = args.variant.split("-")[0]
+    prec = args.prec if args.prec != "split_precond" else "split"
+    step = lambda: cholqr_sharded(ops, A, rank * M, gather, variant=variant, s=S, seed=SEED, passes=PASSES,
+                                  prec=prec)
+    for _ in range(max(3, args.warmup)):
+        Q, R, code = step()
+    assert code == 0, code
+    stream = torch.cuda.current_stream(dev)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        Q, R, code = step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    clk = clocks.stop() if clocks else None
+    # accuracy of the whole factorisation: ||Q^T Q - I|| from the summed shard
+    # Grams (FP64), the residual bound by the largest shard ratio
+    Gq = ops.sum_parts(gather(h.gram(Q, prec="fp64")))
+    orth = float(np.linalg.norm(Gq.cpu().numpy() - np.eye(N)))
+    resid = max_over_ranks(h.resid_error(A, Q, R), dist, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * b_alg(M, N, PASSES) / (ms * 1e-3) / 1e9, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
+            "data": "synthetic",
+            "config": {"workload": f"row-sharded {WORKLOAD}, {M} rows per GPU ({world * M} in all)", "m_per_gpu": M,
+                       "m": world * M, "n": N, "s": S, "kappa": KAPPA, "variant": variant, "prec": prec,
+                       "parallelism": f"row shards x{world}, NCCL allgather of the s x n / n x n partials",
+                       "l2": "each shard's A larger than L2; no flush needed"},
+            "accuracy": {"orth_from_summed_grams": orth, "resid_max_over_shards": resid},
+            "clocks": clk, "cpu_baseline": None, "e2e": None,
+        }), flush=True)
+    h.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def gpu_arm(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -848,7 +922,10 @@ def main():
     ap.add_argument("--m", type=int, default=None, help="rows (profiling runs on a smaller case)")
     ap.add_argument("--n", type=int, default=None, help="columns (s = 2n)")
     ap.add_argument("--kappa", type=float, default=None, help="condition number of A")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "lstsq", "rsvd"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "lstsq", "rsvd", "sharded"],
+                    help="sharded: the row-sharded factorisation (the default under torchrun with N > 1)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: N independent single-GPU factorisations instead of row shards")
     ap.add_argument("--k", type=int, default=None, help="block width of the rsvd workload (default 20)")
     ap.add_argument("--count", type=int, default=512, help="problems in the batched workload")
     args = ap.parse_args()
@@ -887,6 +964,9 @@ def main():
         return
     if args.workload == "rsvd":
         rsvd_arm(args, rank, world, local_rank)
+        return
+    if args.workload == "sharded" or (world > 1 and not args.replicas):
+        sharded_arm(args, rank, world, local_rank)
         return
     gpu_arm(args, rank, world, local_rank)
 

@@ -77,10 +77,9 @@ typedef enum { RXR_LU = 0, RXR_QR = 1, RXR_NONE = 2, RXR_SHIFTED = 3 } rxr_varia
  *                       n <= 128, BF16 above) with FP32 accumulation kept exact
  *                       and combined in FP64, so these contractions are
  *                       FP64-grade (error about 2^-53 of the largest entries per
- *                       column), except the first Gram for 64 < n <= 128
- *                       (BF16x3: three 8-bit significand chunks, about 2^-19)
- *                       and the last apply's correction X (R_P^{-1} - I) for
- *                       n <= 64, formed in FP32 when |R_P^{-1} - I| <= 2^-38.
+ *                       column), except the last apply's correction
+ *                       X (R_P^{-1} - I) for n <= 128, formed in FP32 when
+ *                       |R_P^{-1} - I| <= 2^-38 (error below 2^-55 |X|).
  *                       The sketch takes Omega on the 2^-12 grid (the same
  *                       Philox draws, rint(4096 z) / 4096).  The n x n
  *                       factorisations, inverses and all combining stay FP64.
@@ -255,7 +254,7 @@ RXR_API int rxr_xr_factor(rxr_handle h, const double *Y, int64_t s, int64_t n, i
  * (RXR_FP64).  RXR_FP64: row-wise FP64 substitution fused with the FP64 Gram.
  * RXR_SPLIT_BF16: right-looking blocked substitution (FP64 diagonal blocks,
  * trailing updates on the tensor cores at FP64 grade: normwise backward
- * stable) and the tensor-core Gram (BF16x3 for n <= 128, exact digits above). */
+ * stable) and the FP64-grade tensor-core Gram (exact digit slices). */
 RXR_API int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, const double *R,
                      int64_t ldr, double *X, int64_t ldx, double *G, int64_t ldg, int prec, void *stream);
 
@@ -272,11 +271,12 @@ RXR_API int rxr_gram(rxr_handle h, const double *X, int64_t m, int64_t n, int64_
 /* X <- X R^{-1} in place (Algorithm 1 step 3, the Q of a CholeskyQR pass),
  * R upper triangular n x n (leading dimension ldr >= n, read only), X m x n
  * column-major (ldx >= m).  RXR_FP64: row-wise FP64 substitution.
- * RXR_SPLIT_BF16, n <= 64: T = R^{-1} by FP64 back substitution; when every
+ * RXR_SPLIT_BF16, n <= 128: T = R^{-1} by FP64 back substitution; when every
  * |T - I| <= 2^-38 (R within rounding of I, as after a repeated CholeskyQR
- * pass) X + X (T - I) with the correction in FP32 (error below 2^-56 |X| per
- * term), else X T on the tensor cores at FP64 grade (exact digit splitting).
- * RXR_SPLIT_BF16, n > 64: the blocked substitution of rxr_precond_gram.
+ * pass) X + X (T - I) with the correction in FP32 (error below 2^-55 |X| per
+ * term), else X T on the tensor cores at FP64 grade (exact digit splitting,
+ * n <= 64) or the fused substitution (64 < n <= 128).
+ * RXR_SPLIT_BF16, n > 128: the blocked substitution of rxr_precond_gram.
  * R's diagonal must be nonzero and finite (not checked: X is then not
  * finite).  Blocking; 0 or a negative argument error (-i: argument i). */
 RXR_API int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_t ldx, const double *R, int64_t ldr,
@@ -325,6 +325,43 @@ RXR_API int rxr_rsvd(rxr_handle h, int64_t m, int64_t n, const int64_t *a_ptr, c
                      int64_t nnz, const double *X, int64_t ldx, int64_t k, int iters, int variant, int64_t s,
                      uint64_t seed, int passes, int prec, double *U, int64_t ldu, double *S, double *V, int64_t ldv,
                      void *stream);
+
+/* ---- Row-sharded factorisation (Section 2.4's parallel scheme, whose
+ * communication Section 2.5 tabulates): A is split by contiguous row blocks
+ * across processes or GPUs.  Each shard runs these calls and the stage calls
+ * above on its own rows; between stages the caller gathers the s x n sketch
+ * partials or n x n Gram partials of all shards (an allgather, in rank order)
+ * and sums them with rxr_sum_parts, so that every shard holds the same Y, G and
+ * R and runs the small factorisations itself (no broadcast).  Q's rows stay on
+ * their shard.  paper_2111_11148_gb300/sharded.py composes them over
+ * torch.distributed. ---- */
+
+/* Partial sketch of a row shard: Y = Omega[:, row0 .. row0 + m) A_shard / sqrt(s),
+ * Omega's columns indexed by the GLOBAL row (row0 + i), so the sum of all
+ * shards' partials is the sketch of the whole matrix (Section 2.3's Gaussian
+ * ensemble, drawn as rxr_omega describes).  A (m x n, lda >= m, m >= 1: a shard
+ * may hold fewer rows than n) read-only device buffer; Y (s x n, ldy >= s)
+ * device output; 0 <= row0 <= 2^62 - m; prec as for rxr_sketch.  Blocking; 0,
+ * RXR_ERR_NONFINITE or a negative argument error (-i: argument i). */
+RXR_API int rxr_sketch_part(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s,
+                            uint64_t seed, int64_t row0, double *Y, int64_t ldy, int prec, void *stream);
+
+/* out[e] = sum over k = 0 .. count - 1 of parts[k * len + e] (device arrays;
+ * parts holds count blocks of len doubles, e.g. the gathered partials of count
+ * shards) in a fixed order: k = 0, 1, ... for fewer than 256 blocks; from 256
+ * on, lane l of a warp adds blocks l, l + 32, ... and a fixed shuffle tree
+ * combines the lanes.  Every shard that sums the same gathered blocks gets the
+ * same bits.  out must not overlap parts.
+ * Asynchronous on stream; 0 or a negative argument error. */
+RXR_API int rxr_sum_parts(rxr_handle h, const double *parts, int count, int64_t len, double *out, void *stream);
+
+/* C = A B for upper-triangular n x n A and B (their upper triangles are read;
+ * C's strictly lower part is written as 0): the R = R_P ... R_1 R_s
+ * accumulation of Algorithms 2, 4 and 5.  Device buffers, column-major;
+ * C may alias neither A nor B.  Asynchronous on stream; 0 or a negative
+ * argument error. */
+RXR_API int rxr_trmm_upper(rxr_handle h, const double *A, int64_t lda, const double *B, int64_t ldb, int64_t n,
+                           double *C, int64_t ldc, void *stream);
 
 /* Upper Cholesky factor R (R^T R = G; reads the upper triangle of G).
  * Blocking; returns 0 or RXR_ERR_CHOL_BREAKDOWN (column in rxr_last_info). */

@@ -72,6 +72,7 @@ def _load(parallel: bool = False):
             lib.rxo_omega_z.argtypes = [u64, i64, i64, i64, vp]
             lib.rxo_sketch.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
             lib.rxo_sketch_quantised.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
+            lib.rxo_sketch_shard.argtypes = [vp, i64, i64, i64, i64, u64, i64, vp, i64]
             lib.rxo_row_indices.argtypes = [u64, i64, i64, vp]
             lib.rxo_sketch_rows.argtypes = [vp, i64, i64, i64, i64, u64, vp, i64]
             lib.rxo_geqr_r.argtypes = [vp, i64, i64, i64, vp, i64]
@@ -165,11 +166,16 @@ def omega(seed: int, s: int, m: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- steps
-def sketch(A: np.ndarray, s: int, seed: int) -> np.ndarray:
+def sketch(A: np.ndarray, s: int, seed: int, row0: int = 0) -> np.ndarray:
+    """Y = Omega A; with row0, A holds rows row0 .. row0 + m - 1 of a larger
+    matrix and Omega's columns follow those global rows (a row shard's share)."""
     A = _f64(A)
     m, n = A.shape
     Y = np.zeros((s, n), order="F")
-    _load().rxo_sketch(_p(A), m, n, _ld(A), s, seed, _p(Y), s)
+    if row0:
+        _load().rxo_sketch_shard(_p(A), m, n, _ld(A), s, seed, int(row0), _p(Y), s)
+    else:
+        _load().rxo_sketch(_p(A), m, n, _ld(A), s, seed, _p(Y), s)
     return Y
 
 

@@ -260,25 +260,34 @@ static void pw_finish(pairwise_t *p, double *out)
  * z' = rint(4096 z) / 4096 (round half to even), so that each entry is two
  * 8-bit integers; quantise != 0 selects that matrix. */
 static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
-                        double *Y, int64_t ldy, int quantise);
+                        int64_t row0, double *Y, int64_t ldy, int quantise);
 
 void rxo_sketch(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                 double *Y, int64_t ldy)
 {
-    sketch_impl(A, m, n, lda, s, seed, Y, ldy, 0);
+    sketch_impl(A, m, n, lda, s, seed, 0, Y, ldy, 0);
+}
+
+/* The sketch of a row shard: A holds rows row0 .. row0 + m - 1 of a larger
+ * matrix and Omega's columns are those of the global rows (the row-block
+ * partition of Section 2.4); the shards' sketches add up to the whole one. */
+void rxo_sketch_shard(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed, int64_t row0,
+                      double *Y, int64_t ldy)
+{
+    sketch_impl(A, m, n, lda, s, seed, row0, Y, ldy, 0);
 }
 
 void rxo_sketch_quantised(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                           double *Y, int64_t ldy)
 {
-    sketch_impl(A, m, n, lda, s, seed, Y, ldy, 1);
+    sketch_impl(A, m, n, lda, s, seed, 0, Y, ldy, 1);
 }
 
 /* The partial sum of one 256-row block of Omega A (block rows b0 .. b0 + rows). */
 static void sketch_block(const double *A, int64_t lda, int64_t n, int64_t s, uint64_t seed, int quantise, double c,
-                         int64_t b0, int64_t rows, float *z, double *blk)
+                         int64_t row0, int64_t b0, int64_t rows, float *z, double *blk)
 {
-    rxo_omega_z(seed, s, b0, rows, z);
+    rxo_omega_z(seed, s, row0 + b0, rows, z);
     memset(blk, 0, (size_t)(s * n) * sizeof(double));
     for (int64_t i = 0; i < rows; ++i)
         for (int64_t j = 0; j < n; ++j) {
@@ -296,7 +305,7 @@ static void sketch_block(const double *A, int64_t lda, int64_t n, int64_t s, uin
 #define RXO_BATCH 64
 
 static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
-                        double *Y, int64_t ldy, int quantise)
+                        int64_t row0, double *Y, int64_t ldy, int quantise)
 {
     const double c = 1.0 / sqrt((double)s);
     double *blk = (double *)malloc((size_t)(RXO_BATCH * s * n) * sizeof(double));
@@ -312,7 +321,7 @@ static void sketch_impl(const double *A, int64_t m, int64_t n, int64_t lda, int6
             for (int64_t q = 0; q < nb; ++q) {
                 const int64_t b0 = (g0 + q) * RXO_BLOCK;
                 const int64_t rows = (m - b0 < RXO_BLOCK) ? m - b0 : RXO_BLOCK;
-                sketch_block(A, lda, n, s, seed, quantise, c, b0, rows, z, blk + q * s * n);
+                sketch_block(A, lda, n, s, seed, quantise, c, row0, b0, rows, z, blk + q * s * n);
             }
             free(z);
         }

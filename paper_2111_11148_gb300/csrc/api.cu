@@ -16,7 +16,7 @@ namespace rxr {
 // stream_kernels.cu
 __global__ void k_omega(uint64_t, int64_t, int64_t, int64_t, float *);
 __global__ void k_sketch_fp64(const __grid_constant__ CUtensorMap, int, const double *, int64_t, int64_t, int, int,
-                              uint64_t, int64_t, int64_t, int, double *, RxrStatus *);
+                              uint64_t, int64_t, int64_t, int, double *, RxrStatus *, int64_t);
 __global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, int, double *, int64_t, RxrStatus *);
 cudaError_t launch_subst_gram(int maxt, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap &map, int use_tma,
                               const double *src, int64_t lds, int64_t m, int n, const double *R, int64_t ldr,
@@ -53,6 +53,7 @@ __global__ void k_resid_partial(const double *, int64_t, const double *, int64_t
                                 int, double *);
 __global__ void k_resid_final(const double *, int, double *);
 __global__ void k_fp64_peak(double *, int, double, double);
+__global__ void k_trmm_upper(const double *, const double *, double *, int, RxrStatus *);
 }  // namespace rxr
 
 using namespace rxr;
@@ -220,6 +221,7 @@ void make_plan(Plan &p, int64_t m, int64_t n, int64_t s, int prec, int sms, int6
     p.n = n;
     p.s = s;
     p.prec = prec;
+    p.row0 = 0;
     p.sms = sms;
     const int64_t s_tiles = cdiv(s, kSkSTile), n_tiles = cdiv(n, kSkNTile);
     p.sk_gy = (int)(s_tiles * n_tiles);
@@ -439,7 +441,7 @@ int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, c
     const size_t smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
     k_sketch_fp64<<<dim3(p.sk_gx, p.sk_gy), RXR_THREADS, smem, st>>>(map, use_tma, A, lda, p.m, (int)p.n, (int)p.s,
                                                                      seed, p.sk_panels, p.sk_ppc, box_cols, p.Ypart,
-                                                                     p.status);
+                                                                     p.status, p.row0);
     if (launch_ok()) return RXR_ERR_CUDA;
     const int64_t sn = p.s * p.n;
     const int64_t threads = (p.sk_gx >= kReduceWarpParts) ? 32 * sn : sn;
@@ -581,9 +583,11 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         // the first Gram on the tensor cores: FP64-grade stacked digits for
         // n <= 64, BF16x3 for 64 < n <= 128, FP64-grade 128 x 64 blocks above
         if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
-            // n <= 64: the substitution records X's column exponents and the
-            // FP64-grade stacked-digit Gram (faster than the BF16x3 one here)
-            // follows
+            // n <= 64: the substitution records X's column exponents for the
+            // stacked-digit Gram that follows.  The first Gram is FP64-grade at
+            // every n: R_1 then makes X_2 orthonormal to rounding level, so the
+            // last pass's R_P^{-1} - I stays within 2^-38 and its apply takes
+            // the FP32 correction (a BF16x3 Gram left it near 1e-5 at n = 128)
             int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
             {
                 Timer t(th, 1, st);
@@ -596,11 +600,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
                 if (int e = split_subst(p, A, lda, p.Rs, Q, ldq, st, cx)) return e;
             }
             Timer t(th, 4, st);
-            if (p.wide || cx) {
-                if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st, cx != nullptr)) return e;
-            } else if (int e = split_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st)) {
-                return e;
-            }
+            if (int e = ozaki_gram_enqueue(const_cast<Plan &>(p), Q, ldq, st, cx != nullptr)) return e;
         } else if (precond_only) {
             // the preconditioning placement: X = A R_s^{-1} by FP64 substitution,
             // its Gram on the tensor cores (BF16x3 up to n = 128, digit slices above)
@@ -693,6 +693,10 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
             } else if (int e = ozaki_apply_rows(pm, Q, ldq, 0, p.m, st)) {
                 return e;
             }
+        } else if (p.prec == RXR_SPLIT_BF16 && last && pass > 1 && p.n <= 128) {
+            // 64 < n <= 128: the FP32 correction when R_P^{-1} - I is within
+            // 2^-38, else the fused substitution (chosen on the device)
+            if (int e = delta128_apply_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, st)) return e;
         } else if (p.prec == RXR_SPLIT_BF16) {
             if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st)) return e;
         } else if (int e = enqueue_subst(p, Q, ldq, p.Rp, 0, Q, ldq, !last, false, st)) {
@@ -1177,6 +1181,81 @@ int rxr_sketch(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda,
     return finish_blocking(h, p.status, st);
 }
 
+int rxr_sketch_part(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
+                    int64_t row0, double *Y, int64_t ldy, int prec, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (m < 1) return -3;
+    if (n < 1) return -4;
+    if (lda < m) return -5;
+    if (s < 1 || s > RXR_MAX_S) return -6;
+    if (row0 < 0 || row0 > ((int64_t)1 << 62) - m) return -8;
+    if (Y == nullptr) return -9;
+    if (ldy < s) return -10;
+    if (prec != RXR_FP64 && prec != RXR_SPLIT_BF16 && prec != RXR_SPLIT_PRECOND) return -11;
+    if (n > kMaxStreamN || m > ((int64_t)1 << 31)) return RXR_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    Plan p;
+    make_plan(p, m, n, s, prec, h->sms);
+    p.row0 = row0;
+    if (int e = ensure_ws(h, p.bytes)) return e;
+    bind_plan(p, h->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(p.status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    if (int e = enqueue_sketch(p, A, lda, seed, st)) return e;
+    if (cudaMemcpy2DAsync(Y, ldy * 8, p.Y, s * 8, s * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    return finish_blocking(h, p.status, st);
+}
+
+int rxr_sum_parts(rxr_handle h, const double *parts, int count, int64_t len, double *out, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (parts == nullptr) return -2;
+    if (count < 1) return -3;
+    if (len < 1 || len > INT32_MAX) return -4;
+    if (out == nullptr) return -5;
+    DeviceGuard g(h->device);
+    if (int e = ensure_ws(h, 256)) return e;
+    RxrStatus *status = (RxrStatus *)h->ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, sizeof(RxrStatus), st) != cudaSuccess) return RXR_ERR_CUDA;
+    const int64_t threads = (count >= kReduceWarpParts) ? 32 * len : len;
+    k_reduce_parts<<<(int)std::min<int64_t>(cdiv(threads, 256), 1 << 20), 256, 0, st>>>(parts, count, len, (int)len,
+                                                                                       1, 1.0, 0, out, len, status);
+    return launch_ok();
+}
+
+int rxr_trmm_upper(rxr_handle h, const double *A, int64_t lda, const double *B, int64_t ldb, int64_t n, double *C,
+                   int64_t ldc, void *stream)
+{
+    if (h == nullptr) return RXR_ERR_CUDA;
+    if (A == nullptr) return -2;
+    if (B == nullptr) return -4;
+    if (n < 1 || n > RXR_MAX_N) return -6;
+    if (lda < n) return -3;
+    if (ldb < n) return -5;
+    if (C == nullptr) return -7;
+    if (ldc < n) return -8;
+    DeviceGuard g(h->device);
+    const size_t nn = (size_t)n * n * 8;
+    if (int e = ensure_ws(h, 256 + 3 * align256(nn))) return e;
+    char *w = (char *)h->ws;
+    RxrStatus *status = (RxrStatus *)w;
+    double *a = (double *)(w + 256), *b = (double *)(w + 256 + align256(nn)), *c = (double *)(w + 256 + 2 * align256(nn));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, sizeof(RxrStatus), st) != cudaSuccess ||
+        cudaMemcpy2DAsync(a, n * 8, A, lda * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(b, n * 8, B, ldb * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    k_trmm_upper<<<(int)cdiv(n * n, 256), 256, 0, st>>>(a, b, c, (int)n, status);
+    if (launch_ok()) return RXR_ERR_CUDA;
+    if (cudaMemcpy2DAsync(C, ldc * 8, c, n * 8, n * 8, n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    return 0;
+}
+
 int rxr_sketch_rows(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, int64_t s, uint64_t seed,
                     double *Y, int64_t ldy, void *stream)
 {
@@ -1253,8 +1332,7 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
         if (X == nullptr) return RXR_ERR_UNSUPPORTED;
         int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
         if (int e = split_subst(p, A, lda, p.Rp, X, ldx, st, cx)) return e;
-        if (int e = (p.wide || cx) ? ozaki_gram_enqueue(p, X, ldx, st, cx != nullptr) : split_gram_enqueue(p, X, ldx, st))
-            return e;
+        if (int e = ozaki_gram_enqueue(p, X, ldx, st, cx != nullptr)) return e;
     } else {
         if (int e = enqueue_subst(p, A, lda, p.Rp, 0, X, ldx, true, false, st)) return e;
     }
@@ -1481,6 +1559,8 @@ int rxr_apply_rinv(rxr_handle h, double *X, int64_t m, int64_t n, int64_t ldx, c
         return RXR_ERR_CUDA;
     if (prec == RXR_SPLIT_BF16 && n <= 64) {
         if (int e = ozaki_apply_enqueue(p, X, ldx, p.Rp, st)) return e;
+    } else if (prec == RXR_SPLIT_BF16 && n <= 128) {
+        if (int e = delta128_apply_enqueue(p, X, ldx, p.Rp, st)) return e;
     } else if (prec == RXR_SPLIT_BF16) {
         if (int e = split_subst(p, X, ldx, p.Rp, X, ldx, st)) return e;
     } else if (int e = enqueue_subst(p, X, ldx, p.Rp, 0, X, ldx, false, false, st)) {

@@ -20,7 +20,7 @@
 
 namespace rxr {
 __global__ void k_sketch_fp64(const __grid_constant__ CUtensorMap, int, const double *, int64_t, int64_t, int, int,
-                              uint64_t, int64_t, int64_t, int, double *, RxrStatus *);
+                              uint64_t, int64_t, int64_t, int, double *, RxrStatus *, int64_t);
 __global__ void k_reduce_parts(const double *, int, int64_t, int, int, double, int, double *, int64_t, RxrStatus *);
 }  // namespace rxr
 
@@ -121,7 +121,7 @@ extern "C" RXR_API int rxr_sketch_noalloc(const double *A, int64_t m, int64_t n,
     const int box_cols = (int)std::min<int64_t>(n, kSkNTile);
     const size_t smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
     k_sketch_fp64<<<dim3((unsigned)gx, (unsigned)gy), RXR_THREADS, smem, st>>>(
-        unused, 0, A, lda, m, (int)n, (int)s, seed, panels, ppc, box_cols, parts, st_word);
+        unused, 0, A, lda, m, (int)n, (int)s, seed, panels, ppc, box_cols, parts, st_word, (int64_t)0);
     k_reduce_parts<<<(int)cdiv(s * n, 256), 256, 0, st>>>(parts, (int)gx, s * n, (int)s, (int)n,
                                                           1.0 / sqrt((double)s), 0, Y, ldy, st_word);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;

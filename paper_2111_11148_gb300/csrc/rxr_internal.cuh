@@ -184,13 +184,15 @@ __device__ __forceinline__ bool rxr_nonfinite(double v)
 }
 
 // ---------------------------------------------------------------------------
-// mbarrier + TMA (cp.async.bulk.tensor) helpers.  Every wait is bounded: after
-// kSpinLimit polls the waiter records RXR_ERR_TIMEOUT and gives up.  Each poll
-// may suspend the thread for at most kWaitHintNs (the phase completing wakes it
-// earlier), so a wait that never completes gives up after about a second.
-// ---------------------------------------------------------------------------
+// mbarrier + TMA (cp.async.bulk.tensor) helpers.  Every wait is bounded: a
+// waiter polls with try_wait (its own suspend limit, the fastest wake-up on
+// this part) and gives up after kSpinLimit polls or kWaitLimitNs of the global
+// timer, whichever comes first, recording RXR_ERR_TIMEOUT.  The timer is read
+// once per kPollsPerCheck polls, outside the tight polling loop (any code in
+// that loop slowed the tensor-core Gram's producer/consumer hand-offs).
 constexpr uint32_t kSpinLimit = 1u << 20;
-constexpr uint32_t kWaitHintNs = 1000;
+constexpr uint32_t kPollsPerCheck = 4096;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -228,19 +230,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase), "r"(kWaitHintNs)
+        : "r"(smem_u32(bar)), "r"(phase)
         : "memory");
     return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Returns false (and records a timeout) if the phase never completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, RxrStatus *st)
 {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, phase)) return true;
+    uint64_t t0 = 0;
+    for (uint32_t outer = 0; outer < kSpinLimit / kPollsPerCheck; ++outer) {
+        for (uint32_t it = 0; it < kPollsPerCheck; ++it)
+            if (mbar_try_wait(bar, phase)) return true;
+        const uint64_t t = globaltimer_ns();
+        if (outer == 0)
+            t0 = t;
+        else if (t - t0 > kWaitLimitNs)
+            break;
+    }
     rxr_fail(st, RXR_ERR_TIMEOUT, -1, -1);
     return false;
 }
@@ -355,6 +372,7 @@ struct FinishJob {
 // Launch geometry and workspace offsets of one factorisation.
 struct Plan {
     int64_t m, n, s;
+    int64_t row0;  // global index of A's first row: Omega's columns follow it (row shards)
     int prec;
     int sms;
     // sketch
@@ -409,8 +427,12 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
 int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *colexp_out, int *sel,
                         cudaStream_t st);
 int *split_select_flag(const Plan &p);
+// sel (nullable): a device flag; nonzero makes the substitution return at once
 int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                           int64_t ldx, cudaStream_t st);
+                           int64_t ldx, cudaStream_t st, const int *sel = nullptr);
+// 64 < n <= 128: X <- X R^{-1}, the FP32 correction X + X (R^{-1} - I) when
+// |R^{-1} - I| <= 2^-38 (chosen on the device), else the fused substitution
+int delta128_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);
 // 2-D tensor map of a column-major FP64 matrix (api.cu); false where TMA's
 // alignment rules are not met.  swizzle128: 128-byte swizzle (box_rows <= 16;
 // in shared memory, 16-byte chunk c of box column j sits at chunk c ^ (j mod 8))

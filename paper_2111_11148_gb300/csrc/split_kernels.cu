@@ -1306,9 +1306,11 @@ __host__ __device__ inline size_t f2_smem_bytes(int n)
 
 // One record per column block c (grid.x = blocks): see k_subst_fused128.
 __global__ void __launch_bounds__(256) k_rprep128(const double *__restrict__ R, int64_t ldr, int n,
-                                                  unsigned char *__restrict__ rec, RxrStatus *st)
+                                                  unsigned char *__restrict__ rec, const int *__restrict__ sel,
+                                                  RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
+    if (sel != nullptr && *sel != 0) return;  // the FP32-correction apply was chosen instead
     const int c = blockIdx.x, tid = threadIdx.x;
     const int Np = fu_npad(n, c), Nc = n - kFuBw * (c + 1);
     unsigned char *r = rec + f2_rec_off(n, c);
@@ -1388,9 +1390,11 @@ __device__ __forceinline__ void f2_apply(uint32_t tmem, int q4, int lane, int ei
 __global__ void __launch_bounds__(256, 1)
     k_subst_fused128(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      int use_tma, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
-                     const unsigned char *__restrict__ rec, int64_t tiles_total, RxrStatus *st)
+                     const unsigned char *__restrict__ rec, int64_t tiles_total, const int *__restrict__ sel,
+                     RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
+    if (sel != nullptr && *sel != 0) return;  // the FP32-correction apply was chosen instead
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nb = fu_blocks(n);
     const size_t tile_bytes = (size_t)kFuM * n * 8;
@@ -2063,6 +2067,48 @@ __global__ void __launch_bounds__(32) k_tri_inverse64(const double *__restrict__
     if (lane + 32 < n) T[lane + 32 + (int64_t)c * n] = (lane + 32 <= c) ? s1 : 0.0;
 }
 
+// The same column-oriented back substitution for 64 < n <= 128: lane owns
+// rows lane + 32 q (q < 4) of column c of T; R's leading c + 1 columns are
+// staged in dynamic shared memory (column k at k * 128), (c + 1) * 1 KB.
+__global__ void __launch_bounds__(32) k_tri_inverse128(const double *__restrict__ R, int n, int64_t ldr,
+                                                        double *__restrict__ T, RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    extern __shared__ double rs128[];  // R[i][k] at k * 128 + i
+    const int c = blockIdx.x, lane = threadIdx.x;
+    for (int k = 0; k <= c; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            rs128[k * 128 + i] = (i <= k) ? R[i + (int64_t)k * ldr] : 0.0;
+        }
+    double d[4], sv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        d[q] = (i < n) ? 1.0 / R[i + (int64_t)i * ldr] : 0.0;
+        sv[q] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int k = c; k >= 0; --k) {
+        const int qk = k >> 5;
+        // right only in the owner lane (k & 31) of row k
+        const double own = (qk == 0) ? sv[0] * d[0] : (qk == 1) ? sv[1] * d[1] : (qk == 2) ? sv[2] * d[2] : sv[3] * d[3];
+        const double tk = __shfl_sync(0xFFFFFFFFu, own, k & 31);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (i == k) sv[q] = tk;
+            if (i < k) sv[q] = fma(-rs128[k * 128 + i], tk, sv[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = lane + 32 * q;
+        if (i < n) T[i + (int64_t)c * n] = (i <= c) ? sv[q] : 0.0;
+    }
+}
+
 // One exact window of the split sketch folded into this thread's FP64
 // accumulators (tensor-memory lane 32 q4 + lane, columns col0 .. + 15):
 // weights 2^-8d combined in FP32 pairs, added in FP64 without the column
@@ -2095,7 +2141,9 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int col0, do
 }
 
 // ---------------------------------------------------------------------------
-// Split sketch Y' = Omega' A (see the file header).  grid.y = (s-tile,
+// Split sketch Y' = Omega' A (see the file header; Omega's columns follow the
+// global row index row0 + i, so a row shard's sketch is its share of the
+// whole one).  grid.y = (s-tile,
 // n-tile) output tiles of 128 x 64; grid.x = row chunks (CTA cta0 + blockIdx.x
 // of the whole sketch: a caller may launch the chunks of a matrix that is
 // still arriving one group at a time, with the same result).  Column j of A is
@@ -2116,7 +2164,7 @@ constexpr size_t kSpSmem2 = 2 * (size_t)kSpBuf;
 
 __global__ void __launch_bounds__(512, 1)
     k_sketch_split(const double *__restrict__ A, int64_t lda, int64_t m, int n, int s, uint64_t seed, int64_t cta0,
-                   int64_t subs_total, int64_t subs_per_cta, double *__restrict__ Ypart, RxrStatus *st)
+                   int64_t subs_total, int64_t subs_per_cta, double *__restrict__ Ypart, RxrStatus *st, int64_t row0)
 {
     if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -2210,7 +2258,7 @@ __global__ void __launch_bounds__(512, 1)
             float z[8][4];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                rxr_normal4(seed, (uint64_t)(r0 + 8 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
+                rxr_normal4(seed, (uint64_t)(row0 + r0 + 8 * warp + i), (uint32_t)(s0 / 4 + kq), 0u, z[i]);
 #pragma unroll
             for (int t4 = 0; t4 < 4; ++t4) {
                 uint32_t p0[8], p1[8];  // zeta + 128, in [0, 256]
@@ -2327,7 +2375,7 @@ static size_t split_rec_bytes(int64_t n)
 // of A, later the n <= 64 Gram's columns of X), then the records of R
 size_t split_workspace_bytes(int64_t m, int64_t n, int64_t, int sms)
 {
-    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n) + 256 + 64 * 64 * 4;
+    return split_partial_bytes(m, n, sms) + RXR_MAX_N * sizeof(int) + split_rec_bytes(n) + 256 + 128 * 128 * 4;
 }
 
 // E = R^{-1} - I of the last pass in FP32 (64 x 64), after the selection flags
@@ -2364,19 +2412,19 @@ static unsigned char *split_records(const Plan &p)
 // ---------------------------------------------------------------------------
 constexpr double kDeltaMax = 0x1p-38;
 
-// E = T - I (n <= 64) as FP32, row-major and zero padded to 64 x 64
-// (Ef[k * 64 + j] = E(k, j)), and the selection flag: 1 when every |E(k, j)| <=
-// 2^-38 and T is finite, else 0.
-__global__ void __launch_bounds__(256) k_delta_select(const double *__restrict__ T, int n, float *__restrict__ Ef,
-                                                      int *sel, RxrStatus *st)
+// E = T - I (n <= ld, ld = 64 or 128) as FP32, row-major and zero padded to
+// ld x ld (Ef[k * ld + j] = E(k, j)), and the selection flag: 1 when every
+// |E(k, j)| <= 2^-38 and T is finite, else 0.
+__global__ void __launch_bounds__(256) k_delta_select(const double *__restrict__ T, int n, int ld,
+                                                      float *__restrict__ Ef, int *sel, RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
     __shared__ double red[8];
     const int tid = threadIdx.x;
     double mx = 0.0;
     bool bad = false;
-    for (int e = tid; e < 64 * 64; e += blockDim.x) {
-        const int k = e >> 6, j = e & 63;
+    for (int e = tid; e < ld * ld; e += blockDim.x) {
+        const int k = e / ld, j = e % ld;
         double d = 0.0;
         if (k < n && j < n) {
             d = T[k + (int64_t)j * n] - (k == j ? 1.0 : 0.0);
@@ -2428,24 +2476,28 @@ __device__ __forceinline__ float d2f_pow2(double x, int er)
     return (ed == 0 || ef <= 0) ? 0.0f : __uint_as_float((hi & 0x80000000u) | ((uint32_t)min(ef, 254) << 23) | mant);
 }
 
-__host__ __device__ constexpr size_t delta_smem_bytes(int n)
+// NW warps per CTA own 8 columns each: n <= 8 NW (64 with 8 warps, three CTAs
+// per SM; 128 with 16 warps, one CTA per SM); E's rows are 8 NW floats apart.
+__host__ __device__ constexpr size_t delta_smem_bytes(int n, int nw)
 {
-    return (size_t)n * 64 * 4 + (size_t)n * 128 * 4;
+    return (size_t)n * 8 * nw * 4 + (size_t)n * 128 * 4;
 }
 
-__global__ void __launch_bounds__(256, 3) k_apply_delta(double *X, int64_t ldx, int64_t m, int n,
-                                                        const float *__restrict__ Ef, int64_t tiles_total,
-                                                        const int *__restrict__ sel, RxrStatus *st)
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, NW == 8 ? 3 : 1)
+    k_apply_delta(double *X, int64_t ldx, int64_t m, int n, const float *__restrict__ Ef, int64_t tiles_total,
+                  const int *__restrict__ sel, RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
     if (*sel != 1) return;  // the FP64-grade product was chosen instead
+    constexpr int ES = 8 * NW;
     extern __shared__ __align__(16) float dsm_delta[];
-    float *es = dsm_delta;                                                         // n x 64
-    float *xf = es + n * 64;  // n x 128
+    float *es = dsm_delta;  // n x ES
+    float *xf = es + n * ES;  // n x 128
     __shared__ int rowe[2][128];  // the rows' largest biased exponents (double buffered)
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (int e = tid; e < n * 64; e += blockDim.x) es[e] = Ef[e];
-    rowe[tid >> 7][tid & 127] = 0;
+    for (int e = tid; e < n * ES; e += blockDim.x) es[e] = Ef[e];
+    for (int e = tid; e < 256; e += blockDim.x) rowe[e >> 7][e & 127] = 0;
     __syncthreads();
     const int j0 = 8 * w;
     const int nb = max(0, min(8, n - j0));
@@ -2490,8 +2542,8 @@ __global__ void __launch_bounds__(256, 3) k_apply_delta(double *X, int64_t ldx, 
             for (int c = 0; c < 4; ++c) acc[a][c] = 0ull;
 #pragma unroll 4
         for (int k = 0; k < n; ++k) {
-            const ulonglong2 e01 = *reinterpret_cast<const ulonglong2 *>(es + k * 64 + j0);
-            const ulonglong2 e23 = *reinterpret_cast<const ulonglong2 *>(es + k * 64 + j0 + 4);
+            const ulonglong2 e01 = *reinterpret_cast<const ulonglong2 *>(es + k * ES + j0);
+            const ulonglong2 e23 = *reinterpret_cast<const ulonglong2 *>(es + k * ES + j0 + 4);
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 const uint32_t xv = __float_as_uint(xf[k * 128 + lane + 32 * a]);
@@ -2520,8 +2572,12 @@ __global__ void __launch_bounds__(256, 3) k_apply_delta(double *X, int64_t ldx, 
 static void delta_launch(int sms, double *X, int64_t ldx, int64_t m, int n, const float *Ef, int64_t tiles,
                          const int *sel, RxrStatus *status, cudaStream_t st)
 {
-    k_apply_delta<<<(unsigned)std::min<int64_t>(3 * (int64_t)sms, tiles), 256, delta_smem_bytes(n), st>>>(
-        X, ldx, m, n, Ef, tiles, sel, status);
+    if (n <= 64)
+        k_apply_delta<8><<<(unsigned)std::min<int64_t>(3 * (int64_t)sms, tiles), 256, delta_smem_bytes(n, 8), st>>>(
+            X, ldx, m, n, Ef, tiles, sel, status);
+    else
+        k_apply_delta<16><<<(unsigned)std::min<int64_t>(sms, tiles), 512, delta_smem_bytes(n, 16), st>>>(
+            X, ldx, m, n, Ef, tiles, sel, status);
 }
 
 // Estimate of cond_2(R) = ||R||_2 ||R^{-1}||_2 (n <= 64, one CTA): twelve power
@@ -2614,10 +2670,30 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
 // at once.  T lives in the XR scratch W (s x n doubles >= n^2).
 int ozaki_apply_prepare(Plan &p, const double *R, cudaStream_t st)
 {
-    if (p.n > 64) return RXR_ERR_UNSUPPORTED;
-    k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, p.W, p.status);
-    k_delta_select<<<1, 256, 0, st>>>(p.W, (int)p.n, split_delta(p), split_select_flag(p) + 1, p.status);
+    if (p.n > 128) return RXR_ERR_UNSUPPORTED;
+    if (p.n <= 64) {
+        k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, p.W, p.status);
+        k_delta_select<<<1, 256, 0, st>>>(p.W, (int)p.n, 64, split_delta(p), split_select_flag(p) + 1, p.status);
+    } else {
+        k_tri_inverse128<<<(unsigned)p.n, 32, (size_t)p.n * 128 * sizeof(double), st>>>(R, (int)p.n, p.n, p.W,
+                                                                                       p.status);
+        k_delta_select<<<1, 256, 0, st>>>(p.W, (int)p.n, 128, split_delta(p), split_select_flag(p) + 1, p.status);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+}
+
+// 64 < n <= 128: X <- X R^{-1} by the FP32 correction when R^{-1} - I is
+// within 2^-38 (the last pass after a repeated one), else by the fused
+// substitution; both launched after the selection, the one not chosen returns
+// at once.
+int delta128_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st)
+{
+    if (p.n <= 64 || p.n > 128) return RXR_ERR_UNSUPPORTED;
+    if (int e = ozaki_apply_prepare(p, R, st)) return e;
+    const int *sel = split_select_flag(p) + 1;
+    delta_launch(p.sms, X, ldx, p.m, (int)p.n, split_delta(p), cdiv64(p.m, 128), sel, p.status, st);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    return fused128_subst_enqueue(p, X, ldx, R, p.n, X, ldx, st, sel);
 }
 
 // Rows [r0, r0 + rows) of X (r0 a multiple of 128): both product forms, the
@@ -2695,12 +2771,12 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
 
 // X = B R^{-1} for 64 < n <= 128 in one pass over B (k_rprep128 + k_subst_fused128).
 int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                           int64_t ldx, cudaStream_t st)
+                           int64_t ldx, cudaStream_t st, const int *sel)
 {
     if (p.n <= kFuMaxN || p.n > kF2MaxN) return RXR_ERR_UNSUPPORTED;
     const int n = (int)p.n, nb = fu_blocks(n);
     unsigned char *rec = split_records(p);
-    k_rprep128<<<nb, 256, 0, st>>>(R, ldr, n, rec, p.status);
+    k_rprep128<<<nb, 256, 0, st>>>(R, ldr, n, rec, sel, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     CUtensorMap ms, md;
     const int use_tma =
@@ -2708,7 +2784,7 @@ int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const doubl
     const int64_t tiles = cdiv64(p.m, kFuM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
     k_subst_fused128<<<gx, 256, f2_smem_bytes(n), st>>>(ms, md, use_tma, Bsrc, ldb, X, ldx, p.m, n, rec, tiles,
-                                                         p.status);
+                                                         sel, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
@@ -2774,7 +2850,14 @@ cudaError_t set_split_smem()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)aq_smem_bytes(64));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_apply_delta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)delta_smem_bytes(64));
+        e = cudaFuncSetAttribute(k_apply_delta<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)delta_smem_bytes(64, 8));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_delta<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)delta_smem_bytes(128, 16));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tri_inverse128, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 128 * 128 * (int)sizeof(double));
     return e;
 }
 
@@ -2805,7 +2888,7 @@ int split_sketch_part_enqueue(Plan &p, const double *A, int64_t lda, uint64_t se
     if (cta_end <= cta_begin) return 0;
     const int64_t gy = cdiv64(p.s, kSpM) * cdiv64(p.n, kSpN);
     k_sketch_split<<<dim3((unsigned)(cta_end - cta_begin), (unsigned)gy), 512, kSpSmem2, st>>>(
-        A, lda, p.m, (int)p.n, (int)p.s, seed, cta_begin, cdiv64(p.m, kSpSub), spc, p.Ypart, p.status);
+        A, lda, p.m, (int)p.n, (int)p.s, seed, cta_begin, cdiv64(p.m, kSpSub), spc, p.Ypart, p.status, p.row0);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 

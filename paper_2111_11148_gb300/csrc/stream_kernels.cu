@@ -65,6 +65,9 @@ __device__ __forceinline__ bool load_panel(double *dst, const CUtensorMap *map, 
         const int64_t gr = r0 + row;
         dst[e] = (gr < m && c0 + col < ncols_total) ? src[gr + (int64_t)(c0 + col) * ld] : 0.0;
     }
+    // the panel is read by other threads than those that loaded it (element e
+    // comes from thread e mod blockDim.x): every load lands before any use
+    __syncthreads();
     return true;
 }
 
@@ -103,10 +106,12 @@ constexpr int kSkP = 64;      // rows per panel
 constexpr int kSkSTile = 128; // max sketch rows per tile
 constexpr int kSkNTile = 64;  // max columns per tile
 
+// row0: the global index of A's first row (Omega's columns follow the global
+// rows, so a row shard's partial sketch is its share of the whole one)
 __device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tma, const double *__restrict__ A,
                                             int64_t lda, int64_t m, int n, int s, uint64_t seed, int64_t panels_total,
                                             int64_t panels_per_cta, int box_cols, double *__restrict__ Ypart,
-                                            RxrStatus *st, int bx, int by)
+                                            RxrStatus *st, int bx, int by, int64_t row0 = 0)
 {
     if (rxr_failed_block(st)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -157,7 +162,7 @@ __device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tm
         for (int c = threadIdx.x; c < kSkP * kcount; c += blockDim.x) {
             const int row = c / kcount, kk = c % kcount;
             float v[4];
-            rxr_normal4(seed, (uint64_t)(r0 + row), (uint32_t)(k0 + kk), 0u, v);
+            rxr_normal4(seed, (uint64_t)(row0 + r0 + row), (uint32_t)(k0 + kk), 0u, v);
             double *zr = zp + row * kSkSTile + 4 * kk;
 #pragma unroll
             for (int t = 0; t < 4; ++t) zr[t] = rxr_f2d_exact(v[t]);
@@ -227,10 +232,10 @@ __device__ __forceinline__ void sketch_body(const CUtensorMap *tmapA, int use_tm
 __global__ void __launch_bounds__(RXR_THREADS, 2)
     k_sketch_fp64(const __grid_constant__ CUtensorMap tmapA, int use_tma, const double *__restrict__ A, int64_t lda,
                   int64_t m, int n, int s, uint64_t seed, int64_t panels_total, int64_t panels_per_cta,
-                  int box_cols, double *__restrict__ Ypart, RxrStatus *st)
+                  int box_cols, double *__restrict__ Ypart, RxrStatus *st, int64_t row0)
 {
     sketch_body(&tmapA, use_tma, A, lda, m, n, s, seed, panels_total, panels_per_cta, box_cols, Ypart, st,
-                blockIdx.x, blockIdx.y);
+                blockIdx.x, blockIdx.y, row0);
 }
 
 // ---------------------------------------------------------------------------

@@ -81,6 +81,9 @@ def load() -> ctypes.CDLL:
         "rxr_set_kernel_timing": ([vp, i], i),
         "rxr_sketch_noalloc": ([vp, i64, i64, i64, i64, u64, vp, i64, vp], i),
         "rxr_set_test_hook": ([vp, i, i], i),
+        "rxr_sketch_part": ([vp, vp, i64, i64, i64, i64, u64, i64, vp, i64, i, vp], i),
+        "rxr_sum_parts": ([vp, vp, i, i64, vp, vp], i),
+        "rxr_trmm_upper": ([vp, vp, i64, vp, i64, i64, vp, i64, vp], i),
         "rxr_rsvd": ([vp, i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, i64, i64, i, i, i64, u64, i, i, vp, i64, vp, vp,
                       i64, vp], i),
     }
@@ -99,7 +102,7 @@ def exported_symbols() -> list[str]:
                         "rxr_precond_gram",
                         "rxr_cholesky", "rxr_apply_rinv", "rxr_lstsq", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
                         "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc", "rxr_rsvd",
-                        "rxr_set_test_hook")]
+                        "rxr_set_test_hook", "rxr_sketch_part", "rxr_sum_parts", "rxr_trmm_upper")]
 
 
 def status_string(code: int) -> str:
@@ -177,6 +180,15 @@ class Handle:
     def __enter__(self):
         return self
 
+    def set_workspace(self, buf=None):
+        """rxr_set_workspace: hand the handle caller-owned device memory (a CUDA
+        tensor, kept alive by the handle) or return to self-managed workspace
+        (None)."""
+        self._ws = buf
+        ptr = None if buf is None else _ptr(buf)
+        nbytes = 0 if buf is None else buf.numel() * buf.element_size()
+        _check(load().rxr_set_workspace(self._h, ptr, nbytes), "rxr_set_workspace")
+
     def set_test_hook(self, hook: int, value: int):
         """rxr_set_test_hook: HOOK_STALL (a bounded device wait runs out) or
         HOOK_JACOBI_SWEEPS (cap on the randomized SVD's Jacobi sweeps)."""
@@ -250,6 +262,36 @@ class Handle:
         if code < 0 or code == UNSUPPORTED:  # nothing was factorised
             raise RxrError(code, "rxr_cholqr_batched")
         return Qs, Rs, st.view(cnt, 4).cpu().numpy()
+
+    # ---------------------------------------------------------------- row shards
+    def sketch_part(self, A, s: int, seed: int = 0, row0: int = 0, prec="fp64", stream=None):
+        """Partial sketch of a row shard whose first row is global row row0."""
+        m, n = A.shape
+        Y = empty_colmajor(s, n, device=A.device)
+        _check(load().rxr_sketch_part(self._h, _ptr(A), m, n, _ld(A), s, seed & (2**64 - 1), int(row0), _ptr(Y),
+                                      _ld(Y), _PRECS[prec], _stream(stream)), "rxr_sketch_part")
+        return Y
+
+    def sum_parts(self, parts, out=None, stream=None):
+        """Sum of the blocks parts[0], parts[1], ... (a contiguous CUDA tensor of
+        shape (count, ...)) in that order; returns a tensor of shape parts.shape[1:]."""
+        import torch
+
+        parts = parts.contiguous()
+        count = parts.shape[0]
+        if out is None:
+            out = torch.empty(parts.shape[1:], dtype=torch.float64, device=parts.device)
+        _check(load().rxr_sum_parts(self._h, _ptr(parts), int(count), parts[0].numel(), _ptr(out),
+                                    _stream(stream)), "rxr_sum_parts")
+        return out
+
+    def trmm_upper(self, A, B, stream=None):
+        """A B for upper-triangular column-major A, B (n x n)."""
+        n = A.shape[0]
+        C = empty_colmajor(n, n, device=A.device)
+        _check(load().rxr_trmm_upper(self._h, _ptr(A), _ld(A), _ptr(B), _ld(B), n, _ptr(C), _ld(C),
+                                     _stream(stream)), "rxr_trmm_upper")
+        return C
 
     # ---------------------------------------------------------------- stages
     def sketch(self, A, s: int, seed: int = 0, prec="fp64", stream=None):

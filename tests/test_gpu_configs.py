@@ -105,3 +105,21 @@ def test_batched_against_oracle(h):
         rel, _, _ = _check(As_np[i], Qs[i], Rs[i], ref, ("batched", sp.kappa, i))
         worst = max(worst, rel)
     print(f"batched: worst R vs oracle {worst:.2e} over {len(specs)} problems")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_plain_load_path_repeated(h, prec):
+    # an odd leading dimension rules TMA out, so every panel is staged by plain
+    # loads, each thread loading entries that other warps then read: at n = 8
+    # the substitution starts right after the loads (a missing barrier there
+    # once left 32-row blocks of one odd column stale in about one call in ten)
+    m, n = 40001, 8
+    A_full = usv_matrix(m, n, 1e4, seed=77, lda=m + 1)
+    A = A_full[:m]
+    ref = o.rxr_cholqr(np.asfortranarray(A), o.VARIANT_QR, 2 * n, seed=2, passes=2)
+    Ad = to_dev(A_full)[:m]
+    assert Ad.stride() == (1, m + 1)
+    for _ in range(12):
+        Q, R, code = h.cholqr(Ad, variant="qr", s=2 * n, seed=2, passes=2, prec=prec)
+        assert code == 0
+        _check(np.asfortranarray(A), Q, R, ref, ("plain", 1e4, prec))

@@ -5,8 +5,10 @@ The split sketch computes Y' = Omega' A with Omega' the same Philox draws on
 the 2^-12 grid (the oracle's sketch_quantised); its digit decomposition of A
 is exact up to 2^-55 of each column's largest entry per 512-row window, and its
 tensor-memory sums are exact integers, so it must meet the FP64 sketch bound
-plus that truncation term.  The split Gram keeps three 8-bit significand chunks
-per entry and accumulates in FP32 (truncating) over 24 tensor-core
+plus that truncation term.  The split Gram cuts each column into seven exact
+8-bit digits (FP64 grade: the FP64 Gram bound plus 2^-52 m colmax_j colmax_l);
+the preconditioning placement's BF16x3 Gram keeps three 8-bit significand
+chunks per entry and accumulates in FP32 (truncating) over 24 tensor-core
 accumulations per 64-row tile before each FP64 drain: its bound is
 2^-17 (|X|^T |X|) entrywise.  End to end, the split path must reach the same
 accuracy targets as the FP64 path for every kappa."""
@@ -55,7 +57,8 @@ def test_split_gram_parity(h, m, n):
     X, G = h.precond_gram(to_dev(A), to_dev(R), prec="split")
     Xg, Gg = to_host(X), to_host(G)
     Go = o.gram(Xg)
-    bound = 2.0**-17 * (np.abs(Xg).T @ np.abs(Xg))
+    cm = np.abs(Xg).max(axis=0)
+    bound = 8 * (m + 2) * U * (np.abs(Xg).T @ np.abs(Xg)) + 2.0**-52 * m * np.outer(cm, cm)
     assert np.all(np.abs(Gg - Go) <= bound), np.max(np.abs(Gg - Go) / bound)
     assert np.array_equal(Gg, Gg.T)
 
@@ -211,14 +214,17 @@ def _row_rel_err(Qg, Qo, T):
 
 @pytest.mark.parametrize("m,n,eps", [(1, 1, 1e-14), (677, 7, 1e-14), (128 * 9 + 37, 33, 1e-15),
                                      (4096 + 5, 64, 1e-13), (900, 64, 1e-12), (900, 64, 1e-11),
-                                     (900, 48, 0.3), (3000, 64, 0.05), (250, 1, 0.5)])
+                                     (900, 48, 0.3), (3000, 64, 0.05), (250, 1, 0.5),
+                                     (128 * 9 + 37, 100, 1e-15), (1000, 128, 1e-13), (700, 65, 1e-14),
+                                     (900, 128, 1e-11), (2000, 97, 0.3), (333, 128, 0.05)])
 def test_apply_rinv_split(h, m, n, eps):
-    # X <- X R^{-1}, n <= 64: with R - I at most about 2^-38 the correction
-    # X (R^{-1} - I) is formed in FP32 (error below 2^-56 |X| per term); a
+    # X <- X R^{-1}, n <= 128: with R - I at most about 2^-38 the correction
+    # X (R^{-1} - I) is formed in FP32 (error below 2^-55 |X| per term); a
     # larger R - I (eps = 1e-11 lies above 2^-38 after inversion, 0.05 .. 0.5
-    # far above) takes the FP64-grade tensor-core product.  Both must match the
-    # oracle's substitution to FP64 accuracy, far below what an FP32 product of
-    # X and R^{-1} reaches (about 1e-7).
+    # far above) takes the FP64-grade tensor-core product (n <= 64) or the fused
+    # substitution (64 < n <= 128).  Each must match the oracle's substitution
+    # to FP64 accuracy, far below what an FP32 product of X and R^{-1} reaches
+    # (about 1e-7).
     rng = np.random.default_rng(m + n)
     X = usv_matrix(m, n, 10.0, seed=n)
     R = _upper(n, rng, eps)
@@ -231,10 +237,11 @@ def test_apply_rinv_split(h, m, n, eps):
     assert err <= 64 * U, err
 
 
-def test_apply_rinv_split_odd_ld_and_large(h):
+@pytest.mark.parametrize("n", [64, 128])
+def test_apply_rinv_split_odd_ld_and_large(h, n):
     # a leading dimension that is not a multiple of the tile, and 2^20 + 77 rows
     # (sampled rows against the oracle): the FP32-correction form
-    m, n = (1 << 20) + 77, 64
+    m = (1 << 20) + 77
     rng = np.random.default_rng(5)
     R = _upper(n, rng, 2e-15)
     X = np.asfortranarray(rng.standard_normal((m + 3, n)))

@@ -92,6 +92,22 @@ def test_sketch_matches_explicit_omega_product():
     np.testing.assert_allclose(Y, Om @ A, rtol=0, atol=1e-14 * np.abs(Om).sum(1).max() * np.abs(A).max())
 
 
+@pytest.mark.parametrize("row0", [1, 256, 1000, 2**32 + 5])
+def test_shard_sketch_is_its_share_of_the_whole(row0):
+    # Omega's columns follow the global rows (Section 2.4's row blocks): a shard
+    # holding rows row0 .. row0 + m - 1 takes columns row0 .. of the same Omega
+    m, n, s = 613, 4, 9
+    A = usv_matrix(m, n, 1e3, seed=8)
+    Y = o.sketch(A, s, seed=6, row0=row0)
+    z = o.omega_z(6, s, row0, m).astype(np.float64)         # (rows, s): z of rows row0 ..
+    Om = (1.0 / np.sqrt(float(s))) * z.T
+    np.testing.assert_allclose(Y, Om @ A, rtol=0, atol=1e-14 * np.abs(Om).sum(1).max() * np.abs(A).max())
+    # the shards of a split matrix add up to the whole sketch (to rounding)
+    B = usv_matrix(1500, n, 1e3, seed=9)
+    parts = o.sketch(B[:700], s, 6) + o.sketch(B[700:], s, 6, row0=700)
+    np.testing.assert_allclose(parts, o.sketch(B, s, 6), rtol=0, atol=1e-13 * np.abs(B).max() * 1500)
+
+
 def _cond_x(n, s, seed, m=None, kappa=1e3, variant=o.VARIANT_QR):
     m = m or 20 * s
     A = usv_matrix(m, n, kappa, seed=100 + seed)
