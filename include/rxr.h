@@ -176,19 +176,46 @@ RXR_API int rxr_cholqr_host(rxr_handle h, const double *hA, int64_t m, int64_t n
                     uint64_t seed, int passes, double *hQ, int64_t ldq, double *hR, int64_t ldr, int prec,
                     void *stream);
 
-/* Batched form: `count` independent problems A_k (m_k x n_k) factorised in one
- * stream-ordered launch sequence (one launch per stage for the whole batch;
- * the row panels of all problems share each launch's grid).  Arrays are HOST
- * arrays of length `count`; the matrix pointers in them are device pointers.
- * variant, passes and prec are common; s_k, seed_k per problem.  Per-problem
- * status {code, pass, column, 0} goes to d_status[4k..4k+3] (device, caller
- * owned).  Blocking; returns the first non-zero problem status (or 0), or
- * RXR_ERR_UNSUPPORTED without factorising any problem for RXR_SKETCH_ROWS
- * (the batched stages take the Gaussian sketch only). */
+/* Batched form: `count` independent problems A_k (m_k x n_k) factorised as
+ * one job (the many tall-skinny blocks of block Krylov, LOBPCG or randomized
+ * SVD that Sections 1 and 5 mention).  Arrays are HOST arrays of length count;
+ * the matrix pointers in them are device pointers.  variant, passes and prec
+ * are common; s_k, seed_k per problem.  Per-problem status {code, pass,
+ * column, 0} goes to d_status[4k .. 4k + 3] (device, caller owned).
+ *   RXR_FP64 with RXR_LU, RXR_QR or RXR_NONE (n_k <= 128): one launch per stage
+ *     for the whole batch; the sketch, the substitutions (+ Grams) and the
+ *     reductions run persistent CTAs that pull (problem, row chunk) items from a
+ *     device work queue, the row chunks sized by the tuned table of
+ *     csrc/batched_tuning.h; the O(n^3) steps run one CTA per problem.
+ *   Any other precision or variant: every problem's own launch sequence (the
+ *     same kernels and results as rxr_cholqr), spread over eight streams that
+ *     fork from and join back into `stream`.
+ * Blocking; returns the first non-zero problem status (or 0). */
 RXR_API int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
                        const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
                        double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
                        void *stream, int *d_status);
+
+/* Batched plan: the same batch prepared once -- arguments checked, every
+ * problem's workspace allocated (device memory owned by the plan) and the job
+ * tables copied to the device -- then run any number of times.
+ * rxr_batch_run only enqueues device work on `stream` (memsets and kernel
+ * launches, plus event fork/join across the plan's streams for the
+ * per-problem form): no host synchronisation and no allocation, so it can be
+ * captured into a CUDA graph; the statuses land in d_status when the stream
+ * reaches the end of the run.  The matrices named at creation are read and
+ * written by every run (update their contents in place between runs).  A plan
+ * must not run on two streams at once.  rxr_batch_create: arguments as
+ * rxr_cholqr_batched, plan (17) receives the plan; returns 0, a negative
+ * argument error, RXR_ERR_UNSUPPORTED, RXR_ERR_NOMEM or RXR_ERR_CUDA.  The
+ * handle must outlive the plan. */
+typedef struct rxr_batch *rxr_batch_plan;
+RXR_API int rxr_batch_create(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
+                             const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
+                             double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
+                             int *d_status, rxr_batch_plan *plan);
+RXR_API int rxr_batch_run(rxr_batch_plan plan, void *stream);
+RXR_API int rxr_batch_destroy(rxr_batch_plan plan);
 
 /* Test hooks: they make error paths that correct inputs never reach run on
  * request, without faulting or hanging the GPU.  They are meant for tests.
@@ -206,9 +233,14 @@ RXR_API int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, 
  *   RXR_HOOK_JACOBI_SWEEPS, value in 0..40: caps the sweeps of rxr_rsvd's
  *     Jacobi SVD (0 = the default bound, 40); a cap it reaches before
  *     convergence makes rxr_rsvd return RXR_ERR_NO_CONVERGENCE.
+ *   RXR_HOOK_BATCH_CTAS, value = (bucket << 8) | c: the batched form's row
+ *     chunking for problems of n-bucket `bucket` (0..4: n <= 8, 16, 32, 64,
+ *     128) becomes c CTAs per SM per stage (c = 0: the tuned table of
+ *     csrc/batched_tuning.h); used by the tuning script.
  * Returns 0, -1 (h NULL), -2 (unknown hook) or -3 (value out of range). */
 #define RXR_HOOK_STALL 1
 #define RXR_HOOK_JACOBI_SWEEPS 2
+#define RXR_HOOK_BATCH_CTAS 3
 RXR_API int rxr_set_test_hook(rxr_handle h, int hook, int value);
 
 /* Pass and column (0-based) of the last Cholesky breakdown seen by a blocking

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <vector>
 
+#include "batched_tuning.h"
 #include "rxr_internal.cuh"
 
 namespace rxr {
@@ -30,9 +31,9 @@ __global__ void k_subst_wide(const double *, int64_t, int64_t, int, const double
 __global__ void k_gram_tiles(const double *, int64_t, int64_t, int, int64_t, int64_t, double *, RxrStatus *);
 __global__ void k_sketch_rows(const double *, int64_t, int64_t, int, int64_t, uint64_t, double *, int64_t, RxrStatus *);
 __global__ void k_check_finite(const double *, int64_t, int64_t, int, RxrStatus *);
-__global__ void k_sketch_fp64_batched(const SketchJob *, const int *, int);
-__global__ void k_reduce_parts_batched(const ReduceJob *, const int *, int);
-__global__ void k_subst_gram_batched(const SubstJob *, const int *, int, int);
+__global__ void k_sketch_fp64_batched(const SketchJob *, const int *, int, int, int *);
+__global__ void k_reduce_parts_batched(const ReduceJob *, const int *, int, int, int *);
+__global__ void k_subst_gram_batched(const SubstJob *, const int *, int, int, int, int *);
 __global__ void k_xr_factor_batched(const XrJob *);
 __global__ void k_factor_batched(const FactorJob *, int);
 __global__ void k_finish_batched(const FinishJob *);
@@ -99,7 +100,8 @@ struct rxr_ctx {
     cudaEvent_t io_ev[2 * kIoChunks + 2] = {};
     // test hooks (rxr_set_test_hook)
     int test_stall = 0;
-    int jacobi_sweeps = 0;  // 0: the default bound
+    int jacobi_sweeps = 0;                      // 0: the default bound
+    int batch_ctas[kBatchTuneBuckets] = {};     // 0: the tuned table
 };
 
 namespace {
@@ -772,6 +774,344 @@ int finish_blocking(rxr_handle h, const RxrStatus *d_status, cudaStream_t st)
 }  // namespace
 
 // ===========================================================================
+// Batched form: a plan holds every problem's workspace and, for the FP64
+// stage kernels, the device job tables; a run only enqueues work.
+// ===========================================================================
+constexpr int kBatchStreams = 8;  // streams of the per-problem form
+
+struct rxr_batch {
+    rxr_handle h = nullptr;
+    int count = 0, variant = 0, passes = 2, prec = RXR_FP64;
+    bool tables = false;  // FP64 stage kernels over job tables (else per-problem sequences)
+    std::vector<Plan> plans;
+    std::vector<const double *> A;
+    std::vector<double *> Q, R;
+    std::vector<int64_t> lda, ldq, ldr;
+    std::vector<uint64_t> seed;
+    int *d_status = nullptr;
+    void *ws = nullptr;
+    bool ws_owned = false;
+    // job tables (device, inside ws) and the stage launch shapes
+    RxrStatus *statuses = nullptr;
+    const SketchJob *skj = nullptr;
+    const ReduceJob *ryj = nullptr, *rgj = nullptr;
+    const XrJob *xrj = nullptr;
+    const SubstJob *prej = nullptr, *passj = nullptr;
+    const FactorJob *fj = nullptr;
+    const FinishJob *finj = nullptr;
+    const int *st_sk = nullptr, *st_ry = nullptr, *st_sg = nullptr, *st_rg = nullptr;
+    int tot_sk = 0, tot_ry = 0, tot_sg = 0, tot_rg = 0;
+    int grid_sk = 0, grid_ry = 0, grid_sg = 0, grid_rg = 0;
+    size_t sg_smem = 0;
+    int *counters = nullptr;
+    int ncounters = 0;
+    // per-problem form: streams and the fork/join events
+    cudaStream_t aux[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+};
+
+namespace {
+
+// CTAs per SM of the batch's row chunking for an n-column problem (the table
+// of batched_tuning.h)
+int batch_ctas_per_sm(rxr_handle h, int64_t n)
+{
+    int i = 0;
+    while (i < kBatchTuneBuckets - 1 && n > kBatchTuneN[i]) ++i;
+    return h->batch_ctas[i] > 0 ? h->batch_ctas[i] : kBatchCtasPerSm[i];
+}
+
+int occupancy_grid(const void *fn, int threads, size_t smem, int sms, int items)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess || per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    return std::max(1, std::min(items, per_sm * sms));
+}
+
+void batch_release(rxr_batch *b)
+{
+    if (!b) return;
+    DeviceGuard g(b->h ? b->h->device : 0);
+    if (b->ws_owned && b->ws) cudaFree(b->ws);
+    for (cudaStream_t s : b->aux)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+// Lay the batch out: every problem's plan and workspace, and (FP64 over the
+// stage kernels) the job tables, copied to the device before this returns.
+// handle_ws: use the handle's workspace and pinned staging (the blocking call)
+// instead of allocating the plan's own.
+int batch_build(rxr_batch *b, const double *const *A, const int64_t *m, const int64_t *n, const int64_t *lda,
+                const int64_t *s, const uint64_t *seed, double *const *Q, const int64_t *ldq, double *const *R,
+                const int64_t *ldr, bool handle_ws, cudaStream_t st)
+{
+    rxr_handle h = b->h;
+    const int count = b->count;
+    std::vector<int64_t> sk(count);
+    int64_t total_rows = 0;
+    for (int k = 0; k < count; ++k) {
+        const int base = b->variant & ~RXR_SKETCH_ROWS;
+        sk[k] = ((base == RXR_NONE || base == RXR_SHIFTED) && s[k] < n[k]) ? n[k] : s[k];
+        if (int e = check_args(A[k], m[k], n[k], lda[k], b->variant, sk[k], b->passes, Q[k], ldq[k], R[k], ldr[k],
+                               b->prec))
+            return e;
+        if (b->tables && n[k] > kNarrowN) return RXR_ERR_UNSUPPORTED;  // the FP64 stage kernels: n <= 128
+        total_rows += m[k];
+    }
+    b->plans.resize(count);
+    std::vector<size_t> base(count);
+    size_t off = align256((size_t)count * sizeof(RxrStatus));
+    for (int k = 0; k < count; ++k) {
+        // row chunks in proportion to each problem's rows (the tuned number of
+        // CTAs per SM per stage over the whole batch)
+        const int64_t target = std::max<int64_t>(kSgP, total_rows / ((int64_t)batch_ctas_per_sm(h, n[k]) * h->sms));
+        make_plan(b->plans[k], m[k], n[k], sk[k], b->prec, h->sms, b->tables ? cdiv(m[k], target) : INT64_MAX);
+        base[k] = off;
+        off += align256(b->plans[k].bytes);
+    }
+    const size_t o_tables = off;
+    const size_t o_skj = off;
+    off += align256(count * sizeof(SketchJob));
+    const size_t o_ryj = off;
+    off += align256(count * sizeof(ReduceJob));
+    const size_t o_xrj = off;
+    off += align256(count * sizeof(XrJob));
+    const size_t o_prej = off;
+    off += align256(count * sizeof(SubstJob));
+    const size_t o_passj = off;
+    off += align256(count * sizeof(SubstJob));
+    const size_t o_rgj = off;
+    off += align256(count * sizeof(ReduceJob));
+    const size_t o_fj = off;
+    off += align256(count * sizeof(FactorJob));
+    const size_t o_finj = off;
+    off += align256(count * sizeof(FinishJob));
+    const size_t o_starts = off;
+    off += align256(4 * (size_t)(count + 1) * sizeof(int));
+    const size_t o_counters = off;
+    b->ncounters = 2 * b->passes + 3;
+    off += align256((size_t)b->ncounters * sizeof(int));
+    const size_t tables_bytes = off - o_tables;
+    if (handle_ws) {
+        if (int e = ensure_ws(h, off)) return e;
+        b->ws = h->ws;
+    } else {
+        if (cudaMalloc(&b->ws, off) != cudaSuccess) {
+            (void)cudaGetLastError();
+            b->ws = nullptr;
+            return RXR_ERR_NOMEM;
+        }
+        b->ws_owned = true;
+    }
+    char *ws = (char *)b->ws;
+    b->statuses = (RxrStatus *)ws;
+    b->A.assign(A, A + count);
+    b->Q.assign(Q, Q + count);
+    b->R.assign(R, R + count);
+    b->lda.assign(lda, lda + count);
+    b->ldq.assign(ldq, ldq + count);
+    b->ldr.assign(ldr, ldr + count);
+    b->seed.assign(seed, seed + count);
+    for (int k = 0; k < count; ++k) {
+        bind_plan(b->plans[k], ws + base[k]);
+        b->plans[k].status = b->statuses + k;
+    }
+    auto dev = [&](size_t o) { return ws + o; };
+    b->counters = (int *)dev(o_counters);
+    if (!b->tables) return 0;
+
+    // job tables, built on the host (pinned staging of the handle, or a
+    // temporary host buffer for a plan's own copy)
+    std::vector<char> host_buf;
+    char *hs = nullptr;
+    if (handle_ws) {
+        if (h->h_stage_bytes < tables_bytes) {
+            if (h->h_stage) cudaFreeHost(h->h_stage);
+            h->h_stage = nullptr;
+            h->h_stage_bytes = 0;
+            if (cudaMallocHost(&h->h_stage, tables_bytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return RXR_ERR_NOMEM;
+            }
+            h->h_stage_bytes = tables_bytes;
+        }
+        hs = (char *)h->h_stage;
+    } else {
+        host_buf.resize(tables_bytes);
+        hs = host_buf.data();
+    }
+    auto host_at = [&](size_t o) { return hs + (o - o_tables); };
+    SketchJob *skj = (SketchJob *)host_at(o_skj);
+    ReduceJob *ryj = (ReduceJob *)host_at(o_ryj);
+    XrJob *xrj = (XrJob *)host_at(o_xrj);
+    SubstJob *prej = (SubstJob *)host_at(o_prej);
+    SubstJob *passj = (SubstJob *)host_at(o_passj);
+    ReduceJob *rgj = (ReduceJob *)host_at(o_rgj);
+    FactorJob *fj = (FactorJob *)host_at(o_fj);
+    FinishJob *finj = (FinishJob *)host_at(o_finj);
+    int *st_sk = (int *)host_at(o_starts);
+    int *st_ry = st_sk + (count + 1);
+    int *st_sg = st_ry + (count + 1);
+    int *st_rg = st_sg + (count + 1);
+    st_sk[0] = st_ry[0] = st_sg[0] = st_rg[0] = 0;
+    b->sg_smem = 0;
+    const int variant = b->variant;
+    for (int k = 0; k < count; ++k) {
+        Plan &p = b->plans[k];
+        const int nn = (int)n[k];
+        skj[k] = SketchJob{A[k], lda[k], m[k], nn, (int)sk[k], seed[k], p.sk_panels, p.sk_ppc,
+                           (int)std::min<int64_t>(n[k], kSkNTile), p.sk_gx, p.Ypart, p.status};
+        ryj[k] = ReduceJob{p.Ypart, p.sk_gx, sk[k] * n[k], (int)sk[k], nn, 1.0 / sqrt((double)sk[k]), 0, p.Y, sk[k],
+                           p.status};
+        xrj[k] = XrJob{p.Y, (int)sk[k], nn, sk[k], variant, p.W, p.Rs, p.Racc, p.status};
+        prej[k] = SubstJob{A[k], lda[k], m[k], nn, p.Rs, n[k], variant == RXR_NONE ? 1 : 0, Q[k], ldq[k], 1, p.Gpart,
+                           p.sg_panels, p.sg_ppc, variant == RXR_NONE ? 1 : 0, p.status};
+        passj[k] = SubstJob{Q[k], ldq[k], m[k], nn, p.Rp, n[k], 0, Q[k], ldq[k], 1, p.Gpart, p.sg_panels, p.sg_ppc, 0,
+                            p.status};
+        rgj[k] = ReduceJob{p.Gpart, p.sg_gx, n[k] * n[k], nn, nn, 1.0, 1, p.G, n[k], p.status};
+        fj[k] = FactorJob{p.G, nn, p.Rp, p.Racc, p.C, p.status};
+        finj[k] = FinishJob{p.Racc, nn, R[k], ldr[k], p.status, b->d_status + 4 * k};
+        st_sk[k + 1] = st_sk[k] + p.sk_gx * p.sk_gy;
+        st_ry[k + 1] = st_ry[k] + (int)cdiv(sk[k] * n[k], 256);
+        st_sg[k + 1] = st_sg[k] + p.sg_gx;
+        st_rg[k + 1] = st_rg[k] + (int)cdiv(n[k] * n[k], 256);
+        b->sg_smem = std::max(b->sg_smem, p.sg_smem);  // MAXT <= 3 tiles of n <= 128: the batched kernel's
+    }
+    if (handle_ws) {
+        if (cudaMemcpyAsync(dev(o_tables), hs, tables_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return RXR_ERR_CUDA;
+        }
+    } else if (cudaMemcpy(dev(o_tables), hs, tables_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return RXR_ERR_CUDA;
+    }
+    b->skj = (const SketchJob *)dev(o_skj);
+    b->ryj = (const ReduceJob *)dev(o_ryj);
+    b->xrj = (const XrJob *)dev(o_xrj);
+    b->prej = (const SubstJob *)dev(o_prej);
+    b->passj = (const SubstJob *)dev(o_passj);
+    b->rgj = (const ReduceJob *)dev(o_rgj);
+    b->fj = (const FactorJob *)dev(o_fj);
+    b->finj = (const FinishJob *)dev(o_finj);
+    b->st_sk = (const int *)dev(o_starts);
+    b->st_ry = b->st_sk + (count + 1);
+    b->st_sg = b->st_ry + (count + 1);
+    b->st_rg = b->st_sg + (count + 1);
+    b->tot_sk = st_sk[count];
+    b->tot_ry = st_ry[count];
+    b->tot_sg = st_sg[count];
+    b->tot_rg = st_rg[count];
+    const size_t sk_smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
+    b->grid_sk = occupancy_grid((const void *)k_sketch_fp64_batched, RXR_THREADS, sk_smem, h->sms, b->tot_sk);
+    b->grid_ry = occupancy_grid((const void *)k_reduce_parts_batched, 256, 0, h->sms, b->tot_ry);
+    b->grid_rg = occupancy_grid((const void *)k_reduce_parts_batched, 256, 0, h->sms, b->tot_rg);
+    b->grid_sg = occupancy_grid((const void *)k_subst_gram_batched, RXR_THREADS, b->sg_smem, h->sms, b->tot_sg);
+    return 0;
+}
+
+// Enqueue one run of the batch on `st`: no host synchronisation.
+int batch_enqueue(rxr_batch *b, cudaStream_t st)
+{
+    const int count = b->count;
+    if (!b->tables) {
+        // every problem's own launch sequence, spread over kBatchStreams streams
+        // that fork from and join back into st
+        if (cudaEventRecord(b->fork, st) != cudaSuccess) return RXR_ERR_CUDA;
+        const int K = std::min(count, kBatchStreams);
+        for (int j = 0; j < K; ++j)
+            if (cudaStreamWaitEvent(b->aux[j], b->fork, 0) != cudaSuccess) return RXR_ERR_CUDA;
+        for (int k = 0; k < count; ++k) {
+            cudaStream_t sk = b->aux[k % K];
+            if (int e = enqueue_cholqr(b->h, b->plans[k], b->A[k], b->lda[k], b->variant, b->seed[k], b->passes,
+                                       b->Q[k], b->ldq[k], b->R[k], b->ldr[k], sk, false))
+                return e;
+            k_status_out<<<1, 32, 0, sk>>>(b->plans[k].status, b->d_status + 4 * k);
+            if (launch_ok()) return RXR_ERR_CUDA;
+        }
+        for (int j = 0; j < K; ++j)
+            if (cudaEventRecord(b->join[j], b->aux[j]) != cudaSuccess ||
+                cudaStreamWaitEvent(st, b->join[j], 0) != cudaSuccess)
+                return RXR_ERR_CUDA;
+        return 0;
+    }
+    if (cudaMemsetAsync(b->statuses, 0, (size_t)count * sizeof(RxrStatus), st) != cudaSuccess ||
+        cudaMemsetAsync(b->counters, 0, (size_t)b->ncounters * sizeof(int), st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    int c = 0;  // next work-queue counter
+    if (b->variant != RXR_NONE) {
+        const size_t sk_smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
+        k_sketch_fp64_batched<<<b->grid_sk, RXR_THREADS, sk_smem, st>>>(b->skj, b->st_sk, count, b->tot_sk,
+                                                                        b->counters + c++);
+        k_reduce_parts_batched<<<b->grid_ry, 256, 0, st>>>(b->ryj, b->st_ry, count, b->tot_ry, b->counters + c++);
+    }
+    k_xr_factor_batched<<<count, 512, 0, st>>>(b->xrj);
+    k_subst_gram_batched<<<b->grid_sg, RXR_THREADS, b->sg_smem, st>>>(b->prej, b->st_sg, count, -1, b->tot_sg,
+                                                                      b->counters + c++);
+    k_reduce_parts_batched<<<b->grid_rg, 256, 0, st>>>(b->rgj, b->st_rg, count, b->tot_rg, b->counters + c++);
+    for (int pass = 1; pass <= b->passes; ++pass) {
+        const bool last = (pass == b->passes);
+        k_factor_batched<<<count, 512, 0, st>>>(b->fj, pass);
+        k_subst_gram_batched<<<b->grid_sg, RXR_THREADS, b->sg_smem, st>>>(b->passj, b->st_sg, count, last ? 0 : 1,
+                                                                          b->tot_sg, b->counters + c++);
+        if (!last)
+            k_reduce_parts_batched<<<b->grid_rg, 256, 0, st>>>(b->rgj, b->st_rg, count, b->tot_rg,
+                                                               b->counters + c++);
+    }
+    k_finish_batched<<<count, 256, 0, st>>>(b->finj);
+    return launch_ok();
+}
+
+// A plan for `count` problems: validated arguments, layout, tables, streams.
+int batch_create(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
+                 const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
+                 double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
+                 int *d_status, bool handle_ws, cudaStream_t st, rxr_batch **out)
+{
+    *out = nullptr;
+    if (count < 0) return -2;
+    if (!A || !m || !n || !lda || !s || !seed || !Q || !ldq || !R || !ldr || !d_status) return -3;
+    rxr_batch *b = new rxr_batch();
+    b->h = h;
+    b->count = count;
+    b->variant = variant;
+    b->passes = passes;
+    b->prec = prec;
+    b->d_status = d_status;
+    const int base = variant & ~RXR_SKETCH_ROWS;
+    b->tables = prec == RXR_FP64 && (variant & RXR_SKETCH_ROWS) == 0 && base != RXR_SHIFTED;
+    if (int e = batch_build(b, A, m, n, lda, s, seed, Q, ldq, R, ldr, handle_ws, st)) {
+        batch_release(b);
+        return e;
+    }
+    if (!b->tables) {
+        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            batch_release(b);
+            return RXR_ERR_CUDA;
+        }
+        for (int j = 0; j < kBatchStreams; ++j)
+            if (cudaStreamCreateWithFlags(&b->aux[j], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) != cudaSuccess) {
+                (void)cudaGetLastError();
+                batch_release(b);
+                return RXR_ERR_CUDA;
+            }
+    }
+    *out = b;
+    return 0;
+}
+
+}  // namespace
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 extern "C" {
@@ -955,143 +1295,24 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     if (h == nullptr) return RXR_ERR_CUDA;
     if (count < 0) return -2;
     if (count == 0) return 0;
-    if (!A || !m || !n || !lda || !s || !seed || !Q || !ldq || !R || !ldr || !d_status) return -3;
-    if (prec != RXR_FP64) return RXR_ERR_UNSUPPORTED;
-    for (int k = 0; k < count; ++k)
-        if (n[k] > kNarrowN) return RXR_ERR_UNSUPPORTED;  // batched form: n <= 128
     DeviceGuard g(h->device);
     if (!g.ok) return RXR_ERR_CUDA;
-    std::vector<int64_t> sk(count);
-    int64_t total_rows = 0;
-    for (int k = 0; k < count; ++k) {
-        if ((variant & RXR_SKETCH_ROWS) || variant == RXR_SHIFTED) return RXR_ERR_UNSUPPORTED;
-        sk[k] = (variant == RXR_NONE && s[k] < n[k]) ? n[k] : s[k];
-        if (int e = check_args(A[k], m[k], n[k], lda[k], variant, sk[k], passes, Q[k], ldq[k], R[k], ldr[k], prec))
-            return e;
-        total_rows += m[k];
-    }
-    // row chunks in proportion to each problem's rows, about eight CTAs per SM
-    // per streaming stage over the whole batch
-    const int64_t target_rows = std::max<int64_t>(kSgP, total_rows / (8 * (int64_t)h->sms));
-    std::vector<Plan> plans(count);
-    std::vector<size_t> base(count);
-    size_t off = align256((size_t)count * sizeof(RxrStatus));
-    for (int k = 0; k < count; ++k) {
-        make_plan(plans[k], m[k], n[k], sk[k], prec, h->sms, cdiv(m[k], target_rows));
-        base[k] = off;
-        off += align256(plans[k].bytes);
-    }
-    // job tables
-    const size_t o_skj = off;
-    off += align256(count * sizeof(SketchJob));
-    const size_t o_ryj = off;
-    off += align256(count * sizeof(ReduceJob));
-    const size_t o_xrj = off;
-    off += align256(count * sizeof(XrJob));
-    const size_t o_prej = off;
-    off += align256(count * sizeof(SubstJob));
-    const size_t o_passj = off;
-    off += align256(count * sizeof(SubstJob));
-    const size_t o_rgj = off;
-    off += align256(count * sizeof(ReduceJob));
-    const size_t o_fj = off;
-    off += align256(count * sizeof(FactorJob));
-    const size_t o_finj = off;
-    off += align256(count * sizeof(FinishJob));
-    const size_t o_starts = off;
-    off += align256(4 * (size_t)(count + 1) * sizeof(int));
-    const size_t tables_bytes = off - o_skj;
-    if (int e = ensure_ws(h, off)) return e;
-    char *ws = (char *)h->ws;
-    if (h->h_stage_bytes < tables_bytes) {
-        if (h->h_stage) cudaFreeHost(h->h_stage);
-        h->h_stage = nullptr;
-        h->h_stage_bytes = 0;
-        if (cudaMallocHost(&h->h_stage, tables_bytes) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return RXR_ERR_NOMEM;
-        }
-        h->h_stage_bytes = tables_bytes;
-    }
-    char *hs = (char *)h->h_stage;
-    auto host_at = [&](size_t o) { return hs + (o - o_skj); };
-    SketchJob *skj = (SketchJob *)host_at(o_skj);
-    ReduceJob *ryj = (ReduceJob *)host_at(o_ryj);
-    XrJob *xrj = (XrJob *)host_at(o_xrj);
-    SubstJob *prej = (SubstJob *)host_at(o_prej);
-    SubstJob *passj = (SubstJob *)host_at(o_passj);
-    ReduceJob *rgj = (ReduceJob *)host_at(o_rgj);
-    FactorJob *fj = (FactorJob *)host_at(o_fj);
-    FinishJob *finj = (FinishJob *)host_at(o_finj);
-    int *st_sk = (int *)host_at(o_starts);
-    int *st_ry = st_sk + (count + 1);
-    int *st_sg = st_ry + (count + 1);
-    int *st_rg = st_sg + (count + 1);
-    RxrStatus *statuses = (RxrStatus *)ws;
-    size_t sg_smem = 0;
-    st_sk[0] = st_ry[0] = st_sg[0] = st_rg[0] = 0;
-    for (int k = 0; k < count; ++k) {
-        Plan &p = plans[k];
-        bind_plan(p, ws + base[k]);
-        p.status = statuses + k;
-        const int nn = (int)n[k];
-        skj[k] = SketchJob{A[k], lda[k], m[k], nn, (int)sk[k], seed[k], p.sk_panels, p.sk_ppc,
-                           (int)std::min<int64_t>(n[k], kSkNTile), p.sk_gx, p.Ypart, p.status};
-        ryj[k] = ReduceJob{p.Ypart, p.sk_gx, sk[k] * n[k], (int)sk[k], nn, 1.0 / sqrt((double)sk[k]), 0, p.Y, sk[k],
-                           p.status};
-        xrj[k] = XrJob{p.Y, (int)sk[k], nn, sk[k], variant, p.W, p.Rs, p.Racc, p.status};
-        prej[k] = SubstJob{A[k], lda[k], m[k], nn, p.Rs, n[k], variant == RXR_NONE ? 1 : 0, Q[k], ldq[k], 1, p.Gpart,
-                           p.sg_panels, p.sg_ppc, variant == RXR_NONE ? 1 : 0, p.status};
-        passj[k] = SubstJob{Q[k], ldq[k], m[k], nn, p.Rp, n[k], 0, Q[k], ldq[k], 1, p.Gpart, p.sg_panels, p.sg_ppc, 0,
-                            p.status};
-        rgj[k] = ReduceJob{p.Gpart, p.sg_gx, n[k] * n[k], nn, nn, 1.0, 1, p.G, n[k], p.status};
-        fj[k] = FactorJob{p.G, nn, p.Rp, p.Racc, p.C, p.status};
-        finj[k] = FinishJob{p.Racc, nn, R[k], ldr[k], p.status, d_status + 4 * k};
-        st_sk[k + 1] = st_sk[k] + p.sk_gx * p.sk_gy;
-        st_ry[k + 1] = st_ry[k] + (int)cdiv(sk[k] * n[k], 256);
-        st_sg[k + 1] = st_sg[k] + p.sg_gx;
-        st_rg[k + 1] = st_rg[k] + (int)cdiv(n[k] * n[k], 256);
-        sg_smem = std::max(sg_smem, p.sg_smem);
-    }
-    // sg_smem was sized for MAXT <= 3 tiles of n <= 128, which the batched kernel covers
     cudaStream_t st = (cudaStream_t)stream;
-    auto dev = [&](size_t o) { return ws + o; };
-    if (cudaMemcpyAsync(dev(o_skj), hs, tables_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(statuses, 0, (size_t)count * sizeof(RxrStatus), st) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return RXR_ERR_CUDA;
-    }
-    const int *d_st_sk = (const int *)dev(o_starts);
-    const int *d_st_ry = d_st_sk + (count + 1);
-    const int *d_st_sg = d_st_ry + (count + 1);
-    const int *d_st_rg = d_st_sg + (count + 1);
-    const size_t sk_smem = (size_t)(kSkNTile * kSkP + kSkP * kSkSTile) * sizeof(double);
-    if (variant != RXR_NONE) {
-        k_sketch_fp64_batched<<<st_sk[count], RXR_THREADS, sk_smem, st>>>((const SketchJob *)dev(o_skj), d_st_sk,
-                                                                         count);
-        k_reduce_parts_batched<<<st_ry[count], 256, 0, st>>>((const ReduceJob *)dev(o_ryj), d_st_ry, count);
-    }
-    k_xr_factor_batched<<<count, 512, 0, st>>>((const XrJob *)dev(o_xrj));
-    k_subst_gram_batched<<<st_sg[count], RXR_THREADS, sg_smem, st>>>((const SubstJob *)dev(o_prej), d_st_sg, count,
-                                                                     -1);
-    k_reduce_parts_batched<<<st_rg[count], 256, 0, st>>>((const ReduceJob *)dev(o_rgj), d_st_rg, count);
-    for (int pass = 1; pass <= passes; ++pass) {
-        const bool last = (pass == passes);
-        k_factor_batched<<<count, 512, 0, st>>>((const FactorJob *)dev(o_fj), pass);
-        k_subst_gram_batched<<<st_sg[count], RXR_THREADS, sg_smem, st>>>((const SubstJob *)dev(o_passj), d_st_sg,
-                                                                         count, last ? 0 : 1);
-        if (!last)
-            k_reduce_parts_batched<<<st_rg[count], 256, 0, st>>>((const ReduceJob *)dev(o_rgj), d_st_rg, count);
-    }
-    k_finish_batched<<<count, 256, 0, st>>>((const FinishJob *)dev(o_finj));
-    if (launch_ok()) return RXR_ERR_CUDA;
+    rxr_batch *b = nullptr;
+    if (int e = batch_create(h, count, A, m, n, lda, variant, s, seed, passes, Q, ldq, R, ldr, prec, d_status, true,
+                             st, &b))
+        return e;
+    int e = batch_enqueue(b, st);
     std::vector<int> hs_status((size_t)count * 4);
-    if (cudaMemcpyAsync(hs_status.data(), d_status, (size_t)count * 4 * sizeof(int), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+    if (!e && (cudaMemcpyAsync(hs_status.data(), d_status, (size_t)count * 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                               st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess)) {
         (void)cudaGetLastError();
-        return RXR_ERR_CUDA;
+        e = RXR_ERR_CUDA;
     }
+    if (e) cudaStreamSynchronize(st);
+    batch_release(b);
+    if (e) return e;
     int code = 0;
     for (int k = 0; k < count && code == 0; ++k)
         if (hs_status[4 * k]) {
@@ -1104,6 +1325,35 @@ int rxr_cholqr_batched(rxr_handle h, int count, const double *const *A, const in
     return code;
 }
 
+int rxr_batch_create(rxr_handle h, int count, const double *const *A, const int64_t *m, const int64_t *n,
+                     const int64_t *lda, int variant, const int64_t *s, const uint64_t *seed, int passes,
+                     double *const *Q, const int64_t *ldq, double *const *R, const int64_t *ldr, int prec,
+                     int *d_status, rxr_batch_plan *plan)
+{
+    if (plan == nullptr) return -17;
+    *plan = nullptr;
+    if (h == nullptr) return -1;
+    if (count < 1) return -2;
+    DeviceGuard g(h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    return batch_create(h, count, A, m, n, lda, variant, s, seed, passes, Q, ldq, R, ldr, prec, d_status, false,
+                        nullptr, plan);
+}
+
+int rxr_batch_run(rxr_batch_plan plan, void *stream)
+{
+    if (plan == nullptr) return -1;
+    DeviceGuard g(plan->h->device);
+    if (!g.ok) return RXR_ERR_CUDA;
+    return batch_enqueue(plan, (cudaStream_t)stream);
+}
+
+int rxr_batch_destroy(rxr_batch_plan plan)
+{
+    batch_release(plan);
+    return 0;
+}
+
 int rxr_set_test_hook(rxr_handle h, int hook, int value)
 {
     if (h == nullptr) return -1;
@@ -1113,6 +1363,12 @@ int rxr_set_test_hook(rxr_handle h, int hook, int value)
         if (value < 0 || value > 40) return -3;
         h->jacobi_sweeps = value;
         return 0;
+    case RXR_HOOK_BATCH_CTAS: {
+        const int bucket = value >> 8, ctas = value & 255;
+        if (bucket < 0 || bucket >= kBatchTuneBuckets) return -3;
+        h->batch_ctas[bucket] = ctas;
+        return 0;
+    }
     default: return -2;
     }
 }

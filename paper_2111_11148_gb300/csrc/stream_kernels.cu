@@ -517,10 +517,11 @@ __global__ void __launch_bounds__(RXR_THREADS)
 }
 
 // ---------------------------------------------------------------------------
-// Batched forms: one launch serves every problem of a batch.  Block b belongs
-// to the problem k with start[k] <= b < start[k+1] (binary search over the
-// per-stage block offsets); the problem's own block index is b - start[k].
-// Panels are staged with plain coalesced loads (no per-problem tensor maps).
+// Batched forms: one launch per stage serves every problem of a batch.  Work
+// item b (a row chunk or a reduction block of one problem) belongs to the
+// problem k with start[k] <= b < start[k+1] (binary search over the per-stage
+// item offsets); the problem's own block index is b - start[k].  Panels are
+// staged with plain coalesced loads (no per-problem tensor maps).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_job(const int *__restrict__ start, int count, int b)
 {
@@ -535,33 +536,55 @@ __device__ __forceinline__ int find_job(const int *__restrict__ start, int count
     return lo;
 }
 
-__global__ void __launch_bounds__(RXR_THREADS, 2)
-    k_sketch_fp64_batched(const SketchJob *__restrict__ jobs, const int *__restrict__ start, int count)
+// Persistent forms: gridDim.x CTAs pull work items b = 0 .. total - 1 (a
+// problem's row chunk, or its reduction block) from the device counter
+// *next (zeroed before the launch) until the queue is empty; item b belongs
+// to the problem k with start[k] <= b < start[k+1].
+__device__ __forceinline__ int next_item(int *next)
 {
-    const int k = find_job(start, count, blockIdx.x);
-    const SketchJob j = jobs[k];
-    const int local = blockIdx.x - start[k];
-    sketch_body(nullptr, 0, j.A, j.lda, j.m, j.n, j.s, j.seed, j.panels_total, j.panels_per_cta, j.box_cols,
-                j.Ypart, j.st, local % j.gx, local / j.gx);
+    __shared__ int item;
+    __syncthreads();  // every thread has read the previous item (and the CTA's shared memory is free)
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    return item;
 }
 
-__global__ void k_reduce_parts_batched(const ReduceJob *__restrict__ jobs, const int *__restrict__ start, int count)
+__global__ void __launch_bounds__(RXR_THREADS, 2)
+    k_sketch_fp64_batched(const SketchJob *__restrict__ jobs, const int *__restrict__ start, int count, int total,
+                          int *next)
 {
-    const int k = find_job(start, count, blockIdx.x);
-    const ReduceJob j = jobs[k];
-    reduce_body(j.parts, j.nparts, j.stride, j.rows, j.cols, j.scale, j.symmetric, j.out, j.ldo, j.st,
-                blockIdx.x - start[k], start[k + 1] - start[k]);
+    for (int b = next_item(next); b < total; b = next_item(next)) {
+        const int k = find_job(start, count, b);
+        const SketchJob j = jobs[k];
+        const int local = b - start[k];
+        sketch_body(nullptr, 0, j.A, j.lda, j.m, j.n, j.s, j.seed, j.panels_total, j.panels_per_cta, j.box_cols,
+                    j.Ypart, j.st, local % j.gx, local / j.gx);
+    }
+}
+
+__global__ void k_reduce_parts_batched(const ReduceJob *__restrict__ jobs, const int *__restrict__ start, int count,
+                                       int total, int *next)
+{
+    for (int b = next_item(next); b < total; b = next_item(next)) {
+        const int k = find_job(start, count, b);
+        const ReduceJob j = jobs[k];
+        reduce_body(j.parts, j.nparts, j.stride, j.rows, j.cols, j.scale, j.symmetric, j.out, j.ldo, j.st,
+                    b - start[k], start[k + 1] - start[k]);
+    }
 }
 
 // do_gram < 0 keeps each job's own flag; 0 or 1 overrides it for all jobs
 __global__ void __launch_bounds__(RXR_THREADS)
-    k_subst_gram_batched(const SubstJob *__restrict__ jobs, const int *__restrict__ start, int count, int do_gram)
+    k_subst_gram_batched(const SubstJob *__restrict__ jobs, const int *__restrict__ start, int count, int do_gram,
+                         int total, int *next)
 {
-    const int k = find_job(start, count, blockIdx.x);
-    const SubstJob j = jobs[k];
-    subst_gram_body<3>(nullptr, 0, j.src, j.lds, j.m, j.n, j.R, j.ldr, j.unit_r, j.dst, j.ldd,
-                       do_gram < 0 ? j.do_gram : do_gram, j.Gpart, j.panels_total, j.panels_per_cta, j.check_finite,
-                       j.st, blockIdx.x - start[k]);
+    for (int b = next_item(next); b < total; b = next_item(next)) {
+        const int k = find_job(start, count, b);
+        const SubstJob j = jobs[k];
+        subst_gram_body<3>(nullptr, 0, j.src, j.lds, j.m, j.n, j.R, j.ldr, j.unit_r, j.dst, j.ldd,
+                           do_gram < 0 ? j.do_gram : do_gram, j.Gpart, j.panels_total, j.panels_per_cta,
+                           j.check_finite, j.st, b - start[k]);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -24,7 +24,7 @@ SKETCH_ROWS = 16  # OR-ed into LU / QR: the sketch by row extraction
 FP64, SPLIT_BF16, SPLIT_PRECOND = 0, 1, 3
 (OK, SKETCH_SINGULAR, CHOL_BREAKDOWN, NONFINITE, CUDA_ERROR, TIMEOUT, NOMEM, UNSUPPORTED, BAD_SPARSE,
  NO_CONVERGENCE) = range(10)
-HOOK_STALL, HOOK_JACOBI_SWEEPS = 1, 2  # rxr_set_test_hook
+HOOK_STALL, HOOK_JACOBI_SWEEPS, HOOK_BATCH_CTAS = 1, 2, 3  # rxr_set_test_hook
 KERNEL_SKETCH, KERNEL_PRECOND_GRAM, KERNEL_PASS_GRAM, KERNEL_APPLY = range(4)
 
 _VARIANTS = {"lu": LU, "qr": QR, "none": NONE, "shifted": SHIFTED, "lu-rows": LU | SKETCH_ROWS,
@@ -82,6 +82,9 @@ def load() -> ctypes.CDLL:
         "rxr_sketch_noalloc": ([vp, i64, i64, i64, i64, u64, vp, i64, vp], i),
         "rxr_set_test_hook": ([vp, i, i], i),
         "rxr_sketch_part": ([vp, vp, i64, i64, i64, i64, u64, i64, vp, i64, i, vp], i),
+        "rxr_batch_create": ([vp, i, vp, vp, vp, vp, i, vp, vp, i, vp, vp, vp, vp, i, vp, P(vp)], i),
+        "rxr_batch_run": ([vp, vp], i),
+        "rxr_batch_destroy": ([vp], i),
         "rxr_sum_parts": ([vp, vp, i, i64, vp, vp], i),
         "rxr_trmm_upper": ([vp, vp, i64, vp, i64, i64, vp, i64, vp], i),
         "rxr_rsvd": ([vp, i64, i64, vp, vp, vp, vp, vp, vp, i64, vp, i64, i64, i, i, i64, u64, i, i, vp, i64, vp, vp,
@@ -102,7 +105,8 @@ def exported_symbols() -> list[str]:
                         "rxr_precond_gram",
                         "rxr_cholesky", "rxr_apply_rinv", "rxr_lstsq", "rxr_gram", "rxr_orth_error", "rxr_resid_error", "rxr_fp64_peak",
                         "rxr_last_kernel_ms", "rxr_set_kernel_timing", "rxr_sketch_noalloc", "rxr_rsvd",
-                        "rxr_set_test_hook", "rxr_sketch_part", "rxr_sum_parts", "rxr_trmm_upper")]
+                        "rxr_set_test_hook", "rxr_sketch_part", "rxr_sum_parts", "rxr_trmm_upper",
+                        "rxr_batch_create", "rxr_batch_run", "rxr_batch_destroy")]
 
 
 def status_string(code: int) -> str:
@@ -155,6 +159,48 @@ def _stream(stream) -> ctypes.c_void_p:
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+class BatchPlan:
+    """A prepared batch (rxr_batch_plan): Qs, Rs and the device status array
+    `status` (count x 4 int32) are owned here; run() enqueues one factorisation
+    of every problem on the stream, with no host synchronisation."""
+
+    def __init__(self, handle, As, variant, s, seeds, passes, prec):
+        import torch
+
+        self.handle = handle  # keeps the handle alive
+        self.As = list(As)
+        cnt = len(self.As)
+        self.Qs = [empty_colmajor(a.shape[0], a.shape[1], device=a.device) for a in self.As]
+        self.Rs = [empty_colmajor(a.shape[1], a.shape[1], device=a.device) for a in self.As]
+        s = [2 * a.shape[1] for a in self.As] if s is None else list(s)
+        seeds = list(range(cnt)) if seeds is None else list(seeds)
+        self.status = torch.zeros((cnt, 4), dtype=torch.int32, device=self.As[0].device)
+        arr = lambda T, v: (T * cnt)(*v)
+        vp = ctypes.c_void_p
+        self._p = ctypes.c_void_p()
+        _check(load().rxr_batch_create(
+            handle._h, cnt, arr(vp, [a.data_ptr() for a in self.As]), arr(ctypes.c_int64, [a.shape[0] for a in self.As]),
+            arr(ctypes.c_int64, [a.shape[1] for a in self.As]), arr(ctypes.c_int64, [_ld(a) for a in self.As]),
+            _VARIANTS[variant], arr(ctypes.c_int64, s), arr(ctypes.c_uint64, seeds), int(passes),
+            arr(vp, [q.data_ptr() for q in self.Qs]), arr(ctypes.c_int64, [_ld(q) for q in self.Qs]),
+            arr(vp, [r.data_ptr() for r in self.Rs]), arr(ctypes.c_int64, [_ld(r) for r in self.Rs]), _PRECS[prec],
+            _ptr(self.status), ctypes.byref(self._p)), "rxr_batch_create")
+
+    def run(self, stream=None):
+        _check(load().rxr_batch_run(self._p, _stream(stream)), "rxr_batch_run")
+
+    def close(self):
+        if self._p:
+            load().rxr_batch_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Handle:
@@ -292,6 +338,12 @@ class Handle:
         _check(load().rxr_trmm_upper(self._h, _ptr(A), _ld(A), _ptr(B), _ld(B), n, _ptr(C), _ld(C),
                                      _stream(stream)), "rxr_trmm_upper")
         return C
+
+    def batch_plan(self, As: Sequence, variant="qr", s: Optional[Sequence[int]] = None,
+                   seeds: Optional[Sequence[int]] = None, passes=2, prec="fp64") -> "BatchPlan":
+        """rxr_batch_create for the column-major CUDA tensors As (outputs
+        allocated here); run it with BatchPlan.run."""
+        return BatchPlan(self, As, variant, s, seeds, passes, prec)
 
     # ---------------------------------------------------------------- stages
     def sketch(self, A, s: int, seed: int = 0, prec="fp64", stream=None):

@@ -93,7 +93,13 @@ def test_host_entry_point_rows(h):
     assert np.array_equal(Qh, to_host(Q)) and np.array_equal(Rh, to_host(R))
 
 
-def test_batched_rejects_rows(h):
-    A = [to_dev(usv_matrix(500, 8, 10.0, seed=0))]
-    with pytest.raises(rxr.RxrError):
-        h.cholqr_batched(A, variant="qr-rows")
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_batched_rows_runs_each_problem_as_the_single_call(h, prec):
+    # the row-extraction sketch in a batch: every problem's own launch sequence
+    # (the single call's kernels and partition), so the same bits
+    As = [to_dev(usv_matrix(m, n, 1e6, seed=m)) for m, n in [(500, 8), (3000, 40), (20000, 100)]]
+    Qs, Rs, st = h.cholqr_batched(As, variant="qr-rows", seeds=[4, 5, 6], prec=prec)
+    assert np.all(st == 0)
+    for A, Qb, Rb, seed in zip(As, Qs, Rs, [4, 5, 6]):
+        Q, R, _ = h.cholqr(A, variant="qr-rows", seed=seed, prec=prec)
+        assert torch.equal(Q, Qb) and torch.equal(R, Rb)

@@ -51,9 +51,13 @@ def test_shift_keeps_first_cholesky_alive(h, prec):
     assert code == 0
 
 
-def test_batched_rejects_shifted(h):
-    with pytest.raises(rxr.RxrError):
-        h.cholqr_batched([to_dev(usv_matrix(500, 8, 10.0, seed=0))], variant="shifted", passes=3)
+def test_batched_shifted_runs_each_problem_as_the_single_call(h):
+    As = [to_dev(usv_matrix(m, n, 1e10, seed=m)) for m, n in [(500, 8), (4000, 33)]]
+    Qs, Rs, st = h.cholqr_batched(As, variant="shifted", passes=3)
+    assert np.all(st == 0)
+    for A, Qb, Rb in zip(As, Qs, Rs):
+        Q, R, _ = h.cholqr(A, variant="shifted", passes=3)
+        assert torch.equal(Q, Qb) and torch.equal(R, Rb)
 
 
 @pytest.mark.parametrize("m,n,kappa,passes", [(5000, 16, 1e6, 2), ((1 << 17) + 5, 48, 1e7, 2), (2100, 100, 1e5, 2),
