@@ -657,10 +657,10 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
                 Timer t(th, 2, st);
                 // below ~2^17 rows the inverse and the estimate (~0.1 ms) cost more
                 // than the product saves
-                if (cx && p.m >= ((int64_t)1 << 17)) {
+                if (p.n <= 128 && p.m >= ((int64_t)1 << 17)) {
                     // R_p of a middle pass is well conditioned after the preconditioning:
                     // explicit-inverse product unless the estimate says otherwise
-                    if (cudaMemsetAsync(cx, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+                    if (cx && cudaMemsetAsync(cx, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
                     if (int e = middle_pass_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, cx, split_select_flag(p), st))
                         return e;
                 } else if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st, cx)) {

@@ -674,9 +674,10 @@ constexpr size_t kApSmem = (size_t)kApDigits * (kApATile + kApBTile);
 __global__ void __launch_bounds__(256, 1)
     k_update_ozaki(const double *X, int64_t ldx, int xc0, int K, const double *__restrict__ R, int64_t ldr, int tc0,
                    int N, const double *B, int64_t ldb, double *C, int64_t ldc, int64_t m, int64_t tiles_total,
-                   int64_t tiles_per_cta, RxrStatus *st)
+                   int64_t tiles_per_cta, const int *__restrict__ sel, RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
+    if (sel != nullptr && *sel != 1) return;  // the substitution was chosen instead
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *aop = smem;
     unsigned char *bop = smem + kApDigits * kApATile;
@@ -2580,26 +2581,30 @@ static void delta_launch(int sms, double *X, int64_t ldx, int64_t m, int n, cons
             X, ldx, m, n, Ef, tiles, sel, status);
 }
 
-// Estimate of cond_2(R) = ||R||_2 ||R^{-1}||_2 (n <= 64, one CTA): twelve power
+// Estimate of cond_2(R) = ||R||_2 ||R^{-1}||_2 (n <= 128, one CTA): twelve power
 // iterations on R^T R and on T^T T (T = R^{-1}) from the all-ones vector, in a
 // fixed order (deterministic).  *sel = 1 when the estimate is at most kExplicitCond,
 // else 0: the middle CholeskyQR pass then multiplies by T on the tensor cores
 // instead of substituting.
 constexpr double kExplicitCond = 16.0;
 
-__global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ R, const double *__restrict__ T, int n,
-                                                     int *sel, RxrStatus *st)
+// NM = 64 or 128 (n <= NM), 4 NM threads (four a row), the matrix in
+// NM (NM + 1) doubles of dynamic shared memory.
+template <int NM>
+__global__ void __launch_bounds__(4 * NM) k_cond_select(const double *__restrict__ R, const double *__restrict__ T,
+                                                        int n, int *sel, RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
-    __shared__ double Ms[64 * 65];  // the matrix, column-major with a padded stride (zero below the diagonal)
-    __shared__ double v[64], w[64], red[8];
+    constexpr int LD = NM + 1, NW = NM / 8;  // padded stride; warps
+    extern __shared__ double Ms[];  // the matrix, column-major with a padded stride (zero below the diagonal)
+    __shared__ double v[NM], w[NM], red[NW];
     const int tid = threadIdx.x, row = tid >> 2, q = tid & 3, lane = tid & 31, warp = tid >> 5;
     double est[2];
     for (int which = 0; which < 2; ++which) {
         const double *M = which == 0 ? R : T;  // upper triangular, ld n
-        for (int e = tid; e < 64 * 64; e += blockDim.x) {
-            const int i = e & 63, k = e >> 6;
-            Ms[i + k * 65] = (i <= k && k < n) ? M[i + (int64_t)k * n] : 0.0;
+        for (int e = tid; e < NM * NM; e += blockDim.x) {
+            const int i = e % NM, k = e / NM;
+            Ms[i + k * LD] = (i <= k && k < n) ? M[i + (int64_t)k * n] : 0.0;
         }
         if (q == 0) v[row] = (row < n) ? 1.0 : 0.0;
         __syncthreads();
@@ -2608,7 +2613,7 @@ __global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ 
             // w = M v: four threads per row, terms k = q, q + 4, ...
             double a = 0.0;
 #pragma unroll
-            for (int k = q; k < 64; k += 4) a = fma(Ms[row + k * 65], v[k], a);
+            for (int k = q; k < NM; k += 4) a = fma(Ms[row + k * LD], v[k], a);
             a += __shfl_xor_sync(0xFFFFFFFFu, a, 1);
             a += __shfl_xor_sync(0xFFFFFFFFu, a, 2);
             if (q == 0) w[row] = a;
@@ -2616,7 +2621,7 @@ __global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ 
             // v = M^T w
             double b = 0.0;
 #pragma unroll
-            for (int k = q; k < 64; k += 4) b = fma(Ms[k + row * 65], w[k], b);
+            for (int k = q; k < NM; k += 4) b = fma(Ms[k + row * LD], w[k], b);
             b += __shfl_xor_sync(0xFFFFFFFFu, b, 1);
             b += __shfl_xor_sync(0xFFFFFFFFu, b, 2);
             double t = (q == 0) ? b * b : 0.0;
@@ -2626,7 +2631,7 @@ __global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ 
             __syncthreads();
             double ss = 0.0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) ss += red[k];  // every thread, same order
+            for (int k = 0; k < NW; ++k) ss += red[k];  // every thread, same order
             nrm = sqrt(sqrt(ss));  // ||M^T M v||^(1/2) with ||v|| = 1 before: an estimate of ||M||_2
             const double inv = (ss > 0.0) ? 1.0 / sqrt(ss) : 0.0;
             if (q == 0) v[row] = b * inv;
@@ -2640,18 +2645,61 @@ __global__ void __launch_bounds__(256) k_cond_select(const double *__restrict__ 
     }
 }
 
+// dst = -src (n x n, ld n): the negated block of R^{-1} that the middle
+// pass's block product adds through the trailing-update kernel (C = B - X R)
+__global__ void k_negate(const double *__restrict__ src, int n, double *__restrict__ dst, const RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) dst[e] = -src[e];
+}
+
 // The middle CholeskyQR pass for n <= 64: X <- X R^{-1} by the tensor-core
 // product with T = R^{-1} when R is well conditioned (estimate <= 16), else by
 // the fused substitution; both kernels are launched and the one not selected
 // returns at once (no host synchronisation).  X's column exponents go to
 // colexp_out for the Gram that follows.
+// 64 < n <= 128: X <- X T with T = R^{-1} in 64-column blocks, when the
+// estimate of cond_2(R) is at most 16 (else the fused substitution):
+//   X_b <- X_b T_11,  X_b <- X_b + X_a T_01,  X_a <- X_a T_00,
+// X_a = columns 0..63, X_b = 64..n-1; each step an FP64-grade tensor-core
+// product, in this order so that each reads columns not yet overwritten.
+static int middle_pass128_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *sel, cudaStream_t st)
+{
+    const int n = (int)p.n, nb = n - 64;
+    double *T = p.W;
+    k_tri_inverse128<<<(unsigned)n, 32, (size_t)n * 128 * sizeof(double), st>>>(R, n, p.n, T, p.status);
+    k_cond_select<128><<<1, 512, 128 * 129 * sizeof(double), st>>>(R, T, n, sel, p.status);
+    k_negate<<<(unsigned)cdiv64((int64_t)n * n, 256), 256, 0, st>>>(T, n, p.C, p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    const int64_t tiles = cdiv64(p.m, kAqM);
+    const int gx = (int)std::min<int64_t>(p.sms, tiles);
+    double *Xb = X + 64 * ldx;
+    CUtensorMap mb, ma;
+    const int tma_b = encode_tile_map(&mb, Xb, p.m, nb, ldx, kAqM, nb) ? 1 : 0;
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(nb), st>>>(mb, tma_b, Xb, ldx, p.m, nb, T + 64 + 64 * p.n, p.n, tiles, sel,
+                                                     1, nullptr, p.status);
+    const int64_t utiles = cdiv64(p.m, kApM);
+    int64_t ugx = balanced_chunks(1, p.sms, utiles);
+    const int64_t tpc = cdiv64(utiles, ugx);
+    ugx = cdiv64(utiles, tpc);
+    // C = B - X_a (-T_01): the trailing-update kernel with the negated block
+    k_update_ozaki<<<dim3((unsigned)ugx, 1), 256, kApSmem, st>>>(X, ldx, 0, 64, p.C, p.n, 64, nb, X, ldx, X, ldx,
+                                                                  p.m, utiles, tpc, sel, p.status);
+    const int tma_a = encode_tile_map(&ma, X, p.m, 64, ldx, kAqM, 64) ? 1 : 0;
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T, p.n, tiles, sel, 1, nullptr,
+                                                     p.status);
+    if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+    return fused128_subst_enqueue(p, X, ldx, R, p.n, X, ldx, st, sel);
+}
+
 int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *colexp_out, int *sel,
                         cudaStream_t st)
 {
-    if (p.n > 64) return RXR_ERR_UNSUPPORTED;
+    if (p.n > 128) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
+    if (p.n > 64) return middle_pass128_enqueue(p, X, ldx, R, sel, st);
     k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
-    k_cond_select<<<1, 256, 0, st>>>(R, T, (int)p.n, sel, p.status);
+    k_cond_select<64><<<1, 256, 64 * 65 * sizeof(double), st>>>(R, T, (int)p.n, sel, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int n = (int)p.n;
     CUtensorMap mx;
@@ -2747,7 +2795,7 @@ int blocked_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double
         // the first trailing update reads B (= A) and writes X; later ones work in X
         k_update_ozaki<<<dim3((unsigned)gx, (unsigned)gy), 256, kApSmem, st>>>(
             X, ldx, c0, b, R, ldr, tc0, N, (c0 == 0) ? Bsrc : X, (c0 == 0) ? ldb : ldx, X, ldx, p.m, tiles, tpc,
-            p.status);
+            nullptr, p.status);
         if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     }
     return 0;
@@ -2858,6 +2906,9 @@ cudaError_t set_split_smem()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_tri_inverse128, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  128 * 128 * (int)sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cond_select<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 128 * 129 * (int)sizeof(double));
     return e;
 }
 

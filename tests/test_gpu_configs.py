@@ -123,3 +123,21 @@ def test_plain_load_path_repeated(h, prec):
         Q, R, code = h.cholqr(Ad, variant="qr", s=2 * n, seed=2, passes=2, prec=prec)
         assert code == 0
         _check(np.asfortranarray(A), Q, R, ref, ("plain", 1e4, prec))
+
+
+@pytest.mark.parametrize("n,s_factor", [(128, 2), (128, 1), (100, 2), (100, 1)])
+def test_split_middle_pass_branches_n128(h, n, s_factor):
+    # 64 < n <= 128, m >= 2^17: the middle pass multiplies by R_1^{-1} in 64-column
+    # blocks on the tensor cores when the device's estimate of cond_2(R_1) is at
+    # most 16 (s = 2n: Theorem 3.4's well-conditioned X), else substitutes (s = n
+    # leaves cond(X) far larger); both against the oracle
+    A = usv_matrix(M17, n, 1e12, seed=n + s_factor)
+    s = s_factor * n
+    ref = o.rxr_cholqr(A, o.VARIANT_QR, s, seed=7, passes=2)
+    assert ref.status == 0
+    X1 = np.linalg.solve(ref.Rs.T, A.T).T
+    cond_r1 = np.linalg.cond(X1)
+    Q, R, code = h.cholqr(to_dev(A), variant="qr", s=s, seed=7, passes=2, prec="split")
+    assert code == 0
+    rel, orth, resid = _check(A, Q, R, ref, ("middle", 1e12, n, s))
+    print(f"n={n} s={s}: cond(X_1) {cond_r1:.1f}, R vs oracle {rel:.2e}, orth {orth:.2e}, resid {resid:.2e}")
