@@ -1822,6 +1822,220 @@ __global__ void __launch_bounds__(kG6Producers, 1)
 }
 
 // ---------------------------------------------------------------------------
+// FP64-grade Gram G = X^T X for 64 < n <= 128 on the tensor cores, pipelined
+// like k_gram_oz64.  Column j of X is cut into seven 8-bit digits relative to
+// 2^(e_j + 1), e_j its largest exponent over all m rows.  For each 32-row
+// buffer the digit planes X_0 .. X_6 hold all n columns (the A operand, M = 128,
+// rows >= n zero) and grid.y = J picks the 64 columns 64 J .. 64 J + 63 of the
+// same planes as the B operand (N = 64): one CTA forms the 128 x 64 block
+// G[:, 64 J ..] (tensor memory holds seven accumulator groups d = p + q of 64
+// columns; two blocks would not fit, so each block's CTAs cut all columns).
+// Each group sums at most seven products below 2^14 a row, so a window of
+// four buffers (128 rows) keeps it an integer below 2^24 (exact in FP32);
+// after each window the groups are combined (weights 2^-8d) and added in
+// FP64, and the fixed scale 2^(e_i + e_j - 2058) is applied once at the end.
+// Rows of X arrive by TMA as two 16-row x n-column boxes (128-byte swizzle)
+// into two staging slots; all eight warps write 16-byte digit stores into two
+// operand buffers and signal an mbarrier; lane 0 of warp 3 (whose tensor-
+// memory quarter has nothing on or above the diagonal in either block) waits
+// for it, refills the staging slot and issues the buffer's 56 MMAs.
+// ---------------------------------------------------------------------------
+constexpr int kG8Rows = 32;                       // rows of X per operand buffer (K = 2 x 16)
+constexpr int kG8Window = 4;                      // buffers per exact accumulation window (128 rows)
+constexpr int kG8Plane = 128 * kG8Rows * 2;       // one digit plane, 8 KB
+constexpr int kG8Buf = kOzDigits * kG8Plane;      // 56 KB per buffer
+constexpr int kG8Box = 16 * 128 * 8;              // one 16-row x 128-column staging box, 16 KB
+constexpr int kG8Stage = 2 * kG8Box;              // 32 KB: the buffer's 32 rows
+constexpr size_t kG8Smem = 2 * (size_t)kG8Buf + 2 * (size_t)kG8Stage;  // 176 KB
+
+// Byte offset of element (row, k) in a K-major, no-swizzle operand tile with
+// K = 32 (4 core matrices of 128 bytes along K per 8-row group).
+__device__ __forceinline__ int kmaj32_off(int row, int k)
+{
+    return (row & 7) * 16 + (row >> 3) * 512 + (k & 7) * 2 + (k >> 3) * 128;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_gram_oz128(const __grid_constant__ CUtensorMap tm_x, int use_tma, const double *__restrict__ X, int64_t ldx,
+                 int64_t m, int n, const int *__restrict__ colexp_g, int64_t bufs_total, int64_t bufs_per_cta,
+                 double *__restrict__ Gpart, RxrStatus *st)
+{
+    if (rxr_failed_block(st)) return;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t ready[2];  // producers -> MMA thread: digits of a buffer written (256 arrivals)
+    __shared__ __align__(8) uint64_t done[2];   // MMA thread -> producers: a buffer's MMAs completed (commit)
+    __shared__ __align__(8) uint64_t tfree;     // producers -> MMA thread: a window's accumulators read (256)
+    __shared__ __align__(8) uint64_t full[2];   // TMA -> producers: a staging slot holds its 32 rows of X
+    __shared__ uint32_t tmem_base;
+    __shared__ int cex[128];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int J = blockIdx.y;
+    const bool mma_thread = (warp == 3 && lane == 0);
+
+    // digit buffers zeroed once (rows >= n stay zero); the staging slots are
+    // written by TMA only
+    for (int e = tid; e < (int)(2 * kG8Buf / 16); e += blockDim.x) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_shared();
+    if (tid < 128) {
+        cex[tid] = (tid < n) ? colexp_g[tid] : 0;
+        if (cex[tid] == 0x7FF) rxr_fail(st, RXR_ERR_NONFINITE, 0, -1);  // NaN or Inf in X
+    }
+    if (tid == 0) {
+        mbar_init(&ready[0], 256);
+        mbar_init(&ready[1], 256);
+        mbar_init(&done[0], 1);
+        mbar_init(&done[1], 1);
+        mbar_init(&tfree, 256);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int64_t b_begin = blockIdx.x * bufs_per_cta;
+    const int64_t b_end = min(bufs_total, b_begin + bufs_per_cta);
+    const int nbufs = (b_end > b_begin) ? (int)(b_end - b_begin) : 0;
+    // Waits are per thread and bounded; one that gives up records a timeout in
+    // the status and the thread carries on (every arrival still happens), so
+    // no thread is left waiting and the sums are not published.
+    bool ok = true;
+
+    // epilogue role: tensor-memory lane quarter q4 (rows 32 q4 .. of G), 32
+    // columns of the block per half; quarters with nothing on or above the
+    // diagonal skip the reads
+    const int q4 = warp & 3, half = (warp >> 2) & 1;
+    const bool skip_epi = (J == 0) ? (q4 >= 2 || (q4 == 1 && half == 0)) : (q4 == 3 && half == 0);
+    double acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0.0;
+
+    const int j = tid >> 1, hq = tid & 1;  // column of X and 16-row half of each buffer this thread converts
+    const int ej = cex[j];
+    const bool has_col = j < n;
+    const double *xcol = X + (int64_t)j * ldx;
+    const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 512);
+    constexpr uint32_t idesc = idesc_f16(128, 64);
+    unsigned char *stage = smem + 2 * kG8Buf;  // [2 slots][2 boxes of 16 rows x n columns]
+    const uint32_t box_bytes = (uint32_t)(16 * n * 8);
+    auto issue_load = [&](int it_load) {
+        unsigned char *slot = stage + (it_load & 1) * kG8Stage;
+        mbar_arrive_expect_tx(&full[it_load & 1], 2 * box_bytes);
+        const int r0 = (int)((b_begin + it_load) * kG8Rows);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) tma_load_2d(slot + q * kG8Box, &tm_x, r0 + 16 * q, 0, &full[it_load & 1]);
+    };
+    if (use_tma && mma_thread) {
+        if (nbufs > 0) issue_load(0);
+        if (nbufs > 1) issue_load(1);
+    }
+    for (int it = 0; it < nbufs; ++it) {
+        const int64_t b = b_begin + it;
+        const int buf = it & 1;
+        unsigned char *base = smem + buf * kG8Buf;
+        if (use_tma) ok &= mbar_wait_bounded(&full[buf], (it >> 1) & 1, st);
+        // the MMAs issued two buffers ago read this digit buffer
+        if (it >= 2) ok &= mbar_wait_bounded(&done[buf], ((it - 2) >> 1) & 1, st);
+        if (has_col) {
+            const unsigned char *box = stage + buf * kG8Stage + hq * kG8Box + j * 128;
+#pragma unroll
+            for (int g8 = 0; g8 < 2; ++g8) {
+                // eight rows of column j: swizzled 16-byte chunks 4 g8 .. 4 g8 + 3 of the box
+                double v[8];
+                if (use_tma) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const double2 w = *reinterpret_cast<const double2 *>(box + (((4 * g8 + c) ^ (j & 7)) << 4));
+                        v[2 * c] = w.x;
+                        v[2 * c + 1] = w.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int64_t r = b * kG8Rows + 16 * hq + 8 * g8 + i;
+                        v[i] = (r < m) ? xcol[r] : 0.0;
+                    }
+                }
+                unsigned long long U[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) U[r] = digits_offset((unsigned long long)__double_as_longlong(v[r]), ej);
+#pragma unroll
+                for (int q = 0; q < kOzDigits; ++q)
+                    *reinterpret_cast<uint4 *>(base + q * kG8Plane + kmaj32_off(j, 16 * hq + 8 * g8)) =
+                        pack_plane_f16(U, q);
+            }
+        }
+        fence_proxy_async_shared();
+        mbar_arrive(&ready[buf]);
+        if ((it % kG8Window) == 0 && it > 0) {
+            // the previous window is complete once its last buffer's MMAs
+            // are: read its sums into FP32 pairs, release tensor memory,
+            // then add them in FP64
+            ok &= mbar_wait_bounded(&done[buf ^ 1], ((it - 1) >> 1) & 1, st);
+            tc_fence_after();
+            float hi[32], lo[32];
+            if (!skip_epi) gram64_read(tmem, q4, half, hi, lo);
+            tc_fence_before();
+            mbar_arrive(&tfree);
+            if (!skip_epi) gram64_accumulate(hi, lo, acc);
+        }
+        if (mma_thread) {
+            // every producer's digits of this buffer (and, at a window start,
+            // every read of the last window's sums) are in: issue its MMAs
+            const bool first_of_window = (it % kG8Window) == 0;
+            ok &= mbar_wait_bounded(&ready[buf], (it >> 1) & 1, st);
+            // every producer has read staging slot `buf`: refill it
+            if (use_tma && it + 2 < nbufs) issue_load(it + 2);
+            if (first_of_window && it > 0) ok &= mbar_wait_bounded(&tfree, ((it / kG8Window) - 1) & 1, st);
+            tc_fence_after();
+            const uint64_t dbuf = desc0 + (uint64_t)(buf * (kG8Buf >> 4));
+#pragma unroll
+            for (int kk = 0; kk < kG8Rows / 16; ++kk)
+#pragma unroll
+                for (int p = 0; p < kOzDigits; ++p)
+#pragma unroll
+                    for (int q = 0; p + q < kOzDigits; ++q) {
+                        // p = 0 lists every group first: it starts the window's sums
+                        const uint32_t acc_on = (!first_of_window || kk > 0 || p > 0) ? 1u : 0u;
+                        tc_mma(tmem + (uint32_t)((p + q) * 64), dbuf + (uint64_t)((p * kG8Plane + kk * 256) >> 4),
+                               dbuf + (uint64_t)((q * kG8Plane + J * 4096 + kk * 256) >> 4), idesc, acc_on);
+                    }
+            tc_commit(&done[buf]);
+        }
+    }
+    // last window
+    if (nbufs > 0) {
+        ok &= mbar_wait_bounded(&done[(nbufs - 1) & 1], ((nbufs - 1) >> 1) & 1, st);
+        tc_fence_after();
+        float hi[32], lo[32];
+        if (!skip_epi) {
+            gram64_read(tmem, q4, half, hi, lo);
+            gram64_accumulate(hi, lo, acc);
+        }
+    }
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_before();
+    const int gi = 32 * q4 + lane;
+    if (ok && !skip_epi && gi < n) {
+        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+        const int ei = cex[gi];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int gj = 64 * J + 32 * half + t;
+            if (gj < n && gi <= gj) {
+                const int e = ei + cex[gj] - 2058;
+                out[gi + (int64_t)gj * n] = (ei > 0 && cex[gj] > 0) ? ldexp(acc[t], e) : 0.0;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
 // FP64-grade product Q = X T on the tensor cores for n <= 64 (the last
 // CholeskyQR pass's apply, T = R_P^{-1}), in place.  A CTA walks 128-row
 // tiles of X: one TMA load per tile into shared memory (the next tile's load
@@ -2360,9 +2574,16 @@ static int64_t ozaki_chunks(int64_t m, int64_t n, int sms)
     return balanced_chunks(ozaki_blocks((int)n), sms, cdiv64(m, kOzWin));
 }
 
+// row chunks of k_gram_oz128 (grid.y = the two 64-column blocks, one CTA per SM)
+static int64_t oz128_chunks(int64_t m, int sms)
+{
+    return balanced_chunks(2, sms, cdiv64(m, kG8Rows));
+}
+
 static size_t split_partial_bytes(int64_t m, int64_t n, int sms)
 {
-    const int64_t gx = std::max<int64_t>(std::min<int64_t>(sms, cdiv64(m, kGsWin)), ozaki_chunks(m, n, sms));
+    int64_t gx = std::max<int64_t>(std::min<int64_t>(sms, cdiv64(m, kGsWin)), ozaki_chunks(m, n, sms));
+    if (n > 64 && n <= 128) gx = std::max<int64_t>(gx, oz128_chunks(m, sms));
     return ((size_t)gx * n * n * sizeof(double) + 255) & ~(size_t)255;
 }
 
@@ -2862,6 +3083,27 @@ int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, b
                                                              p.n, p.status);
         return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
     }
+    if (p.n <= 128) {
+        // 64 < n <= 128: the pipelined Gram over the columns' global exponents
+        int *cx = split_colexp(p);
+        if (cudaMemsetAsync(cx, 0, p.n * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+        const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
+        k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(X, ldx, p.m, cx, p.status);
+        const int64_t total = cdiv64(p.m, kG8Rows);
+        int64_t gx = oz128_chunks(p.m, p.sms);
+        const int64_t bpc = cdiv64(total, gx);
+        gx = cdiv64(total, bpc);
+        double *parts = reinterpret_cast<double *>(p.split);
+        CUtensorMap mx;
+        const int use_tma = encode_tile_map(&mx, X, p.m, p.n, ldx, 16, (int)p.n, true) ? 1 : 0;
+        k_gram_oz128<<<dim3((unsigned)gx, 2), 256, kG8Smem, st>>>(mx, use_tma, X, ldx, p.m, (int)p.n, cx, total, bpc,
+                                                                  parts, p.status);
+        if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+        const int64_t nn = p.n * p.n;
+        k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(parts, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G,
+                                                             p.n, p.status);
+        return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
+    }
     const int64_t win_total = cdiv64(p.m, kOzWin);
     int64_t gx = ozaki_chunks(p.m, p.n, p.sms);
     const int64_t wpc = cdiv64(win_total, gx);
@@ -2892,6 +3134,8 @@ cudaError_t set_split_smem()
                                  (int)fu_smem_bytes(kFuMaxN));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gram_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kG6Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gram_oz128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kG8Smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_subst_fused128, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)f2_smem_bytes(kF2MaxN));

@@ -87,7 +87,8 @@ def test_split_matches_fp64_factorisation(h):
 
 
 @pytest.mark.parametrize("m,n,kappa", [(1, 1, 1.0), (700, 8, 1e2), (5000, 64, 1e6), (3000, 100, 1e12), (2100, 128, 1e3),
-                                       (129, 65, 1e15), (700, 200, 1e8), (600, 512, 1e3)])
+                                       (129, 65, 1e15), (700, 200, 1e8), (600, 512, 1e3), (200003, 128, 1e8),
+                                       (262176, 120, 1e12), (76 * 32 * 9 + 64, 96, 1e4)])
 def test_ozaki_gram_is_fp64_grade(h, m, n, kappa):
     # exact 7-digit splitting: G = X^T X to FP64 accuracy, entrywise within the
     # FP64 Gram bound plus the digit truncation 2^-54 * colmax_j * colmax_l * m
@@ -148,7 +149,7 @@ def test_fused_substitution_first_block_is_plain_substitution(h):
     assert np.array_equal(to_host(Xs)[:, :16], to_host(Xf)[:, :16])
 
 
-@pytest.mark.parametrize("m,n", [(64 * 152 * 5 + 13, 64), (4100, 33), (300, 1)])
+@pytest.mark.parametrize("m,n", [(64 * 152 * 5 + 13, 64), (4100, 33), (300, 1), (32 * 152 * 9 + 6, 128), (70001, 97)])
 def test_ozaki_gram_column_scales(h, m, n):
     # columns scaled across the whole FP64 range, one column zero: the Gram must
     # stay FP64-grade column-normwise (the digit scale of each column is its own
