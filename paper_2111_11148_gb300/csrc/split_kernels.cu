@@ -1824,21 +1824,25 @@ __global__ void __launch_bounds__(kG6Producers, 1)
 // ---------------------------------------------------------------------------
 // FP64-grade Gram G = X^T X for 64 < n <= 128 on the tensor cores, pipelined
 // like k_gram_oz64.  Column j of X is cut into seven 8-bit digits relative to
-// 2^(e_j + 1), e_j its largest exponent over all m rows.  For each 32-row
-// buffer the digit planes X_0 .. X_6 hold all n columns (the A operand, M = 128,
-// rows >= n zero) and grid.y = J picks the 64 columns 64 J .. 64 J + 63 of the
-// same planes as the B operand (N = 64): one CTA forms the 128 x 64 block
-// G[:, 64 J ..] (tensor memory holds seven accumulator groups d = p + q of 64
-// columns; two blocks would not fit, so each block's CTAs cut all columns).
+// 2^(e_j + 1), e_j its largest exponent over all m rows.  Two kinds of CTA
+// share the grid (tensor memory holds seven accumulator groups d = p + q of 64
+// columns, so one CTA forms one 128 x 64 block):
+//   J = 1 (the first g1 CTAs): the digit planes X_0 .. X_6 of a 32-row buffer
+//     hold all n columns (the A operand, M = 128, rows >= n zero) and columns
+//     64 .. n - 1 of the same planes are the B operand (N = 64): the blocks
+//     G[0:64, 64:n] and G[64:n, 64:n];
+//   J = 0 (the other g0 CTAs): only columns 0 .. 63 are cut (A rows 64 .. 127
+//     stay zero) for G[0:64, 0:64], half the digit work per row, so these
+//     CTAs take proportionally more rows (g0 / g1 ~ their cost ratio).
 // Each group sums at most seven products below 2^14 a row, so a window of
 // four buffers (128 rows) keeps it an integer below 2^24 (exact in FP32);
 // after each window the groups are combined (weights 2^-8d) and added in
 // FP64, and the fixed scale 2^(e_i + e_j - 2058) is applied once at the end.
 // Rows of X arrive by TMA as two 16-row x n-column boxes (128-byte swizzle)
-// into two staging slots; all eight warps write 16-byte digit stores into two
-// operand buffers and signal an mbarrier; lane 0 of warp 3 (whose tensor-
-// memory quarter has nothing on or above the diagonal in either block) waits
-// for it, refills the staging slot and issues the buffer's 56 MMAs.
+// into two staging slots; eight producer warps write 16-byte digit stores into
+// two operand buffers and signal an mbarrier; lane 0 of a ninth warp waits for
+// it, refills the staging slot and issues the buffer's 56 MMAs (so no producer
+// waits while the MMAs are issued).
 // ---------------------------------------------------------------------------
 constexpr int kG8Rows = 32;                       // rows of X per operand buffer (K = 2 x 16)
 constexpr int kG8Window = 4;                      // buffers per exact accumulation window (128 rows)
@@ -1847,6 +1851,8 @@ constexpr int kG8Buf = kOzDigits * kG8Plane;      // 56 KB per buffer
 constexpr int kG8Box = 16 * 128 * 8;              // one 16-row x 128-column staging box, 16 KB
 constexpr int kG8Stage = 2 * kG8Box;              // 32 KB: the buffer's 32 rows
 constexpr size_t kG8Smem = 2 * (size_t)kG8Buf + 2 * (size_t)kG8Stage;  // 176 KB
+constexpr int kG8Producers = 256;                 // warps 0-7; warp 8 issues the copies and MMAs
+constexpr int kG8Threads = kG8Producers + 32;     // nine warps: 168 registers a thread (an SMSP holds three)
 
 // Byte offset of element (row, k) in a K-major, no-swizzle operand tile with
 // K = 32 (4 core matrices of 128 bytes along K per 8-row group).
@@ -1855,10 +1861,11 @@ __device__ __forceinline__ int kmaj32_off(int row, int k)
     return (row & 7) * 16 + (row >> 3) * 512 + (k & 7) * 2 + (k >> 3) * 128;
 }
 
-__global__ void __launch_bounds__(256, 1)
-    k_gram_oz128(const __grid_constant__ CUtensorMap tm_x, int use_tma, const double *__restrict__ X, int64_t ldx,
-                 int64_t m, int n, const int *__restrict__ colexp_g, int64_t bufs_total, int64_t bufs_per_cta,
-                 double *__restrict__ Gpart, RxrStatus *st)
+__global__ void __launch_bounds__(kG8Threads, 1)
+    k_gram_oz128(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_h, int use_tma,
+                 const double *__restrict__ X, int64_t ldx, int64_t m, int n, const int *__restrict__ colexp_g,
+                 int64_t bufs_total, int g1, int64_t bpc1, int g0, int64_t bpc0, double *__restrict__ Gpart,
+                 RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1869,8 +1876,11 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ uint32_t tmem_base;
     __shared__ int cex[128];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int J = blockIdx.y;
-    const bool mma_thread = (warp == 3 && lane == 0);
+    const int J = ((int)blockIdx.x < g1) ? 1 : 0;
+    const int slot = J ? (int)blockIdx.x : (int)blockIdx.x - g1;  // partial-sum slot and row chunk
+    const int ncut = J ? n : 64;                                  // columns cut into digits
+    const bool producer = tid < kG8Producers;
+    const bool mma_thread = tid == kG8Producers;
 
     // digit buffers zeroed once (rows >= n stay zero); the staging slots are
     // written by TMA only
@@ -1895,8 +1905,9 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const int64_t b_begin = blockIdx.x * bufs_per_cta;
-    const int64_t b_end = min(bufs_total, b_begin + bufs_per_cta);
+    const int64_t bpc = J ? bpc1 : bpc0;
+    const int64_t b_begin = slot * bpc;
+    const int64_t b_end = min(bufs_total, b_begin + bpc);
     const int nbufs = (b_end > b_begin) ? (int)(b_end - b_begin) : 0;
     // Waits are per thread and bounded; one that gives up records a timeout in
     // the status and the thread carries on (every arrival still happens), so
@@ -1907,31 +1918,37 @@ __global__ void __launch_bounds__(256, 1)
     // columns of the block per half; quarters with nothing on or above the
     // diagonal skip the reads
     const int q4 = warp & 3, half = (warp >> 2) & 1;
-    const bool skip_epi = (J == 0) ? (q4 >= 2 || (q4 == 1 && half == 0)) : (q4 == 3 && half == 0);
+    const bool skip_epi =
+        !producer || ((J == 0) ? (q4 >= 2 || (q4 == 1 && half == 0)) : (q4 == 3 && half == 0));
     double acc[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = 0.0;
 
-    const int j = tid >> 1, hq = tid & 1;  // column of X and 16-row half of each buffer this thread converts
-    const int ej = cex[j];
-    const bool has_col = j < n;
+    // this thread's column of X and its rows of each buffer: J = 1, 16-row half
+    // hq (both 8-row groups); J = 0, the 8-row group g8 of half hq
+    const int j = J ? (tid >> 1) : (tid >> 2);
+    const int hq = J ? (tid & 1) : ((tid >> 1) & 1);
+    const int g8_lo = J ? 0 : (tid & 1), g8_hi = J ? 2 : (tid & 1) + 1;
+    const bool has_col = producer && j < ncut;
+    const int ej = has_col ? cex[j] : 0;
     const double *xcol = X + (int64_t)j * ldx;
     const uint64_t desc0 = smem_desc(smem_u32(smem), 128, 512);
     constexpr uint32_t idesc = idesc_f16(128, 64);
     unsigned char *stage = smem + 2 * kG8Buf;  // [2 slots][2 boxes of 16 rows x n columns]
-    const uint32_t box_bytes = (uint32_t)(16 * n * 8);
+    const uint32_t box_bytes = (uint32_t)(16 * ncut * 8);
+    const CUtensorMap *tmap = J ? &tm_x : &tm_h;
     auto issue_load = [&](int it_load) {
-        unsigned char *slot = stage + (it_load & 1) * kG8Stage;
+        unsigned char *sl = stage + (it_load & 1) * kG8Stage;
         mbar_arrive_expect_tx(&full[it_load & 1], 2 * box_bytes);
         const int r0 = (int)((b_begin + it_load) * kG8Rows);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) tma_load_2d(slot + q * kG8Box, &tm_x, r0 + 16 * q, 0, &full[it_load & 1]);
+        for (int q = 0; q < 2; ++q) tma_load_2d(sl + q * kG8Box, tmap, r0 + 16 * q, 0, &full[it_load & 1]);
     };
     if (use_tma && mma_thread) {
         if (nbufs > 0) issue_load(0);
         if (nbufs > 1) issue_load(1);
     }
-    for (int it = 0; it < nbufs; ++it) {
+    for (int it = 0; producer && it < nbufs; ++it) {
         const int64_t b = b_begin + it;
         const int buf = it & 1;
         unsigned char *base = smem + buf * kG8Buf;
@@ -1940,8 +1957,7 @@ __global__ void __launch_bounds__(256, 1)
         if (it >= 2) ok &= mbar_wait_bounded(&done[buf], ((it - 2) >> 1) & 1, st);
         if (has_col) {
             const unsigned char *box = stage + buf * kG8Stage + hq * kG8Box + j * 128;
-#pragma unroll
-            for (int g8 = 0; g8 < 2; ++g8) {
+            for (int g8 = g8_lo; g8 < g8_hi; ++g8) {
                 // eight rows of column j: swizzled 16-byte chunks 4 g8 .. 4 g8 + 3 of the box
                 double v[8];
                 if (use_tma) {
@@ -1981,32 +1997,33 @@ __global__ void __launch_bounds__(256, 1)
             mbar_arrive(&tfree);
             if (!skip_epi) gram64_accumulate(hi, lo, acc);
         }
-        if (mma_thread) {
-            // every producer's digits of this buffer (and, at a window start,
-            // every read of the last window's sums) are in: issue its MMAs
-            const bool first_of_window = (it % kG8Window) == 0;
-            ok &= mbar_wait_bounded(&ready[buf], (it >> 1) & 1, st);
-            // every producer has read staging slot `buf`: refill it
-            if (use_tma && it + 2 < nbufs) issue_load(it + 2);
-            if (first_of_window && it > 0) ok &= mbar_wait_bounded(&tfree, ((it / kG8Window) - 1) & 1, st);
-            tc_fence_after();
-            const uint64_t dbuf = desc0 + (uint64_t)(buf * (kG8Buf >> 4));
+    }
+    for (int it = 0; mma_thread && it < nbufs; ++it) {
+        const int buf = it & 1;
+        // every producer's digits of this buffer (and, at a window start,
+        // every read of the last window's sums) are in: issue its MMAs
+        const bool first_of_window = (it % kG8Window) == 0;
+        ok &= mbar_wait_bounded(&ready[buf], (it >> 1) & 1, st);
+        // every producer has read staging slot `buf`: refill it
+        if (use_tma && it + 2 < nbufs) issue_load(it + 2);
+        if (first_of_window && it > 0) ok &= mbar_wait_bounded(&tfree, ((it / kG8Window) - 1) & 1, st);
+        tc_fence_after();
+        const uint64_t dbuf = desc0 + (uint64_t)(buf * (kG8Buf >> 4));
 #pragma unroll
-            for (int kk = 0; kk < kG8Rows / 16; ++kk)
+        for (int kk = 0; kk < kG8Rows / 16; ++kk)
 #pragma unroll
-                for (int p = 0; p < kOzDigits; ++p)
+            for (int p = 0; p < kOzDigits; ++p)
 #pragma unroll
-                    for (int q = 0; p + q < kOzDigits; ++q) {
-                        // p = 0 lists every group first: it starts the window's sums
-                        const uint32_t acc_on = (!first_of_window || kk > 0 || p > 0) ? 1u : 0u;
-                        tc_mma(tmem + (uint32_t)((p + q) * 64), dbuf + (uint64_t)((p * kG8Plane + kk * 256) >> 4),
-                               dbuf + (uint64_t)((q * kG8Plane + J * 4096 + kk * 256) >> 4), idesc, acc_on);
-                    }
-            tc_commit(&done[buf]);
-        }
+                for (int q = 0; p + q < kOzDigits; ++q) {
+                    // p = 0 lists every group first: it starts the window's sums
+                    const uint32_t acc_on = (!first_of_window || kk > 0 || p > 0) ? 1u : 0u;
+                    tc_mma(tmem + (uint32_t)((p + q) * 64), dbuf + (uint64_t)((p * kG8Plane + kk * 256) >> 4),
+                           dbuf + (uint64_t)((q * kG8Plane + J * 4096 + kk * 256) >> 4), idesc, acc_on);
+                }
+        tc_commit(&done[buf]);
     }
     // last window
-    if (nbufs > 0) {
+    if (producer && nbufs > 0) {
         ok &= mbar_wait_bounded(&done[(nbufs - 1) & 1], ((nbufs - 1) >> 1) & 1, st);
         tc_fence_after();
         float hi[32], lo[32];
@@ -2018,8 +2035,13 @@ __global__ void __launch_bounds__(256, 1)
     ok = __syncthreads_and(ok) != 0;
     tc_fence_before();
     const int gi = 32 * q4 + lane;
+    if (ok && J == 1 && slot >= g0) {
+        // no J = 0 CTA has this slot: its block G[0:64, 0:64] adds zero
+        double *out = Gpart + (int64_t)slot * n * n;
+        for (int e = tid; e < 64 * 64; e += blockDim.x) out[(e & 63) + (int64_t)(e >> 6) * n] = 0.0;
+    }
     if (ok && !skip_epi && gi < n) {
-        double *out = Gpart + (int64_t)blockIdx.x * n * n;
+        double *out = Gpart + (int64_t)slot * n * n;
         const int ei = cex[gi];
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
@@ -2574,10 +2596,31 @@ static int64_t ozaki_chunks(int64_t m, int64_t n, int sms)
     return balanced_chunks(ozaki_blocks((int)n), sms, cdiv64(m, kOzWin));
 }
 
-// row chunks of k_gram_oz128 (grid.y = the two 64-column blocks, one CTA per SM)
+// Row chunks of k_gram_oz128, one CTA per SM: g1 chunks for the J = 1 CTAs and
+// g0 for the J = 0 ones, which cut half the columns and so take more rows each
+// (kG8HalfCost: their time per buffer relative to a J = 1 CTA's).
+constexpr double kG8HalfCost = 1.0;
+struct Oz128Grid {
+    int g1, g0;
+    int64_t bpc1, bpc0;
+};
+static Oz128Grid oz128_grid(int64_t m, int sms)
+{
+    const int64_t total = cdiv64(m, kG8Rows);
+    int64_t g1 = std::max<int64_t>(1, (int64_t)(sms / (1.0 + kG8HalfCost) + 0.5));
+    int64_t g0 = std::max<int64_t>(1, sms - g1);
+    g1 = std::min(g1, total);
+    g0 = std::min(g0, total);
+    Oz128Grid g;
+    g.bpc1 = cdiv64(total, g1);
+    g.g1 = (int)cdiv64(total, g.bpc1);
+    g.bpc0 = cdiv64(total, std::min<int64_t>(g0, g.g1));  // every J = 0 slot has a J = 1 CTA
+    g.g0 = (int)cdiv64(total, g.bpc0);
+    return g;
+}
 static int64_t oz128_chunks(int64_t m, int sms)
 {
-    return balanced_chunks(2, sms, cdiv64(m, kG8Rows));
+    return oz128_grid(m, sms).g1;
 }
 
 static size_t split_partial_bytes(int64_t m, int64_t n, int sms)
@@ -3090,14 +3133,17 @@ int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, b
         const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
         k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(X, ldx, p.m, cx, p.status);
         const int64_t total = cdiv64(p.m, kG8Rows);
-        int64_t gx = oz128_chunks(p.m, p.sms);
-        const int64_t bpc = cdiv64(total, gx);
-        gx = cdiv64(total, bpc);
+        const Oz128Grid gg = oz128_grid(p.m, p.sms);
+        const int64_t gx = gg.g1;  // partial-sum slots
         double *parts = reinterpret_cast<double *>(p.split);
-        CUtensorMap mx;
-        const int use_tma = encode_tile_map(&mx, X, p.m, p.n, ldx, 16, (int)p.n, true) ? 1 : 0;
-        k_gram_oz128<<<dim3((unsigned)gx, 2), 256, kG8Smem, st>>>(mx, use_tma, X, ldx, p.m, (int)p.n, cx, total, bpc,
-                                                                  parts, p.status);
+        CUtensorMap mx, mh;
+        const int use_tma = (encode_tile_map(&mx, X, p.m, p.n, ldx, 16, (int)p.n, true) &&
+                             encode_tile_map(&mh, X, p.m, p.n, ldx, 16, 64, true))
+                                ? 1
+                                : 0;
+        k_gram_oz128<<<(unsigned)(gg.g1 + gg.g0), kG8Threads, kG8Smem, st>>>(mx, mh, use_tma, X, ldx, p.m, (int)p.n, cx,
+                                                                       total, gg.g1, gg.bpc1, gg.g0, gg.bpc0, parts,
+                                                                       p.status);
         if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
         const int64_t nn = p.n * p.n;
         k_reduce_parts<<<(int)cdiv64(nn, 256), 256, 0, st>>>(parts, (int)gx, nn, (int)p.n, (int)p.n, 1.0, 1, p.G,
