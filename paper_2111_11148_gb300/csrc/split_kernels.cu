@@ -1687,7 +1687,11 @@ __global__ void __launch_bounds__(kG6Producers, 1)
     for (int t = 0; t < 32; ++t) acc[t] = 0.0;
 
     if (producer) {
-        const int j = tid >> 2, rq = tid & 3;  // column of X and 16-row quarter of each buffer this thread converts
+        // column of X and 16-row quarter of each buffer this thread converts; the
+        // eight lanes of each quarter-warp take eight consecutive columns, so
+        // their 16-byte digit stores (and swizzled staging reads) fall in
+        // distinct banks
+        const int j = 8 * warp + (lane & 7), rq = lane >> 3;
         const int ej = cex[j];
         const bool has_col = j < n;
         const double *xcol = X + (int64_t)j * ldx;
@@ -1925,10 +1929,12 @@ __global__ void __launch_bounds__(kG8Threads, 1)
     for (int t = 0; t < 32; ++t) acc[t] = 0.0;
 
     // this thread's column of X and its rows of each buffer: J = 1, 16-row half
-    // hq (both 8-row groups); J = 0, the 8-row group g8 of half hq
-    const int j = J ? (tid >> 1) : (tid >> 2);
-    const int hq = J ? (tid & 1) : ((tid >> 1) & 1);
-    const int g8_lo = J ? 0 : (tid & 1), g8_hi = J ? 2 : (tid & 1) + 1;
+    // hq (both 8-row groups); J = 0, the 8-row group g8 of half hq.  The eight
+    // lanes of each quarter-warp take eight consecutive columns, so their
+    // 16-byte digit stores (and swizzled staging reads) fall in distinct banks
+    const int j = J ? (16 * warp + (lane & 15)) : (8 * warp + (lane & 7));
+    const int hq = J ? (lane >> 4) : ((lane >> 3) & 1);
+    const int g8_lo = J ? 0 : (lane >> 4), g8_hi = J ? 2 : (lane >> 4) + 1;
     const bool has_col = producer && j < ncut;
     const int ej = has_col ? cex[j] : 0;
     const double *xcol = X + (int64_t)j * ldx;
@@ -2457,9 +2463,10 @@ __global__ void __launch_bounds__(512, 1)
 
     // roles: warps 0-7 Omega' -> sketch rows 4 kq .. + 3, data rows 8 warp .. + 7;
     // warps 8-15 A digits -> column j, rows 16 rq .. + 15 of each 64-row tile
+    // (the eight lanes of a quarter-warp take eight consecutive columns: their
+    // 16-byte digit stores fall in distinct banks)
     const bool gauss = warp < 8;
-    const int dt = tid - 256;
-    const int j = gauss ? 0 : dt >> 2, rq = dt & 3;
+    const int j = gauss ? 0 : 8 * (warp - 8) + (lane & 7), rq = lane >> 3;
     const int kq = lane;
     const bool has_col = !gauss && j < nw;
     const int ej = cex[j];
