@@ -139,11 +139,11 @@ def hbm_peak() -> tuple[float, str]:
 
 
 def oracle_rows(n: int, parallel: bool) -> int:
-    """Row count of an oracle sample: about 10-20 s of single-core work for the
-    serial build (the oracle's cost per row grows as n^2), and 2x that for the
-    OpenMP build on every host core."""
+    """Row count of an oracle sample: about 10 s of work for the serial build on
+    one core (the oracle's cost per row grows as n^2) and for the OpenMP build
+    on the box's 16 host cores (16x the rows)."""
     base = int(os.environ.get("RXR_BENCH_ORACLE_ROWS", 2**19 * 64 * 64 // (n * n)))
-    return max(n, base * (2 if parallel else 1))
+    return max(n, base * (16 if parallel else 1))
 
 
 def run_oracle_sample(A_sample: np.ndarray, variant: str, parallel: bool = False):
@@ -176,7 +176,7 @@ def cpu_baseline(A_np: np.ndarray, variant: str) -> dict:
         t = run_oracle_sample(np.asfortranarray(A_np[:rows]), variant, parallel)
         out[parallel] = {"value": b_alg(rows, N, PASSES) / t / 1e9, "unit": "GB/s",
                          "cores": oracle.threads(parallel), "kind": "oracle",
-                         "sample": f"first {rows} of {A_np.shape[0]} rows of the same A, one full rxr_cholqr of the "
+                         "sample": f"first {rows} of {M} rows of the same A, one full rxr_cholqr of the "
                                    f"C oracle ({'OpenMP build, every host core' if parallel else 'serial build'}), "
                                    f"{t:.2f} s"}
     line = dict(out[True])
@@ -188,6 +188,39 @@ def make_input():
     from paper_2111_11148_gb300.inputs import usv_matrix
 
     return usv_matrix(M, N, KAPPA, seed=SEED)
+
+
+def make_input_device(dev):
+    """The workload's A = U diag(sigma) V^T built on the GPU, column-major: the
+    recipe of inputs.usv_matrix (sigma and V from inputs.usv_factors; U the
+    Householder Q factor of a seeded N(0,1) m x n matrix) with U drawn by torch's
+    CUDA generator and orthonormalised by torch.linalg.qr on the device: the same
+    distribution, other bytes than the host generator's.  Building the 8.6 GB
+    input on the host (multithreaded LAPACK on the CPU) took about 70 s and left
+    the host link reading pinned memory at 24-60 GB/s instead of 200 GB/s for
+    the rest of the process."""
+    import torch
+
+    from paper_2111_11148_gb300 import rxr
+    from paper_2111_11148_gb300.inputs import usv_factors
+
+    sigma, V = usv_factors(N, KAPPA, SEED)
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED)
+    G = torch.randn((M, N), dtype=torch.float64, device=dev, generator=g)
+    U, _ = torch.linalg.qr(G)
+    del G
+    A = (U * torch.from_numpy(sigma).to(dev)) @ torch.from_numpy(V.T.copy()).to(dev)
+    del U
+    out = rxr.colmajor(A)
+    del A
+    torch.cuda.synchronize(dev)
+    return out
+
+
+def host_rows(A_dev, rows: int) -> np.ndarray:
+    """The first rows of a column-major device matrix as a Fortran-ordered array."""
+    return A_dev[:rows].t().contiguous().cpu().numpy().T
 
 
 def construction_r(n: int, kappa: float, seed: int) -> np.ndarray:
@@ -593,9 +626,8 @@ def measure_config(h, args, dev, stream, peak_fp64, world, dist, main_clocks: bo
     from paper_2111_11148_gb300 import rxr
 
     t0 = time.perf_counter()
-    A_np = make_input()
+    A = make_input_device(dev)
     gen_s = time.perf_counter() - t0
-    A = rxr.colmajor(torch.from_numpy(A_np).to(dev))
     Q = rxr.empty_colmajor(M, N, device=dev)
     R = rxr.empty_colmajor(N, N, device=dev)
     R_ref = construction_r(N, KAPPA, SEED) if args.variant.split("-")[0] in ("qr", "lu", "none", "shifted") else None
@@ -613,14 +645,15 @@ def measure_config(h, args, dev, stream, peak_fp64, world, dist, main_clocks: bo
             # the host-buffer leg right after the device-resident one, before
             # the comparison paths (the host link measured slower after the
             # FP64 path's long run in the same process)
-            e2e = e2e_leg(h, A_np, args, world)
+            e2e = e2e_leg(h, args, world, A)
     ms = max_over_ranks(paths[args.prec]["ms"], dist, dev)
     out = {"ms": ms, "value": job_value(ms, world), "paths": paths, "generation_s": gen_s}
     if extras:
         out["preconditioner"] = preconditioner_conds(h, A, Q, args, args.prec)
         out["e2e"] = e2e
         if world == 1 and not args.no_cpu_baseline and dist is None:
-            out["cpu_baseline"] = cpu_baseline(A_np, args.variant)
+            rows = min(M, max(oracle_rows(N, True), oracle_rows(N, False)))
+            out["cpu_baseline"] = cpu_baseline(host_rows(A, rows), args.variant)
     del A, Q, R
     torch.cuda.empty_cache()
     return out
@@ -866,21 +899,20 @@ def roofline_entry(prec, stages, peak_fp64):
                          "(MEASURED_PEAKS.json has no FP64 figure)"}
 
 
-def e2e_leg(h, A_np, args, world):
+def e2e_leg(h, args, world, A_dev):
     """Same metric through rxr_cholqr_host: pinned host A in, pinned host Q, R out,
     host<->device copies inside the timed region."""
     import torch
 
     # pinned column-major buffers (the transpose of a pinned row-major tensor),
-    # allocated at the start of the process (pinned buffers allocated after the
-    # input generation's many large host allocations measured host->device
-    # copies at 24-60 GB/s instead of 200); A is copied in outside the timed calls
+    # allocated at the start of the process
     tA, tQ = _PINNED.get("A"), _PINNED.get("Q")
     if tA is None or tA.numel() < M * N:
         tA = torch.empty(M * N, dtype=torch.float64).pin_memory()
         tQ = torch.empty(M * N, dtype=torch.float64).pin_memory()
     hA = tA[:M * N].view(N, M).numpy().T
-    hA[...] = A_np
+    tA[:M * N].view(N, M).copy_(A_dev.t())  # the resident A's bytes, outside the timed calls
+    torch.cuda.synchronize()
     hQ = tQ[:M * N].view(N, M).numpy().T
     hR = torch.empty((N, N), dtype=torch.float64).pin_memory().numpy().T
     for _ in range(2):
