@@ -455,16 +455,17 @@ int enqueue_sketch(const Plan &p, const double *A, int64_t lda, uint64_t seed, c
 // Split-path substitution X = B R^{-1}: up to n = 64 one fused pass (FP64
 // diagonal blocks and tensor-core trailing updates on tiles held in shared
 // memory); wider panels take the column-blocked form, one launch per block.
-// colexp_out (n <= 64, nullable): also record the column exponents of X for
+// colexp_out (n <= 128, nullable): also record the column exponents of X for
 // the FP64-grade Gram that follows.
 int split_subst(const Plan &p, const double *src, int64_t lds, const double *R, double *dst, int64_t ldd,
                 cudaStream_t st, int *colexp_out = nullptr)
 {
-    if (p.n <= 64) {
-        if (colexp_out && cudaMemsetAsync(colexp_out, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
-        return fused_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, colexp_out, st);
-    }
-    if (p.n <= 128) return fused128_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
+    if (colexp_out && p.n <= 128 &&
+        cudaMemsetAsync(colexp_out, 0, (p.n <= 64 ? 64 : p.n) * sizeof(int), st) != cudaSuccess)
+        return RXR_ERR_CUDA;
+    if (p.n <= 64) return fused_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, colexp_out, st);
+    if (p.n <= 128)
+        return fused128_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st, nullptr, colexp_out);
     return blocked_subst_enqueue(const_cast<Plan &>(p), src, lds, R, p.n, dst, ldd, st);
 }
 
@@ -585,16 +586,16 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         // the first Gram on the tensor cores: FP64-grade stacked digits for
         // n <= 64, BF16x3 for 64 < n <= 128, FP64-grade 128 x 64 blocks above
         if (p.prec == RXR_SPLIT_BF16 && variant != RXR_NONE) {
-            // n <= 64: the substitution records X's column exponents for the
-            // stacked-digit Gram that follows.  The first Gram is FP64-grade at
+            // n <= 128: the substitution records X's column exponents for the
+            // FP64-grade Gram that follows.  The first Gram is FP64-grade at
             // every n: R_1 then makes X_2 orthonormal to rounding level, so the
             // last pass's R_P^{-1} - I stays within 2^-38 and its apply takes
             // the FP32 correction (a BF16x3 Gram left it near 1e-5 at n = 128)
-            int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
+            int *cx = (p.n <= 128) ? split_colexp(p) : nullptr;
             {
                 Timer t(th, 1, st);
                 // a row sketch reads only the drawn rows: NaN or Inf elsewhere in A is
-                // found by the Gram from X's column exponents (n <= 64) or here
+                // found by the Gram from X's column exponents (n <= 128) or here
                 if (rows && !cx) {
                     k_check_finite<<<4 * p.sms, 256, 0, st>>>(A, lda, p.m, n, p.status);
                     if (launch_ok()) return RXR_ERR_CUDA;
@@ -1586,7 +1587,7 @@ int rxr_precond_gram(rxr_handle h, const double *A, int64_t m, int64_t n, int64_
         return RXR_ERR_CUDA;
     if (prec == RXR_SPLIT_BF16) {
         if (X == nullptr) return RXR_ERR_UNSUPPORTED;
-        int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
+        int *cx = (p.n <= 128) ? split_colexp(p) : nullptr;
         if (int e = split_subst(p, A, lda, p.Rp, X, ldx, st, cx)) return e;
         if (int e = ozaki_gram_enqueue(p, X, ldx, st, cx != nullptr)) return e;
     } else {
@@ -1672,7 +1673,7 @@ int rxr_lstsq(rxr_handle h, const double *A, int64_t m, int64_t n, int64_t lda, 
     if (int e = enqueue_xr(p, p.Y, s, base, p.Rs, n, st)) return e;
     // B = A R_s^{-1} with G = B^T B at FP64 grade (it sets the solution's accuracy)
     if (prec == RXR_SPLIT_BF16) {
-        int *cx = (n <= 64) ? split_colexp(p) : nullptr;
+        int *cx = (n <= 128) ? split_colexp(p) : nullptr;
         if (rows && !cx) {
             k_check_finite<<<4 * p.sms, 256, 0, st>>>(A, lda, m, (int)n, p.status);
             if (launch_ok()) return RXR_ERR_CUDA;

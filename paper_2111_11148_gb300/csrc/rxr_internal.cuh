@@ -428,8 +428,10 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
                         cudaStream_t st);
 int *split_select_flag(const Plan &p);
 // sel (nullable): a device flag; nonzero makes the substitution return at once
+// colexp_out (nullable, zeroed by the caller): X's largest exponent per column
+// is max-ed into it (for the FP64-grade Gram that follows)
 int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                           int64_t ldx, cudaStream_t st, const int *sel = nullptr);
+                           int64_t ldx, cudaStream_t st, const int *sel = nullptr, int *colexp_out = nullptr);
 // 64 < n <= 128: X <- X R^{-1}, the FP32 correction X + X (R^{-1} - I) when
 // |R^{-1} - I| <= 2^-38 (chosen on the device), else the fused substitution
 int delta128_apply_enqueue(Plan &p, double *X, int64_t ldx, const double *R, cudaStream_t st);

@@ -1392,7 +1392,7 @@ __global__ void __launch_bounds__(256, 1)
     k_subst_fused128(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      int use_tma, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int n,
                      const unsigned char *__restrict__ rec, int64_t tiles_total, const int *__restrict__ sel,
-                     RxrStatus *st)
+                     int *colexp_out, RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
     if (sel != nullptr && *sel != 0) return;  // the FP32-correction apply was chosen instead
@@ -1407,7 +1407,9 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ uint32_t tmem_base;
     __shared__ int rowexp[2][kFuM];   // by block parity (the deferred epilogue reads the previous block's)
     __shared__ int defexp[kF2MaxN];   // column exponents of the deferred columns
+    __shared__ int out_exp[kF2MaxN];  // largest exponent per column of X (colexp_out)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < kF2MaxN) out_exp[tid] = 0;
 
     if (tid == 0) {
         mbar_init(&full_bar, 1);
@@ -1558,6 +1560,18 @@ __global__ void __launch_bounds__(256, 1)
             }
             __syncthreads();
         }
+        if (colexp_out != nullptr) {
+            // the tile's largest exponent per column of X (for the FP64-grade
+            // Gram that follows): warp w scans columns 16 w .. 16 w + 15
+            for (int c = 16 * warp; c < min(n, 16 * warp + 16); ++c) {
+                unsigned ex = 0;
+#pragma unroll
+                for (int i = 0; i < kFuM / 32; ++i)
+                    ex = max(ex, ((unsigned)__double2hiint(xs[c * kFuM + lane + 32 * i]) >> 20) & 0x7FFu);
+                ex = __reduce_max_sync(0xFFFFFFFFu, ex);
+                if (lane == 0) out_exp[c] = max(out_exp[c], (int)ex);
+            }
+        }
         // tile done: store it and fetch the next one into the same buffer once
         // the store has read it out
         if (use_tma) {
@@ -1583,6 +1597,7 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0 && use_tma) bulk_wait_all();
     tc_fence_before();
     __syncthreads();
+    if (colexp_out != nullptr && tid < n && out_exp[tid] > 0) atomicMax(colexp_out + tid, out_exp[tid]);
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
@@ -3090,7 +3105,7 @@ int fused_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *
 
 // X = B R^{-1} for 64 < n <= 128 in one pass over B (k_rprep128 + k_subst_fused128).
 int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const double *R, int64_t ldr, double *X,
-                           int64_t ldx, cudaStream_t st, const int *sel)
+                           int64_t ldx, cudaStream_t st, const int *sel, int *colexp_out)
 {
     if (p.n <= kFuMaxN || p.n > kF2MaxN) return RXR_ERR_UNSUPPORTED;
     const int n = (int)p.n, nb = fu_blocks(n);
@@ -3103,7 +3118,7 @@ int fused128_subst_enqueue(Plan &p, const double *Bsrc, int64_t ldb, const doubl
     const int64_t tiles = cdiv64(p.m, kFuM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
     k_subst_fused128<<<gx, 256, f2_smem_bytes(n), st>>>(ms, md, use_tma, Bsrc, ldb, X, ldx, p.m, n, rec, tiles,
-                                                         sel, p.status);
+                                                         sel, colexp_out, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
@@ -3135,10 +3150,14 @@ int ozaki_gram_enqueue(Plan &p, const double *X, int64_t ldx, cudaStream_t st, b
     }
     if (p.n <= 128) {
         // 64 < n <= 128: the pipelined Gram over the columns' global exponents
+        // (recorded by the substitution that produced X, or found here)
         int *cx = split_colexp(p);
-        if (cudaMemsetAsync(cx, 0, p.n * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
-        const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
-        k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(X, ldx, p.m, cx, p.status);
+        if (!colexp_ready) {
+            if (cudaMemsetAsync(cx, 0, p.n * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+            const int bx = (int)std::min<int64_t>(64, cdiv64(p.m, 256));
+            k_colexp<<<dim3((unsigned)bx, (unsigned)p.n), 256, 0, st>>>(X, ldx, p.m, cx, p.status);
+            if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
+        }
         const int64_t total = cdiv64(p.m, kG8Rows);
         const Oz128Grid gg = oz128_grid(p.m, p.sms);
         const int64_t gx = gg.g1;  // partial-sum slots
