@@ -192,13 +192,15 @@ def make_input():
 
 def make_input_device(dev):
     """The workload's A = U diag(sigma) V^T built on the GPU, column-major: the
-    recipe of inputs.usv_matrix (sigma and V from inputs.usv_factors; U the
-    Householder Q factor of a seeded N(0,1) m x n matrix) with U drawn by torch's
-    CUDA generator and orthonormalised by torch.linalg.qr on the device: the same
-    distribution, other bytes than the host generator's.  Building the 8.6 GB
-    input on the host (multithreaded LAPACK on the CPU) took about 70 s and left
-    the host link reading pinned memory at 24-60 GB/s instead of 200 GB/s for
-    the rest of the process."""
+    recipe of inputs.usv_matrix (sigma and V from inputs.usv_factors; U the Q
+    factor, diag(R) > 0, of a seeded N(0,1) m x n matrix) with the Gaussian drawn
+    by torch's CUDA generator and its Q factor taken by two Cholesky QR steps
+    (Gram and product by cuBLAS, the n x n Cholesky factor and its inverse on the
+    host; the Gaussian is well conditioned, so two steps reach orthonormality to
+    rounding): the same distribution, other bytes than the host generator's.
+    Building the 8.6 GB input on the host (multithreaded LAPACK on the CPU) took
+    about 70 s and left the host link reading pinned memory at 24-60 GB/s
+    instead of 200 GB/s for the rest of the process."""
     import torch
 
     from paper_2111_11148_gb300 import rxr
@@ -207,9 +209,10 @@ def make_input_device(dev):
     sigma, V = usv_factors(N, KAPPA, SEED)
     g = torch.Generator(device=dev)
     g.manual_seed(SEED)
-    G = torch.randn((M, N), dtype=torch.float64, device=dev, generator=g)
-    U, _ = torch.linalg.qr(G)
-    del G
+    U = torch.randn((M, N), dtype=torch.float64, device=dev, generator=g)
+    for _ in range(2):
+        Rc = np.linalg.cholesky((U.t() @ U).cpu().numpy()).T
+        U = U @ torch.from_numpy(np.linalg.inv(Rc)).to(dev)
     A = (U * torch.from_numpy(sigma).to(dev)) @ torch.from_numpy(V.T.copy()).to(dev)
     del U
     out = rxr.colmajor(A)
