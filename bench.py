@@ -848,9 +848,12 @@ def launches_per_step(prec, n, m, rows=False):
     npanel = (n + 31) // 32
     xr = 1 if 2 * n * n <= 16384 else 3 * npanel - 1  # one-CTA XR, or blocked: panels, V^T C, updates, finish
     sk = 1 if rows else 2  # row gather, or the Gaussian sketch and its reduction
+    # one Cholesky factor: one CTA up to n = 64, else the blocked form (init, a diagonal block, panel and
+    # update per further 32-column block, and the R accumulation)
+    factor = 1 if n <= 64 else 3 * ((n + 31) // 32)
     if prec == "fp64":
-        # sketch, XR, 3 x (substitution [+ wide Gram] + reduce except last), 2 factors, copy
-        return sk + (8 if n <= 128 else 10) + xr
+        # sketch, XR, 3 x substitution (+ its Gram's reduction except the last), 2 factors, copy
+        return sk + xr + (5 if n <= 128 else 7) + 2 * factor + 1
     if n <= 64:
         # sketch, XR, fused substitution, Gram, reduce, factor, middle pass (above 2^17 rows: inverse,
         # condition estimate, apply, fused substitution, the one not selected returning at once; else the
@@ -858,10 +861,13 @@ def launches_per_step(prec, n, m, rows=False):
         # FP64-grade apply: the one not selected returns at once), copy
         return sk + xr + 4 + (4 if m >= 1 << 17 else 1) + 3 + 4 + 1
     if n <= 128:
-        # sketch, XR, 3 x (record prep, fused substitution), 2 x (Gram, reduce), 2 factors, copy
-        return sk + xr + 3 * 2 + 2 * 2 + 2 + 1 + (1 if rows else 0)
+        # sketch, XR, record prep + fused substitution, Gram, reduce, factor, middle pass (above 2^17 rows:
+        # inverse, condition estimate, three block products, record prep + fused substitution; else record
+        # prep + fused substitution), Gram, reduce, factor, last pass (inverse, selection, FP32-correction
+        # apply, record prep + fused substitution), copy
+        return sk + xr + 2 + 2 + factor + (7 if m >= 1 << 17 else 2) + 2 + factor + 5 + 1
     blocked = 2 * ((n + 63) // 64) - 1  # diagonal solves + trailing updates
-    return sk + xr + 3 * blocked + 2 * 2 + 2 + 1 + (1 if rows else 0)
+    return sk + xr + 3 * blocked + 2 * 2 + 2 * factor + 1 + (1 if rows else 0)
 
 
 def roofline_entry(prec, stages, peak_fp64):
