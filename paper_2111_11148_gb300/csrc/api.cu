@@ -653,7 +653,7 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
         // X <- X R_p^{-1} (in place), with the next pass's Gram unless last; the
         // split path takes that Gram from the tensor cores at FP64 grade
         if (p.prec == RXR_SPLIT_BF16 && !last) {
-            int *cx = (p.n <= 64) ? split_colexp(p) : nullptr;
+            int *cx = (p.n <= 128) ? split_colexp(p) : nullptr;
             {
                 Timer t(th, 2, st);
                 // below ~2^17 rows the inverse and the estimate (~0.1 ms) cost more
@@ -661,7 +661,8 @@ int enqueue_cholqr(rxr_handle h, const Plan &p, const double *A, int64_t lda, in
                 if (p.n <= 128 && p.m >= ((int64_t)1 << 17)) {
                     // R_p of a middle pass is well conditioned after the preconditioning:
                     // explicit-inverse product unless the estimate says otherwise
-                    if (cx && cudaMemsetAsync(cx, 0, 64 * sizeof(int), st) != cudaSuccess) return RXR_ERR_CUDA;
+                    if (cx && cudaMemsetAsync(cx, 0, (p.n <= 64 ? 64 : p.n) * sizeof(int), st) != cudaSuccess)
+                        return RXR_ERR_CUDA;
                     if (int e = middle_pass_enqueue(const_cast<Plan &>(p), Q, ldq, p.Rp, cx, split_select_flag(p), st))
                         return e;
                 } else if (int e = split_subst(p, Q, ldq, p.Rp, Q, ldq, st, cx)) {

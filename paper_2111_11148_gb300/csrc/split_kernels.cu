@@ -2103,7 +2103,7 @@ __host__ __device__ inline size_t aq_smem_bytes(int n)
 __global__ void __launch_bounds__(256, 1)
     k_apply_oz64(const __grid_constant__ CUtensorMap tm_x, int use_tma, double *X, int64_t ldx, int64_t m, int n,
                  const double *__restrict__ T, int64_t ldt, int64_t tiles_total, const int *__restrict__ sel,
-                 int want, int *colexp_out, RxrStatus *st)
+                 int want, int *colexp_out, int nout, int full, double *D, int64_t ldd, RxrStatus *st)
 {
     if (rxr_failed_block(st)) return;
     if (sel != nullptr && *sel != want) return;  // the other form was chosen
@@ -2126,8 +2126,9 @@ __global__ void __launch_bounds__(256, 1)
     if (tid < 64) out_exp[tid] = 0;
     if (tid < 64) {
         unsigned ex = 0;
-        if (tid < n)
-            for (int k = 0; k <= tid; ++k) ex = max(ex, ((unsigned)__double2hiint(T[k + (int64_t)tid * ldt]) >> 20) & 0x7FFu);
+        if (tid < nout)
+            for (int k = 0; k < (full ? n : tid + 1); ++k)
+                ex = max(ex, ((unsigned)__double2hiint(T[k + (int64_t)tid * ldt]) >> 20) & 0x7FFu);
         colexp_t[tid] = (int)ex;
     }
     if (tid == 0) {
@@ -2137,15 +2138,16 @@ __global__ void __launch_bounds__(256, 1)
         fence_barrier_init();
     }
     __syncthreads();
-    // digits of T: B operand element (l, k) = T[k][l] (zero below the diagonal)
-    for (int e = tid; e < n * 8; e += blockDim.x) {
+    // digits of T: B operand element (l, k) = T[k][l] (zero below the diagonal
+    // unless the block is full)
+    for (int e = tid; e < nout * 8; e += blockDim.x) {
         const int l = e >> 3, k0 = 8 * (e & 7);
         unsigned long long U[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int k = k0 + r;
             const unsigned long long bits =
-                (k <= l && k < n) ? (unsigned long long)__double_as_longlong(T[k + (int64_t)l * ldt]) : 0ull;
+                ((full || k <= l) && k < n) ? (unsigned long long)__double_as_longlong(T[k + (int64_t)l * ldt]) : 0ull;
             U[r] = digits_offset(bits, colexp_t[l]);
         }
 #pragma unroll
@@ -2243,7 +2245,15 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int c16 = 0; c16 < 2; ++c16) {
                 const int col0 = 32 * half + 16 * c16;
-                if (col0 >= n) continue;  // warp-uniform
+                if (col0 >= nout) continue;  // warp-uniform
+                // the accumulated destination's 16 values, all in flight before
+                // the tensor-memory reads (none waits for another)
+                double dv[16];
+                if (D != nullptr) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t)
+                        dv[t] = (col0 + t < nout && gr < m) ? __ldcs(D + gr + (int64_t)(col0 + t) * ldd) : 0.0;
+                }
                 uint32_t g[kOzDigits][16];
 #pragma unroll
                 for (int d = 0; d < kOzDigits; ++d)
@@ -2264,15 +2274,20 @@ __global__ void __launch_bounds__(256, 1)
                     }
                     const int l = col0 + t;
                     double qv = 0.0;
-                    if (l < n && gr < m) {
+                    if (l < nout && gr < m) {
                         const int el = colexp_t[l];
                         const int be = er + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
                         qv = (er > 0 && el > 0) ? f2d_pow2(hi, be) + f2d_pow2(lo, be) : 0.0;
-                        X[gr + (int64_t)l * ldx] = qv;
+                        if (D != nullptr) {
+                            qv = dv[t] + qv;
+                            __stcs(D + gr + (int64_t)l * ldd, qv);
+                        } else {
+                            X[gr + (int64_t)l * ldx] = qv;
+                        }
                     }
                     if (colexp_out != nullptr) {
                         const unsigned e = __reduce_max_sync(0xFFFFFFFFu, ((unsigned)__double2hiint(qv) >> 20) & 0x7FFu);
-                        if (lane == 0 && e > 0 && l < n) atomicMax(&out_exp[l], (int)e);
+                        if (lane == 0 && e > 0 && l < nout) atomicMax(&out_exp[l], (int)e);
                     }
                 }
             }
@@ -2284,7 +2299,7 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0 && use_tma && !ok) mbar_wait_bounded(&full_bar, loads & 1u, st);
     tc_fence_before();
     __syncthreads();
-    if (colexp_out != nullptr && tid < n && out_exp[tid] > 0) atomicMax(colexp_out + tid, out_exp[tid]);
+    if (colexp_out != nullptr && tid < nout && out_exp[tid] > 0) atomicMax(colexp_out + tid, out_exp[tid]);
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
@@ -2841,17 +2856,46 @@ __global__ void __launch_bounds__(32 * NW, NW == 8 ? 3 : 1)
                 acc[a][3] = ffma2(xa, e23.y, acc[a][3]);
             }
         }
+        if constexpr (NW == 8) {
+            // X again (from L2), value by value (within 80 registers)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int64_t gr = r0 + lane + 32 * a;
-            const int er = rowe[buf][lane + 32 * a];
+            for (int a = 0; a < 4; ++a) {
+                const int64_t gr = r0 + lane + 32 * a;
+                const int er = rowe[buf][lane + 32 * a];
 #pragma unroll
-            for (int b = 0; b < 8; ++b)
-                if (b < nb && gr < m) {
-                    double *xp = X + gr + (int64_t)(j0 + b) * ldx;
-                    const uint32_t cb = (uint32_t)(acc[a][b >> 1] >> (32 * (b & 1)));
-                    __stcs(xp, __ldcs(xp) + f2d_pow2(__uint_as_float(cb), er));
+                for (int b = 0; b < 8; ++b)
+                    if (b < nb && gr < m) {
+                        double *xp = X + gr + (int64_t)(j0 + b) * ldx;
+                        const uint32_t cb = (uint32_t)(acc[a][b >> 1] >> (32 * (b & 1)));
+                        __stcs(xp, __ldcs(xp) + f2d_pow2(__uint_as_float(cb), er));
+                    }
+            }
+        } else {
+            // X again (from L2), in groups of two rows whose 16 loads are all in
+            // flight before the group's first store (a store between them would
+            // order each load after it)
+#pragma unroll
+            for (int a0 = 0; a0 < 4; a0 += 2) {
+                double xo[2][8];
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        const int64_t gr = r0 + lane + 32 * (a0 + a);
+                        xo[a][b] = (b < nb && gr < m) ? __ldcs(X + gr + (int64_t)(j0 + b) * ldx) : 0.0;
+                    }
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int64_t gr = r0 + lane + 32 * (a0 + a);
+                    const int er = rowe[buf][lane + 32 * (a0 + a)];
+#pragma unroll
+                    for (int b = 0; b < 8; ++b)
+                        if (b < nb && gr < m) {
+                            const uint32_t cb = (uint32_t)(acc[a0 + a][b >> 1] >> (32 * (b & 1)));
+                            __stcs(X + gr + (int64_t)(j0 + b) * ldx, xo[a][b] + f2d_pow2(__uint_as_float(cb), er));
+                        }
                 }
+            }
         }
     }
 }
@@ -2931,14 +2975,6 @@ __global__ void __launch_bounds__(4 * NM) k_cond_select(const double *__restrict
     }
 }
 
-// dst = -src (n x n, ld n): the negated block of R^{-1} that the middle
-// pass's block product adds through the trailing-update kernel (C = B - X R)
-__global__ void k_negate(const double *__restrict__ src, int n, double *__restrict__ dst, const RxrStatus *st)
-{
-    if (rxr_failed_block(st)) return;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) dst[e] = -src[e];
-}
-
 // The middle CholeskyQR pass for n <= 64: X <- X R^{-1} by the tensor-core
 // product with T = R^{-1} when R is well conditioned (estimate <= 16), else by
 // the fused substitution; both kernels are launched and the one not selected
@@ -2948,34 +2984,33 @@ __global__ void k_negate(const double *__restrict__ src, int n, double *__restri
 // estimate of cond_2(R) is at most 16 (else the fused substitution):
 //   X_b <- X_b T_11,  X_b <- X_b + X_a T_01,  X_a <- X_a T_00,
 // X_a = columns 0..63, X_b = 64..n-1; each step an FP64-grade tensor-core
-// product, in this order so that each reads columns not yet overwritten.
-static int middle_pass128_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *sel, cudaStream_t st)
+// product (the second one adds into X_b), in this order so that each reads
+// columns not yet overwritten.  colexp_out (nullable, zeroed by the caller):
+// the columns' largest exponents of the result, from whichever form runs.
+static int middle_pass128_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *colexp_out, int *sel,
+                                  cudaStream_t st)
 {
     const int n = (int)p.n, nb = n - 64;
     double *T = p.W;
     k_tri_inverse128<<<(unsigned)n, 32, (size_t)n * 128 * sizeof(double), st>>>(R, n, p.n, T, p.status);
     k_cond_select<128><<<1, 512, 128 * 129 * sizeof(double), st>>>(R, T, n, sel, p.status);
-    k_negate<<<(unsigned)cdiv64((int64_t)n * n, 256), 256, 0, st>>>(T, n, p.C, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     const int64_t tiles = cdiv64(p.m, kAqM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
     double *Xb = X + 64 * ldx;
     CUtensorMap mb, ma;
     const int tma_b = encode_tile_map(&mb, Xb, p.m, nb, ldx, kAqM, nb) ? 1 : 0;
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(nb), st>>>(mb, tma_b, Xb, ldx, p.m, nb, T + 64 + 64 * p.n, p.n, tiles, sel,
-                                                     1, nullptr, p.status);
-    const int64_t utiles = cdiv64(p.m, kApM);
-    int64_t ugx = balanced_chunks(1, p.sms, utiles);
-    const int64_t tpc = cdiv64(utiles, ugx);
-    ugx = cdiv64(utiles, tpc);
-    // C = B - X_a (-T_01): the trailing-update kernel with the negated block
-    k_update_ozaki<<<dim3((unsigned)ugx, 1), 256, kApSmem, st>>>(X, ldx, 0, 64, p.C, p.n, 64, nb, X, ldx, X, ldx,
-                                                                  p.m, utiles, tpc, sel, p.status);
     const int tma_a = encode_tile_map(&ma, X, p.m, 64, ldx, kAqM, 64) ? 1 : 0;
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T, p.n, tiles, sel, 1, nullptr,
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(nb), st>>>(mb, tma_b, Xb, ldx, p.m, nb, T + 64 + 64 * p.n, p.n, tiles, sel,
+                                                     1, nullptr, nb, 0, nullptr, 0, p.status);
+    // X_b += X_a T_01 (the full 64 x nb block)
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T + 64 * p.n, p.n, tiles, sel, 1,
+                                                     colexp_out ? colexp_out + 64 : nullptr, nb, 1, Xb, ldx,
                                                      p.status);
+    k_apply_oz64<<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T, p.n, tiles, sel, 1, colexp_out,
+                                                     64, 0, nullptr, 0, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
-    return fused128_subst_enqueue(p, X, ldx, R, p.n, X, ldx, st, sel);
+    return fused128_subst_enqueue(p, X, ldx, R, p.n, X, ldx, st, sel, colexp_out);
 }
 
 int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *colexp_out, int *sel,
@@ -2983,7 +3018,7 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
 {
     if (p.n > 128) return RXR_ERR_UNSUPPORTED;
     double *T = p.W;
-    if (p.n > 64) return middle_pass128_enqueue(p, X, ldx, R, sel, st);
+    if (p.n > 64) return middle_pass128_enqueue(p, X, ldx, R, colexp_out, sel, st);
     k_tri_inverse64<<<(unsigned)p.n, 32, 0, st>>>(R, (int)p.n, p.n, T, p.status);
     k_cond_select<64><<<1, 256, 64 * 65 * sizeof(double), st>>>(R, T, (int)p.n, sel, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
@@ -2993,7 +3028,7 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
     const int64_t tiles = cdiv64(p.m, kAqM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
     k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, 1, colexp_out,
-                                                    p.status);
+                                                    n, 0, nullptr, 0, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     return fused_subst_enqueue(p, X, ldx, R, p.n, X, ldx, colexp_out, st, sel);
 }
@@ -3044,7 +3079,7 @@ int ozaki_apply_rows(Plan &p, double *X, int64_t ldx, int64_t r0, int64_t rows, 
     delta_launch(p.sms, Xr, ldx, rows, n, split_delta(p), tiles, sel, p.status, st);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
     k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, Xr, ldx, rows, n, p.W, p.n, tiles, sel, 0, nullptr,
-                                                    p.status);
+                                                    n, 0, nullptr, 0, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
 
