@@ -791,6 +791,12 @@ __global__ void __launch_bounds__(256, 1)
         for (int c16 = 0; c16 < 2; ++c16) {
             const int col0 = half * 32 + c16 * 16;
             if (col0 >= nw) continue;  // warp-uniform
+            // B's 16 values, all in flight before the first store (C may alias B,
+            // so a store between them would order each load after it)
+            double bv[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                bv[t] = (B != nullptr && col0 + t < nw && gr < m) ? B[gr + (int64_t)(tc0 + n0 + col0 + t) * ldb] : 0.0;
             float hi[16], lo[16], v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, hi);
 #pragma unroll
@@ -818,7 +824,7 @@ __global__ void __launch_bounds__(256, 1)
                     const double scale = (ei > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
                     const double prod = (rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t])) * scale;
                     const int64_t cc = tc0 + n0 + l;
-                    C[gr + cc * ldc] = B ? B[gr + cc * ldb] - prod : prod;
+                    C[gr + cc * ldc] = B ? bv[t] - prod : prod;
                 }
             }
         }
