@@ -372,6 +372,36 @@ __device__ __forceinline__ double f2d_pow2(float f, int be)
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// (hi + lo) * 2^(be - 1023) as one double, on the integer pipes: the FP32 pair of
+// a tensor-memory drain (hi, lo zero or normal, in any order) is renormalised by
+// an exact two-sum (s + e = hi + lo, |e| <= ulp(s) / 2), e's bits are aligned
+// below s's 24 in a 53-bit integer (those below 2^-29 ulp(s) are truncated: a
+// relative error below 2^-52), and the double is assembled from it; flush and
+// overflow as f2d_pow2.  One FP64 operation fewer than converting hi and lo
+// and adding them.
+__device__ __forceinline__ double pair2d_pow2(float hi, float lo, int be)
+{
+    const float s = __fadd_rn(hi, lo);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(lo, bb));
+    const uint32_t us = __float_as_uint(s), ue = __float_as_uint(e);
+    const int es = (int)((us >> 23) & 0xFFu), ee = (int)((ue >> 23) & 0xFFu);
+    const uint32_t ms = (us & 0x7FFFFFu) | 0x800000u;
+    const uint32_t me = (ee == 0) ? 0u : ((ue & 0x7FFFFFu) | 0x800000u);
+    const int g = es - ee;  // at least 24 when e is not zero
+    const uint32_t eu = (g <= 29) ? (me << (29 - g)) : (me >> min(g - 29, 31));
+    long long M = ((long long)ms << 29) + ((((us ^ ue) >> 31) != 0u) ? -(long long)eu : (long long)eu);
+    const bool low = M < (1ll << 52);  // M lies in [2^51, 2^53)
+    M = low ? (M << 1) : M;
+    const int E = es - 127 + be - (low ? 1 : 0);
+    const uint32_t sign = us & 0x80000000u;
+    const bool zero = (es == 0) | (E <= 0), inf = E >= 2047;  // selects, not branches
+    const uint32_t h32 =
+        zero ? 0u : inf ? (sign | 0x7FF00000u) : (sign | ((uint32_t)E << 20) | ((uint32_t)(M >> 32) & 0xFFFFFu));
+    const uint32_t l32 = (zero | inf) ? 0u : (uint32_t)M;
+    return __hiloint2double((int)h32, (int)l32);
+}
+
 // Digit q of two offset forms as one packed FP16 pair (value a in the low
 // half): 0x6400 | (digit + 128) encodes the FP16 number 1024 + digit + 128
 // (exact: at most 9 bits over 2^10), so one packed subtraction of 1152 leaves
@@ -629,9 +659,7 @@ __global__ void __launch_bounds__(256, 1)
                 const int lc = col0 + t;  // column b0c + lc of G
                 const int el = b_inside ? exA[b0c - a0c + lc] : exB[lc];
                 const int be = ej + el - 1035;  // biased exponent of 2^(e_j + e_l - 2058)
-                const double scale = (ej > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
-                const double val = rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
-                acc[c16 * 16 + t] = fma(val, scale, acc[c16 * 16 + t]);
+                if (ej > 0 && el > 0 && be > 0 && be < 2047) acc[c16 * 16 + t] += pair2d_pow2(hi[t], lo[t], be);
             }
         }
         tc_fence_before();
@@ -821,8 +849,7 @@ __global__ void __launch_bounds__(256, 1)
                 if (l < nw && gr < m) {
                     const int el = colexp_t[l];
                     const int be = ei + el - 1035;
-                    const double scale = (ei > 0 && el > 0 && be > 0 && be < 2047) ? __hiloint2double(be << 20, 0) : 0.0;
-                    const double prod = (rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t])) * scale;
+                    const double prod = (ei > 0 && el > 0 && be > 0 && be < 2047) ? pair2d_pow2(hi[t], lo[t], be) : 0.0;
                     const int64_t cc = tc0 + n0 + l;
                     C[gr + cc * ldc] = B ? bv[t] - prod : prod;
                 }
@@ -1191,7 +1218,7 @@ __global__ void __launch_bounds__(256, 1)
                             const int be = ei + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
                             if (ei > 0 && el > 0 && be > 0 && be < 2047) {
                                 double *xp = xs + (c16 + kFuBw + l) * kFuM + row;
-                                *xp = (*xp - f2d_pow2(hi, be)) - f2d_pow2(lo, be);
+                                *xp = *xp - pair2d_pow2(hi, lo, be);
                             }
                         }
                     }
@@ -1278,6 +1305,15 @@ __device__ __forceinline__ void gram64_accumulate(const float hi[32], const floa
 {
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] += rxr_f2d_exact(hi[t]) + rxr_f2d_exact(lo[t]);
+}
+
+// The same with one FP64 addition per sum (pair2d_pow2: more integer work,
+// less FP64; k_gram_oz128 gains from it, k_gram_oz64, whose digit production
+// keeps the integer pipes busier, does not).
+__device__ __forceinline__ void gram_accumulate_pair(const float hi[32], const float lo[32], double acc[32])
+{
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] += pair2d_pow2(hi[t], lo[t], 1023);
 }
 
 // ---------------------------------------------------------------------------
@@ -1387,7 +1423,7 @@ __device__ __forceinline__ void f2_apply(uint32_t tmem, int q4, int lane, int ei
                 if (ei > 0 && el > 0) {
                     const int be = ei + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
                     double *xp = xs + (col0 + l) * kFuM + erow;
-                    *xp = (*xp - f2d_pow2(fhi, be)) - f2d_pow2(flo, be);
+                    *xp = *xp - pair2d_pow2(fhi, flo, be);
                 }
             }
         }
@@ -2022,7 +2058,7 @@ __global__ void __launch_bounds__(kG8Threads, 1)
             if (!skip_epi) gram64_read(tmem, q4, half, hi, lo);
             tc_fence_before();
             mbar_arrive(&tfree);
-            if (!skip_epi) gram64_accumulate(hi, lo, acc);
+            if (!skip_epi) gram_accumulate_pair(hi, lo, acc);
         }
     }
     for (int it = 0; mma_thread && it < nbufs; ++it) {
@@ -2056,7 +2092,7 @@ __global__ void __launch_bounds__(kG8Threads, 1)
         float hi[32], lo[32];
         if (!skip_epi) {
             gram64_read(tmem, q4, half, hi, lo);
-            gram64_accumulate(hi, lo, acc);
+            gram_accumulate_pair(hi, lo, acc);
         }
     }
     ok = __syncthreads_and(ok) != 0;
@@ -2283,7 +2319,7 @@ __global__ void __launch_bounds__(256, 1)
                     if (l < nout && gr < m) {
                         const int el = colexp_t[l];
                         const int be = er + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
-                        qv = (er > 0 && el > 0) ? f2d_pow2(hi, be) + f2d_pow2(lo, be) : 0.0;
+                        qv = (er > 0 && el > 0) ? pair2d_pow2(hi, lo, be) : 0.0;
                         if (D != nullptr) {
                             qv = dv[t] + qv;
                             __stcs(D + gr + (int64_t)l * ldd, qv);
@@ -2414,7 +2450,7 @@ __device__ __forceinline__ void sketch_drain(uint32_t tmem, int q4, int col0, do
                 hi = sum;
                 lo = __fadd_rn(lo, err);
             }
-            acc[8 * c8 + t] += rxr_f2d_exact(hi) + rxr_f2d_exact(lo);
+            acc[8 * c8 + t] += pair2d_pow2(hi, lo, 1023);
         }
     }
 }
