@@ -834,7 +834,8 @@ def subst_fp64_flop_per_row(n, bw, sub_ops):
     """FP64 flop a blocked substitution issues per row: the diagonal-block
     solves (bw (bw - 1) / 2 FMAs per block, 2 flop each), the n multiplications
     by 1 / R_jj, and sub_ops FP64 operations per trailing output per block (the
-    subtraction of the tensor-core update)."""
+    subtraction of the tensor-core update: one, the update's FP32 pair turned
+    into one double on the integer pipes)."""
     flop, c0 = 0.0, 0
     while c0 < n:
         b = min(bw, n - c0)
@@ -891,12 +892,12 @@ def roofline_entry(prec, stages, peak_fp64):
         name = "k_subst_gram (FP64 substitution X = A R_s^-1, no Gram)" if N <= 128 else "k_subst_wide"
         hbm_bytes = 16.0 * M * N
     elif N <= 128:
-        flop = subst_fp64_flop_per_row(N, 16, 2) * M
+        flop = subst_fp64_flop_per_row(N, 16, 1) * M
         name = ("k_subst_fused" if N <= 64 else "k_rprep128 + k_subst_fused128") + \
             " (FP64 16-column diagonal solves + FP64 subtraction of tcgen05 updates)"
         hbm_bytes = 16.0 * M * N
     else:
-        flop = subst_fp64_flop_per_row(N, 64, 3) * M
+        flop = subst_fp64_flop_per_row(N, 64, 1) * M
         name = "k_solve_block + k_update_ozaki (blocked substitution: FP64 diagonal blocks, tcgen05 updates)"
         hbm_bytes = 16.0 * M * N
     achieved = flop / (t * 1e-3) / 1e12
