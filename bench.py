@@ -55,14 +55,15 @@ DTYPES = {"fp64": "f64",
           "split_precond": "f64 with fp16 8-bit-digit sketch and bf16x3 first Gram on tcgen05"}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from ncu captures
-# of a smaller case scaled by rows (traffic grows with the rows); None where no
-# capture of the current kernel exists
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the roofline
+# kernel, from an ncu capture of a smaller case (bytes, rows captured), scaled
+# by rows to the workload (traffic grows with the rows); absent where no capture
+# of the current kernel exists
 TRAFFIC = {
-    # k_subst_gram (FP64 precondition + Gram), m = 2^19, n = 64, x 8 rows
-    ("fp64", 64): (268.552704e6 + 225.660672e6) * 8,
-    # k_subst_fused (split precondition), m = 2^19, n = 64, x 8 rows
-    ("split", 64): (268.584960e6 + 216.926208e6) * 8,
+    # k_subst_gram (FP64 precondition + Gram), m = 2^19, n = 64
+    ("fp64", 64): (268.552704e6 + 225.660672e6, 2**19),
+    # k_subst_fused128 (split precondition), m = 2^19, n = 128
+    ("split", 128): (537.306880e6 + 486.197504e6, 2**19),
 }
 HBM_GBS = 6784.2  # measured copy bandwidth of this GPU pool (STREAM-style copy)
 
@@ -901,7 +902,8 @@ def roofline_entry(prec, stages, peak_fp64):
         name = "k_solve_block + k_update_ozaki (blocked substitution: FP64 diagonal blocks, tcgen05 updates)"
         hbm_bytes = 16.0 * M * N
     achieved = flop / (t * 1e-3) / 1e12
-    traffic = TRAFFIC.get((prec, N)) if M == 2**22 else None
+    cap = TRAFFIC.get((prec, N))
+    traffic = cap[0] * M / cap[1] if cap else None
     return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
             "frac": achieved / peak_fp64, "traffic": traffic, "ms": t,
             "hbm_frac": (hbm_bytes / (t * 1e-3) / 1e9) / hbm, "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
