@@ -2142,6 +2142,10 @@ __host__ __device__ inline size_t aq_smem_bytes(int n)
     return (size_t)kAqM * n * 8 + 2 * (size_t)kOzDigits * kAqPlane + (size_t)kOzDigits * kAqTPlane;
 }
 
+// ACC: the product is added into D (a column block of X other than the one
+// read) instead of overwriting the columns read; a template parameter, so that
+// the overwriting form carries none of the adding form's registers.
+template <bool ACC>
 __global__ void __launch_bounds__(256, 1)
     k_apply_oz64(const __grid_constant__ CUtensorMap tm_x, int use_tma, double *X, int64_t ldx, int64_t m, int n,
                  const double *__restrict__ T, int64_t ldt, int64_t tiles_total, const int *__restrict__ sel,
@@ -2291,7 +2295,7 @@ __global__ void __launch_bounds__(256, 1)
                 // the accumulated destination's 16 values, all in flight before
                 // the tensor-memory reads (none waits for another)
                 double dv[16];
-                if (D != nullptr) {
+                if (ACC) {
 #pragma unroll
                     for (int t = 0; t < 16; ++t)
                         dv[t] = (col0 + t < nout && gr < m) ? __ldcs(D + gr + (int64_t)(col0 + t) * ldd) : 0.0;
@@ -2320,7 +2324,7 @@ __global__ void __launch_bounds__(256, 1)
                         const int el = colexp_t[l];
                         const int be = er + el - 1035;  // 2^(e_i + e_l - 2058) as a biased exponent
                         qv = (er > 0 && el > 0) ? pair2d_pow2(hi, lo, be) : 0.0;
-                        if (D != nullptr) {
+                        if (ACC) {
                             qv = dv[t] + qv;
                             __stcs(D + gr + (int64_t)l * ldd, qv);
                         } else {
@@ -3043,13 +3047,13 @@ static int middle_pass128_enqueue(Plan &p, double *X, int64_t ldx, const double 
     CUtensorMap mb, ma;
     const int tma_b = encode_tile_map(&mb, Xb, p.m, nb, ldx, kAqM, nb) ? 1 : 0;
     const int tma_a = encode_tile_map(&ma, X, p.m, 64, ldx, kAqM, 64) ? 1 : 0;
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(nb), st>>>(mb, tma_b, Xb, ldx, p.m, nb, T + 64 + 64 * p.n, p.n, tiles, sel,
+    k_apply_oz64<false><<<gx, 256, aq_smem_bytes(nb), st>>>(mb, tma_b, Xb, ldx, p.m, nb, T + 64 + 64 * p.n, p.n, tiles, sel,
                                                      1, nullptr, nb, 0, nullptr, 0, p.status);
     // X_b += X_a T_01 (the full 64 x nb block)
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T + 64 * p.n, p.n, tiles, sel, 1,
+    k_apply_oz64<true><<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T + 64 * p.n, p.n, tiles, sel, 1,
                                                      colexp_out ? colexp_out + 64 : nullptr, nb, 1, Xb, ldx,
                                                      p.status);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T, p.n, tiles, sel, 1, colexp_out,
+    k_apply_oz64<false><<<gx, 256, aq_smem_bytes(64), st>>>(ma, tma_a, X, ldx, p.m, 64, T, p.n, tiles, sel, 1, colexp_out,
                                                      64, 0, nullptr, 0, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     return fused128_subst_enqueue(p, X, ldx, R, p.n, X, ldx, st, sel, colexp_out);
@@ -3069,7 +3073,7 @@ int middle_pass_enqueue(Plan &p, double *X, int64_t ldx, const double *R, int *c
     const int use_tma = encode_tile_map(&mx, X, p.m, n, ldx, kAqM, n) ? 1 : 0;
     const int64_t tiles = cdiv64(p.m, kAqM);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, 1, colexp_out,
+    k_apply_oz64<false><<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, X, ldx, p.m, n, T, p.n, tiles, sel, 1, colexp_out,
                                                     n, 0, nullptr, 0, p.status);
     if (cudaGetLastError() != cudaSuccess) return RXR_ERR_CUDA;
     return fused_subst_enqueue(p, X, ldx, R, p.n, X, ldx, colexp_out, st, sel);
@@ -3120,7 +3124,7 @@ int ozaki_apply_rows(Plan &p, double *X, int64_t ldx, int64_t r0, int64_t rows, 
     const int use_tma = encode_tile_map(&mx, Xr, rows, n, ldx, kAqM, n) ? 1 : 0;
     delta_launch(p.sms, Xr, ldx, rows, n, split_delta(p), tiles, sel, p.status, st);
     const int gx = (int)std::min<int64_t>(p.sms, tiles);
-    k_apply_oz64<<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, Xr, ldx, rows, n, p.W, p.n, tiles, sel, 0, nullptr,
+    k_apply_oz64<false><<<gx, 256, aq_smem_bytes(n), st>>>(mx, use_tma, Xr, ldx, rows, n, p.W, p.n, tiles, sel, 0, nullptr,
                                                     n, 0, nullptr, 0, p.status);
     return cudaGetLastError() == cudaSuccess ? 0 : RXR_ERR_CUDA;
 }
@@ -3289,7 +3293,11 @@ cudaError_t set_split_smem()
         e = cudaFuncSetAttribute(k_subst_fused128, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)f2_smem_bytes(kF2MaxN));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_apply_oz64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)aq_smem_bytes(64));
+        e = cudaFuncSetAttribute(k_apply_oz64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)aq_smem_bytes(64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_oz64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)aq_smem_bytes(64));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply_delta<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)delta_smem_bytes(64, 8));
