@@ -218,7 +218,8 @@ def make_input_device(dev):
     del U
     out = rxr.colmajor(A)
     del A
-    torch.cuda.synchronize(dev)
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
     return out
 
 
