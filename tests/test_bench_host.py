@@ -73,3 +73,33 @@ def test_launch_count_of_the_split_factorisation():
     assert bench.launches_per_step("split", 128, 2**23) == 2 + 11 + 2 + 2 + 12 + 7 + 2 + 12 + 5 + 1
     assert bench.launches_per_step("split", 64, 2**22) == 19
     assert bench.launches_per_step("fp64", 64, 2**22) == 11
+
+
+def test_bench_line_carries_the_contract_keys(capsys):
+    import json
+    import types
+
+    bench.set_config("c3")
+    stages = {"sketch": 23.0, "precond_subst": 55.0, "pass_subst": 21.0, "last_apply": 8.5, "gram1_tensor": 14.0,
+              "gram2_tensor": 14.0, "xr_factor": 1.3}
+    path = {"ms": 138.0, "stages_ms": stages, "accuracy": {"orth": 3e-15, "resid": 2e-15},
+            "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}}
+    fp64 = dict(path, ms=1084.0, stages_ms={"precond_subst": 254.0})
+    main = {"ms": 138.0, "value": bench.job_value(138.0, 1), "paths": {"split": path, "fp64": fp64},
+            "generation_s": 7.0, "preconditioner": {"cond_Rs": 1e12, "cond_R1": 5.5},
+            "e2e": {"value": 210.0, "unit": "GB/s", "h2d_bytes_per_step": 8 * bench.M * bench.N,
+                    "d2h_bytes_per_step": 8 * bench.M * bench.N + 8 * bench.N ** 2},
+            "cpu_baseline": {"value": 1.1, "unit": "GB/s", "cores": 16, "kind": "oracle", "sample": "rows"}}
+    args = types.SimpleNamespace(steps=10, warmup=3, variant="qr", prec="split")
+    cfg = {"m": bench.M, "n": bench.N, "s": bench.S, "kappa": bench.KAPPA}
+    bench._emit(args, 1, main, cfg, 1.25, {})
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks", "cpu_baseline"):
+        assert key in line, key
+    assert line["metric"] == bench.METRIC and line["unit"] == "GB/s" and line["higher_is_better"] is True
+    assert line["gpu_launches"] == 56 * 10 and line["config"]["workload"].startswith("rQR-CholeskyQR2 m=2^23")
+    rl = line["roofline"]
+    assert rl["bound"] == "alu" and 0 < rl["frac"] == rl["achieved"] / rl["peak"]
+    assert rl["traffic"] == bench.TRAFFIC[("split", 128)][0] * bench.M / bench.TRAFFIC[("split", 128)][1]
+    assert abs(line["speedup_vs_fp64"] - 1084.0 / 138.0) < 1e-12
