@@ -2680,8 +2680,10 @@ static int64_t ozaki_chunks(int64_t m, int64_t n, int sms)
 }
 
 // Row chunks of k_gram_oz128, one CTA per SM: g1 chunks for the J = 1 CTAs and
-// g0 for the J = 0 ones, which cut half the columns and so take more rows each
-// (kG8HalfCost: their time per buffer relative to a J = 1 CTA's).
+// g0 for the J = 0 ones.  kG8HalfCost is a J = 0 CTA's time per buffer relative
+// to a J = 1 CTA's, which sets their share of the rows; 1 (equal chunks) measured
+// fastest: the J = 0 CTAs cut half the columns, but the MMAs and drains are the
+// same, and equal chunks let the two blocks' CTAs share their rows of X in L2.
 constexpr double kG8HalfCost = 1.0;
 struct Oz128Grid {
     int g1, g0;
