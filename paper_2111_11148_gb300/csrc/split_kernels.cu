@@ -1893,8 +1893,8 @@ __global__ void __launch_bounds__(kG6Producers, 1)
 //     64 .. n - 1 of the same planes are the B operand (N = 64): the blocks
 //     G[0:64, 64:n] and G[64:n, 64:n];
 //   J = 0 (the other g0 CTAs): only columns 0 .. 63 are cut (A rows 64 .. 127
-//     stay zero) for G[0:64, 0:64], half the digit work per row, so these
-//     CTAs take proportionally more rows (g0 / g1 ~ their cost ratio).
+//     stay zero) for G[0:64, 0:64], half the digit work per row (the row
+//     split between the two kinds: oz128_grid).
 // Each group sums at most seven products below 2^14 a row, so a window of
 // four buffers (128 rows) keeps it an integer below 2^24 (exact in FP32);
 // after each window the groups are combined (weights 2^-8d) and added in
